@@ -1,0 +1,147 @@
+"""Pins for the oracle's boundary-element parts and the whole preconditioner
+(Sec. 4.1 Eqs. e:green/e:ubound/e:uinter, Sec. 4.2-4.3, Sec. 6.1 Tables t:p1/t:p1eig).
+
+Independent checks: Gauss-Legendre and adaptive quadrature of the element integrals,
+Gauss's identity for the double layer, reproduction of harmonic functions (Table t:p2's
+solution), convergence of P^{-1} f to the continuum solution, and the bounded,
+mesh-independent spectrum and iteration counts that Tables t:p1eig and t:p1 report.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+import synth_inputs as S
+from conftest import rel_l2
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gl(x, a, b, fn, k=64):
+    t, w = np.polynomial.legendre.leggauss(k)
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    L = np.linalg.norm(b - a)
+    pts = a[None, :] + (t[:, None] + 1) / 2 * (b - a)[None, :]
+    return L / 2 * np.sum(w * fn(np.asarray(x, float)[None, :] - pts, (b - a) / L))
+
+
+def test_single_layer_segment_integral_vs_quadrature():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        a, b = rng.uniform(-1, 1, 2), rng.uniform(-1, 1, 2)
+        mid, L = (a + b) / 2, np.linalg.norm(b - a)
+        x = mid + rng.uniform(1.5, 4) * L * np.array([np.cos(t := rng.uniform(0, 6.3)), np.sin(t)])
+        ref = _gl(x, a, b, lambda d, e: np.log(np.hypot(d[:, 0], d[:, 1])))
+        assert abs(O.seg_int_log(x, a, b) - ref) < 1e-12 * max(1, abs(ref))
+
+
+def test_single_layer_self_term():
+    # collocation at the midpoint: int_{-l/2}^{l/2} ln|s| ds = l (ln(l/2) - 1)
+    for L in (0.01, 0.3, 2.0):
+        val, _ = integrate.quad(lambda s: np.log(abs(s)), -L / 2, L / 2, points=[0.0], limit=200)
+        assert abs(O.seg_int_log((0.0, 0.0), (-L / 2, 0.0), (L / 2, 0.0)) - val) < 1e-12
+
+
+def test_double_layer_segment_integral_vs_quadrature():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        a, b = rng.uniform(-1, 1, 2), rng.uniform(-1, 1, 2)
+        mid, L = (a + b) / 2, np.linalg.norm(b - a)
+        x = mid + rng.uniform(1.5, 4) * L * np.array([np.cos(t := rng.uniform(0, 6.3)), np.sin(t)])
+
+        def dlog(d, e):  # d = x - y ; normal = tangent rotated clockwise
+            nvec = np.array([e[1], -e[0]])
+            return -(d @ nvec) / np.sum(d * d, axis=1)
+        ref = _gl(x, a, b, dlog)
+        assert abs(O.seg_int_dlog(x, a, b) - ref) < 1e-12 * max(1, abs(ref))
+
+
+def test_double_layer_gauss_identity():
+    n = 16
+    S_, K = O.bem_matrices(n, 0.0, 0.0, 1.0)
+    assert np.allclose(K.sum(axis=1), -0.5, atol=1e-13)  # smooth boundary point
+    ax, ay, bx, by, cx, cy = O.elements(n, 0.0, 0.0, 1.0)
+    for x in [(0.5, 0.5), (0.01, 0.7), (0.9, 0.95)]:
+        tot = sum(O.seg_int_dlog(x, (ax[k], ay[k]), (bx[k], by[k])) for k in range(4 * n))
+        assert abs(-tot / (2 * np.pi) + 1.0) < 1e-12
+
+
+def _harmonic_error(n):
+    # Sec. 6.1 second problem: u = 2(1+y)/((3+x)^2+(1+y)^2) on [-1,1]^2, harmonic.
+    x0, side = -1.0, 2.0
+    u = lambda x, y: 2 * (1 + y) / ((3 + x) ** 2 + (1 + y) ** 2)
+    S_, K = O.bem_matrices(n, x0, x0, side)
+    ax, ay, bx, by, cx, cy = O.elements(n, x0, x0, side)
+    g = u(cx, cy)
+    q = np.linalg.solve(S_, 0.5 * g + K @ g)  # e:ubound with f = 0
+    X, Y, _ = S.grid_coords(n, x0, x0, side)
+    NG = 4 * n
+    uh = np.empty(n * n)
+    for i in range(n * n):
+        xi = (X[i], Y[i])
+        sl = np.array([O.seg_int_log(xi, (ax[k], ay[k]), (bx[k], by[k])) for k in range(NG)])
+        dl = np.array([O.seg_int_dlog(xi, (ax[k], ay[k]), (bx[k], by[k])) for k in range(NG)])
+        uh[i] = (-sl / (2 * np.pi)) @ q - (-dl / (2 * np.pi)) @ g  # e:uinter with f = 0
+    return rel_l2(uh, u(X, Y))
+
+
+def test_bie_reproduces_harmonic_solution():
+    e1, e2 = _harmonic_error(8), _harmonic_error(16)
+    assert e2 < 1e-2
+    assert e1 / e2 > 1.8  # at least first order (Sec. 6.2, Fig. f:discretization)
+
+
+def test_preconditioner_converges_to_continuum_solution():
+    errs = []
+    for n in (16, 32, 64):
+        f, u = S.manufactured_sin(n)
+        errs.append(rel_l2(O.Problem(n, p=10).apply(f, "fmm"), u))
+    assert errs[0] / errs[1] > 1.8 and errs[1] / errs[2] > 1.8
+    assert errs[2] < 1e-3
+
+
+def _dense(n, mode="direct", p=12, x0=0.0, side=1.0):
+    P = O.Problem(n, p=p, x0=x0, y0=x0, side=side)
+    I = np.eye(n * n)
+    Pm = np.stack([P.apply(e, mode) for e in I], 1)
+    A = np.stack([O.spmv5(n, side / (n + 1), e) for e in I], 1)
+    return Pm, A
+
+
+def test_spectrum_of_preconditioned_matrix_is_bounded():
+    gold = np.loadtxt(os.path.join(GOLD, "paper_table_p1eig.txt"))
+    kap = []
+    for n in (8, 16):
+        Pm, A = _dense(n, x0=-1.0, side=2.0)
+        ev = np.linalg.eigvals(Pm @ A)
+        assert np.abs(ev.imag).max() < 1e-8
+        lo, hi = ev.real.min(), ev.real.max()
+        assert 0.3 < lo and hi < 1.1
+        kap.append(hi / lo)
+    # same regime as the paper's FEM values (Table t:p1eig: 1.77-1.80), h-independent
+    assert abs(kap[1] - kap[0]) < 0.15
+    assert max(kap) < 1.5 * gold[:, 3].max()
+
+
+def test_pcg_iterations_are_mesh_independent():
+    # Table t:p1 setting: -lap u = 1 on [-1,1]^2, u = 0, PCG, six-digit drop, maxit 20.
+    gold = np.loadtxt(os.path.join(GOLD, "paper_table_p1.txt"))
+    its = []
+    for n in (16, 32, 64):
+        P = O.Problem(n, p=10, x0=-1.0, y0=-1.0, side=2.0)
+        x, it, rr, conv = P.solve(np.ones(n * n), "cg", maxit=20, rtol=1e-6, prec="fmm")
+        assert conv
+        its.append(it)
+    assert max(its) - min(its) <= 1
+    assert max(its) <= gold[:, 1].max() + 3
+
+
+def test_fmm_and_direct_preconditioners_give_same_iterations():
+    n = 32
+    f = S.gaussian_mixture(n, 2)
+    P = O.Problem(n, p=10)
+    _, it1, rr1, c1 = P.solve(f, "fgmres", rtol=1e-8, prec="fmm")
+    _, it2, rr2, c2 = P.solve(f, "fgmres", rtol=1e-8, prec="direct")
+    assert c1 and c2 and abs(it1 - it2) <= 1
