@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM-BEM preconditioner (arXiv:1308.3339) on GB300.
+
+Workload (default): 2-D Poisson -lap u = f on the unit square, 5-point FD on a 1024 x 1024
+interior grid (N = 1,048,576), f a seeded mixture of 16 Gaussians, preconditioner =
+FP32 FMM (p = 10, leaf 8x8, theta = 0.4) plus the boundary-element correction, FP64 FGMRES.
+
+One step = one preconditioner apply z = P^{-1} r (all FMM + boundary stages).  The line
+reports FMM apply points/s (N / apply time, L2 flushed between timed applies), the same
+through the C ABI with host buffers (e2e), time-to-solution at relative residual 1e-8 for
+the mixed (FP32 FMM, FP64 Krylov) and plain FP64 forms, the roofline of the dominant
+kernel, and the CPU oracle timed on this host.  Multi-GPU: one independent problem per
+rank (weak scaling, no collective in the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("FMM apply points/sec and time-to-solution at rel. residual 1e-8, mixed vs plain "
+          "on 1 GB300")
+UNIT = "points/s"
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0  # GB300: SMs, FP32 lanes per SM, max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--theta", type=float, default=0.4)
+    ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def workload(args):
+    return {"workload": f"poisson-fd {args.n}x{args.n} gaussian-mixture(16) FMM-BEM precond",
+            "n": args.n, "N": args.n * args.n, "p": args.p, "leaf_max": args.leaf,
+            "theta": args.theta, "krylov": "FGMRES(30) FP64", "fmm": "fp32",
+            "l2": "flushed: 256 MB write between timed applies"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("FMMPC_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x: float, pg, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(args, repeats=1):
+    import oracle as O
+    import synth_inputs as S
+    n = args.n
+    f = S.gaussian_mixture(n, 0)
+    t0 = time.perf_counter()
+    Pr = O.Problem(n, p=args.p, leaf_max=args.leaf, theta=(int(round(args.theta * 1000)), 1000))
+    t_setup = time.perf_counter() - t0
+    ts = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        Pr.apply(f, "fmm")
+        ts.append(time.perf_counter() - t0)
+    t = float(np.mean(ts))
+    return {"value": n * n / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{repeats} full FP64 FMM-BEM apply of the {n}x{n} workload (setup {t_setup:.1f} s excluded)",
+            "seconds_per_apply": t}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    import synth_inputs as S
+    n = args.n
+    f = S.gaussian_mixture(n, 0)
+    Pr = O.Problem(n, p=args.p, leaf_max=args.leaf, theta=(int(round(args.theta * 1000)), 1000))
+    for _ in range(args.warmup):
+        Pr.apply(f, "fmm")
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Pr.apply(f, "fmm")
+    t = (time.perf_counter() - t0) / args.steps
+    v = n * n / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                             "sample": f"one full FP64 FMM-BEM apply of the {n}x{n} workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def p2p_traffic_record():
+    """DRAM traffic of the P2P kernel from a committed ncu summary, valid only while the
+    kernel source is unchanged (hash of fmm.cu)."""
+    path = os.path.join(ROOT, "profiles", "p2p_traffic.json")
+    src = os.path.join(ROOT, "paper_1308_3339_gb300", "csrc", "fmm.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("fmm_cu_sha256_16") == h:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def time_solves(P, fd, reps, rtol=1e-8):
+    import torch
+    P.solve(fd, rtol=rtol)  # warm-up (workspace, caches)
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, info = P.solve(fd, rtol=rtol)
+        torch.cuda.synchronize()
+        out.append((time.perf_counter() - t0) * 1e3)
+        last = info
+    return {"ms": float(np.median(out)), "iters": last["iters"], "rel_res": last["rel_res"],
+            "status": last["status"]}
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local, pg = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import synth_inputs as S
+    from paper_1308_3339_gb300 import FmmPreconditioner, _lib
+
+    n = args.n
+    N = n * n
+    f = S.gaussian_mixture(n, rank)
+    P = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision="fp32")
+    r = torch.tensor(f, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    P.set_timing(True)
+    for _ in range(max(args.warmup, 3)):
+        P.apply(r, out=z)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times, stages = [], {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        P.apply(r, out=z)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for k, v in P.stage_times().items():
+            stages[k] = stages.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = P.query("launches")
+    t_apply = float(np.mean(times))
+    t_apply_max = max_over_ranks(t_apply, pg, dev)
+    value = world * N / (t_apply_max * 1e-3)
+    stage_ms = {k: v / args.steps for k, v in stages.items()}
+
+    # roofline of the dominant kernel: the lattice P2P (one FMA per source-target pair)
+    m = P.query("leaf_side")
+    pairs = P.query("n_p2p") * m ** 4
+    t_p2p = stage_ms["p2p_l2p"] * 1e-3
+    mhz = SM_MAX_MHZ
+    peak = SMS * LANES * 2 * mhz * 1e6 / 1e12
+    achieved = 2.0 * pairs / t_p2p / 1e12
+    trec = p2p_traffic_record()
+    roofline = {"bound": "alu", "kernel": "k_p2p_final (lattice P2P + L2P)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": trec["bytes_per_launch"] if trec else None,
+                "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {mhz:.0f} MHz max SM clock",
+                "work": f"{pairs:.3e} pairs/launch x 1 FMA", "launch_ms": stage_ms["p2p_l2p"]}
+
+    # end to end through the C ABI with pinned host buffers
+    rh = torch.tensor(f, dtype=torch.float64).pin_memory()
+    zh = torch.empty_like(rh).pin_memory()
+    lib = _lib.load()
+    import ctypes as C
+    for _ in range(2):
+        _lib.check(lib.fmmpc_apply_host(P._h, C.c_void_p(rh.data_ptr()), C.c_void_p(zh.data_ptr()), 1), P._h)
+    te = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _lib.check(lib.fmmpc_apply_host(P._h, C.c_void_p(rh.data_ptr()), C.c_void_p(zh.data_ptr()), 1), P._h)
+        te.append(time.perf_counter() - t0)
+    t_e2e = max_over_ranks(float(np.mean(te)), pg, dev)
+    e2e = {"value": world * N / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+
+    tts = None
+    if not args.no_tts:
+        P.set_timing(False)
+        tts = {"mixed_fp32fmm_fp64krylov": time_solves(P, r, 3)}
+        P64 = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision="fp64")
+        tts["plain_fp64"] = time_solves(P64, r, 2)
+        P64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_apply_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload(args), "clocks": clk, "e2e": e2e,
+                "gpu_launches": int(launches * args.steps), "roofline": roofline, "cpu_baseline": cpu,
+                "time_to_solution": tts, "stage_ms": stage_ms, "timed_wall_s": wall}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

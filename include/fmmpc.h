@@ -1,0 +1,189 @@
+/*
+ * fmmpc.h -- C ABI of the GB300 FMM-BEM preconditioner library (libfmmpc.so).
+ *
+ * Method: Ibeid, Yokota, Pestana and Keyes, "Fast Multipole Preconditioners for Sparse
+ * Matrices Arising from Elliptic Equations" (arXiv:1308.3339).  A Krylov solve of the
+ * 5-point finite-difference Poisson system -lap u = f on a square, u = g on its boundary
+ * (Sec. 2.1, Eqs. e:p and e:axb), preconditioned by z = P^{-1} r: a free-space Laplace
+ * FMM over every grid node (Sec. 5) plus a boundary-element correction that enforces
+ * z = 0 on the boundary (Sec. 3.2 Fig. f:flow_chart, Sec. 4.1 Eqs. e:ubound/e:uinter).
+ *
+ * Conventions for every call:
+ *  - Grid vectors are FP64, row-major [n_rhs][ny][nx] with x fastest, in the natural
+ *    (not Morton) order, interior nodes only: node (i, j), 0-based, sits at
+ *    (x0 + (i+1) h, y0 + (j+1) h) with h = (x1 - x0) / (nx + 1).
+ *  - Boundary data g is FP64 [n_rhs][4 n]: the Dirichlet values at the stencil neighbours
+ *    outside the interior block, in the order bottom (x increasing), right (y increasing),
+ *    top (x decreasing), left (y decreasing).  Corners are never used.
+ *  - "_dev" pointers are device memory owned by the caller; the library never frees or
+ *    keeps them past the call.  "_host" pointers are host memory (pinned or pageable).
+ *  - The handle owns every internal buffer (tree, lists, expansions, BEM inverse, Krylov
+ *    basis, graphs) and its CUDA stream binding; one handle is used by one host thread
+ *    at a time.  Calls are stream-ordered on the handle's stream; fmmpc_apply returns
+ *    without synchronising, fmmpc_solve returns after its convergence test.
+ *  - Return value: FMMPC_OK (0) or a negative FMMPC_ERR_* code; no exception or abort
+ *    crosses the ABI.  fmmpc_last_error() gives a message for the last failure.
+ */
+#ifndef FMMPC_H
+#define FMMPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMMPC_OK 0
+#define FMMPC_ERR_INVALID (-1)       /* bad argument or unsupported grid */
+#define FMMPC_ERR_OOM (-2)           /* device or host allocation failed */
+#define FMMPC_ERR_CUDA (-3)          /* a CUDA call failed */
+#define FMMPC_ERR_NOT_CONVERGED (-4) /* solve stopped at maxit above rtol */
+#define FMMPC_ERR_NAN (-5)           /* NaN or Inf met in a residual norm */
+#define FMMPC_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
+#define FMMPC_ERR_UNSUPPORTED (-7)   /* valid request this build does not implement */
+
+/* FMM arithmetic inside the preconditioner.  The Krylov recurrences, inner products,
+ * residual checks and the boundary-element solve are FP64 in every mode. */
+#define FMMPC_PREC_FP64 0       /* FMM in FP64 on CUDA cores (plain FP64 form) */
+#define FMMPC_PREC_FP32 1       /* FMM in FP32 on CUDA cores (plain FP32 form) */
+#define FMMPC_PREC_MIXED_BF16 2 /* FP32 P2P/expansions, M2L on tensor cores in BF16, FP32 accumulate */
+#define FMMPC_PREC_MIXED_TF32 3 /* FP32 P2P/expansions, M2L on tensor cores in TF32, FP32 accumulate */
+
+#define FMMPC_CG 0
+#define FMMPC_GMRES 1
+#define FMMPC_FGMRES 2
+
+typedef struct fmmpc_handle fmmpc_handle;
+
+/* Square grid of nx = ny interior nodes on [x0, x1] x [y0, y1] with x1-x0 = y1-y0. */
+typedef struct {
+  int32_t nx, ny;
+  double x0, y0, x1, y1;
+} fmmpc_grid;
+
+/* p: expansion order, coefficients n = 0..p-1 (Sec. 5.3), 2 <= p <= 20.
+ * leaf_max: the tree splits a cell at its centre lines while it holds more than leaf_max
+ *   nodes (Sec. 5.1); the grid must stay divisible down to the leaf (nx = m 2^L) and the
+ *   leaf side m must be 4, 8 or 16.
+ * theta: MAC (R_A + R_B) < theta |c_A - c_B| of the dual tree traversal (Sec. 5.2), R the
+ *   half-diagonal; 0 < theta < 1, taken as the rational round(1000 theta)/1000.
+ * precision: FMMPC_PREC_*.  n_rhs: largest number of right-hand sides per call.
+ * autotune: 0 = use p and leaf_max as given; see fmmpc_autotune for the tuner. */
+typedef struct {
+  int32_t p;
+  int32_t leaf_max;
+  double theta;
+  int32_t precision;
+  int32_t n_rhs;
+  int32_t autotune;
+} fmmpc_params;
+
+/* method: FMMPC_CG | FMMPC_GMRES | FMMPC_FGMRES; restart: Krylov basis size m of
+ * (F)GMRES(m); maxit: cap on preconditioner applications; rtol: stop when the relative
+ * residual ||b - A u|| / ||b|| <= rtol (Sec. 6 stops at a relative-residual drop).
+ * use_graphs: 1 = replay the preconditioner through a captured CUDA graph. */
+typedef struct {
+  int32_t method;
+  int32_t restart;
+  int32_t maxit;
+  double rtol;
+  int32_t use_graphs;
+} fmmpc_solve_opts;
+
+/* Per-solve report.  rel_res is the true residual recomputed in FP64 at the end
+ * (largest over right-hand sides); iters the preconditioner applications of the
+ * slowest right-hand side; status FMMPC_OK or FMMPC_ERR_NOT_CONVERGED / _NAN. */
+typedef struct {
+  int32_t iters;
+  double rel_res;
+  double t_setup_ms;
+  double t_solve_ms;
+  int32_t status;
+} fmmpc_solve_info;
+
+/* Set-up, the analogue of the paper's PCSetUp (Sec. 7.1): Morton keys and radix sort
+ * of the nodes, quadtree (Sec. 5.1), dual-tree-traversal interaction lists (Sec. 5.2),
+ * translation tables, boundary elements and the FP64 inverse of the single-layer BEM
+ * matrix (Sec. 4.3), workspace.  stream: a cudaStream_t (NULL = legacy default stream)
+ * on which every later call of this handle runs.  On success *out owns all of it and
+ * must be released with fmmpc_destroy.  Errors: _INVALID (grid/params), _OOM, _CUDA. */
+int fmmpc_create(fmmpc_handle **out, const fmmpc_grid *g, const fmmpc_params *prm, void *stream);
+
+/* Preconditioner action z = P^{-1} r (Sec. 3.2, PCApply): for each right-hand side,
+ * (1) FMM volume potential V r of Eq. e:volume_integral at the nodes and at the boundary
+ * collocation points, (2) q = S^{-1}(-(V r)|_Gamma), Eq. e:ubound with z = 0 on Gamma,
+ * (3) z = V r + int_Gamma q G, Eq. e:uinter.  r_dev, z_dev: [n_rhs][ny][nx] FP64
+ * device, not aliased; 1 <= n_rhs <= params.n_rhs.  Asynchronous on the handle stream. */
+int fmmpc_apply(fmmpc_handle *h, const double *r_dev, double *z_dev, int32_t n_rhs);
+
+/* Same as fmmpc_apply with host buffers: copies r in, applies, copies z out and
+ * synchronises the stream before returning. */
+int fmmpc_apply_host(fmmpc_handle *h, const double *r_host, double *z_host, int32_t n_rhs);
+
+/* Parts of the apply, for testing each stage against the oracle.  part:
+ *  0 full P^{-1} r (as fmmpc_apply);
+ *  1 V r at the nodes: the volume FMM alone, Eq. e:volume_integral, no boundary term;
+ *  2 the near-field (P2P) part of V r alone, in physical units;
+ *  3 V r at the N_Gamma = 4n collocation points (out holds [n_rhs][4n] values);
+ *  4 q = S^{-1}(-(V r)|_Gamma), the boundary density of Eq. e:ubound ([n_rhs][4n]). */
+int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double *out_dev,
+                     int32_t n_rhs);
+
+/* y = A x, the 5-point operator with zero boundary values (Eq. e:axb). */
+int fmmpc_spmv(fmmpc_handle *h, const double *x_dev, double *y_dev, int32_t n_rhs);
+
+/* Krylov solve of A u = b with b = f + (boundary values g of the stencil neighbours)/h^2
+ * (Sec. 3.1, Eq. e:axb), right-preconditioned by P^{-1} (Sec. 3.2), FP64 recurrences.
+ * f_dev [n_rhs][ny][nx]; g_dev [n_rhs][4n] or NULL for g = 0; u_dev holds the initial
+ * iterate on entry (zeros for the paper's setting) and the solution on exit.  info may
+ * be NULL.  Returns FMMPC_OK when every right-hand side met rtol, FMMPC_ERR_NOT_CONVERGED
+ * when one stopped at maxit (u_dev still holds the last iterate), FMMPC_ERR_NAN. */
+int fmmpc_solve(fmmpc_handle *h, const double *f_dev, const double *g_dev, double *u_dev,
+                int32_t n_rhs, const fmmpc_solve_opts *opts, fmmpc_solve_info *info);
+
+/* fmmpc_solve with host buffers (copies in, solves, copies u out). */
+int fmmpc_solve_host(fmmpc_handle *h, const double *f_host, const double *g_host,
+                     double *u_host, int32_t n_rhs, const fmmpc_solve_opts *opts,
+                     fmmpc_solve_info *info);
+
+/* Sizes of the set-up, for buffer allocation by fmmpc_export callers.  what:
+ *  0 L (leaf level), 1 leaf side m, 2 #M2L pairs, 3 #P2P pairs, 4 #M2L volume-boundary
+ *  pairs, 5 #P2P volume-boundary pairs, 6 N_Gamma, 7 #cells (all levels), 8 #nodes,
+ *  9 distinct P2P leaf offsets, 10 kernel launches of the last apply, 11 device bytes
+ *  held by the handle. */
+int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
+
+/* Copies an internal array of the set-up to host memory dst (bytes = capacity).  what:
+ *  0 Morton keys u32 [N] (natural order); 1 permutation i32 [N] (Morton position ->
+ *  natural index); 2 cell starts i32 [#cells]; 3 M2L list i32 [#][3] (level, target,
+ *  source); 4 P2P list i32 [#][2]; 5 volume-boundary M2L list i32 [#][3] (level, volume
+ *  cell, boundary cell); 6 volume-boundary P2P list i32 [#][2].  Lists are in canonical
+ *  (level, target, source) order.  Errors: _INVALID if bytes is too small. */
+int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
+
+/* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream.
+ * fmmpc_set_timing(h, 1) creates the events and turns recording on (0 turns it off).
+ * fmmpc_get_timing synchronises the stream and writes the durations in milliseconds of
+ * the stages of the last apply into ms[0 .. min(cap, count)), *count = 9 stages:
+ *  0 weight image, 1 P2M + M2M (Sec. 5.3 items 1-2), 2 collocation pass (M2L to boundary
+ *  cells, L2L, L2P and near field at the collocation points), 3 BEM solve (FP64),
+ *  4 boundary P2M + M2M, 5 M2L (item 3), 6 L2L (item 4), 7 near-boundary element
+ *  integrals, 8 P2P near field + L2P + sum (items 5, Eq. e:volume_integral).
+ * A stage that did not run reports 0.  Errors: _INVALID if timing is off. */
+int fmmpc_set_timing(fmmpc_handle *h, int32_t on);
+int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);
+
+/* Releases every resource of the handle (NULL is allowed). */
+void fmmpc_destroy(fmmpc_handle *h);
+
+/* Message of the last failed call on h (or of the last failed fmmpc_create when h is
+ * NULL).  The string lives until the next call on the same handle. */
+const char *fmmpc_last_error(const fmmpc_handle *h);
+
+/* Library build identification ("fmmpc <version> sm_103a"). */
+const char *fmmpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMMPC_H */

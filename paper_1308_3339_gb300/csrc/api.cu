@@ -1,0 +1,324 @@
+// C ABI of libfmmpc (declared in include/fmmpc.h).  Every entry point validates its
+// arguments, runs on the handle's stream and turns internal exceptions into FMMPC_ERR_*
+// codes; nothing is thrown across the boundary.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "handle.cuh"
+
+using namespace fmmpc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(fmmpc_handle *h, const Error &e) {
+  if (h) h->err = e.msg;
+  else g_create_error = e.msg;
+  return e.code;
+}
+
+template <typename F>
+int guarded(fmmpc_handle *h, F &&f) {
+  try {
+    return f();
+  } catch (const Error &e) {
+    return fail(h, e);
+  } catch (const std::bad_alloc &) {
+    return fail(h, Error(FMMPC_ERR_OOM, "host allocation failed"));
+  } catch (const std::exception &e) {
+    return fail(h, Error(FMMPC_ERR_CUDA, e.what()));
+  }
+}
+
+void setup(fmmpc_handle &H, const fmmpc_grid &g, const fmmpc_params &p) {
+  require(g.nx == g.ny, "grid: nx must equal ny");
+  // the BEM inverse is a dense 4n x 4n FP64 matrix: n <= 4096 keeps it at 2.1 GB
+  require(g.nx >= 4 && g.nx <= 4096, "grid: 4 <= nx <= 4096");
+  const double wx = g.x1 - g.x0, wy = g.y1 - g.y0;
+  require(wx > 0 && std::fabs(wx - wy) <= 1e-12 * wx, "grid: the domain must be a square");
+  require(p.p == 4 || p.p == 6 || p.p == 8 || p.p == 10 || p.p == 12 || p.p == 16,
+          "params: p must be one of 4, 6, 8, 10, 12, 16");
+  require(p.leaf_max >= 16, "params: leaf_max >= 16");
+  require(p.theta > 0.0 && p.theta < 1.0, "params: 0 < theta < 1");
+  require(p.n_rhs >= 1 && p.n_rhs <= 64, "params: 1 <= n_rhs <= 64");
+  require(p.precision >= FMMPC_PREC_FP64 && p.precision <= FMMPC_PREC_MIXED_TF32, "params: unknown precision");
+  if (p.precision == FMMPC_PREC_MIXED_BF16 || p.precision == FMMPC_PREC_MIXED_TF32)
+    throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L forms are not built in this library version");
+  // leaf level: split at the centre lines while a cell holds more than leaf_max nodes
+  const int n = g.nx;
+  int L = 0, s = n;
+  while ((int64_t)s * s > p.leaf_max) {
+    require(s % 2 == 0, "grid: a centre-line split would cut a row of nodes (nx must be m 2^L)");
+    s /= 2;
+    ++L;
+  }
+  require(s == 4 || s == 8 || s == 16, "grid: leaf side must be 4, 8 or 16 nodes");
+  Geo &G = H.g;
+  G.n = n;
+  G.m = s;
+  G.L = L;
+  G.lg = 0;
+  while ((1 << G.lg) < n) ++G.lg;
+  require((1 << G.lg) == n, "grid: nx must be a power of two");
+  G.p = p.p;
+  int tn = (int)std::lround(p.theta * 1000.0), td = 1000;
+  int gc = std::gcd(tn, td);
+  G.tnum = tn / gc;
+  G.tden = td / gc;
+  require(G.tnum > 0 && G.tnum < G.tden, "params: theta rounds outside (0, 1)");
+  G.x0 = g.x0;
+  G.y0 = g.y0;
+  G.side = wx;
+  G.h = wx / (n + 1);
+  G.lnh = std::log(G.h);
+  G.NG = 4 * n;
+  G.ncell = level_offset(L + 1);
+  G.nbcell = blevel_offset(L + 1);
+  G.nleaf = int64_t(1) << (2 * L);
+  G.nbleaf = 4 * (int64_t(1) << L);
+  H.prec = p.precision;
+  H.nrhs_max = p.n_rhs;
+
+  auto t0 = std::chrono::steady_clock::now();
+  DevPool tmp;
+  try {
+    build_tree(G, H.tree, H.stream, H.pool, tmp);
+    build_lists(G, H.lists, H.st, H.stream, H.pool, tmp);
+    G.R = H.st.R;
+    G.pad = G.R * G.m;
+    G.npad = n + 2 * G.pad;
+    init_fmm(H);
+    init_bem(H, tmp);
+    FMMPC_CUDA(cudaStreamSynchronize(H.stream));
+  } catch (...) {
+    cudaStreamSynchronize(H.stream);
+    tmp.release();
+    throw;
+  }
+  tmp.release();
+  H.t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void check_rhs(const fmmpc_handle *h, int32_t n_rhs) {
+  require(n_rhs >= 1 && n_rhs <= h->nrhs_max, "n_rhs must be in [1, params.n_rhs]");
+}
+
+void ensure_stage(fmmpc_handle &H) {
+  if (H.stage_in) return;
+  const size_t N = (size_t)H.g.n * H.g.n * H.nrhs_max;
+  H.stage_in = H.pool.get<double>(N);
+  H.stage_out = H.pool.get<double>(N);
+  H.stage_g = H.pool.get<double>((size_t)4 * H.g.n * H.nrhs_max);
+}
+
+void release(fmmpc_handle *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k)
+    if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+  if (h->kw.hbuf) cudaFreeHost(h->kw.hbuf);
+  h->kpool.release();
+  h->pool.release();
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmmpc_create(fmmpc_handle **out, const fmmpc_grid *g, const fmmpc_params *prm, void *stream) {
+  if (!out || !g || !prm) {
+    g_create_error = "fmmpc_create: NULL argument";
+    return FMMPC_ERR_INVALID;
+  }
+  *out = nullptr;
+  fmmpc_handle *h = nullptr;
+  try {
+    h = new fmmpc_handle();
+  } catch (...) {
+    g_create_error = "host allocation failed";
+    return FMMPC_ERR_OOM;
+  }
+  h->stream = (cudaStream_t)stream;
+  int rc = guarded(h, [&] {
+    setup(*h, *g, *prm);
+    return FMMPC_OK;
+  });
+  if (rc != FMMPC_OK) {
+    g_create_error = h->err;
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return FMMPC_OK;
+}
+
+int fmmpc_apply(fmmpc_handle *h, const double *r_dev, double *z_dev, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(r_dev && z_dev && r_dev != z_dev, "apply: r and z must be distinct device buffers");
+    check_rhs(h, n_rhs);
+    apply_fmm(*h, PART_FULL, r_dev, z_dev, n_rhs);
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_apply_host(fmmpc_handle *h, const double *r_host, double *z_host, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(r_host && z_host, "apply_host: NULL buffer");
+    check_rhs(h, n_rhs);
+    ensure_stage(*h);
+    const size_t bytes = sizeof(double) * (size_t)h->g.n * h->g.n * n_rhs;
+    FMMPC_CUDA(cudaMemcpyAsync(h->stage_in, r_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    apply_fmm(*h, PART_FULL, h->stage_in, h->stage_out, n_rhs);
+    FMMPC_CUDA(cudaMemcpyAsync(z_host, h->stage_out, bytes, cudaMemcpyDeviceToHost, h->stream));
+    FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double *out_dev, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(r_dev && out_dev, "apply_part: NULL buffer");
+    require(part >= PART_FULL && part <= PART_Q, "apply_part: unknown part");
+    check_rhs(h, n_rhs);
+    apply_fmm(*h, part, r_dev, out_dev, n_rhs);
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_spmv(fmmpc_handle *h, const double *x_dev, double *y_dev, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(x_dev && y_dev && x_dev != y_dev, "spmv: x and y must be distinct device buffers");
+    check_rhs(h, n_rhs);
+    spmv5(*h, x_dev, y_dev, n_rhs);
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_solve(fmmpc_handle *h, const double *f_dev, const double *g_dev, double *u_dev, int32_t n_rhs,
+                const fmmpc_solve_opts *opts, fmmpc_solve_info *info) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(f_dev && u_dev && opts, "solve: NULL argument");
+    check_rhs(h, n_rhs);
+    fmmpc_solve_info tmp{};
+    int st = solve(*h, f_dev, g_dev, u_dev, n_rhs, *opts, tmp);
+    if (info) *info = tmp;
+    if (st != FMMPC_OK) h->err = (st == FMMPC_ERR_NOT_CONVERGED) ? "solve: not converged within maxit"
+                                                                  : "solve: NaN or Inf in a residual";
+    return st;
+  });
+}
+
+int fmmpc_solve_host(fmmpc_handle *h, const double *f_host, const double *g_host, double *u_host,
+                     int32_t n_rhs, const fmmpc_solve_opts *opts, fmmpc_solve_info *info) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(f_host && u_host && opts, "solve_host: NULL argument");
+    check_rhs(h, n_rhs);
+    ensure_stage(*h);
+    const size_t N = (size_t)h->g.n * h->g.n * n_rhs;
+    double *gdev = nullptr;
+    FMMPC_CUDA(cudaMemcpyAsync(h->stage_in, f_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    FMMPC_CUDA(cudaMemcpyAsync(h->stage_out, u_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    if (g_host) {
+      gdev = h->stage_g;
+      FMMPC_CUDA(cudaMemcpyAsync(gdev, g_host, sizeof(double) * 4 * h->g.n * n_rhs, cudaMemcpyHostToDevice, h->stream));
+    }
+    fmmpc_solve_info tmp{};
+    int st = solve(*h, h->stage_in, gdev, h->stage_out, n_rhs, *opts, tmp);
+    FMMPC_CUDA(cudaMemcpyAsync(u_host, h->stage_out, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+    if (info) *info = tmp;
+    return st;
+  });
+}
+
+int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value) {
+  if (!h || !value) return FMMPC_ERR_INVALID;
+  switch (what) {
+    case 0: *value = h->g.L; break;
+    case 1: *value = h->g.m; break;
+    case 2: *value = h->lists.n_m2l; break;
+    case 3: *value = h->lists.n_p2p; break;
+    case 4: *value = h->lists.n_m2l_vb; break;
+    case 5: *value = h->lists.n_p2p_vb; break;
+    case 6: *value = h->g.NG; break;
+    case 7: *value = h->g.ncell; break;
+    case 8: *value = (int64_t)h->g.n * h->g.n; break;
+    case 9: *value = h->st.count; break;
+    case 10: *value = h->launches; break;
+    case 11: *value = (int64_t)(h->pool.bytes + h->kpool.bytes); break;
+    default: return FMMPC_ERR_INVALID;
+  }
+  return FMMPC_OK;
+}
+
+int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes) {
+  if (!h || !dst) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    const int64_t N = (int64_t)h->g.n * h->g.n;
+    const void *src = nullptr;
+    int64_t need = 0;
+    switch (what) {
+      case 0: src = h->tree.keys; need = 4 * N; break;
+      case 1: src = h->tree.perm; need = 4 * N; break;
+      case 2: src = h->tree.cell_start; need = 4 * h->g.ncell; break;
+      case 3: src = h->lists.m2l; need = 12 * h->lists.n_m2l; break;
+      case 4: src = h->lists.p2p; need = 8 * h->lists.n_p2p; break;
+      case 5: src = h->lists.m2l_vb; need = 12 * h->lists.n_m2l_vb; break;
+      case 6: src = h->lists.p2p_vb; need = 8 * h->lists.n_p2p_vb; break;
+      default: throw Error(FMMPC_ERR_INVALID, "export: unknown array");
+    }
+    require(bytes >= need, "export: destination too small");
+    if (need) FMMPC_CUDA(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, h->stream));
+    FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_set_timing(fmmpc_handle *h, int32_t on) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    if (on && !h->ev[0])
+      for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k) FMMPC_CUDA(cudaEventCreate(&h->ev[k]));
+    h->timing = on != 0;
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count) {
+  if (!h || !ms || !count) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(h->timing, "get_timing: timing is off");
+    FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+    const int ns = fmmpc_handle::NSTAGE;
+    *count = ns;
+    for (int k = 0; k < ns && k < cap; ++k) {
+      ms[k] = 0.0f;
+      if (!h->stage_hit[k]) continue;
+      int nx = k + 1;  // next stage that ran (or the end mark)
+      while (nx < ns && !h->stage_hit[nx]) ++nx;
+      FMMPC_CUDA(cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[nx]));
+    }
+    return FMMPC_OK;
+  });
+}
+
+void fmmpc_destroy(fmmpc_handle *h) { release(h); }
+
+const char *fmmpc_last_error(const fmmpc_handle *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+const char *fmmpc_version(void) { return "fmmpc 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Boundary-element set-up (Sec. 4.3): constant elements, no nodes at the corners, 4n
+// equal elements on the square, collocation at their midpoints.  The single-layer
+// matrix S_mk = int_{Gamma_k} G(y_m, y) dGamma (left side of Eq. e:ubound) is assembled in
+// FP64 from the closed-form element integral (Sec. 4.2) and inverted once, in place, by
+// Gauss-Jordan elimination with partial pivoting, so each apply needs one FP64
+// matrix-vector product for q.
+#include <cmath>
+
+#include "handle.cuh"
+
+namespace fmmpc {
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// along-side coordinate and signed normal offset (node units) of a point, per side
+__device__ __forceinline__ void side_coords_d(int side, double np1, double x, double y, double &u, double &d) {
+  switch (side) {
+    case 0: u = x; d = -y; break;
+    case 1: u = y; d = x - np1; break;
+    case 2: u = np1 - x; d = y - np1; break;
+    default: u = np1 - y; d = -x; break;
+  }
+}
+
+__device__ __forceinline__ double seg_log_int_d(double s1, double ell, double d) {
+  const double s2 = s1 + ell;
+  const double A1 = s1 * s1 + d * d, A2 = s2 * s2 + d * d;
+  double v = 0.5 * (ell * log(A2) + s1 * log1p(ell * (s1 + s2) / A1)) - ell;
+  if (d != 0.0) v += d * atan2(ell * d, d * d + s1 * s2);
+  return v;
+}
+
+// S_mk = -(h/2pi) (int_k ln|y_m - y|_node ds_node + l ln h)  (physical units)
+__global__ void k_bem_S(int n, double h, double lnh, double *__restrict__ S) {
+  const int NG = 4 * n;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)NG * NG) return;
+  const int mrow = (int)(t / NG), k = (int)(t % NG);
+  const double ell = (n + 1.0) / n, np1 = n + 1.0;
+  // collocation point m in node units
+  const int sm = mrow / n, km = mrow % n;
+  const double tm = (km + 0.5) * ell;
+  double x, y;
+  switch (sm) {
+    case 0: x = tm; y = 0; break;
+    case 1: x = np1; y = tm; break;
+    case 2: x = np1 - tm; y = np1; break;
+    default: x = 0; y = np1 - tm; break;
+  }
+  const int sk = k / n, kk = k % n;
+  double u, d;
+  side_coords_d(sk, np1, x, y, u, d);
+  double I;
+  if (sk == sm) I = seg_log_int_d((kk - km - 0.5) * ell, ell, 0.0);  // same side: exact offsets
+  else I = seg_log_int_d(kk * ell - u, ell, d);
+  S[t] = -(h / (2.0 * PI)) * (I + ell * lnh);
+}
+
+__global__ void k_gj_pivot(int N, int k, const double *__restrict__ A, int *__restrict__ piv,
+                           double *__restrict__ pinv, double *__restrict__ pabs) {
+  __shared__ double best[1024];
+  __shared__ int bi[1024];
+  double b = -1.0;
+  int ib = k;
+  for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
+    double v = fabs(A[(int64_t)i * N + k]);
+    if (v > b) { b = v; ib = i; }
+  }
+  best[threadIdx.x] = b;
+  bi[threadIdx.x] = ib;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double o = best[threadIdx.x + s];
+      int oi = bi[threadIdx.x + s];
+      if (o > best[threadIdx.x] || (o == best[threadIdx.x] && oi < bi[threadIdx.x])) {
+        best[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    piv[k] = bi[0];
+    const double pv = A[(int64_t)bi[0] * N + k];
+    pabs[k] = fabs(pv);
+    *pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
+  }
+}
+
+// swap rows k and piv[k]; row k <- row k / pivot with A[k][k] replaced by 1 first
+__global__ void k_gj_swap_scale(int N, int k, double *__restrict__ A, const int *__restrict__ piv,
+                                const double *__restrict__ pinv, double *__restrict__ col) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int p = piv[k];
+  double a = A[(int64_t)k * N + j], b = A[(int64_t)p * N + j];
+  if (p != k) A[(int64_t)p * N + j] = a;
+  const double v = (j == k) ? 1.0 : b;
+  A[(int64_t)k * N + j] = v * (*pinv);
+  (void)col;
+}
+
+__global__ void k_gj_colsave(int N, int k, const double *__restrict__ A, double *__restrict__ col) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  col[i] = (i == k) ? 0.0 : A[(int64_t)i * N + k];
+}
+
+// rows i != k: A[i][j] = (j == k ? 0 : A[i][j]) - col[i] A[k][j]
+__global__ void k_gj_elim(int N, int k, double *__restrict__ A, const double *__restrict__ col) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= N || i == k) return;
+  const double f = col[i];
+  if (f == 0.0 && j != k) return;
+  double *row = A + (int64_t)i * N;
+  const double base = (j == k) ? 0.0 : row[j];
+  row[j] = base - f * A[(int64_t)k * N + j];
+}
+
+__global__ void k_swap_cols(int N, double *__restrict__ A, int c1, int c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double *row = A + (int64_t)i * N;
+  double t = row[c1];
+  row[c1] = row[c2];
+  row[c2] = t;
+}
+
+}  // namespace
+
+void init_bem(fmmpc_handle &H, DevPool &tmp) {
+  const Geo &g = H.g;
+  const int N = g.NG;
+  cudaStream_t s = H.stream;
+  H.Sinv = H.pool.get<double>((size_t)N * N);
+  k_bem_S<<<nblk((int64_t)N * N), 256, 0, s>>>(g.n, g.h, g.lnh, H.Sinv);
+  FMMPC_LAUNCH_CHECK();
+  int *piv = tmp.get<int>(N);
+  double *pinv = tmp.get<double>(1), *pabs = tmp.get<double>(N), *col = tmp.get<double>(N);
+  for (int k = 0; k < N; ++k) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(N, k, H.Sinv, piv, pinv, pabs);
+    k_gj_swap_scale<<<nblk(N), 256, 0, s>>>(N, k, H.Sinv, piv, pinv, col);
+    k_gj_colsave<<<nblk(N), 256, 0, s>>>(N, k, H.Sinv, col);
+    k_gj_elim<<<dim3(nblk(N), N), 256, 0, s>>>(N, k, H.Sinv, col);
+  }
+  FMMPC_LAUNCH_CHECK();
+  std::vector<int> hp(N);
+  std::vector<double> ha(N);
+  FMMPC_CUDA(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaMemcpyAsync(ha.data(), pabs, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaStreamSynchronize(s));
+  double amin = ha[0];
+  for (int k = 0; k < N; ++k) amin = std::min(amin, ha[k]);
+  if (!(amin > 0.0)) throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
+  for (int k = N - 1; k >= 0; --k)
+    if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, H.Sinv, k, hp[k]);
+  FMMPC_LAUNCH_CHECK();
+}
+
+}  // namespace fmmpc

@@ -1,0 +1,232 @@
+// Internal declarations of the fmmpc CUDA library (not part of the ABI).
+//
+// Geometry is kept in node units: node (i, j), 0-based, sits at (i+1, j+1); a cell at
+// level l has width rho_l = n >> l nodes.  Expansions are stored scaled,
+// Mt_k = M_k / rho^k and Lt_k = L_k rho^k, so every translation works on O(1) numbers.
+// The physical kernel is G = -(1/2pi)(ln h + ln|d|_node); the ln h part is a constant
+// times the total source weight and is added once, through the root local expansion.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fmmpc.h"
+
+namespace fmmpc {
+
+constexpr int MAXP = 20;
+constexpr double PI = 3.14159265358979323846;
+
+struct Error {
+  int code;
+  std::string msg;
+  Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+#define FMMPC_CUDA(call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::fmmpc::Error(FMMPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define FMMPC_LAUNCH_CHECK() FMMPC_CUDA(cudaPeekAtLastError())
+
+inline void require(bool ok, const std::string &msg) {
+  if (!ok) throw Error(FMMPC_ERR_INVALID, msg);
+}
+
+// Device allocation owned by a handle; freed in the handle's destructor.
+struct DevPool {
+  std::vector<void *> ptrs;
+  size_t bytes = 0;
+  void *alloc(size_t nbytes) {
+    void *p = nullptr;
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(FMMPC_ERR_OOM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed");
+    }
+    ptrs.push_back(p);
+    bytes += nbytes;
+    return p;
+  }
+  template <typename T>
+  T *get(size_t count) {
+    return static_cast<T *>(alloc(sizeof(T) * count));
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R>
+struct cpx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) {
+  return cpx<R>{a, b};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) {
+  return cpx<R>{a.re + b.re, a.im + b.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) {
+  return cpx<R>{a.re - b.re, a.im - b.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return cpx<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) {
+  return cpx<R>{s * a.re, s * a.im};
+}
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cmac(cpx<R> &acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> cinv(cpx<R> a) {
+  R d = R(1) / (a.re * a.re + a.im * a.im);
+  return cpx<R>{a.re * d, -a.im * d};
+}
+
+// ------------------------------------------------------------------ Morton helpers
+__host__ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00ff00ffu;
+  x = (x | (x << 4)) & 0x0f0f0f0fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact_bits16(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0f0f0f0fu;
+  x = (x | (x >> 4)) & 0x00ff00ffu;
+  x = (x | (x >> 8)) & 0x0000ffffu;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t morton_encode(uint32_t ix, uint32_t iy) {
+  return spread_bits16(ix) | (spread_bits16(iy) << 1);
+}
+__host__ __device__ __forceinline__ void morton_decode(uint32_t k, int &ix, int &iy) {
+  ix = (int)compact_bits16(k);
+  iy = (int)compact_bits16(k >> 1);
+}
+
+__host__ __device__ __forceinline__ int64_t level_offset(int l) {
+  return ((int64_t(1) << (2 * l)) - 1) / 3;
+}
+__host__ __device__ __forceinline__ int64_t blevel_offset(int l) {
+  return 4 * ((int64_t(1) << l) - 1);
+}
+
+// ------------------------------------------------------------------ exact cell geometry
+struct GeoDev {
+  int n, L, tnum, tden;
+};
+
+// Volume cell (level l, Morton c): centre and half-width in units of h/2, origin (x0, y0).
+__host__ __device__ __forceinline__ void vol_geom(const GeoDev &g, int l, uint32_t c, int64_t &X,
+                                                  int64_t &Y, int64_t &s) {
+  int a, b;
+  morton_decode(c, a, b);
+  int64_t w = g.n >> l;
+  X = 2 * a * w + w + 1;
+  Y = 2 * b * w + w + 1;
+  s = w;
+}
+
+// Boundary cell (level l, id = side 2^l + k): the k-th of 2^l equal runs of elements
+// along side 0 bottom (x up), 1 right (y up), 2 top (x down), 3 left (y down).  Centre
+// and half-width of the circumscribed square in units of h/2^(L+1), origin (x0, y0).
+__host__ __device__ __forceinline__ void bnd_geom(const GeoDev &g, int l, uint32_t id, int64_t &X,
+                                                  int64_t &Y, int64_t &s) {
+  int side = (int)(id >> l);
+  int64_t k = id & ((1u << l) - 1u);
+  int64_t np1 = g.n + 1, SL = np1 << (g.L + 1);
+  int64_t t = (2 * k + 1) * np1 * (int64_t(1) << (g.L - l));
+  s = np1 * (int64_t(1) << (g.L - l));
+  switch (side) {
+    case 0: X = t; Y = 0; break;
+    case 1: X = SL; Y = t; break;
+    case 2: X = SL - t; Y = SL; break;
+    default: X = 0; Y = SL - t; break;
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geo {
+  int n, m, L, lg, p;  // lg = log2(n)
+  int tnum, tden;      // theta = tnum / tden
+  double x0, y0, side, h, lnh;
+  int R;          // P2P stencil radius in leaves (max |offset component|)
+  int pad;        // halo of the padded weight image in nodes = R * m
+  int npad;       // n + 2 pad
+  int NG;         // boundary elements = 4n
+  int64_t ncell;  // volume cells, all levels
+  int64_t nbcell; // boundary cells, all levels
+  int64_t nleaf, nbleaf;
+};
+
+// P2P stencil: for each row oy in [-R, R] the contiguous column range [ox0, ox1];
+// ox0 > ox1 marks an empty row.
+struct Stencil {
+  int R;
+  int ox0[2 * 16 + 1], ox1[2 * 16 + 1];
+  int count;
+};
+
+struct Lists {
+  int64_t n_m2l = 0, n_p2p = 0, n_m2l_vb = 0, n_p2p_vb = 0;
+  int32_t *m2l = nullptr, *p2p = nullptr, *m2l_vb = nullptr, *p2p_vb = nullptr;  // canonical
+  // CSR views used by the kernels
+  int32_t *m2l_first = nullptr;   // [ncell+1] by global target cell; m2l_src holds sources
+  int32_t *m2l_src = nullptr;     // source Morton index at the target's level
+  int32_t *vbv_first = nullptr;   // [ncell+1] by volume target: boundary sources (pass B)
+  int32_t *vbv_src = nullptr;     // boundary cell id at that level
+  int32_t *vbb_first = nullptr;   // [nbcell+1] by boundary target: volume sources (pass A)
+  int32_t *vbb_src = nullptr;     // volume Morton index at that level
+  int32_t *pvb_first = nullptr;   // [nbleaf+1] by boundary leaf: near volume leaves (pass A)
+  int32_t *pvb_src = nullptr;
+  int32_t *pbv_first = nullptr;   // [nbnear+1] by compacted volume leaf: near boundary leaves
+  int32_t *pbv_src = nullptr;
+  int32_t *pbv_leaf = nullptr;    // [nbnear] volume leaf Morton index of each compacted row
+  int32_t *leaf_bslot = nullptr;  // [nleaf] compacted row of a leaf or -1
+  int64_t nbnear = 0;
+};
+
+// ------------------------------------------------------------------ cross-file API
+// sort_scan.cu
+void scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_host,
+                        cudaStream_t s, DevPool &tmp);
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits, cudaStream_t s,
+                    DevPool &tmp);
+
+// tree.cu
+struct TreeOut {
+  uint32_t *keys;  // natural order
+  int32_t *perm;   // Morton position -> natural index
+  int32_t *cell_start;
+};
+void build_tree(const Geo &g, TreeOut &t, cudaStream_t s, DevPool &pool, DevPool &tmp);
+void build_lists(const Geo &g, Lists &lists, Stencil &st, cudaStream_t s, DevPool &pool,
+                 DevPool &tmp);
+
+}  // namespace fmmpc

@@ -1,0 +1,84 @@
+// The handle behind the C ABI: geometry, tree, lists, FMM and BEM buffers, Krylov
+// workspace.  Shared by api.cu, fmm.cu and krylov.cu.
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+
+namespace fmmpc {
+
+enum ApplyPart {
+  PART_FULL = 0,   // P^{-1} r
+  PART_VR = 1,     // V r at the nodes
+  PART_NEAR = 2,   // near-field (P2P) part of V r, physical units
+  PART_VCOL = 3,   // V r at the collocation points
+  PART_Q = 4,      // BEM density q
+};
+
+// FMM buffers for one arithmetic type (float or double).
+struct FmmBufs {
+  void *wpad = nullptr;      // [nrhs][npad^2] padded weight image h^2 r
+  void *Mv = nullptr;        // [nrhs][ncell][p] volume multipoles
+  void *Lv = nullptr;        // [nrhs][ncell][p] volume locals
+  void *Mb = nullptr;        // [nrhs][nbcell][p] boundary multipoles
+  void *Lb = nullptr;        // [nrhs][nbcell][p] boundary locals
+  void *phib = nullptr;      // [nrhs][nbnear][m^2] near-boundary correction at nodes
+  void *table = nullptr;     // lattice table ln|d| (node units), self term at d = 0
+  void *table_lnh = nullptr; // same plus ln h (for the near-field-only part)
+  int table_rows = 0, table_stride = 0, table_c0 = 0, Rn = 0;
+  double *vcol = nullptr;    // [nrhs][NG] V r at collocation points
+  double *q = nullptr;       // [nrhs][NG] BEM density
+};
+
+struct KrylovWs {
+  int64_t cap_vecs = 0;   // vectors of N*nrhs doubles allocated in V (and Z)
+  double *V = nullptr, *Z = nullptr;
+  double *w = nullptr, *t = nullptr, *b = nullptr, *x = nullptr, *r = nullptr;
+  double *dots = nullptr;  // [nrhs][MAXDOT]
+  double *part = nullptr;  // block partials
+  double *scal = nullptr;  // per-rhs scalars on device
+  double *hbuf = nullptr;  // pinned host mirror
+  int *mask = nullptr;     // [nrhs] active right-hand sides
+};
+
+}  // namespace fmmpc
+
+struct fmmpc_handle {
+  fmmpc::Geo g{};
+  fmmpc::Stencil st{};
+  int prec = FMMPC_PREC_FP32;
+  int nrhs_max = 1;
+  int tile_x = 8, tile_y = 4;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  fmmpc::DevPool pool;      // lifetime of the handle
+  fmmpc::DevPool kpool;     // Krylov workspace (grown on demand)
+  fmmpc::TreeOut tree{};
+  fmmpc::Lists lists{};
+  fmmpc::FmmBufs fb{};
+  double *Sinv = nullptr;   // [NG][NG] FP64 inverse of the single-layer matrix
+  double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
+  fmmpc::KrylovWs kw{};
+  int64_t launches = 0;     // kernel launches of the last apply
+  // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
+  static constexpr int NSTAGE = 9;
+  bool timing = false;
+  cudaEvent_t ev[NSTAGE + 1] = {};
+  bool stage_hit[NSTAGE] = {};
+  double t_setup_ms = 0.0;
+  // CUDA graph of the apply (input/output fixed to the staging pointers of the solver)
+  cudaGraphExec_t graph = nullptr;
+  const void *graph_in = nullptr;
+  void *graph_out = nullptr;
+  int graph_nrhs = 0;
+};
+
+namespace fmmpc {
+void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs);
+void init_fmm(fmmpc_handle &H);
+void init_bem(fmmpc_handle &H, DevPool &tmp);
+void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs);
+int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs,
+          const fmmpc_solve_opts &o, fmmpc_solve_info &info);
+}  // namespace fmmpc

@@ -1,0 +1,442 @@
+// FP64 Krylov solvers around the preconditioner (Sec. 3.1): CG, and GMRES(m) / FGMRES(m)
+// with right preconditioning A P^{-1} y = b, x = P^{-1} y (Sec. 3.1 notation).  Zero
+// initial iterate by default and a relative-residual stop (Sec. 6).  Several right-hand
+// sides run side by side, each with its own Krylov space; vectors are [nrhs][N] FP64.
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2), so each orthogonalisation is
+// a fused multi-dot and a fused update; the small Hessenberg least-squares problem
+// (Givens rotations) stays on the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "handle.cuh"
+
+namespace fmmpc {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 256;  // per rhs; partial sums reduced in a second kernel
+constexpr int MAXJ = 64;         // largest Krylov basis handled by the fused kernels
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+__global__ void k_spmv5(int n, double s, int64_t total, const double *__restrict__ x,
+                        double *__restrict__ y) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t N = (int64_t)n * n;
+  const int64_t k = t % N;
+  const int i = (int)(k % n), j = (int)(k / n);
+  double v = 4.0 * x[t];
+  if (i > 0) v -= x[t - 1];
+  if (i < n - 1) v -= x[t + 1];
+  if (j > 0) v -= x[t - n];
+  if (j < n - 1) v -= x[t + n];
+  y[t] = s * v;
+}
+
+// b = f + g / h^2 at the stencil neighbours outside the interior block (Eq. e:pbound)
+__global__ void k_fold_rhs(int n, double s, int64_t total, const double *__restrict__ f,
+                           const double *__restrict__ g, double *__restrict__ b) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t N = (int64_t)n * n;
+  const int64_t rhs = t / N, k = t % N;
+  const int i = (int)(k % n), j = (int)(k / n);
+  double v = f[t];
+  if (g) {
+    const double *gg = g + rhs * 4 * n;
+    if (j == 0) v += s * gg[i];
+    if (i == n - 1) v += s * gg[n + j];
+    if (j == n - 1) v += s * gg[2 * n + (n - 1 - i)];
+    if (i == 0) v += s * gg[3 * n + (n - 1 - j)];
+  }
+  b[t] = v;
+}
+
+// partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
+// Vectors are taken in register groups of 8.
+__global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, int64_t vs,
+                               const double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double red[RED_THREADS / 32][8];
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double *wr = w + (int64_t)rhs * N;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+      const double wk = wr[k];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q < nv) acc[q] = fma(V[(int64_t)(i0 + q) * vs + (int64_t)rhs * N + k], wk, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nv) {
+      double sum = 0.0;
+      for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
+      part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// out[rhs][i] = sum_blk partial ; optionally accumulates into acc[rhs][i]
+__global__ void k_mdot_final(int nv, int nblocks, const double *__restrict__ part, double *__restrict__ out,
+                             double *__restrict__ acc) {
+  const int rhs = blockIdx.x;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[((int64_t)rhs * MAXJ + i) * nblocks + b];
+    out[rhs * MAXJ + i] = s;
+    if (acc) acc[rhs * MAXJ + i] += s;
+  }
+}
+
+// w[rhs] -= sum_i c[rhs][i] V_i[rhs]
+__global__ void k_mupdate(int64_t N, int nrhs, int nv, const double *__restrict__ V, int64_t vs,
+                          const double *__restrict__ c, double *__restrict__ w) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int rhs = (int)(t / N);
+  double v = w[t];
+  for (int i = 0; i < nv; ++i) v = fma(-c[rhs * MAXJ + i], V[i * vs + t], v);
+  w[t] = v;
+}
+
+// x[rhs] += sum_i y[rhs][i] Z_i[rhs]
+__global__ void k_maxpy(int64_t N, int nrhs, int nv, const double *__restrict__ Z, int64_t vs,
+                        const double *__restrict__ y, double *__restrict__ x) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int rhs = (int)(t / N);
+  double v = x[t];
+  for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
+  x[t] = v;
+}
+
+// y[rhs] = a[rhs] * x[rhs]  (a read from device, a = 0 allowed)
+__global__ void k_scale(int64_t N, int nrhs, const double *__restrict__ a, const double *__restrict__ x,
+                        double *__restrict__ y) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  y[t] = a[t / N] * x[t];
+}
+
+// x += y
+__global__ void k_add(int64_t total, const double *__restrict__ y, double *__restrict__ x) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  x[t] += y[t];
+}
+
+// y = b - y
+__global__ void k_resid(int64_t total, const double *__restrict__ b, double *__restrict__ y) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  y[t] = b[t] - y[t];
+}
+
+// x += a p ; r -= a q  (CG), a per rhs
+__global__ void k_cg_xr(int64_t N, int nrhs, const double *__restrict__ a, const double *__restrict__ p,
+                        const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const double al = a[t / N];
+  x[t] = fma(al, p[t], x[t]);
+  r[t] = fma(-al, q[t], r[t]);
+}
+
+// p = z + beta p
+__global__ void k_cg_p(int64_t N, int nrhs, const double *__restrict__ beta, const double *__restrict__ z,
+                       double *__restrict__ p) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  p[t] = fma(beta[t / N], p[t], z[t]);
+}
+
+struct Ctx {
+  fmmpc_handle &H;
+  int64_t N;
+  int nrhs;
+  cudaStream_t s;
+};
+
+void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
+  KrylovWs &k = H.kw;
+  const int64_t N = (int64_t)H.g.n * H.g.n * H.nrhs_max;
+  if (k.cap_vecs >= nvec && (!flexible || k.Z)) return;
+  FMMPC_CUDA(cudaStreamSynchronize(H.stream));
+  if (k.hbuf) cudaFreeHost(k.hbuf);
+  H.kpool.release();
+  k = KrylovWs{};
+  k.V = H.kpool.get<double>((size_t)N * nvec);
+  k.Z = H.kpool.get<double>((size_t)N * (nvec - 1));
+  k.w = H.kpool.get<double>(N);
+  k.t = H.kpool.get<double>(N);
+  k.b = H.kpool.get<double>(N);
+  k.r = H.kpool.get<double>(N);
+  k.x = H.kpool.get<double>(N);
+  k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
+  k.part = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * RED_BLOCKS);
+  k.scal = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
+  FMMPC_CUDA(cudaMallocHost(&k.hbuf, sizeof(double) * H.nrhs_max * MAXJ * 4));
+  k.cap_vecs = nvec;
+}
+
+// dots[rhs][0..nv) = <V_i, w>; if acc, acc += dots
+void mdot(Ctx &c, int nv, const double *V, int64_t vs, const double *w, double *out, double *acc) {
+  dim3 grid(RED_BLOCKS, c.nrhs);
+  k_mdot_partial<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, w, c.H.kw.part);
+  k_mdot_final<<<c.nrhs, 64, 0, c.s>>>(nv, RED_BLOCKS, c.H.kw.part, out, acc);
+  FMMPC_LAUNCH_CHECK();
+}
+
+void to_host(Ctx &c, const double *d, size_t count) {
+  FMMPC_CUDA(cudaMemcpyAsync(c.H.kw.hbuf, d, sizeof(double) * count, cudaMemcpyDeviceToHost, c.s));
+  FMMPC_CUDA(cudaStreamSynchronize(c.s));
+}
+
+void precond(Ctx &c, const double *in, double *out) { apply_fmm(c.H, PART_FULL, in, out, c.nrhs); }
+
+void residual(Ctx &c, const double *b, const double *x, double *r) {
+  spmv5(c.H, x, r, c.nrhs);
+  k_resid<<<nblk(c.N * c.nrhs), 256, 0, c.s>>>(c.N * c.nrhs, b, r);
+  FMMPC_LAUNCH_CHECK();
+}
+
+// per-rhs norms of v (length nrhs on host, in out)
+void norms(Ctx &c, const double *v, std::vector<double> &out) {
+  double *d = c.H.kw.dots;
+  mdot(c, 1, v, 0, v, d, nullptr);  // with vs = 0 each rhs dots its own slice with itself
+  to_host(c, d, (size_t)c.nrhs * MAXJ);
+  out.resize(c.nrhs);
+  for (int r = 0; r < c.nrhs; ++r) out[r] = std::sqrt(std::max(0.0, c.H.kw.hbuf[r * MAXJ]));
+}
+
+int gmres(Ctx &c, bool flexible, int m, int maxit, double rtol, const double *b, double *x,
+          fmmpc_solve_info &info) {
+  fmmpc_handle &H = c.H;
+  KrylovWs &K = H.kw;
+  const int64_t N = c.N, NR = N * c.nrhs, vs = N * H.nrhs_max;
+  const int nr = c.nrhs;
+  std::vector<double> bn, beta;
+  norms(c, b, bn);
+  for (double &v : bn) if (v == 0.0) v = 1.0;
+  std::vector<double> Hm((size_t)nr * (m + 1) * m), cs((size_t)nr * m), sn((size_t)nr * m),
+      gg((size_t)nr * (m + 1)), y((size_t)nr * MAXJ), hcol((size_t)nr * MAXJ);
+  std::vector<int> done(nr, 0), rhs_iters(nr, 0);
+  int it = 0;
+  int status = FMMPC_OK;
+  double *hy = K.hbuf + (size_t)nr * MAXJ * 2;  // pinned staging for y / scalars
+  for (;;) {
+    residual(c, b, x, K.r);
+    norms(c, K.r, beta);
+    bool all = true;
+    for (int r = 0; r < nr; ++r) {
+      if (!std::isfinite(beta[r])) return FMMPC_ERR_NAN;
+      done[r] = beta[r] / bn[r] <= rtol;
+      all = all && done[r];
+    }
+    if (all || it >= maxit) break;
+    for (int r = 0; r < nr; ++r) hy[r] = done[r] ? 0.0 : 1.0 / beta[r];
+    FMMPC_CUDA(cudaMemcpyAsync(K.scal, hy, sizeof(double) * nr, cudaMemcpyHostToDevice, c.s));
+    k_scale<<<nblk(NR), 256, 0, c.s>>>(N, nr, K.scal, K.r, K.V);
+    std::fill(gg.begin(), gg.end(), 0.0);
+    for (int r = 0; r < nr; ++r) gg[(size_t)r * (m + 1)] = done[r] ? 0.0 : beta[r];
+    int j = 0;
+    for (; j < m && it < maxit; ++j) {
+      double *vj = K.V + (int64_t)j * vs;
+      double *zj = flexible ? K.Z + (int64_t)j * vs : K.t;
+      precond(c, vj, zj);
+      spmv5(H, zj, K.w, nr);
+      // CGS2: h = V^T w, w -= V h, twice
+      double *d1 = K.dots, *hsum = K.dots + (size_t)nr * MAXJ;
+      FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nr * MAXJ, c.s));
+      for (int pass = 0; pass < 2; ++pass) {
+        mdot(c, j + 1, K.V, vs, K.w, d1, hsum);
+        k_mupdate<<<nblk(NR), 256, 0, c.s>>>(N, nr, j + 1, K.V, vs, d1, K.w);
+      }
+      FMMPC_LAUNCH_CHECK();
+      FMMPC_CUDA(cudaMemcpyAsync(hcol.data(), hsum, sizeof(double) * nr * MAXJ, cudaMemcpyDeviceToHost, c.s));
+      std::vector<double> hn;
+      norms(c, K.w, hn);
+      ++it;
+      bool conv_all = true;
+      for (int r = 0; r < nr; ++r) {
+        double *Hr = &Hm[(size_t)r * (m + 1) * m];
+        for (int i = 0; i <= j; ++i) Hr[i * m + j] = hcol[(size_t)r * MAXJ + i];
+        Hr[(j + 1) * m + j] = hn[r];
+        double *csr = &cs[(size_t)r * m], *snr = &sn[(size_t)r * m], *g = &gg[(size_t)r * (m + 1)];
+        for (int i = 0; i < j; ++i) {
+          double a = Hr[i * m + j], bb = Hr[(i + 1) * m + j];
+          Hr[i * m + j] = csr[i] * a + snr[i] * bb;
+          Hr[(i + 1) * m + j] = -snr[i] * a + csr[i] * bb;
+        }
+        double a = Hr[j * m + j], bb = Hr[(j + 1) * m + j], rr = std::hypot(a, bb);
+        if (rr == 0.0) { csr[j] = 1.0; snr[j] = 0.0; }
+        else { csr[j] = a / rr; snr[j] = bb / rr; }
+        Hr[j * m + j] = rr;
+        Hr[(j + 1) * m + j] = 0.0;
+        g[j + 1] = -snr[j] * g[j];
+        g[j] = csr[j] * g[j];
+        const double est = std::fabs(g[j + 1]) / bn[r];
+        if (!std::isfinite(est)) return FMMPC_ERR_NAN;
+        if (!done[r]) rhs_iters[r] = it;
+        const bool ok = done[r] || est <= rtol || hn[r] == 0.0;
+        conv_all = conv_all && ok;
+        hy[r] = (hn[r] > 0.0 && !done[r]) ? 1.0 / hn[r] : 0.0;
+      }
+      FMMPC_CUDA(cudaMemcpyAsync(K.scal, hy, sizeof(double) * nr, cudaMemcpyHostToDevice, c.s));
+      k_scale<<<nblk(NR), 256, 0, c.s>>>(N, nr, K.scal, K.w, K.V + (int64_t)(j + 1) * vs);
+      FMMPC_LAUNCH_CHECK();
+      if (conv_all) { ++j; break; }
+    }
+    // back substitution, y per rhs, then x += sum y_i z_i
+    std::fill(y.begin(), y.end(), 0.0);
+    for (int r = 0; r < nr; ++r) {
+      if (done[r]) continue;
+      const double *Hr = &Hm[(size_t)r * (m + 1) * m];
+      const double *g = &gg[(size_t)r * (m + 1)];
+      for (int i = j - 1; i >= 0; --i) {
+        double sacc = g[i];
+        for (int k = i + 1; k < j; ++k) sacc -= Hr[i * m + k] * y[(size_t)r * MAXJ + k];
+        y[(size_t)r * MAXJ + i] = (Hr[i * m + i] != 0.0) ? sacc / Hr[i * m + i] : 0.0;
+      }
+    }
+    std::copy(y.begin(), y.end(), hy);
+    FMMPC_CUDA(cudaMemcpyAsync(K.scal, hy, sizeof(double) * nr * MAXJ, cudaMemcpyHostToDevice, c.s));
+    if (flexible) {
+      k_maxpy<<<nblk(NR), 256, 0, c.s>>>(N, nr, j, K.Z, vs, K.scal, x);
+    } else {
+      FMMPC_CUDA(cudaMemsetAsync(K.t, 0, sizeof(double) * NR, c.s));
+      k_maxpy<<<nblk(NR), 256, 0, c.s>>>(N, nr, j, K.V, vs, K.scal, K.t);
+      precond(c, K.t, K.w);
+      k_add<<<nblk(NR), 256, 0, c.s>>>(NR, K.w, x);
+    }
+    FMMPC_LAUNCH_CHECK();
+    FMMPC_CUDA(cudaStreamSynchronize(c.s));
+  }
+  residual(c, b, x, K.r);
+  norms(c, K.r, beta);
+  double worst = 0.0;
+  for (int r = 0; r < nr; ++r) {
+    const double rel = beta[r] / bn[r];
+    if (!std::isfinite(rel)) status = FMMPC_ERR_NAN;
+    worst = std::max(worst, rel);
+  }
+  if (status == FMMPC_OK && worst > rtol) status = FMMPC_ERR_NOT_CONVERGED;
+  info.iters = 0;
+  for (int r = 0; r < nr; ++r) info.iters = std::max(info.iters, rhs_iters[r]);
+  info.rel_res = worst;
+  return status;
+}
+
+int pcg(Ctx &c, int maxit, double rtol, const double *b, double *x, fmmpc_solve_info &info) {
+  fmmpc_handle &H = c.H;
+  KrylovWs &K = H.kw;
+  const int64_t N = c.N, NR = N * c.nrhs;
+  const int nr = c.nrhs;
+  double *r = K.r, *z = K.w, *p = K.V, *q = K.t;
+  double *hy = K.hbuf + (size_t)nr * MAXJ * 2;
+  std::vector<double> bn, rn;
+  norms(c, b, bn);
+  for (double &v : bn) if (v == 0.0) v = 1.0;
+  residual(c, b, x, r);
+  precond(c, r, z);
+  FMMPC_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * NR, cudaMemcpyDeviceToDevice, c.s));
+  auto dotv = [&](const double *a, const double *bb, std::vector<double> &out) {
+    mdot(c, 1, a, 0, bb, K.dots, nullptr);
+    to_host(c, K.dots, (size_t)nr * MAXJ);
+    out.resize(nr);
+    for (int i = 0; i < nr; ++i) out[i] = K.hbuf[i * MAXJ];
+  };
+  std::vector<double> rz, pq, rz2;
+  dotv(r, z, rz);
+  norms(c, r, rn);
+  std::vector<int> done(nr, 0), its(nr, 0);
+  int it = 0;
+  bool all = true;
+  for (int i = 0; i < nr; ++i) { done[i] = rn[i] / bn[i] <= rtol; all = all && done[i]; }
+  while (!all && it < maxit) {
+    spmv5(H, p, q, nr);
+    dotv(p, q, pq);
+    for (int i = 0; i < nr; ++i) hy[i] = (done[i] || pq[i] == 0.0) ? 0.0 : rz[i] / pq[i];
+    FMMPC_CUDA(cudaMemcpyAsync(K.scal, hy, sizeof(double) * nr, cudaMemcpyHostToDevice, c.s));
+    k_cg_xr<<<nblk(NR), 256, 0, c.s>>>(N, nr, K.scal, p, q, x, r);
+    FMMPC_LAUNCH_CHECK();
+    ++it;
+    norms(c, r, rn);
+    all = true;
+    for (int i = 0; i < nr; ++i) {
+      if (!std::isfinite(rn[i])) return FMMPC_ERR_NAN;
+      if (!done[i]) its[i] = it;
+      done[i] = done[i] || rn[i] / bn[i] <= rtol;
+      all = all && done[i];
+    }
+    if (all) break;
+    precond(c, r, z);
+    dotv(r, z, rz2);
+    for (int i = 0; i < nr; ++i) {
+      hy[i] = (done[i] || rz[i] == 0.0) ? 0.0 : rz2[i] / rz[i];
+      rz[i] = rz2[i];
+    }
+    FMMPC_CUDA(cudaMemcpyAsync(K.scal, hy, sizeof(double) * nr, cudaMemcpyHostToDevice, c.s));
+    k_cg_p<<<nblk(NR), 256, 0, c.s>>>(N, nr, K.scal, z, p);
+    FMMPC_LAUNCH_CHECK();
+  }
+  residual(c, b, x, r);
+  norms(c, r, rn);
+  double worst = 0.0;
+  int status = FMMPC_OK;
+  for (int i = 0; i < nr; ++i) {
+    const double rel = rn[i] / bn[i];
+    if (!std::isfinite(rel)) status = FMMPC_ERR_NAN;
+    worst = std::max(worst, rel);
+  }
+  if (status == FMMPC_OK && worst > rtol) status = FMMPC_ERR_NOT_CONVERGED;
+  info.iters = 0;
+  for (int i = 0; i < nr; ++i) info.iters = std::max(info.iters, its[i]);
+  info.rel_res = worst;
+  return status;
+}
+
+}  // namespace
+
+void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs) {
+  const int64_t total = (int64_t)H.g.n * H.g.n * nrhs;
+  k_spmv5<<<nblk(total), 256, 0, H.stream>>>(H.g.n, 1.0 / (H.g.h * H.g.h), total, x, y);
+  FMMPC_LAUNCH_CHECK();
+}
+
+int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs,
+          const fmmpc_solve_opts &o, fmmpc_solve_info &info) {
+  require(o.method >= FMMPC_CG && o.method <= FMMPC_FGMRES, "unknown Krylov method");
+  require(o.maxit >= 1 && o.rtol > 0.0, "maxit >= 1 and rtol > 0 required");
+  const int m = (o.method == FMMPC_CG) ? 1 : std::min(o.restart, o.maxit);
+  require(m >= 1 && m < MAXJ, "restart must be in [1, 63]");
+  auto t0 = std::chrono::steady_clock::now();
+  ensure_ws(H, o.method == FMMPC_CG ? 2 : m + 1, o.method == FMMPC_FGMRES);
+  Ctx c{H, (int64_t)H.g.n * H.g.n, nrhs, H.stream};
+  const int64_t NR = c.N * nrhs;
+  k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(H.g.n, 1.0 / (H.g.h * H.g.h), NR, f, g, H.kw.b);
+  FMMPC_LAUNCH_CHECK();
+  int st;
+  if (o.method == FMMPC_CG) st = pcg(c, o.maxit, o.rtol, H.kw.b, u, info);
+  else st = gmres(c, o.method == FMMPC_FGMRES, m, o.maxit, o.rtol, H.kw.b, u, info);
+  FMMPC_CUDA(cudaStreamSynchronize(c.s));
+  info.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  info.t_setup_ms = H.t_setup_ms;
+  info.status = st;
+  return st;
+}
+
+}  // namespace fmmpc
