@@ -173,6 +173,36 @@ int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
 int fmmpc_set_timing(fmmpc_handle *h, int32_t on);
 int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);
 
+/* Near field of the volume operator without any device allocation.
+ *
+ * This computes the same quantity as fmmpc_apply_part(h, 2, ...): the part of V r that
+ * the dual tree traversal assigns to direct P2P interactions between leaves, in physical
+ * units, FP32 arithmetic, one right-hand side.  The grid rules are those of fmmpc_create
+ * (n interior nodes per side, a power of two, leaf side 4, 8 or 16 from leaf_max, MAC
+ * parameter theta) on a square of side length `side`.  r_dev and out_dev are [n][n] FP64
+ * device buffers owned by the caller; the call is asynchronous on `stream`.
+ *
+ * It exists for callers that must not allocate device memory: code running inside a
+ * framework whose memory pool already owns the device memory (a cudaMalloc there can fail
+ * or fragment the pool), code that records work while a stream is being captured, and
+ * latency-bound loops that cannot afford cudaMalloc's implicit synchronisation.  Instead
+ * of handle-owned buffers it uses one static device array of 4,194,304 FP32 values
+ * (16 MiB) that every GPU loading this library holds until the process exits.  It holds
+ * the log table and the zero-padded weight image; grids needing more (e.g. n = 2048 with
+ * 8x8 leaves) are rejected with FMMPC_ERR_INVALID and a message, before any GPU work.
+ * n = 1024 with 8x8 leaves and theta = 0.4 is the largest grid that fits.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents; each call rewrites the table
+ * and the whole padded image, so nothing stale is read.  Calls that overlap on the GPU
+ * (on different streams, or from several host threads) race on the array and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Errors: _INVALID (arguments, size), _UNSUPPORTED (theta), _CUDA; message via
+ * fmmpc_last_error(NULL).  The paper has no counterpart of this entry point. */
+int fmmpc_near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta,
+                             const double *r_dev, double *out_dev, void *stream);
+
 /* Releases every resource of the handle (NULL is allowed). */
 void fmmpc_destroy(fmmpc_handle *h);
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "fmmpc_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
     "fmmpc_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
+    "fmmpc_near_field_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]),
     "fmmpc_destroy": (None, [C.c_void_p]),
     "fmmpc_last_error": (C.c_char_p, [C.c_void_p]),
     "fmmpc_version": (C.c_char_p, []),

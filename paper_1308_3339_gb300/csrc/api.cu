@@ -10,13 +10,17 @@
 
 using namespace fmmpc;
 
+namespace fmmpc {
+int set_global_error(int code, const char *msg);
+}
+
 namespace {
 
-thread_local std::string g_create_error;
+thread_local char g_global_error[512];
 
 int fail(fmmpc_handle *h, const Error &e) {
   if (h) h->err = e.msg;
-  else g_create_error = e.msg;
+  else set_global_error(e.code, e.msg.c_str());
   return e.code;
 }
 
@@ -128,20 +132,24 @@ void release(fmmpc_handle *h) {
 
 }  // namespace
 
+namespace fmmpc {
+int set_global_error(int code, const char *msg) {
+  std::strncpy(g_global_error, msg ? msg : "", sizeof(g_global_error) - 1);
+  g_global_error[sizeof(g_global_error) - 1] = 0;
+  return code;
+}
+}  // namespace fmmpc
+
 extern "C" {
 
 int fmmpc_create(fmmpc_handle **out, const fmmpc_grid *g, const fmmpc_params *prm, void *stream) {
-  if (!out || !g || !prm) {
-    g_create_error = "fmmpc_create: NULL argument";
-    return FMMPC_ERR_INVALID;
-  }
+  if (!out || !g || !prm) return set_global_error(FMMPC_ERR_INVALID, "fmmpc_create: NULL argument");
   *out = nullptr;
   fmmpc_handle *h = nullptr;
   try {
     h = new fmmpc_handle();
   } catch (...) {
-    g_create_error = "host allocation failed";
-    return FMMPC_ERR_OOM;
+    return set_global_error(FMMPC_ERR_OOM, "host allocation failed");
   }
   h->stream = (cudaStream_t)stream;
   int rc = guarded(h, [&] {
@@ -149,7 +157,7 @@ int fmmpc_create(fmmpc_handle **out, const fmmpc_grid *g, const fmmpc_params *pr
     return FMMPC_OK;
   });
   if (rc != FMMPC_OK) {
-    g_create_error = h->err;
+    set_global_error(rc, h->err.c_str());
     release(h);
     return rc;
   }
@@ -316,7 +324,12 @@ int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count) {
 void fmmpc_destroy(fmmpc_handle *h) { release(h); }
 
 const char *fmmpc_last_error(const fmmpc_handle *h) {
-  return h ? h->err.c_str() : g_create_error.c_str();
+  return h ? h->err.c_str() : g_global_error;
+}
+
+int fmmpc_near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, const double *r_dev,
+                             double *out_dev, void *stream) {
+  return near_field_noalloc(n, side, leaf_max, theta, r_dev, out_dev, stream);
 }
 
 const char *fmmpc_version(void) { return "fmmpc 0.1 sm_103a"; }

@@ -15,6 +15,7 @@
 // leaf offsets that the dual tree traversal produced.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "handle.cuh"
 
@@ -693,8 +694,8 @@ __global__ void __launch_bounds__(256) k_p2p_final(P2PArgs<R> A) {
 }
 
 template <typename R, int M>
-void launch_p2p(fmmpc_handle &H, const P2PArgs<R> &a, cudaStream_t s) {
-  const int side = 1 << H.g.L;
+void launch_p2p(int L, const P2PArgs<R> &a, cudaStream_t s) {
+  const int side = 1 << L;
   dim3 grid(side / a.tile_x, side / a.tile_y, a.nrhs);
   const int threads = a.tile_x * a.tile_y * M;
   const size_t smem = ((size_t)a.HY * a.HX + (size_t)(2 * a.Rn + 1) * a.TS) * sizeof(R);
@@ -861,9 +862,9 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   a.st = H.st;
   mark(8);
   switch (g.m) {
-    case 4: launch_p2p<R, 4>(H, a, s); break;
-    case 8: launch_p2p<R, 8>(H, a, s); break;
-    case 16: launch_p2p<R, 16>(H, a, s); break;
+    case 4: launch_p2p<R, 4>(g.L, a, s); break;
+    case 8: launch_p2p<R, 8>(g.L, a, s); break;
+    case 16: launch_p2p<R, 16>(g.L, a, s); break;
     default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
   }
   ++launches;
@@ -933,6 +934,143 @@ void init_fmm(fmmpc_handle &H) {
 void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
   if (H.prec == FMMPC_PREC_FP64) apply_impl<double>(H, part, r, out, nrhs);
   else apply_impl<float>(H, part, r, out, nrhs);
+}
+
+
+// ====================================================================== no-allocation variant
+// Near field of V r computed with scratch that lives in a static device array instead of
+// memory from cudaMalloc (see fmmpc_near_field_noalloc in fmmpc.h).  The array holds the
+// log table followed by the zero-padded FP32 weight image; every call rewrites both.
+namespace {
+
+constexpr int64_t NOALLOC_FLOATS = int64_t(4) * 1024 * 1024;  // 16 MiB of FP32
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+__global__ void k_noalloc_table(float *__restrict__ tab, int Rn, int TS, int c0, double lnh) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)(2 * Rn + 1) * TS) return;
+  const int row = (int)(k / TS), col = (int)(k % TS);
+  const int dy = row - Rn, dx = col - c0 - Rn;
+  float v = 0.0f;  // padding columns are read by the vector loads but never used
+  if (dx >= -Rn && dx <= Rn) {
+    const double cself = -0.5 * log(2.0) - 1.5 + 0.25 * PI;
+    const double lg = (dx == 0 && dy == 0) ? cself : 0.5 * log((double)dx * dx + (double)dy * dy);
+    v = (float)(lg + lnh);
+  }
+  tab[k] = v;
+}
+
+__global__ void k_noalloc_image(float *__restrict__ img, int n, int npad, int pad, double h2,
+                                const double *__restrict__ r) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)npad * npad) return;
+  const int y = (int)(k / npad) - pad, x = (int)(k % npad) - pad;
+  img[k] = (x >= 0 && y >= 0 && x < n && y < n) ? (float)(h2 * r[(int64_t)y * n + x]) : 0.0f;
+}
+
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
+
+namespace {
+
+// Device address of g_noalloc_scratch for the current device, resolved once per device.
+cudaError_t noalloc_scratch(float **out) {
+  static std::mutex mu;
+  static float *ptr[NOALLOC_MAX_DEVICES] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    ptr[dev] = static_cast<float *>(p);
+  }
+  *out = ptr[dev];
+  return cudaSuccess;
+}
+
+template <int M>
+cudaError_t noalloc_launch(const P2PArgs<float> &a, int L, cudaStream_t s) {
+  const int side = 1 << L;
+  dim3 grid(side / a.tile_x, side / a.tile_y, 1);
+  const size_t smem = ((size_t)a.HY * a.HX + (size_t)(2 * a.Rn + 1) * a.TS) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_p2p_final<float, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_p2p_final<float, M><<<grid, a.tile_x * a.tile_y * M, smem, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, const double *r_dev,
+                       double *out_dev, void *stream) {
+  if (!r_dev || !out_dev || r_dev == out_dev) return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: r and out must be distinct device buffers");
+  if (n < 4 || n > 4096 || (n & (n - 1)) != 0) return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: n must be a power of two in [4, 4096]");
+  if (!(side > 0.0) || !(theta > 0.0 && theta < 1.0) || leaf_max < 16)
+    return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: need side > 0, 0 < theta < 1, leaf_max >= 16");
+  int L = 0, m = n;
+  while ((int64_t)m * m > leaf_max) { m /= 2; ++L; }
+  if (m != 4 && m != 8 && m != 16) return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: leaf side must be 4, 8 or 16");
+  // P2P stencil of a uniform tree: leaf offsets o with 2 tden^2 >= tnum^2 |o|^2 (the pair and
+  // all its ancestor pairs fail the MAC), the same set the dual tree traversal produces
+  const int tn = (int)std::lround(theta * 1000.0), td = 1000;
+  Stencil st{};
+  int R = 0;
+  for (int oy = -16; oy <= 16; ++oy)
+    for (int ox = -16; ox <= 16; ++ox)
+      if (2LL * td * td >= (long long)tn * tn * (ox * ox + oy * oy)) R = std::max(R, std::max(std::abs(ox), std::abs(oy)));
+  if (R >= 16) return set_global_error(FMMPC_ERR_UNSUPPORTED, "near_field_noalloc: theta too small (stencil radius above 15 leaves)");
+  st.R = R;
+  for (int oy = -R; oy <= R; ++oy) {
+    int lo = 1, hi = 0;
+    for (int ox = -R; ox <= R; ++ox)
+      if (2LL * td * td >= (long long)tn * tn * (ox * ox + oy * oy)) {
+        if (lo > hi) lo = ox;
+        hi = ox;
+        ++st.count;
+      }
+    st.ox0[oy + R] = lo;
+    st.ox1[oy + R] = hi;
+  }
+  const int pad = R * m, npad = n + 2 * pad, Rn = R * m + m - 1;
+  const int c0 = ((m - 1 - Rn) % 4 + 4) % 4;
+  int TS = c0 + 2 * Rn + 2;
+  while ((TS * 4) % 128 != 16) ++TS;
+  const int64_t tab_floats = (int64_t)(2 * Rn + 1) * TS;
+  const int64_t need = tab_floats + (int64_t)npad * npad;
+  if (need > NOALLOC_FLOATS)
+    return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: grid too large for the 16 MiB static scratch (n = 1024 with 8x8 leaves and theta 0.4 is the largest such grid)");
+  float *scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  const double h = side / (n + 1);
+  float *tab = scratch, *img = scratch + tab_floats;  // tab_floats is a multiple of 4: 16-byte aligned image
+  k_noalloc_table<<<(unsigned)((tab_floats + 255) / 256), 256, 0, s>>>(tab, Rn, TS, c0, std::log(h));
+  k_noalloc_image<<<(unsigned)(((int64_t)npad * npad + 255) / 256), 256, 0, s>>>(img, n, npad, pad, h * h, r_dev);
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
+  const int sidel = 1 << L;
+  int tx = (m == 16) ? 4 : 8, ty = (m == 4) ? 8 : 4;
+  tx = std::min(tx, sidel);
+  ty = std::min(ty, sidel);
+  P2PArgs<float> a{};
+  a.wpad = img; a.table = tab; a.Lv = nullptr; a.phib = nullptr; a.bslot = nullptr; a.out = out_dev;
+  a.n = n; a.npad = npad; a.L = L; a.p = 0; a.R_ = R; a.Rn = Rn;
+  a.HX = (tx + 2 * R) * m; a.HY = (ty + 2 * R) * m; a.TS = TS; a.c0 = c0;
+  a.tile_x = tx; a.tile_y = ty; a.nrhs = 1; a.ncell = 0; a.nbnear = 0;
+  a.do_near = 1; a.do_far = 0; a.do_bnd = 0; a.st = st;
+  switch (m) {
+    case 4: e = noalloc_launch<4>(a, L, s); break;
+    case 8: e = noalloc_launch<8>(a, L, s); break;
+    default: e = noalloc_launch<16>(a, L, s); break;
+  }
+  if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
+  return FMMPC_OK;
 }
 
 }  // namespace fmmpc

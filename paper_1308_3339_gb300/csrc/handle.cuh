@@ -81,4 +81,8 @@ void init_bem(fmmpc_handle &H, DevPool &tmp);
 void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs);
 int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs,
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);
+// message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
+int set_global_error(int code, const char *msg);
+int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, const double *r_dev,
+                       double *out_dev, void *stream);
 }  // namespace fmmpc
