@@ -199,14 +199,14 @@ def p2p_traffic_record():
     return None
 
 
-def time_solves(P, fd, reps, rtol=1e-8):
+def time_solves(P, fd, reps, rtol=1e-8, graphs=1):
     import torch
-    P.solve(fd, rtol=rtol)  # warm-up (workspace, caches)
+    P.solve(fd, rtol=rtol, use_graphs=graphs)  # warm-up (workspace, graphs)
     out = []
     for _ in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        u, info = P.solve(fd, rtol=rtol)
+        u, info = P.solve(fd, rtol=rtol, use_graphs=graphs)
         torch.cuda.synchronize()
         out.append((time.perf_counter() - t0) * 1e3)
         last = info
@@ -294,9 +294,10 @@ def run_ours(args):
     tts = None
     if not args.no_tts:
         P.set_timing(False)
-        tts = {"mixed_fp32fmm_fp64krylov": time_solves(P, r, 3)}
+        tts = {"mixed_fp32fmm_fp64krylov_graphs": time_solves(P, r, 3, graphs=1),
+               "plain_fp32_no_graphs": time_solves(P, r, 2, graphs=0)}
         P64 = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision="fp64")
-        tts["plain_fp64"] = time_solves(P64, r, 2)
+        tts["plain_fp64_no_graphs"] = time_solves(P64, r, 2, graphs=0)
         P64.close()
 
     cpu = None

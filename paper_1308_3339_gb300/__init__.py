@@ -84,6 +84,9 @@ class FmmPreconditioner:
         check(self.lib.fmmpc_export(self._h, _lib.EXPORT[what], a.ctypes.data_as(C.c_void_p), a.nbytes), self._h)
         return a
 
+    def set_graphs(self, on: bool = True):
+        check(self.lib.fmmpc_set_graphs(self._h, 1 if on else 0), self._h)
+
     def set_timing(self, on: bool = True):
         check(self.lib.fmmpc_set_timing(self._h, 1 if on else 0), self._h)
 

@@ -57,6 +57,7 @@ SIGNATURES = {
                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "fmmpc_query": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "fmmpc_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
+    "fmmpc_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "fmmpc_near_field_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,

@@ -121,7 +121,10 @@ void ensure_stage(fmmpc_handle &H) {
 void release(fmmpc_handle *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto &e : h->gcache) cudaGraphExecDestroy(e.exec);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->gev_in) cudaEventDestroy(h->gev_in);
+  if (h->gev_out) cudaEventDestroy(h->gev_out);
   for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k)
     if (h->ev[k]) cudaEventDestroy(h->ev[k]);
   if (h->kw.hbuf) cudaFreeHost(h->kw.hbuf);
@@ -291,6 +294,12 @@ int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes) {
     FMMPC_CUDA(cudaStreamSynchronize(h->stream));
     return FMMPC_OK;
   });
+}
+
+int fmmpc_set_graphs(fmmpc_handle *h, int32_t on) {
+  if (!h) return FMMPC_ERR_INVALID;
+  h->graphs = on != 0;
+  return FMMPC_OK;
 }
 
 int fmmpc_set_timing(fmmpc_handle *h, int32_t on) {

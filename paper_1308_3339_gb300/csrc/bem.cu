@@ -3,7 +3,8 @@
 // matrix S_mk = int_{Gamma_k} G(y_m, y) dGamma (left side of Eq. e:ubound) is assembled in
 // FP64 from the closed-form element integral (Sec. 4.2) and inverted once, in place, by
 // Gauss-Jordan elimination with partial pivoting, so each apply needs one FP64
-// matrix-vector product for q.
+// matrix-vector product for q.  The square's 90-degree rotation symmetry makes S (and its
+// inverse) block circulant over the four sides; only the first block row is kept.
 #include <cmath>
 
 #include "handle.cuh"
@@ -136,16 +137,16 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   const Geo &g = H.g;
   const int N = g.NG;
   cudaStream_t s = H.stream;
-  H.Sinv = H.pool.get<double>((size_t)N * N);
-  k_bem_S<<<nblk((int64_t)N * N), 256, 0, s>>>(g.n, g.h, g.lnh, H.Sinv);
+  double *A = tmp.get<double>((size_t)N * N);  // full matrix, inverted in place
+  k_bem_S<<<nblk((int64_t)N * N), 256, 0, s>>>(g.n, g.h, g.lnh, A);
   FMMPC_LAUNCH_CHECK();
   int *piv = tmp.get<int>(N);
   double *pinv = tmp.get<double>(1), *pabs = tmp.get<double>(N), *col = tmp.get<double>(N);
   for (int k = 0; k < N; ++k) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(N, k, H.Sinv, piv, pinv, pabs);
-    k_gj_swap_scale<<<nblk(N), 256, 0, s>>>(N, k, H.Sinv, piv, pinv, col);
-    k_gj_colsave<<<nblk(N), 256, 0, s>>>(N, k, H.Sinv, col);
-    k_gj_elim<<<dim3(nblk(N), N), 256, 0, s>>>(N, k, H.Sinv, col);
+    k_gj_pivot<<<1, 1024, 0, s>>>(N, k, A, piv, pinv, pabs);
+    k_gj_swap_scale<<<nblk(N), 256, 0, s>>>(N, k, A, piv, pinv, col);
+    k_gj_colsave<<<nblk(N), 256, 0, s>>>(N, k, A, col);
+    k_gj_elim<<<dim3(nblk(N), N), 256, 0, s>>>(N, k, A, col);
   }
   FMMPC_LAUNCH_CHECK();
   std::vector<int> hp(N);
@@ -157,8 +158,13 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   for (int k = 0; k < N; ++k) amin = std::min(amin, ha[k]);
   if (!(amin > 0.0)) throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
   for (int k = N - 1; k >= 0; --k)
-    if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, H.Sinv, k, hp[k]);
+    if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, A, k, hp[k]);
   FMMPC_LAUNCH_CHECK();
+  // the inverse is block circulant in the four sides (90-degree rotation of the square):
+  // keep its first block row, n x 4n
+  H.Sinv = H.pool.get<double>((size_t)g.n * N);
+  FMMPC_CUDA(cudaMemcpyAsync(H.Sinv, A, sizeof(double) * (size_t)g.n * N, cudaMemcpyDeviceToDevice, s));
+  FMMPC_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace fmmpc

@@ -5,23 +5,24 @@
 //   plus the near field at the collocation points: (V r)(y_m), the right-hand side of
 //   Eq. e:ubound with z = 0 on Gamma.  q = S^{-1}(-(V r)|_Gamma) in FP64 (Sec. 4.3).
 // Pass B: boundary elements carrying q become sources (exact segment multipoles), M2M up
-//   the boundary trees; one M2L over volume and boundary sources into the volume locals
-//   (item 3), L2L down (item 4); the final kernel sums the lattice near field (P2P),
-//   L2P (item 5) and the closed-form near integrals of the elements: Eq. e:uinter.
+//   the boundary trees; M2L over volume and boundary sources into the volume locals
+//   (item 3), L2L down (item 4); the lattice near field (P2P), L2P (item 5) and the
+//   closed-form near integrals of the elements complete Eq. e:uinter.
 //
-// Everything runs in node units with scaled expansions (see common.cuh).  The near field
-// uses the lattice: G between two nodes depends only on their integer offset, so P2P is
-// a block convolution of the weight image with a table of ln|d| over the stencil of
-// leaf offsets that the dual tree traversal produced.
+// Everything runs in node units with scaled expansions (see common.cuh).  On the uniform
+// tree every M2M and L2L is one of a few fixed p x p matrices (child position, side),
+// built at set-up from the paper's formulas.  The near field uses the lattice: G between
+// two nodes depends only on their integer offset, so P2P is a block convolution of the
+// weight image with a table of ln|d| over the stencil of leaf offsets that the dual tree
+// traversal produced.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <mutex>
 
 #include "handle.cuh"
 
 namespace fmmpc {
-
-__constant__ double c_binom[MAXP + 1][MAXP + 1];
 
 namespace {
 
@@ -39,6 +40,16 @@ __device__ __forceinline__ R dev_log(R x) { return log(x); }
 template <>
 __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
 
+// Fixed translation matrices (complex R, row-major [n][k], P = p):
+//   vm2m[ch]    volume M2M from child ch (Morton position) to its parent
+//   vl2l[ch]    volume L2L from a parent to child ch
+//   bm2m[s][j]  boundary M2M from run child j of side s to its parent run
+//   bp2m[s][e]  row vector: multipole of element e of a leaf run of side s, unit density
+template <typename R>
+struct Mats {
+  const cpx<R> *vm2m, *vl2l, *bm2m, *bp2m;
+};
+
 // ------------------------------------------------------------------ weights
 template <typename R>
 __global__ void k_weights(int n, int npad, int pad, double h2, int64_t total,
@@ -52,78 +63,176 @@ __global__ void k_weights(int n, int npad, int pad, double h2, int64_t total,
 }
 
 // ------------------------------------------------------------------ P2M (item 1)
-// Mt_0 = sum w_j, Mt_k = -sum w_j zt_j^k / k, zt_j = (z_j - c) / rho_L.  Warp per leaf.
-template <typename R>
-__global__ void k_p2m_leaf(Geo g, int nrhs, const R *__restrict__ wpad, cpx<R> *__restrict__ Mv) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= g.nleaf * nrhs) return;
-  const int rhs = (int)(wid / g.nleaf);
-  const uint32_t c = (uint32_t)(wid % g.nleaf);
+// Mt_0 = sum w_j, Mt_k = -sum w_j zt_j^k / k, zt_j = (z_j - c) / rho_L, by one warp.
+template <typename R, int P>
+__device__ __forceinline__ void p2m_warp(const R *__restrict__ W, int npad, int pad, int m, uint32_t c,
+                                         int lane, cpx<R> (&acc)[P]) {
   int a, b;
   morton_decode(c, a, b);
-  const int m = g.m, p = g.p;
-  const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
   const R half = R(0.5) * (m - 1), invm = R(1) / m;
-  cpx<R> acc[MAXP];
 #pragma unroll
-  for (int k = 0; k < MAXP; ++k) acc[k] = mk<R>(0, 0);
+  for (int k = 0; k < P; ++k) acc[k] = mk<R>(0, 0);
   for (int t = lane; t < m * m; t += 32) {
-    int i = t % m, j = t / m;
-    R w = W[(int64_t)(b * m + j + g.pad) * g.npad + a * m + i + g.pad];
-    cpx<R> z = mk<R>((i - half) * invm, (j - half) * invm), pw = z;
+    const int i = t % m, j = t / m;
+    const R w = W[(int64_t)(b * m + j + pad) * npad + a * m + i + pad];
+    const cpx<R> z = mk<R>((i - half) * invm, (j - half) * invm);
+    cpx<R> pw = z;
     acc[0].re += w;
 #pragma unroll
-    for (int k = 1; k < MAXP; ++k)
-      if (k < p) {
-        R s = -w / k;
-        acc[k].re = fma(s, pw.re, acc[k].re);
-        acc[k].im = fma(s, pw.im, acc[k].im);
-        pw = pw * z;
-      }
-  }
-  cpx<R> *out = Mv + (int64_t)rhs * g.ncell * p + (level_offset(g.L) + c) * p;
-#pragma unroll
-  for (int k = 0; k < MAXP; ++k)
-    if (k < p) {
-      R re = warp_sum(acc[k].re), im = warp_sum(acc[k].im);
-      if (lane == 0) out[k] = mk(re, im);
+    for (int k = 1; k < P; ++k) {
+      const R s = -w / R(k);
+      acc[k].re = fma(s, pw.re, acc[k].re);
+      acc[k].im = fma(s, pw.im, acc[k].im);
+      pw = pw * z;
     }
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    acc[k].re = warp_sum(acc[k].re);
+    acc[k].im = warp_sum(acc[k].im);
+  }
 }
 
-// ------------------------------------------------------------------ M2M (item 2)
-// Child at w = (c_child - c_parent)/rho_P = (+-1/4, +-1/4), rho_child = rho_P / 2:
-// Mt_n(P) = -Mt_0 w^n/n + sum_{k=1}^n Mt_k(child) 2^{-k} w^{n-k} C(n-1, k-1).
-template <typename R>
-__global__ void k_m2m_vol(int l, int p, int64_t ncell, int nrhs, cpx<R> *__restrict__ Mv) {
-  const int64_t nc = int64_t(1) << (2 * l);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * nrhs) return;
-  const int rhs = (int)(t / nc);
-  const int64_t c = t % nc;
-  cpx<R> *M = Mv + (int64_t)rhs * ncell * p;
-  cpx<R> acc[MAXP];
-  for (int k = 0; k < p; ++k) acc[k] = mk<R>(0, 0);
-  for (int ch = 0; ch < 4; ++ch) {
-    const cpx<R> *Mc = M + (level_offset(l + 1) + 4 * c + ch) * p;
-    cpx<R> w = mk<R>((ch & 1) ? R(0.25) : R(-0.25), (ch & 2) ? R(0.25) : R(-0.25));
-    cpx<R> wp[MAXP], m[MAXP];
-    wp[0] = mk<R>(1, 0);
-    for (int k = 1; k < p; ++k) wp[k] = wp[k - 1] * w;
-    for (int k = 0; k < p; ++k) m[k] = Mc[k];
-    acc[0] = acc[0] + m[0];
-    for (int nn = 1; nn < p; ++nn) {
-      cpx<R> v = (R(-1) / nn) * (m[0] * wp[nn]);
-      R two = 1;
-      for (int k = 1; k <= nn; ++k) {
-        two *= R(0.5);
-        v = v + (two * (R)c_binom[nn - 1][k - 1]) * (m[k] * wp[nn - k]);
+// parent[n] = sum over 4 children ch, k <= n of T[ch][n][k] child_ch[k]
+template <typename R, int P>
+__device__ __forceinline__ cpx<R> m2m_row(const cpx<R> *__restrict__ T, const cpx<R> *c0, const cpx<R> *c1,
+                                          const cpx<R> *c2, const cpx<R> *c3, int n) {
+  cpx<R> acc = mk<R>(0, 0);
+  const cpx<R> *ch[4] = {c0, c1, c2, c3};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    for (int k = 0; k <= n; ++k) cmac(acc, T[(q * P + n) * P + k], ch[q][k]);
+  return acc;
+}
+
+// P2M for a 4x4 block of leaves (one warp each) fused with the two M2M levels above it.
+template <typename R, int P>
+__global__ void __launch_bounds__(512) k_upward_fused(Geo g, const R *__restrict__ wpad,
+                                                      const cpx<R> *__restrict__ vm2m, cpx<R> *__restrict__ Mv) {
+  __shared__ cpx<R> sl[16][P], sp[4][P], sT[4 * P * P];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int rhs = blockIdx.y;
+  const uint32_t blk = blockIdx.x;
+  for (int i = tid; i < 4 * P * P; i += blockDim.x) sT[i] = vm2m[i];
+  cpx<R> *M = Mv + (int64_t)rhs * g.ncell * P;
+  {
+    cpx<R> acc[P];
+    p2m_warp<R, P>(wpad + (int64_t)rhs * g.npad * g.npad, g.npad, g.pad, g.m, 16 * blk + w, lane, acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        sl[w][k] = acc[k];
+        M[(level_offset(g.L) + 16 * blk + w) * P + k] = acc[k];
       }
-      acc[nn] = acc[nn] + v;
     }
   }
-  cpx<R> *out = M + (level_offset(l) + c) * p;
-  for (int k = 0; k < p; ++k) out[k] = acc[k];
+  __syncthreads();
+  if (tid < 4 * P) {
+    const int pi = tid / P, n = tid % P;
+    const cpx<R> v = m2m_row<R, P>(sT, sl[4 * pi], sl[4 * pi + 1], sl[4 * pi + 2], sl[4 * pi + 3], n);
+    sp[pi][n] = v;
+    M[(level_offset(g.L - 1) + 4 * blk + pi) * P + n] = v;
+  }
+  __syncthreads();
+  if (tid < P) M[(level_offset(g.L - 2) + blk) * P + tid] = m2m_row<R, P>(sT, sp[0], sp[1], sp[2], sp[3], tid);
+}
+
+// M2M levels lfrom down to lto (thread per parent coefficient).  One level: a grid of
+// threads; several levels: one block that walks them with a barrier between levels.
+template <typename R, int P>
+__global__ void k_m2m_levels(int lfrom, int lto, int64_t ncell, int nrhs, const cpx<R> *__restrict__ vm2m,
+                             cpx<R> *__restrict__ Mv) {
+  const bool single = (lfrom == lto);
+  for (int l = lfrom; l >= lto; --l) {
+    const int64_t nc = int64_t(1) << (2 * l), tasks = nc * P * nrhs;
+    const int64_t t0 = single ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
+    const int64_t step = single ? (int64_t)gridDim.x * blockDim.x : blockDim.x;
+    for (int64_t t = t0; t < tasks; t += step) {
+      const int n = (int)(t % P);
+      const int64_t rest = t / P, c = rest % nc;
+      const int rhs = (int)(rest / nc);
+      cpx<R> *M = Mv + (int64_t)rhs * ncell * P;
+      const cpx<R> *ch = M + (level_offset(l + 1) + 4 * c) * P;
+      M[(level_offset(l) + c) * P + n] = m2m_row<R, P>(vm2m, ch, ch + P, ch + 2 * P, ch + 3 * P, n);
+    }
+    if (!single) __syncthreads();
+  }
+}
+
+// L2L from level l to l+1 for l in [lfrom, lto): child[n] += sum_{k >= n} S[ch][n][k] parent[k].
+template <typename R, int P>
+__global__ void k_l2l_levels(int lfrom, int lto, int64_t ncell, int nrhs, const cpx<R> *__restrict__ vl2l,
+                             cpx<R> *__restrict__ Lv) {
+  const bool single = (lto == lfrom + 1);
+  for (int l = lfrom; l < lto; ++l) {
+    const int64_t nc = int64_t(1) << (2 * (l + 1)), tasks = nc * P * nrhs;
+    const int64_t t0 = single ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
+    const int64_t step = single ? (int64_t)gridDim.x * blockDim.x : blockDim.x;
+    for (int64_t t = t0; t < tasks; t += step) {
+      const int n = (int)(t % P);
+      const int64_t rest = t / P, cc = rest % nc;
+      const int rhs = (int)(rest / nc);
+      cpx<R> *L = Lv + (int64_t)rhs * ncell * P;
+      const cpx<R> *Lp = L + (level_offset(l) + (cc >> 2)) * P;
+      const cpx<R> *S = vl2l + (int)(cc & 3) * P * P + n * P;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int k = n; k < P; ++k) cmac(acc, S[k], Lp[k]);
+      cpx<R> &dst = L[(level_offset(l + 1) + cc) * P + n];
+      dst = dst + acc;
+    }
+    if (!single) __syncthreads();
+  }
+}
+
+// Two M2M levels in one block: 16 cells of level lc (a 4x4 Morton block) -> 4 parents ->
+// 1 grandparent, with the intermediate parents kept in shared memory.
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_m2m_2levels(int lc, int64_t ncell, const cpx<R> *__restrict__ vm2m,
+                                                     cpx<R> *__restrict__ Mv) {
+  __shared__ cpx<R> sc[16][P], sp[4][P], sT[4 * P * P];
+  const int tid = threadIdx.x, rhs = blockIdx.y;
+  const uint32_t blk = blockIdx.x;
+  cpx<R> *M = Mv + (int64_t)rhs * ncell * P;
+  for (int i = tid; i < 4 * P * P; i += blockDim.x) sT[i] = vm2m[i];
+  for (int i = tid; i < 16 * P; i += blockDim.x) sc[i / P][i % P] = M[(level_offset(lc) + 16 * blk) * P + i];
+  __syncthreads();
+  if (tid < 4 * P) {
+    const int pi = tid / P, n = tid % P;
+    const cpx<R> v = m2m_row<R, P>(sT, sc[4 * pi], sc[4 * pi + 1], sc[4 * pi + 2], sc[4 * pi + 3], n);
+    sp[pi][n] = v;
+    M[(level_offset(lc - 1) + 4 * blk + pi) * P + n] = v;
+  }
+  __syncthreads();
+  if (tid < P) M[(level_offset(lc - 2) + blk) * P + tid] = m2m_row<R, P>(sT, sp[0], sp[1], sp[2], sp[3], tid);
+}
+
+// Two L2L levels in one block: a cell of level lp adds into its 4 children and their 16
+// children, with the updated children kept in shared memory.
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_l2l_2levels(int lp, int64_t ncell, const cpx<R> *__restrict__ vl2l,
+                                                     cpx<R> *__restrict__ Lv) {
+  __shared__ cpx<R> spar[P], sc[4][P], sS[4 * P * P];
+  const int tid = threadIdx.x, rhs = blockIdx.y;
+  const uint32_t c = blockIdx.x;
+  cpx<R> *L = Lv + (int64_t)rhs * ncell * P;
+  for (int i = tid; i < 4 * P * P; i += blockDim.x) sS[i] = vl2l[i];
+  if (tid < P) spar[tid] = L[(level_offset(lp) + c) * P + tid];
+  __syncthreads();
+  if (tid < 4 * P) {
+    const int ch = tid / P, n = tid % P;
+    cpx<R> acc = L[(level_offset(lp + 1) + 4 * c + ch) * P + n];
+    for (int k = n; k < P; ++k) cmac(acc, sS[(ch * P + n) * P + k], spar[k]);
+    sc[ch][n] = acc;
+    L[(level_offset(lp + 1) + 4 * c + ch) * P + n] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < 16 * P; t += blockDim.x) {
+    const int g = t / P, n = t % P, par = g >> 2, ch = g & 3;
+    cpx<R> *dst = L + (level_offset(lp + 2) + 16 * c + g) * P + n;
+    cpx<R> acc = *dst;
+    for (int k = n; k < P; ++k) cmac(acc, sS[(ch * P + n) * P + k], sc[par][k]);
+    *dst = acc;
+  }
 }
 
 // ------------------------------------------------------------------ M2L (item 3)
@@ -166,21 +275,25 @@ __device__ __forceinline__ void m2l_accum(cpx<R> (&H)[P], const cpx<R> *__restri
   }
 }
 
+// warp-reduce H, scale by (-1)^n/n!, then store (add = 0) or accumulate (add = 1)
 template <typename R, int P>
-__device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__restrict__ out) {
+__device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__restrict__ out, int add) {
   R f = 1;
 #pragma unroll
   for (int n = 0; n < P; ++n) {
     if (n > 0) f = -f / R(n);
     R re = warp_sum(H[n].re), im = warp_sum(H[n].im);
-    if (lane == 0) out[n] = mk(f * re, f * im);
+    if (lane == 0) {
+      cpx<R> v = mk(f * re, f * im);
+      out[n] = add ? out[n] + v : v;
+    }
   }
 }
 
-// Volume targets: warp per (cell, rhs) over all cells of all levels; volume sources
-// from the M2L list and, when with_bnd, boundary sources from the volume-boundary list.
+// Volume targets: warp per (cell, rhs).  do_vol: volume sources from the M2L list;
+// do_bnd: boundary sources from the volume-boundary list; add: accumulate into L.
 template <typename R, int P>
-__global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, int with_bnd,
+__global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, int do_vol, int do_bnd, int add,
                           const int32_t *__restrict__ first, const int32_t *__restrict__ src,
                           const int32_t *__restrict__ bfirst, const int32_t *__restrict__ bsrc,
                           const cpx<R> *__restrict__ Mv, const cpx<R> *__restrict__ Mb,
@@ -200,14 +313,16 @@ __global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, in
   cpx<R> H[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) H[k] = mk<R>(0, 0);
-  const cpx<R> *M = Mv + (int64_t)rhs * ncell * P + level_offset(l) * P;
-  for (int e = first[gidx] + lane; e < first[gidx + 1]; e += 32) {
-    const uint32_t s = (uint32_t)src[e];
-    int sx, sy;
-    morton_decode(s, sx, sy);
-    m2l_accum<R, P>(H, M + (int64_t)s * P, mk<R>((R)(tx - sx), (R)(ty - sy)), lnrho);
+  if (do_vol) {
+    const cpx<R> *M = Mv + (int64_t)rhs * ncell * P + level_offset(l) * P;
+    for (int e = first[gidx] + lane; e < first[gidx + 1]; e += 32) {
+      const uint32_t s = (uint32_t)src[e];
+      int sx, sy;
+      morton_decode(s, sx, sy);
+      m2l_accum<R, P>(H, M + (int64_t)s * P, mk<R>((R)(tx - sx), (R)(ty - sy)), lnrho);
+    }
   }
-  if (with_bnd) {
+  if (do_bnd) {
     int64_t X, Y, sw;
     vol_geom(gd, l, c, X, Y, sw);
     X <<= gd.L;
@@ -222,7 +337,7 @@ __global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, in
                       mk<R>((R)((double)(X - BX) * scale), (R)((double)(Y - BY) * scale)), lnrho);
     }
   }
-  m2l_finish<R, P>(H, lane, Lv + (int64_t)rhs * ncell * P + gidx * P);
+  m2l_finish<R, P>(H, lane, Lv + (int64_t)rhs * ncell * P + gidx * P, add);
 }
 
 // Boundary targets (pass A): warp per (boundary cell, rhs); volume sources.
@@ -256,84 +371,7 @@ __global__ void k_m2l_bnd(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs,
     m2l_accum<R, P>(H, M + (int64_t)v * P,
                     mk<R>((R)((double)(BX - X) * scale), (R)((double)(BY - Y) * scale)), lnrho);
   }
-  m2l_finish<R, P>(H, lane, Lb + (int64_t)rhs * nbcell * P + gb * P);
-}
-
-// ------------------------------------------------------------------ L2L (item 4)
-// Lt_n(child) += 2^{-n} sum_{k=n}^{p-1} Lt_k(parent) w^{k-n} C(k, n),
-// w = (c_child - c_parent) / rho_P.
-template <typename R>
-__device__ __forceinline__ void l2l_add(int p, const cpx<R> *__restrict__ Lp, cpx<R> w,
-                                        cpx<R> *__restrict__ Lc) {
-  cpx<R> wp[MAXP], lp[MAXP];
-  wp[0] = mk<R>(1, 0);
-  for (int k = 1; k < p; ++k) wp[k] = wp[k - 1] * w;
-  for (int k = 0; k < p; ++k) lp[k] = Lp[k];
-  R two = 1;
-  for (int nn = 0; nn < p; ++nn) {
-    cpx<R> v = mk<R>(0, 0);
-    for (int k = nn; k < p; ++k) v = v + (R)c_binom[k][nn] * (lp[k] * wp[k - nn]);
-    Lc[nn] = Lc[nn] + two * v;
-    two *= R(0.5);
-  }
-}
-
-template <typename R>
-__global__ void k_l2l_vol(int l, int p, int64_t ncell, int nrhs, cpx<R> *__restrict__ Lv) {
-  const int64_t nc = int64_t(1) << (2 * (l + 1));
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * nrhs) return;
-  const int rhs = (int)(t / nc);
-  const int64_t cc = t % nc;
-  const int ch = (int)(cc & 3);
-  cpx<R> *Lx = Lv + (int64_t)rhs * ncell * p;
-  cpx<R> w = mk<R>((ch & 1) ? R(0.25) : R(-0.25), (ch & 2) ? R(0.25) : R(-0.25));
-  l2l_add<R>(p, Lx + (level_offset(l) + (cc >> 2)) * p, w, Lx + (level_offset(l + 1) + cc) * p);
-}
-
-__device__ __forceinline__ void side_dir(int side, double &ex, double &ey) {
-  ex = (side == 0) ? 1.0 : (side == 2 ? -1.0 : 0.0);
-  ey = (side == 1) ? 1.0 : (side == 3 ? -1.0 : 0.0);
-}
-// point at arclength t (node units) along side `side` of the boundary square [0, n+1]^2
-__device__ __forceinline__ void side_point(int side, double t, double np1, double &x, double &y) {
-  switch (side) {
-    case 0: x = t; y = 0; break;
-    case 1: x = np1; y = t; break;
-    case 2: x = np1 - t; y = np1; break;
-    default: x = 0; y = np1 - t; break;
-  }
-}
-
-// Along-side coordinate u and signed normal offset d of node coordinates (x, y): for an
-// element starting at arclength t_a, s1 = t_a - u and d = (x - a).n_outward (Sec. 4.3).
-__device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int &u, int &d) {
-  switch (side) {
-    case 0: u = x; d = -y; break;
-    case 1: u = y; d = x - np1; break;
-    case 2: u = np1 - x; d = y - np1; break;
-    default: u = np1 - y; d = -x; break;
-  }
-}
-
-// boundary child run at level l+1 from its parent at level l: w = (2j-1)(n+1)/(4n) e_side
-template <typename R>
-__global__ void k_l2l_bnd(int l, int n, int p, int64_t nbcell, int nrhs, cpx<R> *__restrict__ Lb) {
-  const int64_t nc = 4 * (int64_t(1) << (l + 1));
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * nrhs) return;
-  const int rhs = (int)(t / nc);
-  const int64_t id = t % nc;
-  const int side = (int)(id >> (l + 1));
-  const int64_t kc = id & ((int64_t(1) << (l + 1)) - 1);
-  const int j = (int)(kc & 1);
-  double ex, ey;
-  side_dir(side, ex, ey);
-  const double f = (2 * j - 1) * (n + 1.0) / (4.0 * n);
-  cpx<R> *Lx = Lb + (int64_t)rhs * nbcell * p;
-  const int64_t parent = ((int64_t)side << l) + (kc >> 1);
-  l2l_add<R>(p, Lx + (blevel_offset(l) + parent) * p, mk<R>((R)(f * ex), (R)(f * ey)),
-             Lx + (blevel_offset(l + 1) + id) * p);
+  m2l_finish<R, P>(H, lane, Lb + (int64_t)rhs * nbcell * P + gb * P, 0);
 }
 
 // ------------------------------------------------------------------ root constants
@@ -356,158 +394,149 @@ __global__ void k_root_const(int p, int64_t ncell, int64_t nbcell, int nrhs, dou
   }
 }
 
+// ------------------------------------------------------------------ boundary geometry
+__device__ __forceinline__ void side_dir(int side, double &ex, double &ey) {
+  ex = (side == 0) ? 1.0 : (side == 2 ? -1.0 : 0.0);
+  ey = (side == 1) ? 1.0 : (side == 3 ? -1.0 : 0.0);
+}
+
+// Along-side coordinate u and signed normal offset d of node coordinates (x, y): for an
+// element starting at arclength t_a, s1 = t_a - u and d = (x - a).n_outward (Sec. 4.3).
+__device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int &u, int &d) {
+  switch (side) {
+    case 0: u = x; d = -y; break;
+    case 1: u = y; d = x - np1; break;
+    case 2: u = np1 - x; d = y - np1; break;
+    default: u = np1 - y; d = -x; break;
+  }
+}
+
+// Boundary trees, one block per side: P2M of each leaf run from its element densities
+// (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run,
+// with a barrier between levels.
+template <typename R, int P>
+__global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, Mats<R> mt,
+                                                 cpx<R> *__restrict__ Mb) {
+  const int side = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L;
+  cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
+  const int nleafrun = 1 << L;
+  for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
+    const int k = t / P, nn = t % P;
+    const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
+    const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+    cpx<R> acc = mk<R>(0, 0);
+    for (int e = 0; e < m; ++e) {
+      const R qe = (R)(qr[e] * g.h);
+      acc.re = fma(qe, B[e * P].re, acc.re);
+      acc.im = fma(qe, B[e * P].im, acc.im);
+    }
+    M[(blevel_offset(L) + ((int64_t)side << L) + k) * P + nn] = acc;
+  }
+  __syncthreads();
+  for (int l = L - 1; l >= 0; --l) {
+    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) {
+      const int k = t / P, nn = t % P;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int j = 0; j < 2; ++j) {
+        const cpx<R> *Mc = M + (blevel_offset(l + 1) + ((int64_t)side << (l + 1)) + 2 * k + j) * P;
+        const cpx<R> *T = mt.bm2m + ((side * 2 + j) * P + nn) * P;
+        for (int kk = 0; kk <= nn; ++kk) cmac(acc, T[kk], Mc[kk]);
+      }
+      M[(blevel_offset(l) + ((int64_t)side << l) + k) * P + nn] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ collocation points
 // (V r)(y_m) = -(1/2pi)[ Re sum_n Lt_n zt^n  +  sum_{near nodes} w_j ln|y_m - x_j| ].
-// Warp per (boundary leaf, rhs); m <= 16 collocation points per leaf.
+// Warp per (collocation point, rhs); requires L < 32.
 template <typename R>
 __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<R> *__restrict__ Lb,
                          const int32_t *__restrict__ pfirst, const int32_t *__restrict__ psrc,
                          double *__restrict__ vcol) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= g.nbleaf * nrhs) return;
-  const int rhs = (int)(wid / g.nbleaf);
-  const int64_t bl = wid % g.nbleaf;
+  if (wid >= (int64_t)g.NG * nrhs) return;
+  const int rhs = (int)(wid / g.NG);
+  const int ge = (int)(wid % g.NG);
   const int n = g.n, m = g.m, L = g.L, p = g.p;
-  const int side = (int)(bl >> L);
-  const int64_t kk = bl & ((int64_t(1) << L) - 1);
-  const double ell = (n + 1.0) / n;
-  double ex, ey;
-  side_dir(side, ex, ey);
+  const int side = ge / n, along = ge % n;
+  const int64_t bl = ((int64_t)side << L) + along / m;
   const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
-  R acc[16];
-#pragma unroll
-  for (int e = 0; e < 16; ++e) acc[e] = 0;
   const R inv2n = R(1) / (R)(2 * n);
+  const int64_t numc = (2 * (int64_t)along + 1) * (n + 1);
+  R acc = 0;
   for (int e0 = pfirst[bl]; e0 < pfirst[bl + 1]; ++e0) {
     int a, b;
     morton_decode((uint32_t)psrc[e0], a, b);
     for (int t = lane; t < m * m; t += 32) {
       const int i = a * m + t % m, j = b * m + t / m;
-      const R w = W[(int64_t)(j + g.pad) * g.npad + i + g.pad];
       int u, d;
       side_coords(side, n + 1, i + 1, j + 1, u, d);
-      const R dd = (R)d * (R)d;
-#pragma unroll
-      for (int e = 0; e < 16; ++e)
-        if (e < m) {
-          // (y_e - x) along the side = ((2(k m + e) + 1)(n + 1) - 2 u n) / (2n), exact numerator
-          const int64_t num = (2 * (kk * m + e) + 1) * (int64_t)(n + 1) - 2 * (int64_t)u * n;
-          const R ds = (R)num * inv2n;
-          acc[e] += w * (R(0.5) * dev_log<R>(ds * ds + dd));
-        }
+      // (y_e - x) along the side = ((2 along + 1)(n + 1) - 2 u n) / (2n), exact numerator
+      const R ds = (R)(numc - 2 * (int64_t)u * n) * inv2n;
+      acc += W[(int64_t)(j + g.pad) * g.npad + i + g.pad] * (R(0.5) * dev_log<R>(ds * ds + (R)d * (R)d));
     }
   }
-  const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(L) + bl) * p;
-#pragma unroll
-  for (int e = 0; e < 16; ++e)
-    if (e < m) {
-      R s = warp_sum(acc[e]);
-      if (lane == e) {
-        const double off = (e + 0.5 - 0.5 * m) * ell / m;  // (y_e - c) / rho_L along the side
-        cpx<R> z = mk<R>((R)(off * ex), (R)(off * ey)), v = mk<R>(0, 0);
-        for (int k = p - 1; k >= 0; --k) v = v * z + Lc[k];
-        vcol[(int64_t)rhs * g.NG + side * n + kk * m + e] = -((double)s + (double)v.re) / (2.0 * PI);
-      }
-    }
+  acc = warp_sum(acc);
+  // far field: the local expansion of every ancestor run evaluated at y (L2L re-centring
+  // is exact, so this equals pushing the locals down to the leaf run and evaluating there)
+  R far = 0;
+  if (lane <= L) {
+    const int l = lane, nl = n >> l;
+    const int64_t id = ((int64_t)side << l) + along / nl;
+    const double off = ((n + 1.0) / n) * ((along % nl) + 0.5 - 0.5 * nl) / nl;
+    double ex, ey;
+    side_dir(side, ex, ey);
+    const cpx<R> z = mk<R>((R)(off * ex), (R)(off * ey));
+    const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
+    cpx<R> v = mk<R>(0, 0);
+    for (int kk = p - 1; kk >= 0; --kk) v = v * z + Lc[kk];
+    far = v.re;
+  }
+  far = warp_sum(far);
+  if (lane == 0) vcol[(int64_t)rhs * g.NG + ge] = -((double)acc + (double)far) / (2.0 * PI);
 }
 
 // ------------------------------------------------------------------ BEM solve (FP64)
-// q = -S^{-1} (V r)|_Gamma with the inverse formed at set-up.  Warp per (row, rhs).
-__global__ void k_bem_gemv(int NG, int nrhs, const double *__restrict__ Sinv,
-                           const double *__restrict__ vcol, double *__restrict__ q) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= (int64_t)NG * nrhs) return;
-  const int row = (int)(wid % NG), rhs = (int)(wid / NG);
-  const double *S = Sinv + (int64_t)row * NG;
-  const double *v = vcol + (int64_t)rhs * NG;
-  double acc = 0.0;
-  for (int k = lane; k < NG; k += 32) acc = fma(S[k], v[k], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) q[(int64_t)rhs * NG + row] = -acc;
-}
-
-// ------------------------------------------------------------------ boundary P2M / M2M
-// Element e of a leaf run: density q_e (physical) -> qt = q_e h per node-unit length.
-// About its midpoint: Mt_0 = qt rho 2a, Mt_k = -qt rho 2 e^k a^{k+1} / (k (k+1)) for even
-// k (0 for odd), a = half-length / rho; shifted to the run centre by the M2M formula at
-// equal scale (w = (y_e - c) / rho, no 2^{-k}).
-template <typename R>
-__global__ void k_p2m_bnd(Geo g, int nrhs, const double *__restrict__ q, cpx<R> *__restrict__ Mb) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nbleaf * nrhs) return;
-  const int rhs = (int)(t / g.nbleaf);
-  const int64_t bl = t % g.nbleaf;
-  const int n = g.n, m = g.m, L = g.L, p = g.p;
-  const int side = (int)(bl >> L);
-  const int64_t kk = bl & ((int64_t(1) << L) - 1);
-  double ex, ey;
-  side_dir(side, ex, ey);
-  const double ell = (n + 1.0) / n, rho = m, a = ell / (2.0 * rho);
-  const cpx<R> es = mk<R>((R)ex, (R)ey);
-  cpx<R> acc[MAXP], el[MAXP], wp[MAXP];
-  for (int k = 0; k < p; ++k) acc[k] = mk<R>(0, 0);
-  for (int e = 0; e < m; ++e) {
-    const double qr = q[(int64_t)rhs * g.NG + side * n + kk * m + e] * g.h * rho;
-    el[0] = mk<R>((R)(qr * 2.0 * a), 0);
-    cpx<R> ep = mk<R>(1, 0);
-    double ak = a;
-    for (int k = 1; k < p; ++k) {
-      ep = ep * es;
-      ak *= a;  // a^{k+1}
-      el[k] = (k % 2 == 0) ? (R)(-qr * 2.0 * ak / (k * (k + 1.0))) * ep : mk<R>(0, 0);
-    }
-    const double off = (e + 0.5 - 0.5 * m) * ell / rho;
-    const cpx<R> w = mk<R>((R)(off * ex), (R)(off * ey));
-    wp[0] = mk<R>(1, 0);
-    for (int k = 1; k < p; ++k) wp[k] = wp[k - 1] * w;
-    acc[0] = acc[0] + el[0];
-    for (int nn = 1; nn < p; ++nn) {
-      cpx<R> v = (R(-1) / nn) * (el[0] * wp[nn]);
-      for (int k = 1; k <= nn; ++k) v = v + (R)c_binom[nn - 1][k - 1] * (el[k] * wp[nn - k]);
-      acc[nn] = acc[nn] + v;
-    }
-  }
-  cpx<R> *out = Mb + (int64_t)rhs * g.nbcell * p + (blevel_offset(L) + bl) * p;
-  for (int k = 0; k < p; ++k) out[k] = acc[k];
-}
-
-template <typename R>
-__global__ void k_m2m_bnd(int l, int n, int p, int64_t nbcell, int nrhs, cpx<R> *__restrict__ Mb) {
-  const int64_t nc = 4 * (int64_t(1) << l);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * nrhs) return;
-  const int rhs = (int)(t / nc);
-  const int64_t id = t % nc;
-  const int side = (int)(id >> l);
-  const int64_t k = id & ((int64_t(1) << l) - 1);
-  double ex, ey;
-  side_dir(side, ex, ey);
-  cpx<R> *M = Mb + (int64_t)rhs * nbcell * p;
-  cpx<R> acc[MAXP], wp[MAXP], mc[MAXP];
-  for (int q = 0; q < p; ++q) acc[q] = mk<R>(0, 0);
-  for (int j = 0; j < 2; ++j) {
-    const int64_t child = ((int64_t)side << (l + 1)) + 2 * k + j;
-    const cpx<R> *Mc = M + (blevel_offset(l + 1) + child) * p;
-    const double f = (2 * j - 1) * (n + 1.0) / (4.0 * n);
-    const cpx<R> w = mk<R>((R)(f * ex), (R)(f * ey));
-    wp[0] = mk<R>(1, 0);
-    for (int q = 1; q < p; ++q) wp[q] = wp[q - 1] * w;
-    for (int q = 0; q < p; ++q) mc[q] = Mc[q];
-    acc[0] = acc[0] + mc[0];
-    for (int nn = 1; nn < p; ++nn) {
-      cpx<R> v = (R(-1) / nn) * (mc[0] * wp[nn]);
-      R two = 1;
-      for (int q = 1; q <= nn; ++q) {
-        two *= R(0.5);
-        v = v + (two * (R)c_binom[nn - 1][q - 1]) * (mc[q] * wp[nn - q]);
+// q = -S^{-1} (V r)|_Gamma with the inverse formed at set-up.  Rotating the square by 90
+// degrees maps element (side s, index k) to (s+1, k), so S and its inverse are block
+// circulant in the four sides: S^{-1}[(s,m),(t,k)] = B[m][((t - s) mod 4) n + k], with B
+// its first block row (n x 4n).  Block per m: each entry of B is read once and serves the
+// four outputs q[(s, m)], s = 0..3.  One right-hand side at a time, staged in shared memory.
+__global__ void __launch_bounds__(256) k_bem_apply(int n, int nrhs, const double *__restrict__ B,
+                                                   const double *__restrict__ vcol, double *__restrict__ q) {
+  extern __shared__ double sv[];  // 4n values of one right-hand side
+  __shared__ double red[8][4];
+  const int mrow = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int NG = 4 * n;
+  const double *Brow = B + (int64_t)mrow * NG;
+  for (int rr = 0; rr < nrhs; ++rr) {
+    for (int i = tid; i < NG; i += 256) sv[i] = vcol[(int64_t)rr * NG + i];
+    __syncthreads();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      for (int k = tid; k < n; k += 256) {
+        const double bv = Brow[j * n + k];
+#pragma unroll
+        for (int sg = 0; sg < 4; ++sg) acc[sg] = fma(bv, sv[((sg + j) & 3) * n + k], acc[sg]);
       }
-      acc[nn] = acc[nn] + v;
+#pragma unroll
+    for (int sg = 0; sg < 4; ++sg) {
+      const double v = warp_sum(acc[sg]);
+      if (lane == 0) red[w][sg] = v;
     }
+    __syncthreads();
+    if (tid < 4) {
+      double t = 0.0;
+      for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
+      q[(int64_t)rr * NG + tid * n + mrow] = -t;
+    }
+    __syncthreads();
   }
-  cpx<R> *out = M + (blevel_offset(l) + id) * p;
-  for (int q = 0; q < p; ++q) out[q] = acc[q];
 }
 
 // ------------------------------------------------------------------ near boundary field
@@ -523,59 +552,58 @@ __device__ __forceinline__ R seg_log_int(R s1, R ell, R d) {
   return v;
 }
 
-// Warp per (volume leaf next to the boundary, rhs): phib = sum_k qt_k int_k ln|x - y| ds.
+// Block of 256 per (volume leaf next to the boundary, rhs): each thread takes one node and
+// a strided share of the element list; partial sums meet in shared memory.
 template <typename R>
-__global__ void k_bnd_near(Geo g, int64_t nbnear, int nrhs, const int32_t *__restrict__ leaf,
-                           const int32_t *__restrict__ first, const int32_t *__restrict__ src,
-                           const double *__restrict__ q, R *__restrict__ phib) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= nbnear * nrhs) return;
-  const int rhs = (int)(wid / nbnear);
-  const int64_t slot = wid % nbnear;
-  const int n = g.n, m = g.m, L = g.L;
+__global__ void __launch_bounds__(256) k_bnd_near(Geo g, int64_t nbnear, int nrhs, const int32_t *__restrict__ leaf,
+                                                  const int32_t *__restrict__ first, const int32_t *__restrict__ src,
+                                                  const double *__restrict__ q, R *__restrict__ phib) {
+  __shared__ R red[256];
+  const int slot = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L, mm = m * m;
+  const int ngrp = blockDim.x / mm;
+  const int t = threadIdx.x % mm, grp = threadIdx.x / mm;
   int a, b;
   morton_decode((uint32_t)leaf[slot], a, b);
   const R ell = (R)((n + 1.0) / n), invn = R(1) / (R)n, hR = (R)g.h;
   const double *qr = q + (int64_t)rhs * g.NG;
-  for (int t = lane; t < m * m; t += 32) {
-    const int x = a * m + t % m + 1, y = b * m + t / m + 1;
-    R acc = 0;
-    for (int e0 = first[slot]; e0 < first[slot + 1]; ++e0) {
-      const int bl = src[e0];
+  const int x = a * m + t % m + 1, y = b * m + t / m + 1;
+  const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
+  R acc = 0;
+  if (grp < ngrp)
+    for (int idx = grp; idx < cnt; idx += ngrp) {
+      const int bl = src[f0 + idx / m], e = idx % m;
       const int side = bl >> L;
       const int64_t kk = bl & ((int64_t(1) << L) - 1);
       int u, d;
       side_coords(side, n + 1, x, y, u, d);
-      for (int e = 0; e < m; ++e) {
-        // s1 = t_a - u with t_a = (k m + e)(n + 1)/n: exact integer numerator over n
-        const int64_t num = (kk * m + e) * (int64_t)(n + 1) - (int64_t)u * n;
-        const R qt = (R)qr[side * n + kk * m + e] * hR;
-        acc += qt * seg_log_int<R>((R)num * invn, ell, (R)d);
-      }
+      // s1 = t_a - u with t_a = (k m + e)(n + 1)/n: exact integer numerator over n
+      const int64_t num = (kk * m + e) * (int64_t)(n + 1) - (int64_t)u * n;
+      acc += (R)qr[side * n + kk * m + e] * hR * seg_log_int<R>((R)num * invn, ell, (R)d);
     }
-    phib[((int64_t)rhs * nbnear + slot) * m * m + t] = acc;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < mm) {
+    R s = 0;
+    for (int q2 = 0; q2 < ngrp; ++q2) s += red[q2 * mm + threadIdx.x];
+    phib[((int64_t)rhs * nbnear + slot) * mm + threadIdx.x] = s;
   }
 }
 
-// ------------------------------------------------------------------ near field + L2P + sum
+// ------------------------------------------------------------------ near field (P2P)
 // One CTA per tile of TX x TY leaves, one thread per (leaf, row of m targets).  The
 // weight image of the tile and its halo of R leaves, and the table of ln|d| over the
-// stencil's node offsets, are staged in shared memory.  For every stencil row oy and
-// source row sy a thread slides along the contiguous run of source leaves: per source
-// leaf it loads the m weights of the row and the 2m-1 table values of the window and does
-// m x m FMAs; partial sums are folded into Kahan-compensated accumulators (Sec. 7.1).
+// stencil's node offsets (rows |dy| only: the table is even in dy), are staged in shared
+// memory.  For every stencil row oy and source row sy a thread slides along the
+// contiguous run of source leaves: per source leaf it loads the m weights of the row and
+// the 2m-1 table values of the window and does m x m FMAs.  The sum over a stencil row is
+// folded into Kahan-compensated accumulators (Sec. 7.1).  out = -near / (2 pi).
 template <typename R>
 struct P2PArgs {
   const R *wpad;
   const R *table;
-  const cpx<R> *Lv;
-  const R *phib;
-  const int32_t *bslot;
   double *out;
-  int n, npad, L, p, R_, Rn, HX, HY, TS, c0, tile_x, tile_y, nrhs;
-  int64_t ncell, nbnear;
-  int do_near, do_far, do_bnd;
+  int n, npad, L, R_, Rn, HX, HY, TS, c0, tile_x, tile_y, nrhs;
   Stencil st;
 };
 
@@ -596,14 +624,14 @@ __device__ __forceinline__ void lds_vec(const R *__restrict__ p, R (&v)[K]) {
 }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(256) k_p2p_final(P2PArgs<R> A) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_p2p(P2PArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *halo = reinterpret_cast<R *>(smem_raw);
   R *tab = halo + (int64_t)A.HY * A.HX;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rhs = blockIdx.z;
   const int lx0 = blockIdx.x * A.tile_x, ly0 = blockIdx.y * A.tile_y;
-  if (A.do_near) {
+  {
     const R *W = A.wpad + (int64_t)rhs * A.npad * A.npad;
     constexpr int VW = 16 / sizeof(R);
     const int vx = A.HX / VW;
@@ -616,7 +644,7 @@ __global__ void __launch_bounds__(256) k_p2p_final(P2PArgs<R> A) {
       else
         *reinterpret_cast<double2 *>(dst) = *reinterpret_cast<const double2 *>(src);
     }
-    const int tv = (2 * A.Rn + 1) * A.TS / VW;
+    const int tv = (A.Rn + 1) * A.TS / VW;
     for (int idx = tid; idx < tv; idx += nthr) {
       if constexpr (sizeof(R) == 4)
         reinterpret_cast<float4 *>(tab)[idx] = reinterpret_cast<const float4 *>(A.table)[idx];
@@ -630,67 +658,98 @@ __global__ void __launch_bounds__(256) k_p2p_final(P2PArgs<R> A) {
   R sum[M], comp[M];
 #pragma unroll
   for (int t = 0; t < M; ++t) sum[t] = comp[t] = 0;
-  if (A.do_near) {
-    const int Rr = A.R_;
-    for (int oy = -Rr; oy <= Rr; ++oy) {
-      const int ox0 = A.st.ox0[oy + Rr], ox1 = A.st.ox1[oy + Rr];
-      if (ox0 > ox1) continue;
-      for (int sy = 0; sy < M; ++sy) {
-        const R *hrow = halo + ((lyl + Rr + oy) * M + sy) * A.HX + (lxl + Rr) * M;
-        const R *trow = tab + (-oy * M + ty - sy + A.Rn) * A.TS + A.c0 + A.Rn - (M - 1);
-        R part[M];
+  const int Rr = A.R_;
+  for (int oy = -Rr; oy <= Rr; ++oy) {
+    const int ox0 = A.st.ox0[oy + Rr], ox1 = A.st.ox1[oy + Rr];
+    if (ox0 > ox1) continue;
+    R part[M];
 #pragma unroll
-        for (int t = 0; t < M; ++t) part[t] = 0;
-        for (int c = ox0; c <= ox1; ++c) {
-          R w[M], tw[2 * M];
-          lds_vec<R, M>(hrow + c * M, w);
-          lds_vec<R, 2 * M>(trow - c * M, tw);
+    for (int t = 0; t < M; ++t) part[t] = 0;
+    for (int sy = 0; sy < M; ++sy) {
+      const R *hrow = halo + ((lyl + Rr + oy) * M + sy) * A.HX + (lxl + Rr) * M;
+      const int dy = -oy * M + ty - sy;
+      const R *trow = tab + (dy < 0 ? -dy : dy) * A.TS + A.c0 + A.Rn - (M - 1);
+      for (int c = ox0; c <= ox1; ++c) {
+        R w[M], tw[2 * M];
+        lds_vec<R, M>(hrow + c * M, w);
+        lds_vec<R, 2 * M>(trow - c * M, tw);
 #pragma unroll
-          for (int tx = 0; tx < M; ++tx)
+        for (int tx = 0; tx < M; ++tx)
 #pragma unroll
-            for (int sx = 0; sx < M; ++sx) part[tx] = fma(w[sx], tw[tx - sx + M - 1], part[tx]);
-        }
-#pragma unroll
-        for (int t = 0; t < M; ++t) {  // Kahan
-          const R y = part[t] - comp[t];
-          const R s = sum[t] + y;
-          comp[t] = (s - sum[t]) - y;
-          sum[t] = s;
-        }
+          for (int sx = 0; sx < M; ++sx) part[tx] = fma(w[sx], tw[tx - sx + M - 1], part[tx]);
       }
+    }
+#pragma unroll
+    for (int t = 0; t < M; ++t) {  // Kahan
+      const R y = part[t] - comp[t];
+      const R s = sum[t] + y;
+      comp[t] = (s - sum[t]) - y;
+      sum[t] = s;
     }
   }
   const int gx = lx0 + lxl, gy = ly0 + lyl;
-  const uint32_t leafc = morton_encode((uint32_t)gx, (uint32_t)gy);
-  R far[M];
-#pragma unroll
-  for (int t = 0; t < M; ++t) far[t] = 0;
-  if (A.do_far) {
-    const cpx<R> *Lc = A.Lv + (int64_t)rhs * A.ncell * A.p + (level_offset(A.L) + leafc) * A.p;
-    const R zy = (ty - R(0.5) * (M - 1)) / M;
-    cpx<R> acc[M];
-#pragma unroll
-    for (int t = 0; t < M; ++t) acc[t] = mk<R>(0, 0);
-    for (int k = A.p - 1; k >= 0; --k) {
-      const cpx<R> Lk = Lc[k];
-#pragma unroll
-      for (int t = 0; t < M; ++t) acc[t] = acc[t] * mk<R>((t - R(0.5) * (M - 1)) / M, zy) + Lk;
-    }
-#pragma unroll
-    for (int t = 0; t < M; ++t) far[t] = acc[t].re;
-  }
-  const R *pb = nullptr;
-  if (A.do_bnd) {
-    const int slot = A.bslot[leafc];
-    if (slot >= 0) pb = A.phib + ((int64_t)rhs * A.nbnear + slot) * M * M + ty * M;
-  }
   double *o = A.out + (int64_t)rhs * A.n * A.n + (int64_t)(gy * M + ty) * A.n + gx * M;
 #pragma unroll
-  for (int t = 0; t < M; ++t) {
-    double v = ((double)sum[t] - (double)comp[t]) + (double)far[t];
-    if (pb) v += (double)pb[t];
-    o[t] = -v / (2.0 * PI);
+  for (int t = 0; t < M; ++t) o[t] = -((double)sum[t] - (double)comp[t]) / (2.0 * PI);
+}
+
+// z += -(1/2pi) (L2P of the leaf local expansion + near-boundary element integrals).
+// Thread per (leaf, row of m targets, rhs).
+template <typename R, int M>
+__global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, int nrhs, int do_bnd,
+                            const cpx<R> *__restrict__ Lv, const R *__restrict__ phib,
+                            const int32_t *__restrict__ bslot, double *__restrict__ out) {
+  const int64_t nleaf = int64_t(1) << (2 * L);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nleaf * M * nrhs) return;
+  const int ty = (int)(t % M);
+  const int64_t rest = t / M, leafc = rest % nleaf;
+  const int rhs = (int)(rest / nleaf);
+  int gx, gy;
+  morton_decode((uint32_t)leafc, gx, gy);
+  const cpx<R> *Lc = Lv + (int64_t)rhs * ncell * p + (level_offset(L) + leafc) * p;
+  const R zy = (ty - R(0.5) * (M - 1)) / M;
+  cpx<R> acc[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) acc[q] = mk<R>(0, 0);
+  for (int k = p - 1; k >= 0; --k) {
+    const cpx<R> Lk = Lc[k];
+#pragma unroll
+    for (int q = 0; q < M; ++q) acc[q] = acc[q] * mk<R>((q - R(0.5) * (M - 1)) / M, zy) + Lk;
   }
+  const R *pb = nullptr;
+  if (do_bnd) {
+    const int slot = bslot[leafc];
+    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M;
+  }
+  double *o = out + (int64_t)rhs * n * n + (int64_t)(gy * M + ty) * n + gx * M;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    double v = (double)acc[q].re;
+    if (pb) v += (double)pb[q];
+    o[q] += -v / (2.0 * PI);
+  }
+}
+
+// P2M for trees with L < 2 (n <= 2 m): warp per leaf in one block.
+template <typename R, int P>
+__global__ void k_p2m_small(Geo g, int nrhs, const R *__restrict__ wpad, cpx<R> *__restrict__ Mv) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nw = g.nleaf * nrhs;
+  for (int64_t wi = w; wi < nw; wi += blockDim.x / 32) {
+    const int rhs = (int)(wi / g.nleaf);
+    const uint32_t c = (uint32_t)(wi % g.nleaf);
+    cpx<R> acc[P];
+    p2m_warp<R, P>(wpad + (int64_t)rhs * g.npad * g.npad, g.npad, g.pad, g.m, c, lane, acc);
+    if (lane == 0)
+      for (int k = 0; k < P; ++k) Mv[(int64_t)rhs * g.ncell * P + (level_offset(g.L) + c) * P + k] = acc[k];
+  }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename R, int M>
+size_t p2p_smem(const P2PArgs<R> &a) {
+  return ((size_t)a.HY * a.HX + (size_t)(a.Rn + 1) * a.TS) * sizeof(R);
 }
 
 template <typename R, int M>
@@ -698,69 +757,155 @@ void launch_p2p(int L, const P2PArgs<R> &a, cudaStream_t s) {
   const int side = 1 << L;
   dim3 grid(side / a.tile_x, side / a.tile_y, a.nrhs);
   const int threads = a.tile_x * a.tile_y * M;
-  const size_t smem = ((size_t)a.HY * a.HX + (size_t)(2 * a.Rn + 1) * a.TS) * sizeof(R);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    FMMPC_CUDA(cudaFuncSetAttribute(k_p2p_final<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-    configured = smem;
-  }
-  k_p2p_final<R, M><<<grid, threads, smem, s>>>(a);
+  k_p2p<R, M><<<grid, threads, p2p_smem<R, M>(a), s>>>(a);
   FMMPC_LAUNCH_CHECK();
 }
 
-template <typename R, int P>
-void launch_m2l_vol(fmmpc_handle &H, int nrhs, int with_bnd, cudaStream_t s) {
-  const Geo &g = H.g;
-  GeoDev gd{g.n, g.L, g.tnum, g.tden};
-  k_m2l_vol<R, P><<<nblk(g.ncell * nrhs * 32), 256, 0, s>>>(
-      gd, g.ncell, g.nbcell, nrhs, with_bnd, H.lists.m2l_first, H.lists.m2l_src, H.lists.vbv_first,
-      H.lists.vbv_src, (const cpx<R> *)H.fb.Mv, (const cpx<R> *)H.fb.Mb, (cpx<R> *)H.fb.Lv);
-  FMMPC_LAUNCH_CHECK();
+// Kernels that need more than 48 KB of dynamic shared memory: raise their limit once, at
+// set-up (the attribute is per function), to the per-block maximum minus static use.
+template <typename K>
+void raise_smem_limit(K kernel) {
+  cudaFuncAttributes fa{};
+  FMMPC_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  int dev = 0, optin = 0;
+  FMMPC_CUDA(cudaGetDevice(&dev));
+  FMMPC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  FMMPC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
 }
-
-template <typename R, int P>
-void launch_m2l_bnd(fmmpc_handle &H, int nrhs, cudaStream_t s) {
-  const Geo &g = H.g;
-  GeoDev gd{g.n, g.L, g.tnum, g.tden};
-  k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(
-      gd, g.ncell, g.nbcell, nrhs, H.lists.vbb_first, H.lists.vbb_src, (const cpx<R> *)H.fb.Mv,
-      (cpx<R> *)H.fb.Lb);
-  FMMPC_LAUNCH_CHECK();
-}
-
-#define FMMPC_DISPATCH_P(p, CALL) \
-  switch (p) {                     \
-    case 4: CALL(4); break;        \
-    case 6: CALL(6); break;        \
-    case 8: CALL(8); break;        \
-    case 10: CALL(10); break;      \
-    case 12: CALL(12); break;      \
-    case 16: CALL(16); break;      \
-    default: throw Error(FMMPC_ERR_UNSUPPORTED, "expansion order p must be one of 4, 6, 8, 10, 12, 16"); \
-  }
 
 template <typename R>
+void set_p2p_smem_limit() {
+  raise_smem_limit(k_p2p<R, 4>);
+  raise_smem_limit(k_p2p<R, 8>);
+  raise_smem_limit(k_p2p<R, 16>);
+  raise_smem_limit(k_bem_apply);
+}
+
+template <typename R>
+void run_p2p(fmmpc_handle &H, const void *table, double *out, int nrhs, cudaStream_t s) {
+  const Geo &g = H.g;
+  P2PArgs<R> a{};
+  a.wpad = (const R *)H.fb.wpad;
+  a.table = (const R *)table;
+  a.out = out;
+  a.n = g.n; a.npad = g.npad; a.L = g.L; a.R_ = g.R; a.Rn = H.fb.Rn;
+  a.HX = (H.tile_x + 2 * g.R) * g.m;
+  a.HY = (H.tile_y + 2 * g.R) * g.m;
+  a.TS = H.fb.table_stride; a.c0 = H.fb.table_c0;
+  a.tile_x = H.tile_x; a.tile_y = H.tile_y; a.nrhs = nrhs;
+  a.st = H.st;
+  switch (g.m) {
+    case 4: launch_p2p<R, 4>(g.L, a, s); break;
+    case 8: launch_p2p<R, 8>(g.L, a, s); break;
+    case 16: launch_p2p<R, 16>(g.L, a, s); break;
+    default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
+  }
+}
+
+template <typename R>
+void run_far_final(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s) {
+  const Geo &g = H.g;
+  const int64_t tasks = g.nleaf * g.m * nrhs;
+  const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
+  const R *pb = (const R *)H.fb.phib;
+  switch (g.m) {
+    case 4: k_far_final<R, 4><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
+    case 8: k_far_final<R, 8><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
+    default: k_far_final<R, 16><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
+  }
+  FMMPC_LAUNCH_CHECK();
+}
+
+template <typename R>
+Mats<R> mats_of(fmmpc_handle &H) {
+  const int P = H.g.p;
+  const cpx<R> *base = (const cpx<R> *)H.fb.mats;
+  Mats<R> mt;
+  mt.vm2m = base;
+  mt.vl2l = base + 4 * P * P;
+  mt.bm2m = base + 8 * P * P;
+  mt.bp2m = base + 16 * P * P;
+  return mt;
+}
+
+// Upward pass of the volume tree: P2M fused with two M2M levels, then two M2M levels per
+// launch (one for a last odd level).
+template <typename R, int P>
+int run_upward(fmmpc_handle &H, int nrhs, cudaStream_t s) {
+  const Geo &g = H.g;
+  const R *wpad = (const R *)H.fb.wpad;
+  cpx<R> *Mv = (cpx<R> *)H.fb.Mv;
+  Mats<R> mt = mats_of<R>(H);
+  int launches = 0;
+  int lc;  // level whose cells are complete
+  if (g.L >= 2) {
+    k_upward_fused<R, P><<<dim3((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs), 512, 0, s>>>(g, wpad, mt.vm2m, Mv);
+    lc = g.L - 2;
+  } else {
+    k_p2m_small<R, P><<<1, 256, 0, s>>>(g, nrhs, wpad, Mv);
+    lc = g.L;
+  }
+  ++launches;
+  FMMPC_LAUNCH_CHECK();
+  while (lc >= 2) {
+    k_m2m_2levels<R, P><<<dim3((unsigned)(int64_t(1) << (2 * (lc - 2))), nrhs), 256, 0, s>>>(lc, g.ncell, mt.vm2m, Mv);
+    lc -= 2;
+    ++launches;
+  }
+  if (lc == 1) {
+    k_m2m_levels<R, P><<<1, 256, 0, s>>>(0, 0, g.ncell, nrhs, mt.vm2m, Mv);
+    ++launches;
+  }
+  FMMPC_LAUNCH_CHECK();
+  return launches;
+}
+
+// Downward pass: two L2L levels per launch from the root (one for a last odd level).
+template <typename R, int P>
+int run_l2l(fmmpc_handle &H, int nrhs, cudaStream_t s) {
+  const Geo &g = H.g;
+  cpx<R> *Lv = (cpx<R> *)H.fb.Lv;
+  Mats<R> mt = mats_of<R>(H);
+  int launches = 0;
+  int lp = 0;
+  while (lp + 2 <= g.L) {
+    k_l2l_2levels<R, P><<<dim3((unsigned)(int64_t(1) << (2 * lp)), nrhs), 256, 0, s>>>(lp, g.ncell, mt.vl2l, Lv);
+    lp += 2;
+    ++launches;
+  }
+  if (lp < g.L) {
+    const int64_t tasks = (int64_t(1) << (2 * (lp + 1))) * P * nrhs;
+    k_l2l_levels<R, P><<<nblk(tasks), 256, 0, s>>>(lp, lp + 1, g.ncell, nrhs, mt.vl2l, Lv);
+    ++launches;
+  }
+  FMMPC_LAUNCH_CHECK();
+  return launches;
+}
+
+template <typename R, int P>
 void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
   const Geo &g = H.g;
   const Lists &Ls = H.lists;
   cudaStream_t s = H.stream;
+  GeoDev gd{g.n, g.L, g.tnum, g.tden};
   R *wpad = (R *)H.fb.wpad;
   cpx<R> *Mv = (cpx<R> *)H.fb.Mv, *Lv = (cpx<R> *)H.fb.Lv;
   cpx<R> *Mb = (cpx<R> *)H.fb.Mb, *Lb = (cpx<R> *)H.fb.Lb;
+  Mats<R> mt = mats_of<R>(H);
   int64_t launches = 0;
   const int64_t N = (int64_t)g.n * g.n;
   // stage marks: event k opens stage k; a stage that does not run keeps stage_hit = false
   int cur = -1;
   auto mark = [&](int stage) {
     if (!H.timing) return;
-    FMMPC_CUDA(cudaEventRecord(H.ev[stage], s));
+    // external record nodes keep the events timeable when the apply is captured in a graph
+    FMMPC_CUDA(cudaEventRecordWithFlags(H.ev[stage], s, cudaEventRecordExternal));
     if (cur >= 0) H.stage_hit[cur] = true;
     cur = stage;
   };
   auto mark_end = [&]() {
     if (!H.timing) return;
-    FMMPC_CUDA(cudaEventRecord(H.ev[fmmpc_handle::NSTAGE], s));
+    FMMPC_CUDA(cudaEventRecordWithFlags(H.ev[fmmpc_handle::NSTAGE], s, cudaEventRecordExternal));
     if (cur >= 0) H.stage_hit[cur] = true;
   };
   if (H.timing)
@@ -769,33 +914,25 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   k_weights<R><<<nblk(N * nrhs), 256, 0, s>>>(g.n, g.npad, g.pad, g.h * g.h, N * nrhs, r, wpad);
   FMMPC_LAUNCH_CHECK();
   ++launches;
-  const bool need_far = part != PART_NEAR;
-  const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q;
-  if (need_far) {
-    mark(1);
-    k_p2m_leaf<R><<<nblk(g.nleaf * nrhs * 32), 256, 0, s>>>(g, nrhs, wpad, Mv);
-    FMMPC_LAUNCH_CHECK();
-    ++launches;
-    for (int l = g.L - 1; l >= 0; --l) {
-      k_m2m_vol<R><<<nblk((int64_t(1) << (2 * l)) * nrhs, 128), 128, 0, s>>>(l, g.p, g.ncell, nrhs, Mv);
-      FMMPC_LAUNCH_CHECK();
-      ++launches;
-    }
+  if (part == PART_NEAR) {
+    mark(8);
+    run_p2p<R>(H, H.fb.table_lnh, out, nrhs, s);
+    mark_end();
+    H.launches = launches + 1;
+    return;
   }
+  const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q;
+  mark(1);
+  launches += run_upward<R, P>(H, nrhs, s);
   if (with_bnd) {
     mark(2);
-#define CALL_MB(PP) launch_m2l_bnd<R, PP>(H, nrhs, s)
-    FMMPC_DISPATCH_P(g.p, CALL_MB)
-#undef CALL_MB
-    k_root_const<R><<<1, 32, 0, s>>>(g.p, g.ncell, g.nbcell, nrhs, g.lnh, 0, Mv, Mb, Lv, Lb);
-    launches += 2;
-    for (int l = 0; l < g.L; ++l) {
-      k_l2l_bnd<R><<<nblk(4 * (int64_t(1) << (l + 1)) * nrhs, 128), 128, 0, s>>>(l, g.n, g.p, g.nbcell, nrhs, Lb);
-      ++launches;
-    }
-    k_colloc<R><<<nblk(g.nbleaf * nrhs * 32, 128), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src, H.fb.vcol);
+    k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbb_first,
+                                                              Ls.vbb_src, Mv, Lb);
+    k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, 0, Mv, Mb, Lv, Lb);
+    k_colloc<R><<<nblk((int64_t)g.NG * nrhs * 32, 128), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
+                                                                   H.fb.vcol);
     FMMPC_LAUNCH_CHECK();
-    ++launches;
+    launches += 3;
     if (part == PART_VCOL) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.vcol, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
@@ -803,7 +940,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(3);
-    k_bem_gemv<<<nblk((int64_t)g.NG * nrhs * 32), 256, 0, s>>>(g.NG, nrhs, H.Sinv, H.fb.vcol, H.fb.q);
+    k_bem_apply<<<g.n, 256, sizeof(double) * g.NG, s>>>(g.n, nrhs, H.Sinv, H.fb.vcol, H.fb.q);
     FMMPC_LAUNCH_CHECK();
     ++launches;
     if (part == PART_Q) {
@@ -813,63 +950,96 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(4);
-    k_p2m_bnd<R><<<nblk(g.nbleaf * nrhs, 128), 128, 0, s>>>(g, nrhs, H.fb.q, Mb);
+    k_bnd_up<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, H.fb.q, mt, Mb);
     FMMPC_LAUNCH_CHECK();
     ++launches;
-    for (int l = g.L - 1; l >= 0; --l) {
-      k_m2m_bnd<R><<<nblk(4 * (int64_t(1) << l) * nrhs, 128), 128, 0, s>>>(l, g.n, g.p, g.nbcell, nrhs, Mb);
-      ++launches;
-    }
-    FMMPC_LAUNCH_CHECK();
   }
-  if (need_far) {
-    mark(5);
-#define CALL_MV(PP) launch_m2l_vol<R, PP>(H, nrhs, with_bnd ? 1 : 0, s)
-    FMMPC_DISPATCH_P(g.p, CALL_MV)
-#undef CALL_MV
-    k_root_const<R><<<1, 32, 0, s>>>(g.p, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);
-    launches += 2;
-    mark(6);
-    for (int l = 0; l < g.L; ++l) {
-      k_l2l_vol<R><<<nblk((int64_t(1) << (2 * (l + 1))) * nrhs, 128), 128, 0, s>>>(l, g.p, g.ncell, nrhs, Lv);
-      ++launches;
-    }
-    FMMPC_LAUNCH_CHECK();
-  }
+  mark(5);
+  k_m2l_vol<R, P><<<nblk(g.ncell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, 1, with_bnd ? 1 : 0, 0,
+                                                           Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src,
+                                                           Mv, Mb, Lv);
+  k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);
+  FMMPC_LAUNCH_CHECK();
+  launches += 2;
+  mark(6);
+  launches += run_l2l<R, P>(H, nrhs, s);
   if (with_bnd && Ls.nbnear > 0) {
     mark(7);
-    k_bnd_near<R><<<nblk(Ls.nbnear * nrhs * 32, 128), 128, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
-                                                                  Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
+    k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
+                                                                 Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
     FMMPC_LAUNCH_CHECK();
     ++launches;
   }
-  P2PArgs<R> a;
-  a.wpad = wpad;
-  a.table = (const R *)(part == PART_NEAR ? H.fb.table_lnh : H.fb.table);
-  a.Lv = Lv;
-  a.phib = (const R *)H.fb.phib;
-  a.bslot = Ls.leaf_bslot;
-  a.out = out;
-  a.n = g.n; a.npad = g.npad; a.L = g.L; a.p = g.p; a.R_ = g.R; a.Rn = H.fb.Rn;
-  a.HX = (H.tile_x + 2 * g.R) * g.m;
-  a.HY = (H.tile_y + 2 * g.R) * g.m;
-  a.TS = H.fb.table_stride; a.c0 = H.fb.table_c0;
-  a.tile_x = H.tile_x; a.tile_y = H.tile_y; a.nrhs = nrhs;
-  a.ncell = g.ncell; a.nbnear = Ls.nbnear;
-  a.do_near = 1;
-  a.do_far = need_far ? 1 : 0;
-  a.do_bnd = (part == PART_FULL && Ls.nbnear > 0) ? 1 : 0;
-  a.st = H.st;
   mark(8);
-  switch (g.m) {
-    case 4: launch_p2p<R, 4>(g.L, a, s); break;
-    case 8: launch_p2p<R, 8>(g.L, a, s); break;
-    case 16: launch_p2p<R, 16>(g.L, a, s); break;
-    default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
-  }
-  ++launches;
+  run_p2p<R>(H, H.fb.table, out, nrhs, s);
+  run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
+  launches += 2;
   mark_end();
   H.launches = launches;
+}
+
+// Translation matrices from the paper's formulas in scaled form (double, then cast).
+template <typename R>
+void build_mats(fmmpc_handle &H, std::vector<cpx<R>> &out) {
+  const Geo &g = H.g;
+  const int P = g.p;
+  typedef std::complex<double> C;
+  static double bin[2 * MAXP + 2][2 * MAXP + 2];
+  for (int a = 0; a < 2 * MAXP + 2; ++a)
+    for (int b = 0; b < 2 * MAXP + 2; ++b)
+      bin[a][b] = (b == 0) ? 1.0 : (a == 0 ? 0.0 : bin[a - 1][b - 1] + bin[a - 1][b]);
+  auto powc = [](C z, int k) { C r(1, 0); for (int i = 0; i < k; ++i) r *= z; return r; };
+  // M2M from a child at offset w in parent units with child scale = parent scale / sc:
+  // T[0][0] = 1, T[n][0] = -w^n / n, T[n][k] = sc^{-k} w^{n-k} C(n-1, k-1)
+  auto m2m = [&](C w, double sc, std::vector<C> &T) {
+    T.assign(P * P, C(0, 0));
+    T[0] = 1.0;
+    for (int nn = 1; nn < P; ++nn) {
+      T[nn * P] = -powc(w, nn) / (double)nn;
+      for (int k = 1; k <= nn; ++k) T[nn * P + k] = std::pow(1.0 / sc, k) * powc(w, nn - k) * bin[nn - 1][k - 1];
+    }
+  };
+  // L2L to a child at w: S[n][k] = 2^{-n} w^{k-n} C(k, n)
+  auto l2l = [&](C w, std::vector<C> &S) {
+    S.assign(P * P, C(0, 0));
+    for (int nn = 0; nn < P; ++nn)
+      for (int k = nn; k < P; ++k) S[nn * P + k] = std::pow(0.5, nn) * powc(w, k - nn) * bin[k][nn];
+  };
+  std::vector<C> all, T;
+  for (int ch = 0; ch < 4; ++ch) {
+    m2m(C((ch & 1) ? 0.25 : -0.25, (ch & 2) ? 0.25 : -0.25), 2.0, T);
+    all.insert(all.end(), T.begin(), T.end());
+  }
+  for (int ch = 0; ch < 4; ++ch) {
+    l2l(C((ch & 1) ? 0.25 : -0.25, (ch & 2) ? 0.25 : -0.25), T);
+    all.insert(all.end(), T.begin(), T.end());
+  }
+  const int m = g.m, n = g.n;
+  const C edir[4] = {C(1, 0), C(0, 1), C(-1, 0), C(0, -1)};
+  // boundary run child j of side s sits at w = (2j - 1)(n+1)/(4n) e_s parent run-widths
+  for (int sd = 0; sd < 4; ++sd)
+    for (int j = 0; j < 2; ++j) {
+      m2m((2 * j - 1) * (n + 1.0) / (4.0 * n) * edir[sd], 2.0, T);
+      all.insert(all.end(), T.begin(), T.end());
+    }
+  // element e of a leaf run, unit density, about its midpoint at scale rho = m:
+  // Mt_0 = 2 a rho, Mt_k = -2 e^k a^{k+1} rho / (k (k+1)) for even k (0 for odd), then
+  // shifted to the run centre at equal scale (w = (y_e - c) / rho)
+  const double ell = (n + 1.0) / n, rho = m, a = ell / (2.0 * rho);
+  for (int sd = 0; sd < 4; ++sd)
+    for (int e = 0; e < m; ++e) {
+      std::vector<C> el(P, C(0, 0));
+      el[0] = 2.0 * a * rho;
+      for (int k = 2; k < P; k += 2) el[k] = -2.0 * powc(edir[sd], k) * std::pow(a, k + 1) * rho / (k * (k + 1.0));
+      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
+      for (int nn = 0; nn < P; ++nn) {
+        C v(0, 0);
+        for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
+        all.push_back(v);
+      }
+    }
+  out.resize(all.size());
+  for (size_t i = 0; i < all.size(); ++i) out[i] = mk<R>((R)all[i].real(), (R)all[i].imag());
 }
 
 template <typename R>
@@ -885,8 +1055,12 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.phib = H.pool.get<R>((size_t)nr * std::max<int64_t>(1, H.lists.nbnear) * g.m * g.m);
   H.fb.vcol = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
-  // lattice table: rows dy in [-Rn, Rn], columns dx at c0 + Rn + dx; stride chosen so that
-  // consecutive rows start 16 bytes apart modulo the 128-byte bank window
+  std::vector<cpx<R>> mats;
+  build_mats<R>(H, mats);
+  H.fb.mats = H.pool.get<cpx<R>>(mats.size());
+  FMMPC_CUDA(cudaMemcpyAsync(H.fb.mats, mats.data(), sizeof(cpx<R>) * mats.size(), cudaMemcpyHostToDevice, H.stream));
+  // lattice table, rows dy = 0..Rn (the table is even in dy), columns dx at c0 + Rn + dx;
+  // stride chosen so that consecutive rows start 16 bytes apart modulo the 128-byte bank window
   const int Rn = g.R * g.m + g.m - 1;
   const int c0 = ((g.m - 1 - Rn) % 4 + 4) % 4;
   int TS = c0 + 2 * Rn + 2;
@@ -894,14 +1068,14 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.Rn = Rn;
   H.fb.table_c0 = c0;
   H.fb.table_stride = TS;
-  H.fb.table_rows = 2 * Rn + 1;
+  H.fb.table_rows = Rn + 1;
   const double cself = -0.5 * std::log(2.0) - 1.5 + 0.25 * PI;  // mean of ln|x| on the unit cell
-  std::vector<R> t0((size_t)(2 * Rn + 1) * TS, R(0)), t1((size_t)(2 * Rn + 1) * TS, R(0));
-  for (int dy = -Rn; dy <= Rn; ++dy)
+  std::vector<R> t0((size_t)(Rn + 1) * TS, R(0)), t1((size_t)(Rn + 1) * TS, R(0));
+  for (int dy = 0; dy <= Rn; ++dy)
     for (int dx = -Rn; dx <= Rn; ++dx) {
       const double v = (dx == 0 && dy == 0) ? cself : 0.5 * std::log((double)dx * dx + (double)dy * dy);
-      t0[(size_t)(dy + Rn) * TS + c0 + Rn + dx] = (R)v;
-      t1[(size_t)(dy + Rn) * TS + c0 + Rn + dx] = (R)(v + g.lnh);
+      t0[(size_t)dy * TS + c0 + Rn + dx] = (R)v;
+      t1[(size_t)dy * TS + c0 + Rn + dx] = (R)(v + g.lnh);
     }
   H.fb.table = H.pool.get<R>(t0.size());
   H.fb.table_lnh = H.pool.get<R>(t1.size());
@@ -910,32 +1084,96 @@ void alloc_fmm(fmmpc_handle &H) {
   FMMPC_CUDA(cudaStreamSynchronize(H.stream));
 }
 
+template <typename R>
+void dispatch_apply(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
+  switch (H.g.p) {
+    case 4: apply_impl<R, 4>(H, part, r, out, nrhs); break;
+    case 6: apply_impl<R, 6>(H, part, r, out, nrhs); break;
+    case 8: apply_impl<R, 8>(H, part, r, out, nrhs); break;
+    case 10: apply_impl<R, 10>(H, part, r, out, nrhs); break;
+    case 12: apply_impl<R, 12>(H, part, r, out, nrhs); break;
+    case 16: apply_impl<R, 16>(H, part, r, out, nrhs); break;
+    default: throw Error(FMMPC_ERR_UNSUPPORTED, "expansion order p must be one of 4, 6, 8, 10, 12, 16");
+  }
+}
+
 }  // namespace
 
 void init_fmm(fmmpc_handle &H) {
-  double bin[MAXP + 1][MAXP + 1];
-  for (int a = 0; a <= MAXP; ++a)
-    for (int b = 0; b <= MAXP; ++b)
-      bin[a][b] = (b == 0) ? 1.0 : (a == 0 ? 0.0 : bin[a - 1][b - 1] + bin[a - 1][b]);
-  FMMPC_CUDA(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
   const int side = 1 << H.g.L;
   const int m = H.g.m;
-  int tx = (m == 4) ? 8 : (m == 8 ? 8 : 4), ty = (m == 4) ? 8 : (m == 8 ? 4 : 4);
+  int tx = (m == 16) ? 4 : 8, ty = (m == 4) ? 8 : 4;
   H.tile_x = std::min(tx, side);
   H.tile_y = std::min(ty, side);
   if (H.prec == FMMPC_PREC_FP64) {
     if (m == 16) throw Error(FMMPC_ERR_UNSUPPORTED, "FP64 mode supports leaf side 4 or 8");
+    set_p2p_smem_limit<double>();
     alloc_fmm<double>(H);
   } else {
+    set_p2p_smem_limit<float>();
     alloc_fmm<float>(H);
   }
+  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
+  FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_in, cudaEventDisableTiming));
+  FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_out, cudaEventDisableTiming));
 }
+
+namespace {
+
+void apply_direct(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
+  if (H.prec == FMMPC_PREC_FP64) dispatch_apply<double>(H, part, r, out, nrhs);
+  else dispatch_apply<float>(H, part, r, out, nrhs);
+}
+
+// The full apply replayed from a CUDA graph captured on the handle's internal stream, one
+// graph per (r, z, n_rhs, timing) seen; the internal stream is ordered after and before
+// the caller's stream with events, so the call keeps the stream semantics of the ABI.
+void apply_graph(fmmpc_handle &H, const double *r, double *out, int nrhs) {
+  GraphEntry *hit = nullptr;
+  for (auto &e : H.gcache)
+    if (e.r == r && e.out == out && e.nrhs == nrhs && e.timing == H.timing) hit = &e;
+  if (!hit) {
+    if (H.gcache.size() >= 64) {
+      auto old = std::min_element(H.gcache.begin(), H.gcache.end(),
+                                  [](const GraphEntry &a, const GraphEntry &b) { return a.last < b.last; });
+      cudaGraphExecDestroy(old->exec);
+      H.gcache.erase(old);
+    }
+    cudaStream_t user = H.stream;
+    H.stream = H.gstream;
+    cudaGraph_t graph = nullptr;
+    FMMPC_CUDA(cudaStreamBeginCapture(H.gstream, cudaStreamCaptureModeThreadLocal));
+    try {
+      apply_direct(H, PART_FULL, r, out, nrhs);
+    } catch (...) {
+      cudaStreamEndCapture(H.gstream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      H.stream = user;
+      throw;
+    }
+    H.stream = user;
+    FMMPC_CUDA(cudaStreamEndCapture(H.gstream, &graph));
+    GraphEntry e{r, out, nrhs, H.timing, nullptr, 0};
+    cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FMMPC_CUDA(ie);
+    H.gcache.push_back(e);
+    hit = &H.gcache.back();
+  }
+  hit->last = ++H.gclock;
+  FMMPC_CUDA(cudaEventRecord(H.gev_in, H.stream));
+  FMMPC_CUDA(cudaStreamWaitEvent(H.gstream, H.gev_in, 0));
+  FMMPC_CUDA(cudaGraphLaunch(hit->exec, H.gstream));
+  FMMPC_CUDA(cudaEventRecord(H.gev_out, H.gstream));
+  FMMPC_CUDA(cudaStreamWaitEvent(H.stream, H.gev_out, 0));
+}
+
+}  // namespace
 
 void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
-  if (H.prec == FMMPC_PREC_FP64) apply_impl<double>(H, part, r, out, nrhs);
-  else apply_impl<float>(H, part, r, out, nrhs);
+  if (part == PART_FULL && H.graphs) apply_graph(H, r, out, nrhs);
+  else apply_direct(H, part, r, out, nrhs);
 }
-
 
 // ====================================================================== no-allocation variant
 // Near field of V r computed with scratch that lives in a static device array instead of
@@ -948,9 +1186,8 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 
 __global__ void k_noalloc_table(float *__restrict__ tab, int Rn, int TS, int c0, double lnh) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)(2 * Rn + 1) * TS) return;
-  const int row = (int)(k / TS), col = (int)(k % TS);
-  const int dy = row - Rn, dx = col - c0 - Rn;
+  if (k >= (int64_t)(Rn + 1) * TS) return;
+  const int dy = (int)(k / TS), dx = (int)(k % TS) - c0 - Rn;
   float v = 0.0f;  // padding columns are read by the vector loads but never used
   if (dx >= -Rn && dx <= Rn) {
     const double cself = -0.5 * log(2.0) - 1.5 + 0.25 * PI;
@@ -997,10 +1234,10 @@ template <int M>
 cudaError_t noalloc_launch(const P2PArgs<float> &a, int L, cudaStream_t s) {
   const int side = 1 << L;
   dim3 grid(side / a.tile_x, side / a.tile_y, 1);
-  const size_t smem = ((size_t)a.HY * a.HX + (size_t)(2 * a.Rn + 1) * a.TS) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_p2p_final<float, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = ((size_t)a.HY * a.HX + (size_t)(a.Rn + 1) * a.TS) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_p2p<float, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_p2p_final<float, M><<<grid, a.tile_x * a.tile_y * M, smem, s>>>(a);
+  k_p2p<float, M><<<grid, a.tile_x * a.tile_y * M, smem, s>>>(a);
   return cudaPeekAtLastError();
 }
 
@@ -1040,7 +1277,7 @@ int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, c
   const int c0 = ((m - 1 - Rn) % 4 + 4) % 4;
   int TS = c0 + 2 * Rn + 2;
   while ((TS * 4) % 128 != 16) ++TS;
-  const int64_t tab_floats = (int64_t)(2 * Rn + 1) * TS;
+  const int64_t tab_floats = (int64_t)(Rn + 1) * TS;
   const int64_t need = tab_floats + (int64_t)npad * npad;
   if (need > NOALLOC_FLOATS)
     return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: grid too large for the 16 MiB static scratch (n = 1024 with 8x8 leaves and theta 0.4 is the largest such grid)");
@@ -1059,11 +1296,11 @@ int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, c
   tx = std::min(tx, sidel);
   ty = std::min(ty, sidel);
   P2PArgs<float> a{};
-  a.wpad = img; a.table = tab; a.Lv = nullptr; a.phib = nullptr; a.bslot = nullptr; a.out = out_dev;
-  a.n = n; a.npad = npad; a.L = L; a.p = 0; a.R_ = R; a.Rn = Rn;
+  a.wpad = img; a.table = tab; a.out = out_dev;
+  a.n = n; a.npad = npad; a.L = L; a.R_ = R; a.Rn = Rn;
   a.HX = (tx + 2 * R) * m; a.HY = (ty + 2 * R) * m; a.TS = TS; a.c0 = c0;
-  a.tile_x = tx; a.tile_y = ty; a.nrhs = 1; a.ncell = 0; a.nbnear = 0;
-  a.do_near = 1; a.do_far = 0; a.do_bnd = 0; a.st = st;
+  a.tile_x = tx; a.tile_y = ty; a.nrhs = 1;
+  a.st = st;
   switch (m) {
     case 4: e = noalloc_launch<4>(a, L, s); break;
     case 8: e = noalloc_launch<8>(a, L, s); break;

@@ -25,10 +25,20 @@ struct FmmBufs {
   void *Lb = nullptr;        // [nrhs][nbcell][p] boundary locals
   void *phib = nullptr;      // [nrhs][nbnear][m^2] near-boundary correction at nodes
   void *table = nullptr;     // lattice table ln|d| (node units), self term at d = 0
+  void *mats = nullptr;      // fixed M2M / L2L / boundary P2M translation matrices
   void *table_lnh = nullptr; // same plus ln h (for the near-field-only part)
   int table_rows = 0, table_stride = 0, table_c0 = 0, Rn = 0;
   double *vcol = nullptr;    // [nrhs][NG] V r at collocation points
   double *q = nullptr;       // [nrhs][NG] BEM density
+};
+
+struct GraphEntry {
+  const double *r;
+  double *out;
+  int nrhs;
+  bool timing;
+  cudaGraphExec_t exec;
+  uint64_t last;
 };
 
 struct KrylovWs {
@@ -57,7 +67,7 @@ struct fmmpc_handle {
   fmmpc::TreeOut tree{};
   fmmpc::Lists lists{};
   fmmpc::FmmBufs fb{};
-  double *Sinv = nullptr;   // [NG][NG] FP64 inverse of the single-layer matrix
+  double *Sinv = nullptr;   // [n][4n] first block row of the FP64 inverse of the single-layer matrix
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
   int64_t launches = 0;     // kernel launches of the last apply
@@ -67,11 +77,12 @@ struct fmmpc_handle {
   cudaEvent_t ev[NSTAGE + 1] = {};
   bool stage_hit[NSTAGE] = {};
   double t_setup_ms = 0.0;
-  // CUDA graph of the apply (input/output fixed to the staging pointers of the solver)
-  cudaGraphExec_t graph = nullptr;
-  const void *graph_in = nullptr;
-  void *graph_out = nullptr;
-  int graph_nrhs = 0;
+  // CUDA graphs of the full apply, replayed on an internal stream (fmmpc_set_graphs)
+  bool graphs = true;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  std::vector<fmmpc::GraphEntry> gcache;
+  uint64_t gclock = 0;
 };
 
 namespace fmmpc {

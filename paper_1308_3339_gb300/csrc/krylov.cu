@@ -425,6 +425,12 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
   require(m >= 1 && m < MAXJ, "restart must be in [1, 63]");
   auto t0 = std::chrono::steady_clock::now();
   ensure_ws(H, o.method == FMMPC_CG ? 2 : m + 1, o.method == FMMPC_FGMRES);
+  struct GraphsGuard {  // the solve's use_graphs option holds for this call only
+    fmmpc_handle &H;
+    bool saved;
+    ~GraphsGuard() { H.graphs = saved; }
+  } guard{H, H.graphs};
+  H.graphs = o.use_graphs != 0;
   Ctx c{H, (int64_t)H.g.n * H.g.n, nrhs, H.stream};
   const int64_t NR = c.N * nrhs;
   k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(H.g.n, 1.0 / (H.g.h * H.g.h), NR, f, g, H.kw.b);

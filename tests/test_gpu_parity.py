@@ -168,3 +168,14 @@ def test_full_size_1024_apply_matches_oracle_and_direct_sum():
     idx = np.random.default_rng(0).choice(n * n, 192, replace=False).astype(np.int32)
     vr = host(P.apply_part("vr", rd))[idx]
     assert rel_l2(vr, O.direct_V_nodes(n, 0.0, 0.0, 1.0, r, idx)) < 1e-5
+
+
+def test_graph_replay_matches_direct_launches():
+    n = 128
+    P = gpu(n, p=10)
+    r = dev(S.random_field(n, 8))
+    P.set_graphs(False)
+    a = host(P.apply(r))
+    P.set_graphs(True)
+    b, c = host(P.apply(r)), host(P.apply(r))  # capture, then replay
+    assert np.array_equal(a, b) and np.array_equal(b, c)
