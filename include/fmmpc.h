@@ -212,6 +212,54 @@ int fmmpc_near_field_noalloc(int32_t n, double side, int32_t leaf_max, double th
 /* Releases every resource of the handle (NULL is allowed). */
 void fmmpc_destroy(fmmpc_handle *h);
 
+/* One candidate of the autotuner. */
+typedef struct {
+  int32_t leaf_max;
+  int32_t p;
+  double rel_err;   /* relative L2 difference of its apply from the FP64 p = 16 apply */
+  double solve_ms;  /* measured time-to-solution (0 when the gate failed) */
+  int32_t iters;
+  int32_t ok;       /* 1 if within the gate and converged */
+} fmmpc_tune_entry;
+
+/* Autotuner: picks leaf_max in {16, 64, 256} and p in {6, 8, 10, 12} by measured
+ * time-to-solution of opts on the right-hand side f_dev ([ny][nx] FP64, device), among
+ * the candidates whose preconditioner apply is within relative L2 error tol of an FP64
+ * p = 16 reference apply (accuracy traded for speed as in Sec. 6.2, Fig. f:convergence;
+ * the paper fixes p and theta by hand, Sec. 7.1).  base supplies theta, precision and
+ * n_rhs.  *best receives the chosen parameters; report (capacity cap, may be NULL) the
+ * candidates, *count their number.  Results are cached per (grid, precision, n_rhs, tol)
+ * in the process; a report request bypasses the cache.  fmmpc_create with
+ * params.autotune = 1 runs this on a synthetic smooth right-hand side with tol = 1e-5.
+ * Allocates and frees temporary handles.  Errors: _INVALID (no candidate passed). */
+int fmmpc_autotune(const fmmpc_grid *g, const fmmpc_params *base, const fmmpc_solve_opts *opts,
+                   const double *f_dev, double tol, void *stream, fmmpc_params *best,
+                   fmmpc_tune_entry *report, int32_t cap, int32_t *count);
+
+/* Batches of independent problems of uneven size, solved together. */
+typedef struct fmmpc_batch fmmpc_batch;
+
+/* One handle per grid (each on its own internal stream, ordered after `stream`), with
+ * params shared; params.autotune = 1 tunes leaf size and p per distinct grid. */
+int fmmpc_create_batched(fmmpc_batch **out, int32_t nprob, const fmmpc_grid *grids,
+                         const fmmpc_params *prm, void *stream);
+
+/* FGMRES(m) on every problem in lockstep: each Arnoldi step launches all active
+ * problems' preconditioner applies (CUDA graphs on their streams, running concurrently),
+ * SpMVs and orthogonalisations, then synchronises once for the whole batch; converged
+ * problems drop out.  f_dev[i], u_dev[i] (initial iterate in, solution out) and g_dev[i]
+ * (NULL array or entries for g = 0) are device pointers of problem i's grid.  infos[i]
+ * receives each problem's report.  Returns FMMPC_OK when all converged, otherwise the
+ * first failing status.  opts->method must be FMMPC_FGMRES. */
+int fmmpc_solve_batched(fmmpc_batch *b, const double *const *f_dev, const double *const *g_dev,
+                        double *const *u_dev, const fmmpc_solve_opts *opts,
+                        fmmpc_solve_info *infos);
+
+/* fmmpc_query on problem prob of the batch; what = 100 gives its expansion order p. */
+int fmmpc_batch_query(const fmmpc_batch *b, int32_t prob, int32_t what, int64_t *value);
+const char *fmmpc_batch_last_error(const fmmpc_batch *b);
+void fmmpc_destroy_batched(fmmpc_batch *b);
+
 /* Message of the last failed call on h (or of the last failed fmmpc_create when h is
  * NULL).  The string lives until the next call on the same handle. */
 const char *fmmpc_last_error(const fmmpc_handle *h);

@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import FmmpcError, check
 
-__all__ = ["FmmPreconditioner", "FmmpcError", "version"]
+__all__ = ["FmmPreconditioner", "FmmBatch", "FmmpcError", "autotune", "version"]
 
 
 def version() -> str:
@@ -157,3 +157,73 @@ class FmmPreconditioner:
                                        u.ctypes.data_as(C.c_void_p), k, C.byref(opts), C.byref(info))
         check(rc, self._h)
         return u, dict(iters=info.iters, rel_res=info.rel_res, t_solve_ms=info.t_solve_ms)
+
+
+def autotune(f, n: int, tol: float = 1e-5, precision: str = "fp32", theta: float = 0.4,
+             side: float = 1.0, x0: float = 0.0, y0: float = 0.0, method: str = "fgmres",
+             restart: int = 30, maxit: int = 100, rtol: float = 1e-8, stream=None):
+    """fmmpc_autotune: best (leaf_max, p) for right-hand side f and the candidate report."""
+    import torch
+    lib = _lib.load()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    g = _lib.Grid(n, n, x0, y0, x0 + side, y0 + side)
+    base = _lib.Params(10, 64, theta, _lib.PREC[precision], 1, 0)
+    opts = _lib.SolveOpts(_lib.METHOD[method], restart, maxit, rtol, 1)
+    best = _lib.Params()
+    rep = (_lib.TuneEntry * 16)()
+    cnt = C.c_int32()
+    rc = lib.fmmpc_autotune(C.byref(g), C.byref(base), C.byref(opts), _ptr(f), tol,
+                            C.c_void_p(stream.cuda_stream), C.byref(best), rep, 16, C.byref(cnt))
+    check(rc, None)
+    report = [dict(leaf_max=e.leaf_max, p=e.p, rel_err=e.rel_err, solve_ms=e.solve_ms, iters=e.iters,
+                   ok=bool(e.ok)) for e in rep[: cnt.value]]
+    return dict(leaf_max=best.leaf_max, p=best.p), report
+
+
+class FmmBatch:
+    """Independent problems of uneven size solved together (fmmpc_create_batched)."""
+
+    def __init__(self, sides, p: int = 10, leaf_max: int = 64, theta: float = 0.4,
+                 precision: str = "fp32", autotune: bool = False, stream=None):
+        import torch
+        self.lib = _lib.load()
+        self.sides = [int(s) for s in sides]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        grids = (_lib.Grid * len(self.sides))(*[_lib.Grid(s, s, 0.0, 0.0, 1.0, 1.0) for s in self.sides])
+        prm = _lib.Params(p, leaf_max, theta, _lib.PREC[precision], 1, 1 if autotune else 0)
+        h = C.c_void_p()
+        check(self.lib.fmmpc_create_batched(C.byref(h), len(self.sides), grids, C.byref(prm),
+                                            C.c_void_p(self.stream.cuda_stream)), None)
+        self._h = h
+
+    def config(self, i: int):
+        v = C.c_int64()
+        self.lib.fmmpc_batch_query(self._h, i, 1, C.byref(v))
+        leaf = v.value
+        self.lib.fmmpc_batch_query(self._h, i, 100, C.byref(v))
+        return dict(leaf_side=leaf, p=v.value)
+
+    def solve(self, fs, us=None, restart: int = 30, maxit: int = 200, rtol: float = 1e-8, use_graphs: int = 1):
+        import torch
+        k = len(self.sides)
+        us = [torch.zeros_like(f) for f in fs] if us is None else us
+        fp = (C.c_void_p * k)(*[f.data_ptr() for f in fs])
+        up = (C.c_void_p * k)(*[u.data_ptr() for u in us])
+        opts = _lib.SolveOpts(_lib.METHOD["fgmres"], restart, maxit, rtol, use_graphs)
+        infos = (_lib.SolveInfo * k)()
+        rc = self.lib.fmmpc_solve_batched(self._h, fp, None, up, C.byref(opts), infos)
+        out = [dict(iters=i.iters, rel_res=i.rel_res, status=i.status, t_solve_ms=i.t_solve_ms) for i in infos]
+        if rc != 0:
+            raise FmmpcError(rc, (self.lib.fmmpc_batch_last_error(self._h) or b"").decode())
+        return us, out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fmmpc_destroy_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -37,6 +37,11 @@ class SolveOpts(C.Structure):
                 ("rtol", C.c_double), ("use_graphs", C.c_int32)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("leaf_max", C.c_int32), ("p", C.c_int32), ("rel_err", C.c_double),
+                ("solve_ms", C.c_double), ("iters", C.c_int32), ("ok", C.c_int32)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("rel_res", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_solve_ms", C.c_double), ("status", C.c_int32)]
@@ -63,6 +68,15 @@ SIGNATURES = {
     "fmmpc_near_field_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                                            C.c_void_p, C.c_void_p]),
     "fmmpc_destroy": (None, [C.c_void_p]),
+    "fmmpc_autotune": (C.c_int, [C.POINTER(Grid), C.POINTER(Params), C.POINTER(SolveOpts), C.c_void_p,
+                                 C.c_double, C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_int32,
+                                 C.POINTER(C.c_int32)]),
+    "fmmpc_create_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(Params), C.c_void_p]),
+    "fmmpc_solve_batched": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts),
+                                      C.c_void_p]),
+    "fmmpc_batch_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
+    "fmmpc_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fmmpc_destroy_batched": (None, [C.c_void_p]),
     "fmmpc_last_error": (C.c_char_p, [C.c_void_p]),
     "fmmpc_version": (C.c_char_p, []),
 }

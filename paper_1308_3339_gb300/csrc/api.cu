@@ -136,6 +136,27 @@ void release(fmmpc_handle *h) {
 }  // namespace
 
 namespace fmmpc {
+int create_handle(fmmpc_handle **out, const fmmpc_grid &g, const fmmpc_params &prm, void *stream) {
+  fmmpc_handle *h = nullptr;
+  try {
+    h = new fmmpc_handle();
+  } catch (...) {
+    return set_global_error(FMMPC_ERR_OOM, "host allocation failed");
+  }
+  h->stream = (cudaStream_t)stream;
+  int rc = guarded(h, [&] {
+    setup(*h, g, prm);
+    return FMMPC_OK;
+  });
+  if (rc != FMMPC_OK) {
+    set_global_error(rc, h->err.c_str());
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return FMMPC_OK;
+}
+
 int set_global_error(int code, const char *msg) {
   std::strncpy(g_global_error, msg ? msg : "", sizeof(g_global_error) - 1);
   g_global_error[sizeof(g_global_error) - 1] = 0;
@@ -148,24 +169,45 @@ extern "C" {
 int fmmpc_create(fmmpc_handle **out, const fmmpc_grid *g, const fmmpc_params *prm, void *stream) {
   if (!out || !g || !prm) return set_global_error(FMMPC_ERR_INVALID, "fmmpc_create: NULL argument");
   *out = nullptr;
-  fmmpc_handle *h = nullptr;
-  try {
-    h = new fmmpc_handle();
-  } catch (...) {
-    return set_global_error(FMMPC_ERR_OOM, "host allocation failed");
+  fmmpc_params p = *prm;
+  if (p.autotune) {
+    // tune on a smooth synthetic right-hand side (a few Gaussian bumps) of this grid
+    int rc = FMMPC_OK;
+    try {
+      const int n = g->nx;
+      require(n >= 4 && n <= 4096 && g->ny == n, "fmmpc_create: grid outside the supported range");
+      std::vector<double> f((size_t)n * n);
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const double x = (i + 1.0) / (n + 1), y = (j + 1.0) / (n + 1);
+          f[(size_t)j * n + i] = std::exp(-((x - 0.3) * (x - 0.3) + (y - 0.6) * (y - 0.6)) / 0.005) -
+                                 0.7 * std::exp(-((x - 0.7) * (x - 0.7) + (y - 0.35) * (y - 0.35)) / 0.002) +
+                                 0.3 * std::sin(3.0 * x) * std::cos(2.0 * y);
+        }
+      DevPool tmp;
+      double *fd = tmp.get<double>(f.size());
+      cudaStream_t s = (cudaStream_t)stream;
+      FMMPC_CUDA(cudaMemcpyAsync(fd, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice, s));
+      fmmpc_solve_opts o{FMMPC_FGMRES, 30, 100, 1e-8, 1};
+      std::vector<fmmpc_tune_entry> rep;
+      fmmpc_params best = p;
+      try {
+        rc = autotune(*g, p, o, fd, 1e-5, stream, best, rep, false);
+      } catch (...) {
+        cudaStreamSynchronize(s);
+        tmp.release();
+        throw;
+      }
+      cudaStreamSynchronize(s);
+      tmp.release();
+      p = best;
+      p.autotune = 0;
+    } catch (const Error &e) {
+      return set_global_error(e.code, e.msg.c_str());
+    }
+    if (rc != FMMPC_OK) return rc;
   }
-  h->stream = (cudaStream_t)stream;
-  int rc = guarded(h, [&] {
-    setup(*h, *g, *prm);
-    return FMMPC_OK;
-  });
-  if (rc != FMMPC_OK) {
-    set_global_error(rc, h->err.c_str());
-    release(h);
-    return rc;
-  }
-  *out = h;
-  return FMMPC_OK;
+  return create_handle(out, *g, p, stream);
 }
 
 int fmmpc_apply(fmmpc_handle *h, const double *r_dev, double *z_dev, int32_t n_rhs) {
@@ -331,6 +373,106 @@ int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count) {
 }
 
 void fmmpc_destroy(fmmpc_handle *h) { release(h); }
+
+int fmmpc_autotune(const fmmpc_grid *g, const fmmpc_params *base, const fmmpc_solve_opts *opts, const double *f_dev,
+                   double tol, void *stream, fmmpc_params *best, fmmpc_tune_entry *report, int32_t cap,
+                   int32_t *count) {
+  if (!g || !base || !opts || !f_dev || !best || !(tol > 0.0)) return set_global_error(FMMPC_ERR_INVALID, "autotune: bad argument");
+  try {
+    std::vector<fmmpc_tune_entry> rep;
+    fmmpc_params b = *base;
+    int rc = autotune(*g, *base, *opts, f_dev, tol, stream, b, rep, report && cap > 0);
+    if (rc != FMMPC_OK) return rc;
+    *best = b;
+    if (count) *count = (int32_t)rep.size();
+    for (int i = 0; report && i < cap && i < (int)rep.size(); ++i) report[i] = rep[i];
+    return FMMPC_OK;
+  } catch (const Error &e) {
+    return set_global_error(e.code, e.msg.c_str());
+  }
+}
+
+}  // extern "C"
+
+struct fmmpc_batch {
+  std::vector<fmmpc_handle *> hs;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::string err;
+};
+
+extern "C" {
+
+void fmmpc_destroy_batched(fmmpc_batch *b) {
+  if (!b) return;
+  for (auto *h : b->hs) fmmpc_destroy(h);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  if (b->ev) cudaEventDestroy(b->ev);
+  delete b;
+}
+
+int fmmpc_create_batched(fmmpc_batch **out, int32_t nprob, const fmmpc_grid *grids, const fmmpc_params *prm,
+                         void *stream) {
+  if (!out || !grids || !prm || nprob < 1) return set_global_error(FMMPC_ERR_INVALID, "create_batched: bad argument");
+  *out = nullptr;
+  fmmpc_batch *b = new (std::nothrow) fmmpc_batch();
+  if (!b) return set_global_error(FMMPC_ERR_OOM, "host allocation failed");
+  b->user = (cudaStream_t)stream;
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    fmmpc_destroy_batched(b);
+    return set_global_error(FMMPC_ERR_CUDA, "create_batched: event creation failed");
+  }
+  for (int i = 0; i < nprob; ++i) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      fmmpc_destroy_batched(b);
+      return set_global_error(FMMPC_ERR_CUDA, "create_batched: stream creation failed");
+    }
+    b->streams.push_back(s);
+    fmmpc_handle *h = nullptr;
+    const int rc = fmmpc_create(&h, &grids[i], prm, s);  // autotunes per grid when prm->autotune
+    if (rc != FMMPC_OK) {
+      fmmpc_destroy_batched(b);
+      return rc;
+    }
+    b->hs.push_back(h);
+  }
+  *out = b;
+  return FMMPC_OK;
+}
+
+int fmmpc_solve_batched(fmmpc_batch *b, const double *const *f_dev, const double *const *g_dev, double *const *u_dev,
+                        const fmmpc_solve_opts *opts, fmmpc_solve_info *infos) {
+  if (!b || !f_dev || !u_dev || !opts) return FMMPC_ERR_INVALID;
+  try {
+    // order the problem streams after the caller's stream, and the caller's after them
+    FMMPC_CUDA(cudaEventRecord(b->ev, b->user));
+    for (auto s : b->streams) FMMPC_CUDA(cudaStreamWaitEvent(s, b->ev, 0));
+    const int rc = solve_batched(b->hs, f_dev, g_dev, u_dev, *opts, infos);
+    for (auto s : b->streams) {
+      FMMPC_CUDA(cudaEventRecord(b->ev, s));
+      FMMPC_CUDA(cudaStreamWaitEvent(b->user, b->ev, 0));
+    }
+    if (rc != FMMPC_OK) b->err = "solve_batched: a problem did not converge (see infos)";
+    return rc;
+  } catch (const Error &e) {
+    b->err = e.msg;
+    return e.code;
+  }
+}
+
+int fmmpc_batch_query(const fmmpc_batch *b, int32_t prob, int32_t what, int64_t *value) {
+  if (!b || prob < 0 || prob >= (int)b->hs.size()) return FMMPC_ERR_INVALID;
+  if (what == 100) {
+    if (!value) return FMMPC_ERR_INVALID;
+    *value = b->hs[prob]->g.p;
+    return FMMPC_OK;
+  }
+  return fmmpc_query(b->hs[prob], what, value);
+}
+
+const char *fmmpc_batch_last_error(const fmmpc_batch *b) { return b ? b->err.c_str() : ""; }
 
 const char *fmmpc_last_error(const fmmpc_handle *h) {
   return h ? h->err.c_str() : g_global_error;

@@ -44,6 +44,10 @@ inline void require(bool ok, const std::string &msg) {
 struct DevPool {
   std::vector<void *> ptrs;
   size_t bytes = 0;
+  DevPool() = default;
+  DevPool(const DevPool &) = delete;
+  DevPool &operator=(const DevPool &) = delete;
+  ~DevPool() { release(); }
   void *alloc(size_t nbytes) {
     void *p = nullptr;
     if (nbytes == 0) nbytes = 16;

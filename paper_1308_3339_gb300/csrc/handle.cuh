@@ -94,6 +94,11 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);
 // message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
 int set_global_error(int code, const char *msg);
+int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,
+                  double *const *u, const fmmpc_solve_opts &o, fmmpc_solve_info *infos);
+int autotune(const fmmpc_grid &g, const fmmpc_params &base, const fmmpc_solve_opts &opts, const double *f_dev,
+             double tol, void *stream, fmmpc_params &best, std::vector<fmmpc_tune_entry> &report, bool want_report);
+int create_handle(fmmpc_handle **out, const fmmpc_grid &g, const fmmpc_params &p, void *stream);
 int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, const double *r_dev,
                        double *out_dev, void *stream);
 }  // namespace fmmpc

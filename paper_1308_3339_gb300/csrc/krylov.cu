@@ -446,3 +446,204 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
 }
 
 }  // namespace fmmpc
+
+// ====================================================================== batched solves
+// Several independent problems (different grids) solved together by FGMRES(m), in
+// lockstep: every Arnoldi step launches each active problem's preconditioner (a CUDA
+// graph on that problem's stream, so the problems' applies overlap on the GPU), its SpMV
+// and CGS2 kernels, and one host synchronisation serves the whole batch.  Converged
+// problems drop out; each keeps its own Hessenberg system.
+namespace fmmpc {
+
+namespace {
+
+struct BatchState {
+  std::vector<double> Hm, cs, sn, g, y;
+  double bn = 1.0, beta = 0.0;
+  bool done = false, in_cycle = false;
+  int j = 0, iters = 0, status = FMMPC_OK;
+};
+
+void sync_all(std::vector<fmmpc_handle *> &hs) {
+  for (auto *h : hs) FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// <v, v> of problem H into hbuf[slot] (asynchronous)
+void norm2_async(fmmpc_handle &H, const double *v, double *dev_out, int slot) {
+  Ctx c{H, (int64_t)H.g.n * H.g.n, 1, H.stream};
+  mdot(c, 1, v, 0, v, dev_out, nullptr);
+  FMMPC_CUDA(cudaMemcpyAsync(H.kw.hbuf + slot, dev_out, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+}
+
+}  // namespace
+
+int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,
+                  double *const *u, const fmmpc_solve_opts &o, fmmpc_solve_info *infos) {
+  require(o.method == FMMPC_FGMRES, "batched solve: FGMRES only");
+  require(o.maxit >= 1 && o.rtol > 0.0, "maxit >= 1 and rtol > 0 required");
+  const int m = std::min(o.restart, o.maxit);
+  require(m >= 1 && m < MAXJ, "restart must be in [1, 63]");
+  const int np = (int)hs.size();
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<BatchState> st(np);
+  std::vector<bool> saved_graphs(np);
+  for (int p = 0; p < np; ++p) {
+    fmmpc_handle &H = *hs[p];
+    saved_graphs[p] = H.graphs;
+    H.graphs = o.use_graphs != 0;
+    ensure_ws(H, m + 1, true);
+    const int64_t N = (int64_t)H.g.n * H.g.n;
+    k_fold_rhs<<<nblk(N), 256, 0, H.stream>>>(H.g.n, 1.0 / (H.g.h * H.g.h), N, f[p], gb ? gb[p] : nullptr, H.kw.b);
+    FMMPC_LAUNCH_CHECK();
+    norm2_async(H, H.kw.b, H.kw.dots, 0);
+    BatchState &s = st[p];
+    s.Hm.assign((size_t)(m + 1) * m, 0.0);
+    s.cs.assign(m, 0.0);
+    s.sn.assign(m, 0.0);
+    s.g.assign(m + 1, 0.0);
+    s.y.assign(MAXJ, 0.0);
+  }
+  sync_all(hs);
+  for (int p = 0; p < np; ++p) {
+    st[p].bn = std::sqrt(std::max(0.0, hs[p]->kw.hbuf[0]));
+    if (st[p].bn == 0.0) st[p].bn = 1.0;
+  }
+  for (;;) {
+    // residuals of the problems still running
+    for (int p = 0; p < np; ++p) {
+      if (st[p].done) continue;
+      fmmpc_handle &H = *hs[p];
+      Ctx c{H, (int64_t)H.g.n * H.g.n, 1, H.stream};
+      residual(c, H.kw.b, u[p], H.kw.r);
+      norm2_async(H, H.kw.r, H.kw.dots, 0);
+    }
+    sync_all(hs);
+    bool any = false;
+    for (int p = 0; p < np; ++p) {
+      BatchState &s = st[p];
+      s.in_cycle = false;
+      if (s.done) continue;
+      fmmpc_handle &H = *hs[p];
+      s.beta = std::sqrt(std::max(0.0, H.kw.hbuf[0]));
+      if (!std::isfinite(s.beta)) { s.done = true; s.status = FMMPC_ERR_NAN; continue; }
+      if (s.beta / s.bn <= o.rtol) { s.done = true; continue; }
+      if (s.iters >= o.maxit) { s.done = true; s.status = FMMPC_ERR_NOT_CONVERGED; continue; }
+      s.in_cycle = true;
+      s.j = 0;
+      any = true;
+      std::fill(s.g.begin(), s.g.end(), 0.0);
+      s.g[0] = s.beta;
+      const int64_t N = (int64_t)H.g.n * H.g.n;
+      double *hy = H.kw.hbuf + 2 * MAXJ;
+      hy[0] = 1.0 / s.beta;
+      FMMPC_CUDA(cudaMemcpyAsync(H.kw.scal, hy, sizeof(double), cudaMemcpyHostToDevice, H.stream));
+      k_scale<<<nblk(N), 256, 0, H.stream>>>(N, 1, H.kw.scal, H.kw.r, H.kw.V);
+      FMMPC_LAUNCH_CHECK();
+    }
+    if (!any) break;
+    for (int jj = 0; jj < m; ++jj) {
+      bool active = false;
+      for (int p = 0; p < np; ++p) {
+        BatchState &s = st[p];
+        if (!s.in_cycle) continue;
+        active = true;
+        fmmpc_handle &H = *hs[p];
+        const int64_t N = (int64_t)H.g.n * H.g.n, vs = N * H.nrhs_max;
+        Ctx c{H, N, 1, H.stream};
+        double *vj = H.kw.V + (int64_t)s.j * vs, *zj = H.kw.Z + (int64_t)s.j * vs;
+        apply_fmm(H, PART_FULL, vj, zj, 1);
+        spmv5(H, zj, H.kw.w, 1);
+        double *d1 = H.kw.dots, *hsum = H.kw.dots + MAXJ;
+        FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * MAXJ, H.stream));
+        for (int pass = 0; pass < 2; ++pass) {
+          mdot(c, s.j + 1, H.kw.V, vs, H.kw.w, d1, hsum);
+          k_mupdate<<<nblk(N), 256, 0, H.stream>>>(N, 1, s.j + 1, H.kw.V, vs, d1, H.kw.w);
+        }
+        FMMPC_LAUNCH_CHECK();
+        FMMPC_CUDA(cudaMemcpyAsync(H.kw.hbuf + MAXJ, hsum, sizeof(double) * (s.j + 1), cudaMemcpyDeviceToHost, H.stream));
+        norm2_async(H, H.kw.w, H.kw.scal + MAXJ, 0);
+      }
+      if (!active) break;
+      sync_all(hs);
+      for (int p = 0; p < np; ++p) {
+        BatchState &s = st[p];
+        if (!s.in_cycle) continue;
+        fmmpc_handle &H = *hs[p];
+        const int j = s.j;
+        const double hn = std::sqrt(std::max(0.0, H.kw.hbuf[0]));
+        double *Hr = s.Hm.data();
+        for (int i = 0; i <= j; ++i) Hr[i * m + j] = H.kw.hbuf[MAXJ + i];
+        Hr[(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hr[i * m + j], b = Hr[(i + 1) * m + j];
+          Hr[i * m + j] = s.cs[i] * a + s.sn[i] * b;
+          Hr[(i + 1) * m + j] = -s.sn[i] * a + s.cs[i] * b;
+        }
+        const double a = Hr[j * m + j], b = Hr[(j + 1) * m + j], rr = std::hypot(a, b);
+        if (rr == 0.0) { s.cs[j] = 1.0; s.sn[j] = 0.0; }
+        else { s.cs[j] = a / rr; s.sn[j] = b / rr; }
+        Hr[j * m + j] = rr;
+        Hr[(j + 1) * m + j] = 0.0;
+        s.g[j + 1] = -s.sn[j] * s.g[j];
+        s.g[j] = s.cs[j] * s.g[j];
+        ++s.iters;
+        ++s.j;
+        const double est = std::fabs(s.g[j + 1]) / s.bn;
+        const bool stop = !std::isfinite(est) || est <= o.rtol || hn == 0.0 || s.iters >= o.maxit || s.j >= m;
+        if (!stop) {
+          const int64_t N = (int64_t)H.g.n * H.g.n, vs = N * H.nrhs_max;
+          double *hy = H.kw.hbuf + 2 * MAXJ;
+          hy[0] = 1.0 / hn;
+          FMMPC_CUDA(cudaMemcpyAsync(H.kw.scal, hy, sizeof(double), cudaMemcpyHostToDevice, H.stream));
+          k_scale<<<nblk(N), 256, 0, H.stream>>>(N, 1, H.kw.scal, H.kw.w, H.kw.V + (int64_t)s.j * vs);
+          FMMPC_LAUNCH_CHECK();
+        } else {
+          // end of this problem's cycle: y from the triangular system, x += Z y
+          s.in_cycle = false;
+          std::fill(s.y.begin(), s.y.end(), 0.0);
+          for (int i = s.j - 1; i >= 0; --i) {
+            double acc = s.g[i];
+            for (int k = i + 1; k < s.j; ++k) acc -= Hr[i * m + k] * s.y[k];
+            s.y[i] = (Hr[i * m + i] != 0.0) ? acc / Hr[i * m + i] : 0.0;
+          }
+          const int64_t N = (int64_t)H.g.n * H.g.n, vs = N * H.nrhs_max;
+          double *hy = H.kw.hbuf + 2 * MAXJ;
+          std::copy(s.y.begin(), s.y.begin() + MAXJ, hy);
+          FMMPC_CUDA(cudaMemcpyAsync(H.kw.scal, hy, sizeof(double) * MAXJ, cudaMemcpyHostToDevice, H.stream));
+          k_maxpy<<<nblk(N), 256, 0, H.stream>>>(N, 1, s.j, H.kw.Z, vs, H.kw.scal, u[p]);
+          FMMPC_LAUNCH_CHECK();
+        }
+      }
+      // the host buffers are reused by the next step: finish the copies issued above
+      sync_all(hs);
+    }
+  }
+  // true residuals
+  for (int p = 0; p < np; ++p) {
+    fmmpc_handle &H = *hs[p];
+    Ctx c{H, (int64_t)H.g.n * H.g.n, 1, H.stream};
+    residual(c, H.kw.b, u[p], H.kw.r);
+    norm2_async(H, H.kw.r, H.kw.dots, 0);
+  }
+  sync_all(hs);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int worst = FMMPC_OK;
+  for (int p = 0; p < np; ++p) {
+    const double rel = std::sqrt(std::max(0.0, hs[p]->kw.hbuf[0])) / st[p].bn;
+    int status = st[p].status;
+    if (!std::isfinite(rel)) status = FMMPC_ERR_NAN;
+    else if (status == FMMPC_OK && rel > o.rtol) status = FMMPC_ERR_NOT_CONVERGED;
+    if (infos) {
+      infos[p].iters = st[p].iters;
+      infos[p].rel_res = rel;
+      infos[p].t_setup_ms = hs[p]->t_setup_ms;
+      infos[p].t_solve_ms = ms;
+      infos[p].status = status;
+    }
+    if (status != FMMPC_OK && worst == FMMPC_OK) worst = status;
+    hs[p]->graphs = saved_graphs[p];
+  }
+  return worst;
+}
+
+}  // namespace fmmpc
