@@ -150,7 +150,8 @@ int fmmpc_solve_host(fmmpc_handle *h, const double *f_host, const double *g_host
  *  0 L (leaf level), 1 leaf side m, 2 #M2L pairs, 3 #P2P pairs, 4 #M2L volume-boundary
  *  pairs, 5 #P2P volume-boundary pairs, 6 N_Gamma, 7 #cells (all levels), 8 #nodes,
  *  9 distinct P2P leaf offsets, 10 kernel launches of the last apply, 11 device bytes
- *  held by the handle. */
+ *  held by the handle, 12 device error flags of the tensor-core kernels (non-zero: a
+ *  bounded wait gave up; synchronises), 13 1 if the near field runs on the tensor cores. */
 int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
 
 /* Copies an internal array of the set-up to host memory dst (bytes = capacity).  what:
@@ -160,6 +161,11 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
  *  cell, boundary cell); 6 volume-boundary P2P list i32 [#][2].  Lists are in canonical
  *  (level, target, source) order.  Errors: _INVALID if bytes is too small. */
 int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
+
+/* Near-field engine: 0 the tensor-core lattice P2P where the grid allows it (8x8 leaves,
+ * at least 128 leaves per row, FP32 or mixed precision: three TF32 products per pair in
+ * FP32 mode, one in the mixed modes), 1 (the default) the CUDA-core kernel. */
+int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 
 /* on = 1 (the default): fmmpc_apply records its kernels once per distinct (r, z, n_rhs)
  * into a CUDA graph on an internal stream and replays it (ordered after and before the

@@ -17,7 +17,8 @@ PREC = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_tf32": 3}
 METHOD = {"cg": 0, "gmres": 1, "fgmres": 2}
 PART = {"full": 0, "vr": 1, "near": 2, "vcol": 3, "q": 4}
 QUERY = {"L": 0, "leaf_side": 1, "n_m2l": 2, "n_p2p": 3, "n_m2l_vb": 4, "n_p2p_vb": 5, "NG": 6,
-         "n_cell": 7, "N": 8, "stencil": 9, "launches": 10, "device_bytes": 11}
+         "n_cell": 7, "N": 8, "stencil": 9, "launches": 10, "device_bytes": 11, "device_errors": 12,
+         "tc_p2p": 13}
 STAGES = ["weights", "upward", "colloc", "bem", "bnd_upward", "m2l", "l2l", "bnd_near", "p2p_l2p"]
 EXPORT = {"keys": 0, "perm": 1, "cell_start": 2, "m2l": 3, "p2p": 4, "m2l_vb": 5, "p2p_vb": 6}
 
@@ -63,6 +64,7 @@ SIGNATURES = {
     "fmmpc_query": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "fmmpc_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
     "fmmpc_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fmmpc_set_p2p_engine": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "fmmpc_near_field_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,

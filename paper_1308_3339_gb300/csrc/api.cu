@@ -95,6 +95,7 @@ void setup(fmmpc_handle &H, const fmmpc_grid &g, const fmmpc_params &p) {
     G.pad = G.R * G.m;
     G.npad = n + 2 * G.pad;
     init_fmm(H);
+    init_tc_p2p(H);
     init_bem(H, tmp);
     FMMPC_CUDA(cudaStreamSynchronize(H.stream));
   } catch (...) {
@@ -310,6 +311,16 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value) {
     case 9: *value = h->st.count; break;
     case 10: *value = h->launches; break;
     case 11: *value = (int64_t)(h->pool.bytes + h->kpool.bytes); break;
+    case 12: {  // device-side error flags of the tensor-core kernels (bounded waits that gave up)
+      int e = 0;
+      if (h->tcp.err) {
+        cudaStreamSynchronize(h->stream);
+        if (cudaMemcpy(&e, h->tcp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FMMPC_ERR_CUDA;
+      }
+      *value = e;
+      break;
+    }
+    case 13: *value = (h->tcp.enabled && h->p2p_engine == 0) ? 1 : 0; break;
     default: return FMMPC_ERR_INVALID;
   }
   return FMMPC_OK;
@@ -336,6 +347,14 @@ int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes) {
     FMMPC_CUDA(cudaStreamSynchronize(h->stream));
     return FMMPC_OK;
   });
+}
+
+int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine) {
+  if (!h || engine < 0 || engine > 1) return FMMPC_ERR_INVALID;
+  h->p2p_engine = engine;
+  for (auto &e : h->gcache) cudaGraphExecDestroy(e.exec);  // captured graphs used the old engine
+  h->gcache.clear();
+  return FMMPC_OK;
 }
 
 int fmmpc_set_graphs(fmmpc_handle *h, int32_t on) {

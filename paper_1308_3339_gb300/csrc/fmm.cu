@@ -914,11 +914,13 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   k_weights<R><<<nblk(N * nrhs), 256, 0, s>>>(g.n, g.npad, g.pad, g.h * g.h, N * nrhs, r, wpad);
   FMMPC_LAUNCH_CHECK();
   ++launches;
+  const bool tc = H.tcp.enabled && H.p2p_engine == 0;
   if (part == PART_NEAR) {
     mark(8);
-    run_p2p<R>(H, H.fb.table_lnh, out, nrhs, s);
+    if (tc) launches += run_p2p_tc(H, r, true, out, nrhs, s);
+    else { run_p2p<R>(H, H.fb.table_lnh, out, nrhs, s); ++launches; }
     mark_end();
-    H.launches = launches + 1;
+    H.launches = launches;
     return;
   }
   const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q;
@@ -971,9 +973,10 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     ++launches;
   }
   mark(8);
-  run_p2p<R>(H, H.fb.table, out, nrhs, s);
+  if (tc) launches += run_p2p_tc(H, r, false, out, nrhs, s);
+  else { run_p2p<R>(H, H.fb.table, out, nrhs, s); ++launches; }
   run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
-  launches += 2;
+  ++launches;
   mark_end();
   H.launches = launches;
 }

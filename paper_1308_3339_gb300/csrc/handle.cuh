@@ -32,6 +32,15 @@ struct FmmBufs {
   double *q = nullptr;       // [nrhs][NG] BEM density
 };
 
+// tensor-core lattice P2P (p2p_tc.cu)
+struct TcP2P {
+  bool enabled = false;
+  int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, smem = 0;
+  int row_oy[33] = {}, row_q0[33] = {}, row_q1[33] = {}, row_ox0[33] = {};
+  float *ahi = nullptr, *alo = nullptr, *bmat = nullptr, *bmat_lnh = nullptr;
+  int *err = nullptr;
+};
+
 struct GraphEntry {
   const double *r;
   double *out;
@@ -70,6 +79,8 @@ struct fmmpc_handle {
   double *Sinv = nullptr;   // [n][4n] first block row of the FP64 inverse of the single-layer matrix
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
+  fmmpc::TcP2P tcp{};
+  int p2p_engine = 1;       // 0: tensor cores where eligible, 1: CUDA cores
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
   static constexpr int NSTAGE = 9;
@@ -92,6 +103,9 @@ void init_bem(fmmpc_handle &H, DevPool &tmp);
 void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs);
 int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs,
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);
+bool tc_p2p_eligible(const fmmpc_handle &H);
+void init_tc_p2p(fmmpc_handle &H);
+int run_p2p_tc(fmmpc_handle &H, const double *r, bool with_lnh, double *out, int nrhs, cudaStream_t s);
 // message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
 int set_global_error(int code, const char *msg);
 int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,

@@ -179,3 +179,23 @@ def test_graph_replay_matches_direct_launches():
     P.set_graphs(True)
     b, c = host(P.apply(r)), host(P.apply(r))  # capture, then replay
     assert np.array_equal(a, b) and np.array_equal(b, c)
+
+
+def test_tensor_core_near_field_matches_oracle():
+    # 1024^2 with 8x8 leaves: 128 leaves per row, the tensor-core P2P runs (3 TF32 products)
+    n = 1024
+    r = S.random_field(n, 21)
+    P = gpu(n, p=10)
+    P.set_p2p_engine("tc")
+    assert P.query("tc_p2p") == 1
+    rd = dev(r)
+    near_tc = host(P.apply_part("near", rd))
+    z_tc = host(P.apply(rd))
+    assert P.query("device_errors") == 0
+    P.set_p2p_engine("simt")
+    assert P.query("tc_p2p") == 0
+    ref = O.Problem(n, p=10).apply(r, "fmm", stages=True)
+    # The tensor core adds each product into the FP32 accumulator with truncation; over a
+    # chain of 37 offsets x 24 MMAs the bias reaches ~888 * 2^-24 ~ 5e-5 of the partial sums.
+    assert rel_l2(near_tc, ref["near"]) < 5e-5
+    assert rel_l2(z_tc, ref["z"]) < FP32_TOL
