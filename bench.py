@@ -39,8 +39,8 @@ SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0  # GB300: SMs, FP32 lanes per SM, max 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--p", type=int, default=10)
@@ -76,10 +76,16 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        # the timed region starts once the sampler is producing lines (at most ~3 s)
+        for _ in range(300):
+            if self.proc.poll() is not None or os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -184,19 +190,68 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def p2p_traffic_record():
-    """DRAM traffic of the P2P kernel from a committed ncu summary, valid only while the
-    kernel source is unchanged (hash of fmm.cu)."""
-    path = os.path.join(ROOT, "profiles", "p2p_traffic.json")
-    src = os.path.join(ROOT, "paper_1308_3339_gb300", "csrc", "fmm.cu")
+def traffic_record(kernel: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, valid only while
+    the kernel's source file is unchanged (its hash is stored beside the figure)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))
+        rec = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, "paper_1308_3339_gb300", "csrc", rec["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("fmm_cu_sha256_16") == h:
+        if rec.get("source_sha256_16") == h:
             return rec
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def rooflines(P, stage_ms):
+    """Roofline of the P2P (tensor cores) and M2L (FP32 CUDA cores) kernels from their
+    live CUDA-event times; the dominant one (larger time) is reported as `roofline`."""
+    m = P.query("leaf_side")
+    pk = load_peaks()
+    out = {}
+    # P2P: one FMA (2 flops) per source-target pair of the near-field lists
+    pairs = P.query("n_p2p") * m ** 4
+    t = stage_ms["p2p"]
+    if P.query("tc_p2p"):
+        if pk:
+            peak, src = pk["bf16_tflops"] * 1.1 / 2.25, (
+                f"measured bf16 burst {pk['bf16_tflops']:.1f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25")
+        else:
+            peak, src = 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
+        out["p2p"] = {"bound": "tensor", "kernel": "k_p2p_tc (lattice P2P, tcgen05 TF32)",
+                      "achieved": 2.0 * pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                      "peak_source": src + "; each FP32-accurate product takes 3 TF32 MMAs (hi*hi, hi*lo, lo*hi)",
+                      "work": f"{pairs:.4e} pairs/launch x 2 flop", "launch_ms": t}
+    else:
+        peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        out["p2p"] = {"bound": "alu", "kernel": "k_p2p_final (lattice P2P + L2P, CUDA cores)",
+                      "achieved": 2.0 * pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                      "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
+                      "work": f"{pairs:.4e} pairs/launch x 2 flop", "launch_ms": t}
+    # M2L: 8 p^2 real flops per (target, source) pair, volume lists plus boundary-to-volume
+    p = P.p
+    m2l_pairs = P.query("n_m2l") + P.query("n_m2l_vb")
+    t = stage_ms["m2l"]
+    peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out["m2l"] = {"bound": "alu", "kernel": "k_m2l_vol (+ k_root_const, 1 block)",
+                  "achieved": 8.0 * p * p * m2l_pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                  "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
+                  "work": f"{m2l_pairs} pairs/launch x 8p^2 flop (p={p})", "launch_ms": t}
+    for k, v in out.items():
+        v["frac"] = v["achieved"] / v["peak"]
+        rec = traffic_record(v["kernel"].split()[0])
+        v["traffic"] = rec["bytes_per_launch"] if rec else None
+    dom = max(out, key=lambda k: out[k]["launch_ms"])
+    return out[dom], out
 
 
 def time_solves(P, fd, reps, rtol=1e-8, graphs=1):
@@ -260,19 +315,7 @@ def run_ours(args):
     value = world * N / (t_apply_max * 1e-3)
     stage_ms = {k: v / args.steps for k, v in stages.items()}
 
-    # roofline of the dominant kernel: the lattice P2P (one FMA per source-target pair)
-    m = P.query("leaf_side")
-    pairs = P.query("n_p2p") * m ** 4
-    t_p2p = stage_ms["p2p_l2p"] * 1e-3
-    mhz = SM_MAX_MHZ
-    peak = SMS * LANES * 2 * mhz * 1e6 / 1e12
-    achieved = 2.0 * pairs / t_p2p / 1e12
-    trec = p2p_traffic_record()
-    roofline = {"bound": "alu", "kernel": "k_p2p_final (lattice P2P + L2P)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": trec["bytes_per_launch"] if trec else None,
-                "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {mhz:.0f} MHz max SM clock",
-                "work": f"{pairs:.3e} pairs/launch x 1 FMA", "launch_ms": stage_ms["p2p_l2p"]}
+    roofline, all_rooflines = rooflines(P, stage_ms)
 
     # end to end through the C ABI with pinned host buffers
     rh = torch.tensor(f, dtype=torch.float64).pin_memory()
@@ -309,7 +352,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_apply_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload(args), "clocks": clk, "e2e": e2e,
-                "gpu_launches": int(launches * args.steps), "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": int(launches * args.steps), "roofline": roofline, "rooflines": all_rooflines,
+                "cpu_baseline": cpu,
                 "time_to_solution": tts, "stage_ms": stage_ms, "timed_wall_s": wall}
         print(json.dumps(line), flush=True)
     if pg is not None:

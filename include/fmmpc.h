@@ -162,9 +162,9 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
  *  (level, target, source) order.  Errors: _INVALID if bytes is too small. */
 int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
 
-/* Near-field engine: 0 the tensor-core lattice P2P where the grid allows it (8x8 leaves,
- * at least 128 leaves per row, FP32 or mixed precision: three TF32 products per pair in
- * FP32 mode, one in the mixed modes), 1 (the default) the CUDA-core kernel. */
+/* Near-field engine: 0 (the default) the tensor-core lattice P2P where the grid allows it
+ * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision: three TF32 products
+ * per pair in FP32 mode, one in the mixed modes), 1 the CUDA-core kernel. */
 int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 
 /* on = 1 (the default): fmmpc_apply records its kernels once per distinct (r, z, n_rhs)
@@ -176,11 +176,12 @@ int fmmpc_set_graphs(fmmpc_handle *h, int32_t on);
 /* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream.
  * fmmpc_set_timing(h, 1) creates the events and turns recording on (0 turns it off).
  * fmmpc_get_timing synchronises the stream and writes the durations in milliseconds of
- * the stages of the last apply into ms[0 .. min(cap, count)), *count = 9 stages:
+ * the stages of the last apply into ms[0 .. min(cap, count)), *count = 10 stages:
  *  0 weight image, 1 P2M + M2M (Sec. 5.3 items 1-2), 2 collocation pass (M2L to boundary
  *  cells, local expansions and near field at the collocation points), 3 BEM solve (FP64),
  *  4 boundary multipoles, 5 M2L (item 3), 6 L2L (item 4), 7 near-boundary element
- *  integrals, 8 P2P near field + L2P + sum (item 5, Eq. e:volume_integral).
+ *  integrals, 8 P2P near field (item 5, Eq. e:volume_integral; with the CUDA-core engine
+ *  this stage also holds L2P and the sum), 9 L2P + sum (tensor-core engine).
  * A stage that did not run reports 0.  Errors: _INVALID if timing is off. */
 int fmmpc_set_timing(fmmpc_handle *h, int32_t on);
 int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);

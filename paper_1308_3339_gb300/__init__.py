@@ -84,7 +84,7 @@ class FmmPreconditioner:
         check(self.lib.fmmpc_export(self._h, _lib.EXPORT[what], a.ctypes.data_as(C.c_void_p), a.nbytes), self._h)
         return a
 
-    def set_p2p_engine(self, engine: str = "simt"):
+    def set_p2p_engine(self, engine: str = "tc"):
         """Near-field engine: "tc" (tensor cores where the grid allows it) or "simt"."""
         check(self.lib.fmmpc_set_p2p_engine(self._h, {"tc": 0, "simt": 1}[engine]), self._h)
 

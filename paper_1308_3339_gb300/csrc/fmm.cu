@@ -915,9 +915,10 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   FMMPC_LAUNCH_CHECK();
   ++launches;
   const bool tc = H.tcp.enabled && H.p2p_engine == 0;
+  if (tc) launches += prep_p2p_tc(H, r, nrhs, s);
   if (part == PART_NEAR) {
     mark(8);
-    if (tc) launches += run_p2p_tc(H, r, true, out, nrhs, s);
+    if (tc) launches += run_p2p_tc(H, true, out, nrhs, s);
     else { run_p2p<R>(H, H.fb.table_lnh, out, nrhs, s); ++launches; }
     mark_end();
     H.launches = launches;
@@ -973,9 +974,15 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     ++launches;
   }
   mark(8);
-  if (tc) launches += run_p2p_tc(H, r, false, out, nrhs, s);
-  else { run_p2p<R>(H, H.fb.table, out, nrhs, s); ++launches; }
-  run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
+  if (tc) {
+    launches += run_p2p_tc(H, false, out, nrhs, s);
+    mark(9);
+    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
+  } else {
+    run_p2p<R>(H, H.fb.table, out, nrhs, s);  // the CUDA-core kernel also evaluates L2P and the sum
+    ++launches;
+    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
+  }
   ++launches;
   mark_end();
   H.launches = launches;

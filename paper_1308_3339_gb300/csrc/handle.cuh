@@ -35,7 +35,7 @@ struct FmmBufs {
 // tensor-core lattice P2P (p2p_tc.cu)
 struct TcP2P {
   bool enabled = false;
-  int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, smem = 0;
+  int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, nofs = 0, smem = 0;
   int row_oy[33] = {}, row_q0[33] = {}, row_q1[33] = {}, row_ox0[33] = {};
   float *ahi = nullptr, *alo = nullptr, *bmat = nullptr, *bmat_lnh = nullptr;
   int *err = nullptr;
@@ -80,10 +80,10 @@ struct fmmpc_handle {
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
   fmmpc::TcP2P tcp{};
-  int p2p_engine = 1;       // 0: tensor cores where eligible, 1: CUDA cores
+  int p2p_engine = 0;       // 0: tensor cores where eligible, 1: CUDA cores
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
-  static constexpr int NSTAGE = 9;
+  static constexpr int NSTAGE = 10;
   bool timing = false;
   cudaEvent_t ev[NSTAGE + 1] = {};
   bool stage_hit[NSTAGE] = {};
@@ -105,7 +105,8 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);
 bool tc_p2p_eligible(const fmmpc_handle &H);
 void init_tc_p2p(fmmpc_handle &H);
-int run_p2p_tc(fmmpc_handle &H, const double *r, bool with_lnh, double *out, int nrhs, cudaStream_t s);
+int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s);
+int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream_t s);
 // message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
 int set_global_error(int code, const char *msg);
 int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,

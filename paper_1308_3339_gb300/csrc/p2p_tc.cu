@@ -5,18 +5,25 @@
 // leaf X + o depends only on their offset, so for each stencil offset o the near field is
 // a matrix product: D[leaf][t] += sum_k W[leaf + o][k] * B_o[t][k], B_o[t][k] = ln|d(t, k, o)|
 // (node units, cell-mean value at d = 0), t, k the 64 nodes of an 8x8 leaf.  One CTA takes
-// 128 consecutive target leaves of one leaf row (M = 128, N = 64, K = 64 per offset) and
-// sweeps the 37 stencil offsets, accumulating in TMEM.  FP32 accuracy from TF32 inputs:
-// each operand is split hi + lo (hi a TF32 number, lo = x - hi) and the product is taken as
-// hi*hi + hi*lo + lo*hi (three MMAs; the lo*lo term is below FP32 rounding).
+// 128 consecutive target leaves of one leaf row (M = 128, N = 64) and sweeps the 37 stencil
+// offsets in two halves of K = 32.  FP32 accuracy from TF32 inputs: each operand is split
+// hi + lo (both TF32 numbers, rounded to nearest) and the product is taken as
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
 //
-// Data: the weights of each padded leaf row are stored as 16 chunks of 4 FP32 values per
-// leaf, leaves contiguous within a chunk, so the 134 leaves a tile needs from one row are
-// 16 contiguous 2144-byte runs -- 1-D bulk copies straight into the canonical K-major
-// layout, and a shift by ox leaves is a 16-byte shift of the descriptor start.  The B_o
-// pairs (hi, lo) are precomputed in the same layout (32 KB per offset).  A producer thread
-// streams rows and offsets into double buffers; one thread issues the MMAs; all four
-// warps read TMEM and write the result.
+// The tensor core truncates when it adds into its FP32 accumulator, so a long chain of
+// MMAs into one accumulator drifts (~2^-24 of the partial sum per MMA).  Each (offset,
+// K half) group therefore starts a fresh accumulator -- the two small correction products
+// first, the hi*hi products last -- and four epilogue warps drain it into per-thread FP32
+// sums with Kahan compensation while the next groups run in the other TMEM buffers (four
+// in flight: the commit-to-barrier round trip is longer than two groups of MMAs).
+//
+// Data: per padded leaf row and K half, each leaf's 32 weights are one 128-byte row in the
+// 128-byte swizzle (chunk c of leaf X at position c ^ (X % 8)), leaves contiguous, so the
+// 134 leaves a tile needs are one 1-D bulk copy straight into the MMA operand layout, and
+// a shift by ox leaves is a 128-byte shift of the descriptor start whose eight-row reads
+// stay free of bank conflicts.  The B_o pairs (hi, lo) are precomputed per K half in the
+// same layout (16 KB per group).  Warp 0 streams strips
+// (two slots) and B groups (eight slots); warp 1 issues the MMAs; warps 2-5 drain TMEM.
 #include <cmath>
 #include <cstring>
 
@@ -30,15 +37,18 @@ namespace {
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 constexpr int TC_TILE = 128;       // target leaves per CTA
-constexpr int TC_BYTES_B = 32768;  // one offset: hi + lo, 64 x 64 FP32 each
+constexpr int TC_BGRP = 16384;     // one (offset, K half) group of B: hi + lo, 64 x 32 FP32 each
+constexpr int TC_NB = 8;           // B stages
+constexpr int TC_NACC = 4;         // TMEM accumulators (64 columns each) in flight
+constexpr int TC_THREADS = 192;    // producer, MMA issuer, four epilogue warps
 constexpr int TC_MAXROWS = 33;
 
 struct TcArgs {
-  const float *ahi, *alo;  // [nrhs][NLY][16][NLX][4]
-  const float *bmat;       // [nofs][hi, lo][16][64][4]
+  const float *ahi, *alo;  // [nrhs][NLY][K half][NLX][32], swizzled per leaf
+  const float *bmat;       // [nofs][K half][hi, lo][64][32], swizzled per row t
   double *out;
   int *err;
-  int n, R, NLX, NLY, NS, nrows, npass;
+  int n, R, NLX, NLY, NS, nrows, nofs, npass;
   int row_oy[TC_MAXROWS], row_q0[TC_MAXROWS], row_q1[TC_MAXROWS], row_ox0[TC_MAXROWS];
 };
 
@@ -56,28 +66,36 @@ __global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int64_t t
   const int64_t N = (int64_t)n * n;
   const int64_t rhs = t / N, q = t - rhs * N;
   const int i = (int)(q % n), j = (int)(q / n);
-  const int X = i / 8 + R, Y = j / 8 + R, k = (j % 8) * 8 + (i % 8);
-  const int64_t idx = (((rhs * NLY + Y) * 16 + k / 4) * NLX + X) * 4 + (k % 4);
+  const int X = i / 8 + R, Y = j / 8 + R, k = (j % 8) * 8 + (i % 8), kk = k % 32;
+  const int64_t idx = (((rhs * NLY + Y) * 2 + k / 32) * NLX + X) * 32 + (((kk / 4) ^ (X & 7)) * 4) + (kk % 4);
   const double w = h2 * r[t];
   const float hi = tf32_round((float)w);
   ahi[idx] = hi;
-  alo[idx] = (float)(w - (double)hi);
+  alo[idx] = tf32_round((float)(w - (double)hi));
 }
 
-__global__ void __launch_bounds__(128, 1) k_p2p_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full_s[2], empty_s[2], full_b[2], empty_b[2], done;
+  __shared__ uint64_t full_s[2], empty_s[2], full_b[TC_NB], empty_b[TC_NB], acc_full[TC_NACC], acc_empty[TC_NACC], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, used_s, used_b;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int SB = 16 * a.NS * 16;  // bytes of one strip (hi or lo)
-  unsigned char *strips = smem;   // [2 buffers][hi, lo][SB]
-  unsigned char *bm = smem + 4 * SB;  // [2 buffers][32 KB]
+  const int SH = (a.NS * 128 + 1023) & ~1023;  // bytes of one K half of a strip (hi or lo)
+  // the swizzle is taken from absolute address bits: operands start on 1024-byte boundaries
+  unsigned char *strips = smem + ((1024u - (tc::smem_addr(smem) & 1023u)) & 1023u);  // [2][hi, lo][SH]
+  unsigned char *bm = strips + 4 * SH;                                                 // [TC_NB][TC_BGRP]
   const int lx0 = blockIdx.x * TC_TILE, ly = blockIdx.y, rhs = blockIdx.z;
+  const int nunits = 2 * a.nrows, ngroups = 2 * a.nofs;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&full_s[b], 1);
       tc::mbar_init(&empty_s[b], 1);
+    }
+    for (int b = 0; b < TC_NACC; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 4);
+    }
+    for (int b = 0; b < TC_NB; ++b) {
       tc::mbar_init(&full_b[b], 1);
       tc::mbar_init(&empty_b[b], 1);
     }
@@ -87,112 +105,156 @@ __global__ void __launch_bounds__(128, 1) k_p2p_tc(TcArgs a) {
     used_s = 0;
     used_b = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 64);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 64 * TC_NACC);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  const int64_t rhs_off = (int64_t)rhs * a.NLY * 16 * a.NLX * 4;
+  const int64_t rhs_off = (int64_t)rhs * a.NLY * 2 * a.NLX * 32;
   int issued_s = 0, issued_b = 0;
-  if (warp == 0 && lane == 0) {
-    // producer: weight rows of the stencil, then the B pairs of that row's offsets
-    int boff = 0;
-    for (int r = 0; r < a.nrows && !abort_flag; ++r) {
-      const int sb = r & 1;
-      if (r >= 2 && !tc::mbar_wait(&empty_s[sb], ((r >> 1) - 1) & 1, &abort_flag)) break;
-      tc::mbar_expect_tx(&full_s[sb], 2 * SB);
-      const int64_t Y = ly + a.R + a.row_oy[r];
-      for (int hl = 0; hl < 2; ++hl) {
-        const float *src = (hl ? a.alo : a.ahi) + rhs_off;
-        unsigned char *dst = strips + (sb * 2 + hl) * SB;
-        for (int c = 0; c < 16; ++c)
-          tc::bulk_g2s(dst + c * a.NS * 16, src + ((Y * 16 + c) * a.NLX + lx0) * 4, a.NS * 16, &full_s[sb]);
-      }
-      issued_s = r + 1;
-      bool stop = false;
-      for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
-        const int bi = boff & 1;
-        if (boff >= 2 && !tc::mbar_wait(&empty_b[bi], ((boff >> 1) - 1) & 1, &abort_flag)) { stop = true; break; }
-        tc::mbar_expect_tx(&full_b[bi], TC_BYTES_B);
-        tc::bulk_g2s(bm + bi * TC_BYTES_B, a.bmat + (int64_t)q * (TC_BYTES_B / 4), TC_BYTES_B, &full_b[bi]);
-        issued_b = ++boff;
-      }
-      if (stop) break;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = tc::idesc_tf32(128, 64);
-    int boff = 0;
-    bool first = true, ok = true;
-    for (int r = 0; r < a.nrows && ok; ++r) {
-      const int sb = r & 1;
-      if (!tc::mbar_wait(&full_s[sb], (r >> 1) & 1, &abort_flag)) { ok = false; break; }
-      used_s = r + 1;
-      tc::fence_after();
-      const uint32_t sh = tc::smem_addr(strips + (sb * 2) * SB), sl = tc::smem_addr(strips + (sb * 2 + 1) * SB);
-      for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
-        const int bi = boff & 1;
-        if (!tc::mbar_wait(&full_b[bi], (boff >> 1) & 1, &abort_flag)) { ok = false; break; }
-        used_b = boff + 1;
-        tc::fence_after();
-        const int ox = a.row_ox0[r] + (q - a.row_q0[r]);
-        const uint32_t bh = tc::smem_addr(bm + bi * TC_BYTES_B), bl = bh + TC_BYTES_B / 2;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const uint32_t aoff = (uint32_t)((2 * s * a.NS + a.R + ox) * 16);
-          const uint64_t ahd = tc::desc_kmajor(sh + aoff, a.NS * 16, 128);
-          const uint64_t bhd = tc::desc_kmajor(bh + s * 2048, 1024, 128);
-          tc::mma_tf32(tmem, ahd, bhd, idesc, first ? 0u : 1u);
-          first = false;
-          if (a.npass == 3) {
-            const uint64_t ald = tc::desc_kmajor(sl + aoff, a.NS * 16, 128);
-            const uint64_t bld = tc::desc_kmajor(bl + s * 2048, 1024, 128);
-            tc::mma_tf32(tmem, ahd, bld, idesc, 1u);
-            tc::mma_tf32(tmem, ald, bhd, idesc, 1u);
-          }
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: per (stencil row, K half) the weight strip, then that row's B groups
+      int g = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok && !abort_flag; ++u) {
+        const int r = u >> 1, kh = u & 1, slot = u & 1;
+        if (u >= 2 && !tc::mbar_wait(&empty_s[slot], ((u >> 1) - 1) & 1, &abort_flag)) { ok = false; break; }
+        tc::mbar_expect_tx(&full_s[slot], 2 * a.NS * 128);
+        const int64_t Y = ly + a.R + a.row_oy[r];
+        const int64_t off = rhs_off + ((Y * 2 + kh) * a.NLX + lx0) * 32;
+        tc::bulk_g2s(strips + (slot * 2) * SH, a.ahi + off, a.NS * 128, &full_s[slot]);
+        tc::bulk_g2s(strips + (slot * 2 + 1) * SH, a.alo + off, a.NS * 128, &full_s[slot]);
+        issued_s = u + 1;
+        for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
+          const int bi = g % TC_NB;
+          if (g >= TC_NB && !tc::mbar_wait(&empty_b[bi], ((g / TC_NB) - 1) & 1, &abort_flag)) { ok = false; break; }
+          tc::mbar_expect_tx(&full_b[bi], TC_BGRP);
+          tc::bulk_g2s(bm + bi * TC_BGRP, a.bmat + ((int64_t)q * 2 + kh) * (TC_BGRP / 4), TC_BGRP, &full_b[bi]);
+          issued_b = ++g;
         }
-        tc::commit(&empty_b[bi]);
-        ++boff;
       }
-      tc::commit(&empty_s[sb]);
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(a.err, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: one fresh accumulator per (offset, K half) group, alternating buffers
+      const uint32_t idesc = tc::idesc_tf32(128, 64);
+      int g = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        const int r = u >> 1, slot = u & 1;
+        if (!tc::mbar_wait(&full_s[slot], (u >> 1) & 1, &abort_flag)) { ok = false; break; }
+        used_s = u + 1;
+        tc::fence_after();
+        const uint32_t sh = tc::smem_addr(strips + (slot * 2) * SH), sl = tc::smem_addr(strips + (slot * 2 + 1) * SH);
+        for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
+          const int bi = g % TC_NB, ab = g % TC_NACC;
+          if (!tc::mbar_wait(&full_b[bi], (g / TC_NB) & 1, &abort_flag)) { ok = false; break; }
+          used_b = g + 1;
+          if (g >= TC_NACC && !tc::mbar_wait(&acc_empty[ab], ((g / TC_NACC) - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const int ox = a.row_ox0[r] + (q - a.row_q0[r]);
+          const uint32_t bh = tc::smem_addr(bm + bi * TC_BGRP), bl = bh + TC_BGRP / 2;
+          const uint32_t d = tmem + 64 * ab;
+          uint32_t acc = 0;
+          const uint32_t arow = sh + (uint32_t)((a.R + ox) * 128), lrow = sl + (uint32_t)((a.R + ox) * 128);
+          if (a.npass == 3) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              tc::mma_tf32(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bl + 32 * s), idesc, acc);
+              acc = 1;
+              tc::mma_tf32(d, tc::desc_sw128(lrow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, 1u);
+            }
+          }
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            tc::mma_tf32(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, acc);
+            acc = 1;
+          }
+          tc::commit(&acc_full[ab]);  // the epilogue also releases the B and strip slots
+          ++g;
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(a.err, 1);
+      }
+      tc::commit(&done);  // completes when every MMA issued above has finished
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one target leaf per thread
+    const int qd = warp & 3;
+    float sum[64], cmp[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) sum[i] = cmp[i] = 0.0f;
+    bool ok = true;
+    int u = 0, uend = a.row_q1[0] - a.row_q0[0];  // groups of the current strip unit end at uend
+    for (int g = 0; g < ngroups; ++g) {
+      const int ab = g % TC_NACC;
+      if (!tc::mbar_wait(&acc_full[ab], (g / TC_NACC) & 1, &abort_flag)) { ok = false; break; }
+      if (warp == 2 && lane == 0) {
+        // the group's MMAs have completed: its B slot, and at a unit's end the strip slot, are free
+        tc::mbar_arrive(&empty_b[g % TC_NB]);
+        if (g + 1 == uend) tc::mbar_arrive(&empty_s[u & 1]);
+      }
+      if (g + 1 == uend && ++u < nunits) uend += a.row_q1[u >> 1] - a.row_q0[u >> 1];
+      tc::fence_after();
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * ab + 32 * hf, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float y = v[i] - cmp[32 * hf + i];
+          const float t = sum[32 * hf + i] + y;
+          cmp[32 * hf + i] = (t - sum[32 * hf + i]) - y;
+          sum[32 * hf + i] = t;
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[ab]);
     }
     if (!ok) {
       abort_flag = 1;
-      atomicOr(a.err, 1);
+      if (lane == 0) atomicOr(a.err, 2);
     }
-    tc::commit(&done);  // completes when every MMA issued above has finished
+    if (ok && !abort_flag) {
+      const int X = lx0 + 32 * qd + lane;
+      double *o = a.out + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
+      const double sc = -1.0 / (2.0 * PI);
+#pragma unroll
+      for (int tr = 0; tr < 8; ++tr) {
+        double2 *orow = reinterpret_cast<double2 *>(o + (int64_t)tr * a.n);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int t0 = 8 * tr + 2 * c;
+          orow[c] = make_double2(sc * ((double)sum[t0] - (double)cmp[t0]), sc * ((double)sum[t0 + 1] - (double)cmp[t0 + 1]));
+        }
+      }
+    }
   }
   __syncwarp();
   const bool finished = tc::mbar_wait(&done, 0, nullptr);
-  __syncwarp();
-  tc::fence_after();
-  if (finished && !abort_flag) {
-    const int X = lx0 + 32 * warp + lane;
-    double *o = a.out + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const int t = c0 + jj;
-        o[(int64_t)(t / 8) * a.n + (t % 8)] = -(double)v[jj] / (2.0 * PI);
-      }
-    }
-  } else if (!finished && lane == 0) {
-    atomicOr(a.err, 2);
-  }
+  if (!finished && lane == 0) atomicOr(a.err, 4);
   tc::fence_before();
   __syncthreads();
   if (abort_flag && warp == 0 && lane == 0) {
     // drain bulk copies that were issued but never consumed (bounded waits)
     for (int u = used_s; u < issued_s; ++u) tc::mbar_wait(&full_s[u & 1], (u >> 1) & 1, nullptr);
-    for (int u = used_b; u < issued_b; ++u) tc::mbar_wait(&full_b[u & 1], (u >> 1) & 1, nullptr);
+    for (int u = used_b; u < issued_b; ++u) tc::mbar_wait(&full_b[u % TC_NB], (u / TC_NB) & 1, nullptr);
   }
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, 64);
+    tc::tmem_dealloc(tmem, 64 * TC_NACC);
   }
 }
 
@@ -226,7 +288,7 @@ void init_tc_p2p(fmmpc_handle &H) {
   H.tcp.NLY = NL;
   H.tcp.NS = TC_TILE + 2 * g.R;
   H.tcp.npass = (H.prec == FMMPC_PREC_FP32) ? 3 : 1;
-  const size_t strip_floats = (size_t)H.nrhs_max * NL * 16 * NL * 4;
+  const size_t strip_floats = (size_t)H.nrhs_max * NL * 2 * NL * 32;
   H.tcp.ahi = H.pool.get<float>(strip_floats);
   H.tcp.alo = H.pool.get<float>(strip_floats);
   FMMPC_CUDA(cudaMemsetAsync(H.tcp.ahi, 0, sizeof(float) * strip_floats, H.stream));
@@ -252,20 +314,22 @@ void init_tc_p2p(fmmpc_handle &H) {
   }
   const double cself = -0.5 * std::log(2.0) - 1.5 + 0.25 * PI;
   for (int variant = 0; variant < 2; ++variant) {
-    std::vector<float> B((size_t)nofs * (TC_BYTES_B / 4), 0.0f);
+    // group (q, K half): [hi: 64 rows t][32 k] swizzled, then [lo: same]
+    std::vector<float> B((size_t)nofs * 2 * (TC_BGRP / 4), 0.0f);
     for (int r = 0; r < H.tcp.nrows; ++r)
       for (int q = q0s[r]; q < q1s[r]; ++q) {
         const int ox = ox0s[r] + (q - q0s[r]), oy = oys[r];
-        float *Bq = B.data() + (size_t)q * (TC_BYTES_B / 4);
         for (int t = 0; t < 64; ++t)
           for (int k = 0; k < 64; ++k) {
             const int dx = (t % 8) - (k % 8) - 8 * ox, dy = (t / 8) - (k / 8) - 8 * oy;
             double v = (dx == 0 && dy == 0) ? cself : 0.5 * std::log((double)dx * dx + (double)dy * dy);
             if (variant) v += g.lnh;
             const float hi = tf32_round_host(v);
-            const size_t e = ((size_t)(k / 4) * 64 + t) * 4 + (k % 4);
-            Bq[e] = hi;
-            Bq[TC_BYTES_B / 8 + e] = (float)(v - (double)hi);
+            const int kh = k / 32, kk = k % 32;
+            float *Bg = B.data() + ((size_t)q * 2 + kh) * (TC_BGRP / 4);
+            const size_t e = (size_t)t * 32 + (((kk / 4) ^ (t & 7)) * 4) + (kk % 4);
+            Bg[e] = hi;
+            Bg[TC_BGRP / 8 + e] = tf32_round_host(v - (double)hi);
           }
       }
     float *dB = H.pool.get<float>(B.size());
@@ -273,19 +337,26 @@ void init_tc_p2p(fmmpc_handle &H) {
     FMMPC_CUDA(cudaStreamSynchronize(H.stream));
     (variant ? H.tcp.bmat_lnh : H.tcp.bmat) = dB;
   }
+  H.tcp.nofs = nofs;
   H.tcp.err = H.pool.get<int>(1);
   FMMPC_CUDA(cudaMemsetAsync(H.tcp.err, 0, sizeof(int), H.stream));
-  const int smem = 4 * 16 * H.tcp.NS * 16 + 2 * TC_BYTES_B;
+  const int smem = 4 * ((H.tcp.NS * 128 + 1023) & ~1023) + TC_NB * TC_BGRP + 1024;  // + alignment slack
   FMMPC_CUDA(cudaFuncSetAttribute(k_p2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   H.tcp.smem = smem;
 }
 
-// out[...] = -near / (2 pi) on the tensor cores; r is the FP64 right-hand side.
-int run_p2p_tc(fmmpc_handle &H, const double *r, bool with_lnh, double *out, int nrhs, cudaStream_t s) {
+// TF32 hi/lo weight strips of the right-hand side r (FP64), for run_p2p_tc.
+int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s) {
   const Geo &g = H.g;
   const int64_t total = (int64_t)g.n * g.n * nrhs;
   k_tc_strips<<<nblk(total), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, total, r, H.tcp.ahi, H.tcp.alo);
   FMMPC_LAUNCH_CHECK();
+  return 1;
+}
+
+// out[...] = -near / (2 pi) on the tensor cores, from the strips prep_p2p_tc wrote.
+int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream_t s) {
+  const Geo &g = H.g;
   TcArgs a{};
   a.ahi = H.tcp.ahi;
   a.alo = H.tcp.alo;
@@ -298,6 +369,7 @@ int run_p2p_tc(fmmpc_handle &H, const double *r, bool with_lnh, double *out, int
   a.NLY = H.tcp.NLY;
   a.NS = H.tcp.NS;
   a.nrows = H.tcp.nrows;
+  a.nofs = H.tcp.nofs;
   a.npass = H.tcp.npass;
   for (int i = 0; i < a.nrows; ++i) {
     a.row_oy[i] = H.tcp.row_oy[i];
@@ -306,9 +378,9 @@ int run_p2p_tc(fmmpc_handle &H, const double *r, bool with_lnh, double *out, int
     a.row_ox0[i] = H.tcp.row_ox0[i];
   }
   dim3 grid((1 << g.L) / TC_TILE, 1 << g.L, nrhs);
-  k_p2p_tc<<<grid, 128, H.tcp.smem, s>>>(a);
+  k_p2p_tc<<<grid, TC_THREADS, H.tcp.smem, s>>>(a);
   FMMPC_LAUNCH_CHECK();
-  return 2;
+  return 1;
 }
 
 }  // namespace fmmpc

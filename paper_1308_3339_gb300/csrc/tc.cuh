@@ -1,9 +1,10 @@
 // Thin wrappers over the sm_103a tensor-core and asynchronous-copy instructions used by
 // the tensor-core kernels: tcgen05 (MMA with TMEM accumulators), mbarrier, 1-D bulk copies.
 //
-// Shared-memory operand descriptor (no swizzle, K-major): bits 0-13 start address >> 4,
-// 16-29 leading byte offset >> 4 (distance between 8x16-byte core matrices along K),
-// 32-45 stride byte offset >> 4 (distance between 8-row groups along M or N), bits 46-47 = 1.
+// Shared-memory operand descriptor (K-major): bits 0-13 start address >> 4, 16-29 leading
+// byte offset >> 4 (no swizzle: distance between 8x16-byte core matrices along K), 32-45
+// stride byte offset >> 4 (distance between 8-row groups along M or N), bits 46-48 = 0b001,
+// 49-51 base offset, 61-63 swizzle mode (0 none, 2 128-byte).
 // Instruction descriptor: bits 4-5 accumulator format (1 = F32), 7-9 / 10-12 A / B format
 // (2 = TF32 for kind::tf32), 15 / 16 A / B major (0 = K-major), 17-22 N >> 3, 24-28 M >> 4.
 // Every wait is bounded: it gives up after a fixed number of polls and reports failure.
@@ -22,6 +23,21 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t lbo_byt
   d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// K-major operand in the 128-byte swizzle: rows of 128 bytes (32 TF32 values of K), the
+// 16-byte chunk c of row r stored at chunk position c ^ (r % 8).  The swizzle is applied to
+// absolute shared-memory address bits, so with the base-offset field left at 0 the start may
+// be any row of a 1024-byte-aligned buffer (and advanced by 32 bytes per K step of 8);
+// sbo = 1024, the distance between 8-row groups.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                   // leading byte offset: unused in this mode
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
   return d;
 }
 
@@ -84,16 +100,50 @@ __device__ __forceinline__ bool mbar_test(uint64_t *mbar, uint32_t parity) {
   return r != 0;
 }
 
-// Polls the barrier phase with the given parity; false after ~max_polls polls or when
-// *abort becomes non-zero (another thread of the block gave up).
+// Suspends until the phase with the given parity completes or about hint_ns elapse.
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(smem_addr(mbar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return r != 0;
+}
+
+// Waits for the barrier phase with the given parity; false after max_tries suspended
+// tries of ~4 us (about a second) or when *abort becomes non-zero (another thread of the
+// block gave up).  try_wait sleeps in hardware instead of spinning on shared memory, which
+// would take bandwidth from the tensor core's operand reads.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, volatile int *abort,
-                                          int max_polls = 1 << 22) {
-  for (int i = 0; i < max_polls; ++i) {
-    if (mbar_test(mbar, parity)) return true;
+                                          int max_tries = 1 << 18) {
+  for (int i = 0; i < max_tries; ++i) {
+    if (mbar_try(mbar, parity, 4000u)) return true;
     if (abort && *abort) return false;
-    if (i > 64) __nanosleep(32);
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns per thread (warp-wide), then wait; the wait is
+// in the same statement so no use of the registers can be scheduled before it
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 1-D bulk copy global -> shared, completion counted in bytes on mbar (16-byte aligned
