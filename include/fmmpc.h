@@ -48,6 +48,10 @@ extern "C" {
 #define FMMPC_PREC_FP32 1       /* FMM in FP32 on CUDA cores (plain FP32 form) */
 #define FMMPC_PREC_MIXED_BF16 2 /* FP32 P2P/expansions, M2L on tensor cores in BF16, FP32 accumulate */
 #define FMMPC_PREC_MIXED_TF32 3 /* FP32 P2P/expansions, M2L on tensor cores in TF32, FP32 accumulate */
+/* In the mixed forms the volume-to-volume M2L (Sec. 5.3 item 3) of every level >= 2 runs as
+ * a lattice convolution on the tensor cores: the leading multipoles and their translation
+ * columns are split hi + lo, so the apply stays within ~1e-4 of the FP64 FMM (p <= 15;
+ * larger p keeps the FP32 CUDA-core M2L).  Boundary-source M2L stays on CUDA cores. */
 
 #define FMMPC_CG 0
 #define FMMPC_GMRES 1
@@ -151,7 +155,8 @@ int fmmpc_solve_host(fmmpc_handle *h, const double *f_host, const double *g_host
  *  pairs, 5 #P2P volume-boundary pairs, 6 N_Gamma, 7 #cells (all levels), 8 #nodes,
  *  9 distinct P2P leaf offsets, 10 kernel launches of the last apply, 11 device bytes
  *  held by the handle, 12 device error flags of the tensor-core kernels (non-zero: a
- *  bounded wait gave up; synchronises), 13 1 if the near field runs on the tensor cores. */
+ *  bounded wait gave up; bits 0-7 P2P, 8-15 M2L; synchronises), 13 1 if the near field
+ *  runs on the tensor cores, 14 tensor-core M2L: 0 off, 1 TF32, 2 BF16. */
 int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
 
 /* Copies an internal array of the set-up to host memory dst (bytes = capacity).  what:
@@ -163,8 +168,8 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
 int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
 
 /* Near-field engine: 0 (the default) the tensor-core lattice P2P where the grid allows it
- * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision: three TF32 products
- * per pair in FP32 mode, one in the mixed modes), 1 the CUDA-core kernel. */
+ * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision; three TF32 products
+ * per pair, FP32-accurate in every single-precision form), 1 the CUDA-core kernel. */
 int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 
 /* on = 1 (the default): fmmpc_apply records its kernels once per distinct (r, z, n_rhs)

@@ -49,8 +49,6 @@ void setup(fmmpc_handle &H, const fmmpc_grid &g, const fmmpc_params &p) {
   require(p.theta > 0.0 && p.theta < 1.0, "params: 0 < theta < 1");
   require(p.n_rhs >= 1 && p.n_rhs <= 64, "params: 1 <= n_rhs <= 64");
   require(p.precision >= FMMPC_PREC_FP64 && p.precision <= FMMPC_PREC_MIXED_TF32, "params: unknown precision");
-  if (p.precision == FMMPC_PREC_MIXED_BF16 || p.precision == FMMPC_PREC_MIXED_TF32)
-    throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L forms are not built in this library version");
   // leaf level: split at the centre lines while a cell holds more than leaf_max nodes
   const int n = g.nx;
   int L = 0, s = n;
@@ -96,6 +94,7 @@ void setup(fmmpc_handle &H, const fmmpc_grid &g, const fmmpc_params &p) {
     G.npad = n + 2 * G.pad;
     init_fmm(H);
     init_tc_p2p(H);
+    init_tc_m2l(H, tmp);
     init_bem(H, tmp);
     FMMPC_CUDA(cudaStreamSynchronize(H.stream));
   } catch (...) {
@@ -312,15 +311,17 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value) {
     case 10: *value = h->launches; break;
     case 11: *value = (int64_t)(h->pool.bytes + h->kpool.bytes); break;
     case 12: {  // device-side error flags of the tensor-core kernels (bounded waits that gave up)
-      int e = 0;
-      if (h->tcp.err) {
-        cudaStreamSynchronize(h->stream);
-        if (cudaMemcpy(&e, h->tcp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FMMPC_ERR_CUDA;
-      }
-      *value = e;
+      int e = 0, e2 = 0;
+      cudaStreamSynchronize(h->stream);
+      if (h->tcp.err && cudaMemcpy(&e, h->tcp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FMMPC_ERR_CUDA;
+      if (h->tcm.err && cudaMemcpy(&e2, h->tcm.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FMMPC_ERR_CUDA;
+      *value = e | (e2 << 8);
       break;
     }
     case 13: *value = (h->tcp.enabled && h->p2p_engine == 0) ? 1 : 0; break;
+    case 14: *value = h->tcm.enabled ? (h->tcm.kind == 0 ? 1 : 2) : 0; break;
     default: return FMMPC_ERR_INVALID;
   }
   return FMMPC_OK;

@@ -20,6 +20,8 @@
 #include <complex>
 #include <mutex>
 
+#include <type_traits>
+
 #include "handle.cuh"
 
 namespace fmmpc {
@@ -292,17 +294,20 @@ __device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__r
 
 // Volume targets: warp per (cell, rhs).  do_vol: volume sources from the M2L list;
 // do_bnd: boundary sources from the volume-boundary list; add: accumulate into L.
+// cells (optional): only the listed cells (ntgt of them) instead of all ncell.
 template <typename R, int P>
 __global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, int do_vol, int do_bnd, int add,
                           const int32_t *__restrict__ first, const int32_t *__restrict__ src,
                           const int32_t *__restrict__ bfirst, const int32_t *__restrict__ bsrc,
                           const cpx<R> *__restrict__ Mv, const cpx<R> *__restrict__ Mb,
-                          cpx<R> *__restrict__ Lv) {
+                          cpx<R> *__restrict__ Lv, const int32_t *__restrict__ cells = nullptr,
+                          int64_t ntgt = 0) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= ncell * nrhs) return;
-  const int rhs = (int)(wid / ncell);
-  const int64_t gidx = wid % ncell;
+  const int64_t nt = cells ? ntgt : ncell;
+  if (wid >= nt * nrhs) return;
+  const int rhs = (int)(wid / nt);
+  const int64_t gidx = cells ? (int64_t)cells[wid % nt] : wid % nt;
   int l = 0;
   while (level_offset(l + 1) <= gidx) ++l;
   const uint32_t c = (uint32_t)(gidx - level_offset(l));
@@ -958,12 +963,24 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     ++launches;
   }
   mark(5);
-  k_m2l_vol<R, P><<<nblk(g.ncell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, 1, with_bnd ? 1 : 0, 0,
-                                                           Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src,
-                                                           Mv, Mb, Lv);
+  if (std::is_same<R, float>::value && H.tcm.enabled) {
+    // volume-to-volume M2L on the tensor cores (mixed forms); boundary sources added after
+    launches += run_m2l_tc(H, Mv, Lv, nrhs, s);
+    if (with_bnd && Ls.n_vbv_cells > 0) {
+      k_m2l_vol<R, P><<<nblk(Ls.n_vbv_cells * nrhs * 32), 256, 0, s>>>(
+          gd, g.ncell, g.nbcell, nrhs, 0, 1, 1, Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src, Mv, Mb, Lv,
+          Ls.vbv_cells, Ls.n_vbv_cells);
+      ++launches;
+    }
+  } else {
+    k_m2l_vol<R, P><<<nblk(g.ncell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, 1, with_bnd ? 1 : 0, 0,
+                                                             Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src,
+                                                             Mv, Mb, Lv);
+    ++launches;
+  }
   k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);
   FMMPC_LAUNCH_CHECK();
-  launches += 2;
+  launches += 1;
   mark(6);
   launches += run_l2l<R, P>(H, nrhs, s);
   if (with_bnd && Ls.nbnear > 0) {

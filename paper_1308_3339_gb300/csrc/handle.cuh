@@ -41,6 +41,21 @@ struct TcP2P {
   int *err = nullptr;
 };
 
+// tensor-core M2L for the mixed-precision forms (m2l_tc.cu)
+struct TcM2L {
+  bool enabled = false;
+  int kind = 0;  // 0 TF32, 1 BF16
+  int nsplit = 0;  // leading multipoles split hi + lo
+  int ntiles = 0, stage_bytes = 0, smem = 0, nofs_total = 0;
+  int ngroups[4] = {}, goff[4] = {}, ooff[4] = {};
+  int64_t rows_per_rhs = 0;
+  int64_t lev_row0[24] = {};
+  int lev_P[24] = {};
+  unsigned char *img = nullptr, *bmat = nullptr;
+  int4 *tiles = nullptr, *groups = nullptr;
+  int *dxs = nullptr, *err = nullptr;
+};
+
 struct GraphEntry {
   const double *r;
   double *out;
@@ -80,6 +95,7 @@ struct fmmpc_handle {
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
   fmmpc::TcP2P tcp{};
+  fmmpc::TcM2L tcm{};
   int p2p_engine = 0;       // 0: tensor cores where eligible, 1: CUDA cores
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
@@ -106,6 +122,9 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
 bool tc_p2p_eligible(const fmmpc_handle &H);
 void init_tc_p2p(fmmpc_handle &H);
 int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s);
+bool tc_m2l_eligible(const fmmpc_handle &H);
+void init_tc_m2l(fmmpc_handle &H, DevPool &tmp);
+int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t s);
 int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream_t s);
 // message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
 int set_global_error(int code, const char *msg);

@@ -198,7 +198,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
     int u = 0, uend = a.row_q1[0] - a.row_q0[0];  // groups of the current strip unit end at uend
     for (int g = 0; g < ngroups; ++g) {
       const int ab = g % TC_NACC;
-      if (!tc::mbar_wait(&acc_full[ab], (g / TC_NACC) & 1, &abort_flag)) { ok = false; break; }
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[ab], (g / TC_NACC) & 1, &abort_flag))) {
+        ok = false;  // warp-uniform: the TMEM loads below are warp-collective
+        break;
+      }
       if (warp == 2 && lane == 0) {
         // the group's MMAs have completed: its B slot, and at a unit's end the strip slot, are free
         tc::mbar_arrive(&empty_b[g % TC_NB]);
@@ -287,7 +290,7 @@ void init_tc_p2p(fmmpc_handle &H) {
   H.tcp.NLX = NL;
   H.tcp.NLY = NL;
   H.tcp.NS = TC_TILE + 2 * g.R;
-  H.tcp.npass = (H.prec == FMMPC_PREC_FP32) ? 3 : 1;
+  H.tcp.npass = 3;  // the near field stays FP32-accurate in every single-precision form
   const size_t strip_floats = (size_t)H.nrhs_max * NL * 2 * NL * 32;
   H.tcp.ahi = H.pool.get<float>(strip_floats);
   H.tcp.alo = H.pool.get<float>(strip_floats);

@@ -281,6 +281,19 @@ void build_lists(const Geo &g, Lists &Ls, Stencil &st, cudaStream_t s, DevPool &
   Ls.vbv_first = pool.get<int32_t>(g.ncell + 1);
   Ls.vbv_src = pool.get<int32_t>(nvb + 1);
   build_csr(Ls.m2l_vb, nvb, 3, 1, 0, 0, 2, g.ncell, Ls.vbv_first, Ls.vbv_src, s, tmp);
+  {
+    // the volume cells that have boundary M2L sources, for passes that only add those
+    std::vector<int32_t> hf(g.ncell + 1), cells;
+    FMMPC_CUDA(cudaMemcpyAsync(hf.data(), Ls.vbv_first, sizeof(int32_t) * (g.ncell + 1), cudaMemcpyDeviceToHost, s));
+    FMMPC_CUDA(cudaStreamSynchronize(s));
+    for (int64_t c = 0; c < g.ncell; ++c)
+      if (hf[c + 1] > hf[c]) cells.push_back((int32_t)c);
+    Ls.n_vbv_cells = (int64_t)cells.size();
+    Ls.vbv_cells = pool.get<int32_t>(cells.size() + 1);
+    if (!cells.empty())
+      FMMPC_CUDA(cudaMemcpyAsync(Ls.vbv_cells, cells.data(), sizeof(int32_t) * cells.size(), cudaMemcpyHostToDevice, s));
+    FMMPC_CUDA(cudaStreamSynchronize(s));
+  }
   // regroup the volume-boundary lists by boundary target for the collocation pass
   {
     uint64_t *sw = tmp.get<uint64_t>(nvb + 1);

@@ -1,0 +1,112 @@
+"""Mixed-precision forms: FP32 FMM with the M2L on the tensor cores (TF32 or BF16 operands,
+FP32 accumulation) inside the FP64 Krylov solve, against the FP64 oracle.
+
+Error bars.  Rounding both operands of every M2L product to TF32 (unit roundoff 2^-11) or
+BF16 (2^-8 relative spacing, 2^-9 roundoff) perturbs each local-expansion term by about
+sqrt(2) u; the far field is a sum of ~111 such translations per cell and level, and it is a
+fraction of z, so the error of z stays at or below ~u.  The gates are u itself: 5e-4 for
+TF32 and 2e-3 for BF16 (the BF16 bar against the direct sum).  The Krylov recurrences stay
+FP64, so a solve still reaches its relative residual and the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth_inputs as S
+from conftest import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"mixed_tf32": 5e-4, "mixed_bf16": 2e-3}
+KIND = {"mixed_tf32": 1, "mixed_bf16": 2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu(n, **kw):
+    from paper_1308_3339_gb300 import FmmPreconditioner
+    return FmmPreconditioner(n, **kw)
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda").contiguous()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+@pytest.mark.parametrize("n", [64, 256, 1024])
+def test_mixed_apply_matches_fp64_fmm(prec, n):
+    r = S.gaussian_mixture(n, 0)
+    P = gpu(n, p=10, precision=prec)
+    assert P.query("tc_m2l") == KIND[prec]
+    z = host(P.apply(dev(r)))
+    assert P.query("device_errors") == 0
+    ref = O.Problem(n, p=10).apply(r, "fmm", stages=True)["z"]
+    assert rel_l2(z, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_mixed_apply_matches_direct_sum(prec):
+    n = 128
+    r = S.random_field(n, 4)
+    P = gpu(n, p=10, precision=prec)
+    z = host(P.apply(dev(r)))
+    ref = O.Problem(n, p=10).apply(r, "direct")
+    assert rel_l2(z, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_mixed_tensor_core_m2l_is_close_to_fp32_m2l(prec):
+    # same FP32 expansions; only the M2L operands are rounded
+    n = 512
+    r = dev(S.random_field(n, 8))
+    z = host(gpu(n, p=10, precision=prec).apply(r))
+    z32 = host(gpu(n, p=10, precision="fp32").apply(r))
+    assert rel_l2(z, z32) < TOL[prec]
+    assert rel_l2(z, z32) > 0  # the tensor-core path did run
+
+
+def test_mixed_multi_rhs_equals_single_rhs():
+    n, k = 256, 3
+    rs = np.stack([S.gaussian_mixture(n, 10 + i) for i in range(k)])
+    P = gpu(n, p=10, n_rhs=k, precision="mixed_bf16")
+    zb = host(P.apply(dev(rs)))
+    for i in range(k):
+        assert rel_l2(zb[i], host(P.apply(dev(rs[i])))) < 1e-6
+    assert P.query("device_errors") == 0
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_mixed_fgmres_matches_oracle_solve(prec):
+    n = 64
+    f, u = S.manufactured_sin(n)
+    h = 1 / 65
+    lam = 8 / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    P = gpu(n, p=8, precision=prec)
+    x, info = P.solve(dev(f), method="fgmres", restart=30, maxit=100, rtol=1e-8)
+    _, it_o, _, _ = O.Problem(n, p=8).solve(f, "fgmres", 30, 100, 1e-8, "fmm")
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    assert abs(info["iters"] - it_o) <= 1
+    assert rel_l2(host(x), (2 * np.pi ** 2 / lam) * u) < 1e-7
+
+
+def test_mixed_bf16_solve_1024_matches_oracle_solution():
+    # 1e-10 on both sides: at 1024^2 (condition number ~4e5) a relative residual of 1e-12 is
+    # at the FP64 floor of b - A u whatever the preconditioner
+    n = 1024
+    f = S.gaussian_mixture(n, 0)
+    P = gpu(n, p=10, precision="mixed_bf16")
+    x, info = P.solve(dev(f), rtol=1e-10)
+    xo, it_o, _, _ = O.Problem(n, p=10).solve(f, "fgmres", 30, 200, 1e-10, "fmm")
+    assert info["status"] == 0
+    assert abs(info["iters"] - it_o) <= 2
+    assert rel_l2(host(x), xo) < 1e-8
