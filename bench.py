@@ -34,18 +34,24 @@ METRIC = ("FMM apply points/sec and time-to-solution at rel. residual 1e-8, mixe
           "on 1 GB300")
 UNIT = "points/s"
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0  # GB300: SMs, FP32 lanes per SM, max SM clock
+FORMS = {"mixed_bf16": "FP32 P2P (3xTF32 tensor cores) and expansions, BF16 tensor-core M2L",
+         "mixed_tf32": "FP32 P2P (3xTF32 tensor cores) and expansions, TF32 tensor-core M2L",
+         "fp32": "FP32 FMM, CUDA-core M2L", "fp64": "FP64 FMM on CUDA cores"}
+DTYPES = {"mixed_bf16": "f32+bf16", "mixed_tf32": "f32+tf32", "fp32": "f32", "fp64": "f64"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--side", dest="n", type=int, default=1024, help="interior grid side n")
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--theta", type=float, default=0.4)
+    ap.add_argument("--precision", default="mixed_tf32", choices=["mixed_bf16", "mixed_tf32", "fp32", "fp64"],
+                    help="FMM form of the headline apply (FP64 Krylov in every form)")
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -54,7 +60,7 @@ def parse():
 def workload(args):
     return {"workload": f"poisson-fd {args.n}x{args.n} gaussian-mixture(16) FMM-BEM precond",
             "n": args.n, "N": args.n * args.n, "p": args.p, "leaf_max": args.leaf,
-            "theta": args.theta, "krylov": "FGMRES(30) FP64", "fmm": "fp32",
+            "theta": args.theta, "krylov": "FGMRES(30) FP64", "fmm": FORMS[args.precision],
             "l2": "flushed: 256 MB write between timed applies"}
 
 
@@ -237,15 +243,28 @@ def rooflines(P, stage_ms):
                       "achieved": 2.0 * pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                       "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
                       "work": f"{pairs:.4e} pairs/launch x 2 flop", "launch_ms": t}
-    # M2L: 8 p^2 real flops per (target, source) pair, volume lists plus boundary-to-volume
+    # M2L: 8 p^2 real flops per (target, source) pair
     p = P.p
-    m2l_pairs = P.query("n_m2l") + P.query("n_m2l_vb")
     t = stage_ms["m2l"]
-    peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    out["m2l"] = {"bound": "alu", "kernel": "k_m2l_vol (+ k_root_const, 1 block)",
-                  "achieved": 8.0 * p * p * m2l_pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                  "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
-                  "work": f"{m2l_pairs} pairs/launch x 8p^2 flop (p={p})", "launch_ms": t}
+    tcm = P.query("tc_m2l")
+    if tcm:
+        pairs_m = P.query("n_m2l")  # volume pairs; boundary sources run in stage m2l_bnd
+        if tcm == 2:
+            peak = pk["bf16_tflops"] if pk else 1900.0
+            src = "measured bf16 burst" if pk else "fallback bf16 1.9 PFLOP/s"
+        else:
+            peak = (pk["bf16_tflops"] if pk else 1900.0) * 1.1 / 2.25
+            src = "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25" if pk else "fallback bf16 x 1.1/2.25"
+        out["m2l"] = {"bound": "tensor", "kernel": "k_m2l_tc (+ k_m2l_pack, operand images)",
+                      "achieved": 8.0 * p * p * pairs_m / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                      "peak_source": src, "work": f"{pairs_m} pairs/launch x 8p^2 flop (p={p})", "launch_ms": t}
+    else:
+        m2l_pairs = P.query("n_m2l") + P.query("n_m2l_vb")
+        peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        out["m2l"] = {"bound": "alu", "kernel": "k_m2l_vol (+ k_root_const, 1 block)",
+                      "achieved": 8.0 * p * p * m2l_pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                      "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
+                      "work": f"{m2l_pairs} pairs/launch x 8p^2 flop (p={p})", "launch_ms": t}
     for k, v in out.items():
         v["frac"] = v["achieved"] / v["peak"]
         rec = traffic_record(v["kernel"].split()[0])
@@ -281,7 +300,7 @@ def run_ours(args):
     n = args.n
     N = n * n
     f = S.gaussian_mixture(n, rank)
-    P = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision="fp32")
+    P = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision=args.precision)
     r = torch.tensor(f, dtype=torch.float64, device=dev)
     z = torch.empty_like(r)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -337,11 +356,27 @@ def run_ours(args):
     tts = None
     if not args.no_tts:
         P.set_timing(False)
-        tts = {"mixed_fp32fmm_fp64krylov_graphs": time_solves(P, r, 3, graphs=1),
-               "plain_fp32_no_graphs": time_solves(P, r, 2, graphs=0)}
-        P64 = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision="fp64")
-        tts["plain_fp64_no_graphs"] = time_solves(P64, r, 2, graphs=0)
-        P64.close()
+        tts = {}
+        for form in ("mixed_tf32", "mixed_bf16", "fp32", "fp64"):
+            Pf = P if form == args.precision else FmmPreconditioner(n, p=args.p, leaf_max=args.leaf,
+                                                                     theta=args.theta, precision=form)
+            graphs = 1 if form.startswith("mixed") else 0  # the plain forms replay no graphs
+            Pf.set_graphs(bool(graphs))
+            ta = []
+            for i in range(13):
+                flush.zero_()
+                e0.record(stream)
+                Pf.apply(r, out=z)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= 3:
+                    ta.append(e0.elapsed_time(e1))
+            tts[form] = {"apply_ms": float(np.mean(ta)), "graphs": bool(graphs),
+                         **time_solves(Pf, r, 3 if graphs else 2, graphs=graphs)}
+            if Pf is not P:
+                Pf.close()
+            else:
+                Pf.set_graphs(True)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -350,7 +385,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_apply_max, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
                 "config": workload(args), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(launches * args.steps), "roofline": roofline, "rooflines": all_rooflines,
                 "cpu_baseline": cpu,

@@ -181,12 +181,13 @@ int fmmpc_set_graphs(fmmpc_handle *h, int32_t on);
 /* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream.
  * fmmpc_set_timing(h, 1) creates the events and turns recording on (0 turns it off).
  * fmmpc_get_timing synchronises the stream and writes the durations in milliseconds of
- * the stages of the last apply into ms[0 .. min(cap, count)), *count = 10 stages:
+ * the stages of the last apply into ms[0 .. min(cap, count)), *count = 11 stages:
  *  0 weight image, 1 P2M + M2M (Sec. 5.3 items 1-2), 2 collocation pass (M2L to boundary
  *  cells, local expansions and near field at the collocation points), 3 BEM solve (FP64),
- *  4 boundary multipoles, 5 M2L (item 3), 6 L2L (item 4), 7 near-boundary element
- *  integrals, 8 P2P near field (item 5, Eq. e:volume_integral; with the CUDA-core engine
- *  this stage also holds L2P and the sum), 9 L2P + sum (tensor-core engine).
+ *  4 boundary multipoles, 5 M2L (item 3; with the tensor-core M2L its volume part only),
+ *  6 boundary-source M2L added after the tensor-core M2L, 7 L2L (item 4), 8 near-boundary
+ *  element integrals, 9 P2P near field (item 5, Eq. e:volume_integral; with the CUDA-core
+ *  engine this stage also holds L2P and the sum), 10 L2P + sum (tensor-core engine).
  * A stage that did not run reports 0.  Errors: _INVALID if timing is off. */
 int fmmpc_set_timing(fmmpc_handle *h, int32_t on);
 int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);

@@ -19,7 +19,7 @@ PART = {"full": 0, "vr": 1, "near": 2, "vcol": 3, "q": 4}
 QUERY = {"L": 0, "leaf_side": 1, "n_m2l": 2, "n_p2p": 3, "n_m2l_vb": 4, "n_p2p_vb": 5, "NG": 6,
          "n_cell": 7, "N": 8, "stencil": 9, "launches": 10, "device_bytes": 11, "device_errors": 12,
          "tc_p2p": 13, "tc_m2l": 14}
-STAGES = ["weights", "upward", "colloc", "bem", "bnd_upward", "m2l", "l2l", "bnd_near", "p2p", "l2p"]
+STAGES = ["weights", "upward", "colloc", "bem", "bnd_upward", "m2l", "m2l_bnd", "l2l", "bnd_near", "p2p", "l2p"]
 EXPORT = {"keys": 0, "perm": 1, "cell_start": 2, "m2l": 3, "p2p": 4, "m2l_vb": 5, "p2p_vb": 6}
 
 

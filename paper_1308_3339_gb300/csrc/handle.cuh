@@ -99,7 +99,7 @@ struct fmmpc_handle {
   int p2p_engine = 0;       // 0: tensor cores where eligible, 1: CUDA cores
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
-  static constexpr int NSTAGE = 10;
+  static constexpr int NSTAGE = 11;
   bool timing = false;
   cudaEvent_t ev[NSTAGE + 1] = {};
   bool stage_hit[NSTAGE] = {};

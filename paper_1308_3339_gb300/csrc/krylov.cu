@@ -58,20 +58,23 @@ __global__ void k_fold_rhs(int n, double s, int64_t total, const double *__restr
 // partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
 // Vectors are taken in register groups of 8.
 __global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, int64_t vs,
-                               const double *__restrict__ w, double *__restrict__ part) {
+                               const double *__restrict__ w, double *__restrict__ part, int with_self) {
   __shared__ double red[RED_THREADS / 32][8];
   const int rhs = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double *wr = w + (int64_t)rhs * N;
-  for (int i0 = 0; i0 < nv; i0 += 8) {
+  const int nt = nv + (with_self ? 1 : 0);  // index nv: <w, w>
+  for (int i0 = 0; i0 < nt; i0 += 8) {
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
       const double wk = wr[k];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 8; ++q) {
         if (i0 + q < nv) acc[q] = fma(V[(int64_t)(i0 + q) * vs + (int64_t)rhs * N + k], wk, acc[q]);
+        else if (i0 + q == nv && with_self) acc[q] = fma(wk, wk, acc[q]);
+      }
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -80,7 +83,7 @@ __global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, 
       if (lane == 0) red[wid][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nv) {
+    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nt) {
       double sum = 0.0;
       for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
       part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
@@ -89,15 +92,46 @@ __global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, 
   }
 }
 
-// out[rhs][i] = sum_blk partial ; optionally accumulates into acc[rhs][i]
+// out[rhs][i] = sum_blk partial, i < nv; acc[rhs][i] += the same for i < nacc.  One warp
+// per (rhs, i): lanes stride over the block partials, then a shuffle reduction.
 __global__ void k_mdot_final(int nv, int nblocks, const double *__restrict__ part, double *__restrict__ out,
-                             double *__restrict__ acc) {
-  const int rhs = blockIdx.x;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[((int64_t)rhs * MAXJ + i) * nblocks + b];
-    out[rhs * MAXJ + i] = s;
-    if (acc) acc[rhs * MAXJ + i] += s;
+                             double *__restrict__ acc, int nacc) {
+  const int rhs = blockIdx.x, lane = threadIdx.x & 31;
+  const int i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= nv) return;
+  const double *pp = part + ((int64_t)rhs * MAXJ + i) * nblocks;
+  double sacc = 0.0;
+  for (int b = lane; b < nblocks; b += 32) sacc += pp[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+  if (lane == 0) {
+    out[rhs * MAXJ + i] = sacc;
+    if (acc && i < nacc) acc[rhs * MAXJ + i] += sacc;
+  }
+}
+
+// w[rhs] -= sum_i c[rhs][i] V_i[rhs], and part[rhs][0][blk] = sum over a slice of the new w^2
+__global__ void k_mupdate_sq(int64_t N, int nv, const double *__restrict__ V, int64_t vs,
+                             const double *__restrict__ c, double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double red[RED_THREADS / 32];
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double *wr = w + (int64_t)rhs * N;
+  double sq = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    double v = wr[k];
+    for (int i = 0; i < nv; ++i) v = fma(-c[rhs * MAXJ + i], V[(int64_t)i * vs + (int64_t)rhs * N + k], v);
+    wr[k] = v;
+    sq = fma(v, v, sq);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) red[wid] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) t += red[q];
+    part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -188,15 +222,26 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
   k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
   k.part = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * RED_BLOCKS);
   k.scal = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
-  FMMPC_CUDA(cudaMallocHost(&k.hbuf, sizeof(double) * H.nrhs_max * MAXJ * 4));
+  FMMPC_CUDA(cudaMallocHost(&k.hbuf, sizeof(double) * H.nrhs_max * MAXJ * 8));
   k.cap_vecs = nvec;
 }
 
 // dots[rhs][0..nv) = <V_i, w>; if acc, acc += dots
-void mdot(Ctx &c, int nv, const double *V, int64_t vs, const double *w, double *out, double *acc) {
+// with_self: out[rhs][nv] = <w, w> as well (not accumulated into acc)
+void mdot(Ctx &c, int nv, const double *V, int64_t vs, const double *w, double *out, double *acc,
+          bool with_self = false) {
   dim3 grid(RED_BLOCKS, c.nrhs);
-  k_mdot_partial<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, w, c.H.kw.part);
-  k_mdot_final<<<c.nrhs, 64, 0, c.s>>>(nv, RED_BLOCKS, c.H.kw.part, out, acc);
+  k_mdot_partial<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, w, c.H.kw.part, with_self ? 1 : 0);
+  const int nt = nv + (with_self ? 1 : 0);
+  k_mdot_final<<<dim3(c.nrhs, (nt + 7) / 8), 256, 0, c.s>>>(nt, RED_BLOCKS, c.H.kw.part, out, acc, nv);
+  FMMPC_LAUNCH_CHECK();
+}
+
+// w -= V coef (nv vectors), then out[rhs][0] = ||w||^2
+void update_sq(Ctx &c, int nv, const double *V, int64_t vs, const double *coef, double *w, double *out) {
+  dim3 grid(RED_BLOCKS, c.nrhs);
+  k_mupdate_sq<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, coef, w, c.H.kw.part);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.s>>>(1, RED_BLOCKS, c.H.kw.part, out, nullptr, 0);
   FMMPC_LAUNCH_CHECK();
 }
 
@@ -258,17 +303,39 @@ int gmres(Ctx &c, bool flexible, int m, int maxit, double rtol, const double *b,
       double *zj = flexible ? K.Z + (int64_t)j * vs : K.t;
       precond(c, vj, zj);
       spmv5(H, zj, K.w, nr);
-      // CGS2: h = V^T w, w -= V h, twice
+      // classical Gram-Schmidt, h = V^T w, w -= V h, with the DGKS test: a second pass only
+      // where the first removed more than half of ||w||^2 (cancellation has then cost
+      // orthogonality).  ||w||^2 before comes with the dots, after with the update.
       double *d1 = K.dots, *hsum = K.dots + (size_t)nr * MAXJ;
+      double *hb = K.hbuf + (size_t)4 * nr * MAXJ;  // pinned: h, then <.,w> with ||w||^2, ||w||^2 after
       FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nr * MAXJ, c.s));
-      for (int pass = 0; pass < 2; ++pass) {
-        mdot(c, j + 1, K.V, vs, K.w, d1, hsum);
-        k_mupdate<<<nblk(NR), 256, 0, c.s>>>(N, nr, j + 1, K.V, vs, d1, K.w);
+      double *wsq = K.scal + (size_t)nr * MAXJ;  // device: ||w||^2 after, [rhs][MAXJ]
+      mdot(c, j + 1, K.V, vs, K.w, d1, hsum, true);
+      update_sq(c, j + 1, K.V, vs, d1, K.w, wsq);
+      std::vector<double> hn(nr), wb(nr);
+      auto fetch = [&]() {
+        FMMPC_CUDA(cudaMemcpyAsync(hb, hsum, sizeof(double) * nr * MAXJ, cudaMemcpyDeviceToHost, c.s));
+        FMMPC_CUDA(cudaMemcpyAsync(hb + (size_t)nr * MAXJ, d1, sizeof(double) * nr * MAXJ, cudaMemcpyDeviceToHost, c.s));
+        FMMPC_CUDA(cudaMemcpyAsync(hb + (size_t)2 * nr * MAXJ, wsq, sizeof(double) * nr * MAXJ,
+                                   cudaMemcpyDeviceToHost, c.s));
+        FMMPC_CUDA(cudaStreamSynchronize(c.s));
+      };
+      fetch();
+      bool reorth = false;
+      for (int r = 0; r < nr; ++r) {
+        wb[r] = hb[(size_t)nr * MAXJ + (size_t)r * MAXJ + (j + 1)];
+        const double wa = hb[(size_t)2 * nr * MAXJ + (size_t)r * MAXJ];
+        if (!done[r] && wa < 0.5 * wb[r]) reorth = true;
       }
-      FMMPC_LAUNCH_CHECK();
-      FMMPC_CUDA(cudaMemcpyAsync(hcol.data(), hsum, sizeof(double) * nr * MAXJ, cudaMemcpyDeviceToHost, c.s));
-      std::vector<double> hn;
-      norms(c, K.w, hn);
+      if (reorth) {
+        mdot(c, j + 1, K.V, vs, K.w, d1, hsum);
+        update_sq(c, j + 1, K.V, vs, d1, K.w, wsq);
+        fetch();
+      }
+      for (int r = 0; r < nr; ++r) {
+        for (int i = 0; i <= j; ++i) hcol[(size_t)r * MAXJ + i] = hb[(size_t)r * MAXJ + i];
+        hn[r] = std::sqrt(std::max(0.0, hb[(size_t)2 * nr * MAXJ + (size_t)r * MAXJ]));
+      }
       ++it;
       bool conv_all = true;
       for (int r = 0; r < nr; ++r) {

@@ -16,15 +16,18 @@
 // dy P + dx.  One CTA takes such a tile of targets (M = 128) and sweeps its class's offsets,
 // D[t][u] += sum_v X[t + shift][v] B_o[u][v] with K = 2p real inputs and N = 32 outputs: 2p
 // real parts of L~ plus the two sums of M~_0 that carry the ln rho term.  Padding targets are
-// computed and dropped.  The monopole (for BF16 also the next two terms) dominates the translated
+// computed and dropped.  The low-order terms dominate the translated
 // field and meets the large log o + ln rho, so their products are split hi + lo in the
-// spare K columns (K = 24 for TF32 at p = 10, 32 for BF16): rounded input x rounded
+// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded input x rounded
 // matrix, input residual x rounded matrix, rounded input x matrix residual.
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Offsets are grouped by (source parity, dy); one 144-row window of the
 // source sub-image serves every dx of a group.  Warp 0 streams window + B groups through
-// four stages, warp 1 issues the MMAs, warps 2-5 write L~ from TMEM.
+// two stages (two CTAs share an SM, so their copy and MMA round trips overlap), warp 1
+// issues the MMAs, one fresh TMEM accumulator per group (four in
+// flight), and warps 2-5 drain each into Kahan-compensated FP32 sums: one long chain of
+// MMAs would drift with the tensor core's truncating adds (~2^-24 of the partial per MMA).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -45,7 +48,8 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 constexpr int M2L_WROWS = 144;                  // window rows (128 targets + 2 x 4 shift + alignment)
 constexpr int M2L_WBYTES = M2L_WROWS * 128;     // 18 KB
 constexpr int M2L_BBYTES = 32 * 128;            // one offset's B operand: 32 outputs x 128 B
-constexpr int M2L_NSTG = 4;
+constexpr int M2L_NSTG = 2;                     // stages per CTA (two CTAs per SM)
+constexpr int M2L_NACC = 4;                     // TMEM accumulators (32 columns each) in flight
 constexpr int M2L_THREADS = 192;
 constexpr int M2L_TAIL = 256;                   // zero rows after each sub-image (window overrun)
 constexpr int M2L_MAXGRP = 128, M2L_MAXOFS = 225;  // per class: (source parity, dy) groups, offsets
@@ -133,9 +137,9 @@ __global__ void k_m2l_pack(M2lArgs a, int nrhs, int64_t ncell_lo, int64_t ncell_
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
+__global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t full[M2L_NSTG], empty[M2L_NSTG], done;
+  __shared__ uint64_t full[M2L_NSTG], empty[M2L_NSTG], acc_full[M2L_NACC], acc_empty[M2L_NACC], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, used;
   __shared__ int4 sgrp[M2L_MAXGRP];  // the class's groups and offsets, off the issue path
@@ -154,12 +158,16 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
+    for (int b = 0; b < M2L_NACC; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 4);
+    }
     tc::mbar_init(&done, 1);
     tc::mbar_init_fence();
     abort_flag = 0;
     used = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 32 * M2L_NACC);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -167,6 +175,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
+      // producer: per group, the source window and the group's B operands into one stage
       bool ok = true;
       for (int gi = 0; gi < ng && !abort_flag; ++gi) {
         const int s = gi % M2L_NSTG;
@@ -188,19 +197,26 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // MMA issuer: one fresh accumulator per group; one commit per group (the epilogue,
+      // which waits for the same completion, releases the stage)
       const uint32_t idesc = KIND == 0 ? tc::idesc_tf32(128, 32)
                                        : ((1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24));
-      const int nks = a.nks;  // K steps of 32 bytes (8 TF32 or 16 BF16 inputs each) covering 2p
+      const int nks = a.nks;  // K steps of 32 bytes (8 TF32 or 16 BF16 inputs each)
       bool ok = true;
-      uint32_t acc = 0;
       for (int gi = 0; gi < ng; ++gi) {
-        const int s = gi % M2L_NSTG;
+        const int s = gi % M2L_NSTG, ab = gi % M2L_NACC;
         if (!tc::mbar_wait(&full[s], (gi / M2L_NSTG) & 1, &abort_flag)) { ok = false; break; }
         used = gi + 1;
+        if (gi >= M2L_NACC && !tc::mbar_wait(&acc_empty[ab], ((gi / M2L_NACC) - 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
         tc::fence_after();
         const int4 g = grp[gi];
         const int ws = floor8(f0 + g.y * P - 4);
         const uint32_t st = tc::smem_addr(smem + s * a.stage_bytes);
+        const uint32_t d = tmem + 32 * ab;
+        uint32_t acc = 0;
         for (int k = 0; k < g.w; ++k) {
           const int dx = sdx[g.z + k];
           const uint32_t arow = st + (uint32_t)((f0 + g.y * P + dx - ws) * 128);
@@ -208,17 +224,17 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
           for (int ks = 0; ks < nks; ++ks) {
             const uint64_t ad = tc::desc_sw128(arow + 32 * ks), bd = tc::desc_sw128(brow + 32 * ks);
             if (KIND == 0) {
-              tc::mma_tf32(tmem, ad, bd, idesc, acc);
+              tc::mma_tf32(d, ad, bd, idesc, acc);
             } else {
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
             acc = 1;
           }
         }
-        tc::commit(&empty[s]);
+        tc::commit(&acc_full[ab]);
       }
       if (!ok) {
         abort_flag = 1;
@@ -226,37 +242,64 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
       }
       tc::commit(&done);
     }
-  }
-  __syncwarp();
-  const bool finished = __all_sync(0xffffffffu, tc::mbar_wait(&done, 0, nullptr));  // warp-uniform
-  if (!finished && lane == 0) atomicOr(a.err, 4);
-  tc::fence_after();
-  if (warp >= 2 && finished && !abort_flag) {
+  } else {
+    // epilogue: drain each group's accumulator into FP32 sums (Kahan), one target per thread
     const int qd = warp & 3;
-    float v[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16), v);
+    float sum[32], cmp[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sum[i] = cmp[i] = 0.0f;
+    bool ok = true;
+    for (int gi = 0; gi < ng; ++gi) {
+      const int ab = gi % M2L_NACC;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[ab], (gi / M2L_NACC) & 1, &abort_flag))) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      if (warp == 2 && lane == 0) tc::mbar_arrive(&empty[gi % M2L_NSTG]);  // the group's MMAs are done
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 32 * ab, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float y = v[i] - cmp[i];
+        const float t = sum[i] + y;
+        cmp[i] = (t - sum[i]) - y;
+        sum[i] = t;
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[ab]);
+    }
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicOr(a.err, 2);
+    }
     const int f = f0 + 32 * qd + lane;
     const int S = P - 8;
     const int i = f % P - 4, j = f / P - 4;
-    if (i >= 0 && i < S && j >= 0 && j < S && ng > 0) {
+    if (ok && !abort_flag && i >= 0 && i < S && j >= 0 && j < S) {
       const int x = 2 * i + (c & 1), y = 2 * j + (c >> 1);
       const int64_t gidx = level_offset(l) + morton_encode((uint32_t)x, (uint32_t)y);
       cpx<float> *L = a.Lv + ((int64_t)rhs * a.ncell + gidx) * a.p;
       const float lnrho = logf((float)(a.n >> l));
-      for (int nn = 0; nn < a.p; ++nn) {
-        float re = v[2 * nn], im = v[2 * nn + 1];
-        if (nn == 0) {
-          re += lnrho * v[2 * a.p];
-          im += lnrho * v[2 * a.p + 1];
-        }
-        L[nn] = mk<float>(re, im);
+      float tot[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) tot[u] = sum[u] - cmp[u];
+      float m0r = 0.f, m0i = 0.f;  // the sums of M~_0 in outputs 2p, 2p + 1 (p <= 15)
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        if (u == 2 * a.p) m0r = tot[u];
+        if (u == 2 * a.p + 1) m0i = tot[u];
       }
-    } else if (i >= 0 && i < S && j >= 0 && j < S) {
-      const int x = 2 * i + (c & 1), y = 2 * j + (c >> 1);
-      const int64_t gidx = level_offset(l) + morton_encode((uint32_t)x, (uint32_t)y);
-      for (int nn = 0; nn < a.p; ++nn) a.Lv[((int64_t)rhs * a.ncell + gidx) * a.p + nn] = mk<float>(0.f, 0.f);
+      L[0] = mk<float>(tot[0] + lnrho * m0r, tot[1] + lnrho * m0i);
+#pragma unroll
+      for (int nn = 1; nn < 16; ++nn)
+        if (nn < a.p) L[nn] = mk<float>(tot[2 * nn], tot[2 * nn + 1]);
     }
   }
+  __syncwarp();
+  const bool finished = __all_sync(0xffffffffu, tc::mbar_wait(&done, 0, nullptr));  // warp-uniform
+  if (!finished && lane == 0) atomicOr(a.err, 4);
   tc::fence_before();
   __syncthreads();
   if (abort_flag && warp == 0 && lane == 0)
@@ -264,7 +307,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, 32);
+    tc::tmem_dealloc(tmem, 32 * M2L_NACC);
   }
 }
 
@@ -353,7 +396,8 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   const int L = g.L, p = g.p;
   T.kind = (H.prec == FMMPC_PREC_MIXED_TF32) ? 0 : 1;
   // hi/lo splits of the leading multipoles in the spare K columns (24 for TF32, 32 for BF16)
-  const int kcap = (T.kind == 0 && 2 * p <= 20) ? 24 : 32;  // TF32: 3 K steps while 2p <= 20
+  // K capacity: TF32 32 inputs (4 steps of 8, one 128-byte row); BF16 48 (3 steps of 16)
+  const int kcap = T.kind == 0 ? 32 : 48;
   T.nsplit = std::max(0, std::min(p, (kcap - 2 * p) / 4));
   // offset sets by class, from the lists themselves, then checked against every list
   int *dtab = tmp.get<int>(4 * 225), *derr = tmp.get<int>(1);
