@@ -754,7 +754,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_p2p(P2PArgs<R> 
 template <typename R, int M>
 __global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, int nrhs, int do_bnd,
                             const cpx<R> *__restrict__ Lv, const R *__restrict__ phib,
-                            const int32_t *__restrict__ bslot, double *__restrict__ out) {
+                            const int32_t *__restrict__ bslot, double *__restrict__ out,
+                            const double *__restrict__ near2) {
   const int64_t nleaf = int64_t(1) << (2 * L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nleaf * M * nrhs) return;
@@ -778,12 +779,13 @@ __global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, 
     const int slot = bslot[leafc];
     if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M;
   }
-  double *o = out + (int64_t)rhs * n * n + (int64_t)(gy * M + ty) * n + gx * M;
+  const int64_t off = (int64_t)rhs * n * n + (int64_t)(gy * M + ty) * n + gx * M;
+  double *o = out + off;
 #pragma unroll
   for (int q = 0; q < M; ++q) {
     double v = (double)acc[q].re;
     if (pb) v += (double)pb[q];
-    o[q] += -v / (2.0 * PI);
+    o[q] += -v / (2.0 * PI) + (near2 ? near2[off + q] : 0.0);
   }
 }
 
@@ -859,15 +861,16 @@ void run_p2p(fmmpc_handle &H, const void *table, double *out, int nrhs, cudaStre
 }
 
 template <typename R>
-void run_far_final(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s) {
+void run_far_final(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s,
+                   const double *near2 = nullptr) {
   const Geo &g = H.g;
   const int64_t tasks = g.nleaf * g.m * nrhs;
   const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
   const R *pb = (const R *)H.fb.phib;
   switch (g.m) {
-    case 4: k_far_final<R, 4><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
-    case 8: k_far_final<R, 8><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
-    default: k_far_final<R, 16><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out); break;
+    case 4: k_far_final<R, 4><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
+    case 8: k_far_final<R, 8><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
+    default: k_far_final<R, 16><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
   }
   FMMPC_LAUNCH_CHECK();
 }
@@ -974,7 +977,10 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   if (tc) launches += prep_p2p_tc(H, r, nrhs, s);
   if (part == PART_NEAR) {
     mark(9);
-    if (tc) launches += run_p2p_tc(H, true, out, nrhs, s);
+    if (tc) {
+      launches += run_p2p_tc(H, true, out, nrhs, s);
+      launches += add_near2(H, out, nrhs, s);
+    }
     else { run_p2p<R>(H, H.fb.table_lnh, out, nrhs, s); ++launches; }
     mark_end();
     H.launches = launches;
@@ -1046,7 +1052,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   if (tc) {
     launches += run_p2p_tc(H, false, out, nrhs, s);
     mark(10);
-    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
+    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s, H.tcp.near2);
   } else {
     run_p2p<R>(H, H.fb.table, out, nrhs, s);  // the CUDA-core kernel also evaluates L2P and the sum
     ++launches;

@@ -35,9 +35,10 @@ struct FmmBufs {
 // tensor-core lattice P2P (p2p_tc.cu)
 struct TcP2P {
   bool enabled = false;
-  int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, nofs = 0, smem = 0;
+  int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, nofs = 0, smem = 0, usplit = 0;
   int row_oy[33] = {}, row_q0[33] = {}, row_q1[33] = {}, row_ox0[33] = {};
   float *ahi = nullptr, *alo = nullptr, *bmat = nullptr, *bmat_lnh = nullptr;
+  double *near2 = nullptr;  // second half of the near field, added by L2P
   int *err = nullptr;
 };
 
@@ -126,6 +127,7 @@ bool tc_m2l_eligible(const fmmpc_handle &H);
 void init_tc_m2l(fmmpc_handle &H, DevPool &tmp);
 int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t s);
 int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream_t s);
+int add_near2(fmmpc_handle &H, double *out, int nrhs, cudaStream_t s);
 // message for fmmpc_last_error(NULL), kept in a fixed thread-local buffer; returns code
 int set_global_error(int code, const char *msg);
 int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,

@@ -14,8 +14,11 @@
 // MMAs into one accumulator drifts (~2^-24 of the partial sum per MMA).  Each (offset,
 // K half) group therefore starts a fresh accumulator -- the two small correction products
 // first, the hi*hi products last -- and four epilogue warps drain it into per-thread FP32
-// sums with Kahan compensation while the next groups run in the other TMEM buffers (four
-// in flight: the commit-to-barrier round trip is longer than two groups of MMAs).
+// sums while the next groups run in the other TMEM buffers (four in flight: the
+// commit-to-barrier round trip is longer than two groups of MMAs).  Each tile's 74 groups
+// are split between two CTAs (37 each; the second writes a scratch image that the L2P pass
+// adds), and two CTAs share an SM, so one's copies and barrier round trips overlap the
+// other's MMAs.
 //
 // Data: per padded leaf row and K half, each leaf's 32 weights are one 128-byte row in the
 // 128-byte swizzle (chunk c of leaf X at position c ^ (X % 8)), leaves contiguous, so the
@@ -38,7 +41,7 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 constexpr int TC_TILE = 128;       // target leaves per CTA
 constexpr int TC_BGRP = 16384;     // one (offset, K half) group of B: hi + lo, 64 x 32 FP32 each
-constexpr int TC_NB = 8;           // B stages
+constexpr int TC_NB = 2;           // B stages per CTA (two CTAs per SM)
 constexpr int TC_NACC = 4;         // TMEM accumulators (64 columns each) in flight
 constexpr int TC_THREADS = 192;    // producer, MMA issuer, four epilogue warps
 constexpr int TC_MAXROWS = 33;
@@ -46,9 +49,9 @@ constexpr int TC_MAXROWS = 33;
 struct TcArgs {
   const float *ahi, *alo;  // [nrhs][NLY][K half][NLX][32], swizzled per leaf
   const float *bmat;       // [nofs][K half][hi, lo][64][32], swizzled per row t
-  double *out;
+  double *out, *out2;  // first and second half of the stencil (grid z = 2 rhs + half)
   int *err;
-  int n, R, NLX, NLY, NS, nrows, nofs, npass;
+  int n, R, NLX, NLY, NS, nrows, nofs, npass, usplit;
   int row_oy[TC_MAXROWS], row_q0[TC_MAXROWS], row_q1[TC_MAXROWS], row_ox0[TC_MAXROWS];
 };
 
@@ -74,7 +77,7 @@ __global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int64_t t
   alo[idx] = tf32_round((float)(w - (double)hi));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t full_s[2], empty_s[2], full_b[TC_NB], empty_b[TC_NB], acc_full[TC_NACC], acc_empty[TC_NACC], done;
   __shared__ uint32_t tmem_base;
@@ -84,8 +87,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
   // the swizzle is taken from absolute address bits: operands start on 1024-byte boundaries
   unsigned char *strips = smem + ((1024u - (tc::smem_addr(smem) & 1023u)) & 1023u);  // [2][hi, lo][SH]
   unsigned char *bm = strips + 4 * SH;                                                 // [TC_NB][TC_BGRP]
-  const int lx0 = blockIdx.x * TC_TILE, ly = blockIdx.y, rhs = blockIdx.z;
-  const int nunits = 2 * a.nrows, ngroups = 2 * a.nofs;
+  const int lx0 = blockIdx.x * TC_TILE, ly = blockIdx.y, rhs = blockIdx.z >> 1, half = blockIdx.z & 1;
+  // this CTA's strip units (stencil row, K half): [u0, u1); the other half goes to a.out2
+  const int u0 = half ? a.usplit : 0, u1 = half ? 2 * a.nrows : a.usplit;
+  int ngroups = 0;
+  for (int u = u0; u < u1; ++u) ngroups += a.row_q1[u >> 1] - a.row_q0[u >> 1];
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&full_s[b], 1);
@@ -117,15 +123,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
       // producer: per (stencil row, K half) the weight strip, then that row's B groups
       int g = 0;
       bool ok = true;
-      for (int u = 0; u < nunits && ok && !abort_flag; ++u) {
-        const int r = u >> 1, kh = u & 1, slot = u & 1;
-        if (u >= 2 && !tc::mbar_wait(&empty_s[slot], ((u >> 1) - 1) & 1, &abort_flag)) { ok = false; break; }
+      for (int u = u0; u < u1 && ok && !abort_flag; ++u) {
+        const int lu = u - u0, r = u >> 1, kh = u & 1, slot = lu & 1;
+        if (lu >= 2 && !tc::mbar_wait(&empty_s[slot], ((lu >> 1) - 1) & 1, &abort_flag)) { ok = false; break; }
         tc::mbar_expect_tx(&full_s[slot], 2 * a.NS * 128);
         const int64_t Y = ly + a.R + a.row_oy[r];
         const int64_t off = rhs_off + ((Y * 2 + kh) * a.NLX + lx0) * 32;
         tc::bulk_g2s(strips + (slot * 2) * SH, a.ahi + off, a.NS * 128, &full_s[slot]);
         tc::bulk_g2s(strips + (slot * 2 + 1) * SH, a.alo + off, a.NS * 128, &full_s[slot]);
-        issued_s = u + 1;
+        issued_s = lu + 1;
         for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
           const int bi = g % TC_NB;
           if (g >= TC_NB && !tc::mbar_wait(&empty_b[bi], ((g / TC_NB) - 1) & 1, &abort_flag)) { ok = false; break; }
@@ -145,10 +151,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
       const uint32_t idesc = tc::idesc_tf32(128, 64);
       int g = 0;
       bool ok = true;
-      for (int u = 0; u < nunits && ok; ++u) {
-        const int r = u >> 1, slot = u & 1;
-        if (!tc::mbar_wait(&full_s[slot], (u >> 1) & 1, &abort_flag)) { ok = false; break; }
-        used_s = u + 1;
+      for (int u = u0; u < u1 && ok; ++u) {
+        const int lu = u - u0, r = u >> 1, slot = lu & 1;
+        if (!tc::mbar_wait(&full_s[slot], (lu >> 1) & 1, &abort_flag)) { ok = false; break; }
+        used_s = lu + 1;
         tc::fence_after();
         const uint32_t sh = tc::smem_addr(strips + (slot * 2) * SH), sl = tc::smem_addr(strips + (slot * 2 + 1) * SH);
         for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
@@ -191,11 +197,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one target leaf per thread
     const int qd = warp & 3;
-    float sum[64], cmp[64];
+    float sum[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) sum[i] = cmp[i] = 0.0f;
+    for (int i = 0; i < 64; ++i) sum[i] = 0.0f;
     bool ok = true;
-    int u = 0, uend = a.row_q1[0] - a.row_q0[0];  // groups of the current strip unit end at uend
+    int u = u0, uend = a.row_q1[u0 >> 1] - a.row_q0[u0 >> 1];  // groups of the current unit end at uend
     for (int g = 0; g < ngroups; ++g) {
       const int ab = g % TC_NACC;
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[ab], (g / TC_NACC) & 1, &abort_flag))) {
@@ -205,21 +211,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
       if (warp == 2 && lane == 0) {
         // the group's MMAs have completed: its B slot, and at a unit's end the strip slot, are free
         tc::mbar_arrive(&empty_b[g % TC_NB]);
-        if (g + 1 == uend) tc::mbar_arrive(&empty_s[u & 1]);
+        if (g + 1 == uend) tc::mbar_arrive(&empty_s[(u - u0) & 1]);
       }
-      if (g + 1 == uend && ++u < nunits) uend += a.row_q1[u >> 1] - a.row_q0[u >> 1];
+      if (g + 1 == uend && ++u < u1) uend += a.row_q1[u >> 1] - a.row_q0[u >> 1];
       tc::fence_after();
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * ab + 32 * hf, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float y = v[i] - cmp[32 * hf + i];
-          const float t = sum[32 * hf + i] + y;
-          cmp[32 * hf + i] = (t - sum[32 * hf + i]) - y;
-          sum[32 * hf + i] = t;
-        }
+        for (int i = 0; i < 32; ++i) sum[32 * hf + i] += v[i];
       }
       tc::fence_before();
       __syncwarp();
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
     }
     if (ok && !abort_flag) {
       const int X = lx0 + 32 * qd + lane;
-      double *o = a.out + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
+      double *o = (half ? a.out2 : a.out) + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
       const double sc = -1.0 / (2.0 * PI);
 #pragma unroll
       for (int tr = 0; tr < 8; ++tr) {
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int t0 = 8 * tr + 2 * c;
-          orow[c] = make_double2(sc * ((double)sum[t0] - (double)cmp[t0]), sc * ((double)sum[t0 + 1] - (double)cmp[t0 + 1]));
+          orow[c] = make_double2(sc * (double)sum[t0], sc * (double)sum[t0 + 1]);
         }
       }
     }
@@ -259,6 +260,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_p2p_tc(TcArgs a) {
     tc::fence_after();
     tc::tmem_dealloc(tmem, 64 * TC_NACC);
   }
+}
+
+__global__ void k_add_near2(int64_t total, const double *__restrict__ b, double *__restrict__ a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) a[t] += b[t];
 }
 
 float tf32_round_host(double v) {
@@ -341,6 +347,16 @@ void init_tc_p2p(fmmpc_handle &H) {
     (variant ? H.tcp.bmat_lnh : H.tcp.bmat) = dB;
   }
   H.tcp.nofs = nofs;
+  {  // split the strip units (row, K half) into two halves of about equal group counts
+    int acc = 0, best = 1, bestd = 1 << 30;
+    for (int u = 0; u < 2 * H.tcp.nrows; ++u) {
+      acc += q1s[u >> 1] - q0s[u >> 1];
+      const int d = std::abs(2 * acc - 2 * nofs);
+      if (u + 1 < 2 * H.tcp.nrows && d < bestd) { bestd = d; best = u + 1; }
+    }
+    H.tcp.usplit = best;
+  }
+  H.tcp.near2 = H.pool.get<double>((size_t)H.nrhs_max * g.n * g.n);
   H.tcp.err = H.pool.get<int>(1);
   FMMPC_CUDA(cudaMemsetAsync(H.tcp.err, 0, sizeof(int), H.stream));
   const int smem = 4 * ((H.tcp.NS * 128 + 1023) & ~1023) + TC_NB * TC_BGRP + 1024;  // + alignment slack
@@ -373,6 +389,8 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
   a.NS = H.tcp.NS;
   a.nrows = H.tcp.nrows;
   a.nofs = H.tcp.nofs;
+  a.usplit = H.tcp.usplit;
+  a.out2 = H.tcp.near2;
   a.npass = H.tcp.npass;
   for (int i = 0; i < a.nrows; ++i) {
     a.row_oy[i] = H.tcp.row_oy[i];
@@ -380,8 +398,16 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
     a.row_q1[i] = H.tcp.row_q1[i];
     a.row_ox0[i] = H.tcp.row_ox0[i];
   }
-  dim3 grid((1 << g.L) / TC_TILE, 1 << g.L, nrhs);
+  dim3 grid((1 << g.L) / TC_TILE, 1 << g.L, 2 * nrhs);
   k_p2p_tc<<<grid, TC_THREADS, H.tcp.smem, s>>>(a);
+  FMMPC_LAUNCH_CHECK();
+  return 1;
+}
+
+// out += the second half of the near field (PART_NEAR, where no L2P pass follows).
+int add_near2(fmmpc_handle &H, double *out, int nrhs, cudaStream_t s) {
+  const int64_t total = (int64_t)H.g.n * H.g.n * nrhs;
+  k_add_near2<<<nblk(total), 256, 0, s>>>(total, H.tcp.near2, out);
   FMMPC_LAUNCH_CHECK();
   return 1;
 }
