@@ -131,6 +131,21 @@ __global__ void k_swap_cols(int N, double *__restrict__ A, int c1, int c2) {
   row[c2] = t;
 }
 
+// T[m] = [C0+C1+C2+C3 | C0-C1+C2-C3 | C0-C2 | C1-C3][m] from the first n rows of the inverse
+__global__ void k_bem_dft(int n, const double *__restrict__ A, double *__restrict__ T) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int64_t m = t / n;
+  const int k = (int)(t % n);
+  const double *row = A + m * 4 * n;
+  const double c0 = row[k], c1 = row[n + k], c2 = row[2 * n + k], c3 = row[3 * n + k];
+  double *o = T + m * 4 * n;
+  o[k] = (c0 + c2) + (c1 + c3);
+  o[n + k] = (c0 + c2) - (c1 + c3);
+  o[2 * n + k] = c0 - c2;
+  o[3 * n + k] = c1 - c3;
+}
+
 }  // namespace
 
 void init_bem(fmmpc_handle &H, DevPool &tmp) {
@@ -161,9 +176,11 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
     if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, A, k, hp[k]);
   FMMPC_LAUNCH_CHECK();
   // the inverse is block circulant in the four sides (90-degree rotation of the square):
-  // keep its first block row, n x 4n
+  // keep its first block row [C0 | C1 | C2 | C3] (n x 4n), stored as its side-DFT
+  // [C0+C1+C2+C3 | C0-C1+C2-C3 | C0-C2 | C1-C3] for the apply
   H.Sinv = H.pool.get<double>((size_t)g.n * N);
-  FMMPC_CUDA(cudaMemcpyAsync(H.Sinv, A, sizeof(double) * (size_t)g.n * N, cudaMemcpyDeviceToDevice, s));
+  k_bem_dft<<<nblk((int64_t)g.n * g.n), 256, 0, s>>>(g.n, A, H.Sinv);
+  FMMPC_LAUNCH_CHECK();
   FMMPC_CUDA(cudaStreamSynchronize(s));
 }
 

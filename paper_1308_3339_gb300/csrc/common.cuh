@@ -20,6 +20,8 @@ namespace fmmpc {
 
 constexpr int MAXP = 20;
 constexpr double PI = 3.14159265358979323846;
+// -1/(2 pi): kernels multiply by it (FP64 division is a long instruction sequence)
+constexpr double NEG_INV_2PI = -0.15915494309189533576888376337251436;
 
 struct Error {
   int code;

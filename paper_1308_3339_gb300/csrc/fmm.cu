@@ -553,43 +553,73 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
     far = v.re;
   }
   far = warp_sum(far);
-  if (lane == 0) vcol[(int64_t)rhs * g.NG + ge] = -((double)acc + (double)far) / (2.0 * PI);
+  if (lane == 0) vcol[(int64_t)rhs * g.NG + ge] = ((double)acc + (double)far) * NEG_INV_2PI;
 }
 
 // ------------------------------------------------------------------ BEM solve (FP64)
 // q = -S^{-1} (V r)|_Gamma with the inverse formed at set-up.  Rotating the square by 90
 // degrees maps element (side s, index k) to (s+1, k), so S and its inverse are block
-// circulant in the four sides: S^{-1}[(s,m),(t,k)] = B[m][((t - s) mod 4) n + k], with B
-// its first block row (n x 4n).  Block per m: each entry of B is read once and serves the
-// four outputs q[(s, m)], s = 0..3.  One right-hand side at a time, staged in shared memory.
-__global__ void __launch_bounds__(256) k_bem_apply(int n, int nrhs, const double *__restrict__ B,
-                                                   const double *__restrict__ vcol, double *__restrict__ q) {
-  extern __shared__ double sv[];  // 4n values of one right-hand side
+// circulant in the four sides: q_s = -sum_d C_d v_{s+d}, C_d the blocks of the first block
+// row.  A 4-point DFT over the side index diagonalises this: with
+//   C^0 = C0+C1+C2+C3, C^2 = C0-C1+C2-C3, A = C0-C2, B = C1-C3 (stored at set-up) and
+//   v^0 = v0+v1+v2+v3, v^2 = v0-v1+v2-v3, a = v0-v2, b = v1-v3,
+// P0 = C^0 v^0, P2 = C^2 v^2, R + iI = (A + iB)(a - ib), and
+//   q0 = -(P0+P2+2R)/4, q1 = -(P0-P2-2I)/4, q2 = -(P0+P2-2R)/4, q3 = -(P0-P2+2I)/4:
+// 6 n^2 FP64 multiply-adds instead of 16 n^2 (FP64 is the bound on this part).
+
+// vt[rhs] = [v^0 | v^2 | a | b] from vcol[rhs] = [v0 | v1 | v2 | v3]
+__global__ void k_bem_vt(int n, int nrhs, const double *__restrict__ vcol, double *__restrict__ vt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * n) return;
+  const int64_t rr = t / n;
+  const int k = (int)(t % n);
+  const double *v = vcol + rr * 4 * n;
+  const double v0 = v[k], v1 = v[n + k], v2 = v[2 * n + k], v3 = v[3 * n + k];
+  double *o = vt + rr * 4 * n;
+  o[k] = (v0 + v2) + (v1 + v3);
+  o[n + k] = (v0 + v2) - (v1 + v3);
+  o[2 * n + k] = v0 - v2;
+  o[3 * n + k] = v1 - v3;
+}
+
+// Block per row m of the transformed first block row T[m] = [C^0 | C^2 | A | B][m].
+__global__ void __launch_bounds__(256) k_bem_apply(int n, int nrhs, const double *__restrict__ T,
+                                                   const double *__restrict__ vt, double *__restrict__ q) {
   __shared__ double red[8][4];
   const int mrow = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int NG = 4 * n;
-  const double *Brow = B + (int64_t)mrow * NG;
+  const double *Tr = T + (int64_t)mrow * NG;
   for (int rr = 0; rr < nrhs; ++rr) {
-    for (int i = tid; i < NG; i += 256) sv[i] = vcol[(int64_t)rr * NG + i];
-    __syncthreads();
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      for (int k = tid; k < n; k += 256) {
-        const double bv = Brow[j * n + k];
-#pragma unroll
-        for (int sg = 0; sg < 4; ++sg) acc[sg] = fma(bv, sv[((sg + j) & 3) * n + k], acc[sg]);
-      }
+    const double *v = vt + (int64_t)rr * NG;
+    double p0 = 0.0, p2 = 0.0, re = 0.0, im = 0.0;
+    for (int k = tid; k < n; k += 256) {
+      const double c0 = Tr[k], c2 = Tr[n + k], ca = Tr[2 * n + k], cb = Tr[3 * n + k];
+      const double a = v[2 * n + k], b = v[3 * n + k];
+      p0 = fma(c0, v[k], p0);
+      p2 = fma(c2, v[n + k], p2);
+      re = fma(ca, a, fma(cb, b, re));
+      im = fma(cb, a, fma(-ca, b, im));
+    }
+    double acc[4] = {p0, p2, re, im};
 #pragma unroll
     for (int sg = 0; sg < 4; ++sg) {
-      const double v = warp_sum(acc[sg]);
-      if (lane == 0) red[w][sg] = v;
+      const double x = warp_sum(acc[sg]);
+      if (lane == 0) red[w][sg] = x;
     }
     __syncthreads();
-    if (tid < 4) {
-      double t = 0.0;
-      for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
-      q[(int64_t)rr * NG + tid * n + mrow] = -t;
+    if (tid == 0) {
+      double P0 = 0.0, P2 = 0.0, R = 0.0, I = 0.0;
+      for (int ww = 0; ww < 8; ++ww) {
+        P0 += red[ww][0];
+        P2 += red[ww][1];
+        R += red[ww][2];
+        I += red[ww][3];
+      }
+      double *qr = q + (int64_t)rr * NG;
+      qr[mrow] = -0.25 * (P0 + P2 + 2.0 * R);
+      qr[n + mrow] = -0.25 * (P0 - P2 - 2.0 * I);
+      qr[2 * n + mrow] = -0.25 * (P0 + P2 - 2.0 * R);
+      qr[3 * n + mrow] = -0.25 * (P0 - P2 + 2.0 * I);
     }
     __syncthreads();
   }
@@ -746,7 +776,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_p2p(P2PArgs<R> 
   const int gx = lx0 + lxl, gy = ly0 + lyl;
   double *o = A.out + (int64_t)rhs * A.n * A.n + (int64_t)(gy * M + ty) * A.n + gx * M;
 #pragma unroll
-  for (int t = 0; t < M; ++t) o[t] = -((double)sum[t] - (double)comp[t]) / (2.0 * PI);
+  for (int t = 0; t < M; ++t) o[t] = ((double)sum[t] - (double)comp[t]) * NEG_INV_2PI;
 }
 
 // z += -(1/2pi) (L2P of the leaf local expansion + near-boundary element integrals).
@@ -785,7 +815,7 @@ __global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, 
   for (int q = 0; q < M; ++q) {
     double v = (double)acc[q].re;
     if (pb) v += (double)pb[q];
-    o[q] += -v / (2.0 * PI) + (near2 ? near2[off + q] : 0.0);
+    o[q] += v * NEG_INV_2PI + (near2 ? near2[off + q] : 0.0);
   }
 }
 
@@ -836,7 +866,6 @@ void set_p2p_smem_limit() {
   raise_smem_limit(k_p2p<R, 4>);
   raise_smem_limit(k_p2p<R, 8>);
   raise_smem_limit(k_p2p<R, 16>);
-  raise_smem_limit(k_bem_apply);
 }
 
 template <typename R>
@@ -970,11 +999,14 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   if (H.timing)
     for (int k = 0; k < fmmpc_handle::NSTAGE; ++k) H.stage_hit[k] = false;
   mark(0);
-  k_weights<R><<<nblk(N * nrhs), 256, 0, s>>>(g.n, g.npad, g.pad, g.h * g.h, N * nrhs, r, wpad);
-  FMMPC_LAUNCH_CHECK();
-  ++launches;
-  const bool tc = H.tcp.enabled && H.p2p_engine == 0;
-  if (tc) launches += prep_p2p_tc(H, r, nrhs, s);
+  const bool tc = std::is_same<R, float>::value && H.tcp.enabled && H.p2p_engine == 0;
+  if (tc) {
+    launches += prep_p2p_tc(H, r, nrhs, s, (float *)wpad);  // strips and weight image in one pass
+  } else {
+    k_weights<R><<<nblk(N * nrhs), 256, 0, s>>>(g.n, g.npad, g.pad, g.h * g.h, N * nrhs, r, wpad);
+    FMMPC_LAUNCH_CHECK();
+    ++launches;
+  }
   if (part == PART_NEAR) {
     mark(9);
     if (tc) {
@@ -1005,9 +1037,10 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(3);
-    k_bem_apply<<<g.n, 256, sizeof(double) * g.NG, s>>>(g.n, nrhs, H.Sinv, H.fb.vcol, H.fb.q);
+    k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
+    k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv, H.fb.vt, H.fb.q);
     FMMPC_LAUNCH_CHECK();
-    ++launches;
+    launches += 2;
     if (part == PART_Q) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.q, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
@@ -1140,6 +1173,7 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.phib = H.pool.get<R>((size_t)nr * std::max<int64_t>(1, H.lists.nbnear) * g.m * g.m);
   H.fb.vcol = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
+  H.fb.vt = H.pool.get<double>((size_t)nr * g.NG);
   std::vector<cpx<R>> mats;
   build_mats<R>(H, mats);
   H.fb.mats = H.pool.get<cpx<R>>(mats.size());

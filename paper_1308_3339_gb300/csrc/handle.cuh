@@ -30,6 +30,7 @@ struct FmmBufs {
   int table_rows = 0, table_stride = 0, table_c0 = 0, Rn = 0;
   double *vcol = nullptr;    // [nrhs][NG] V r at collocation points
   double *q = nullptr;       // [nrhs][NG] BEM density
+  double *vt = nullptr;      // [nrhs][NG] side-DFT of vcol for the block-circulant apply
 };
 
 // tensor-core lattice P2P (p2p_tc.cu)
@@ -122,7 +123,7 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);
 bool tc_p2p_eligible(const fmmpc_handle &H);
 void init_tc_p2p(fmmpc_handle &H);
-int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s);
+int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s, float *wimg);
 bool tc_m2l_eligible(const fmmpc_handle &H);
 void init_tc_m2l(fmmpc_handle &H, DevPool &tmp);
 int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t s);

@@ -61,14 +61,17 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.
+// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.  The
+// same pass writes the FP32 zero-padded weight image the other stages read (w, npad, pad).
 __global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int64_t total, const double *__restrict__ r,
-                            float *__restrict__ ahi, float *__restrict__ alo) {
+                            float *__restrict__ ahi, float *__restrict__ alo, float *__restrict__ wimg, int npad,
+                            int pad) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int64_t N = (int64_t)n * n;
   const int64_t rhs = t / N, q = t - rhs * N;
   const int i = (int)(q % n), j = (int)(q / n);
+  wimg[rhs * npad * (int64_t)npad + (int64_t)(j + pad) * npad + i + pad] = (float)(h2 * r[t]);
   const int X = i / 8 + R, Y = j / 8 + R, k = (j % 8) * 8 + (i % 8), kk = k % 32;
   const int64_t idx = (((rhs * NLY + Y) * 2 + k / 32) * NLX + X) * 32 + (((kk / 4) ^ (X & 7)) * 4) + (kk % 4);
   const double w = h2 * r[t];
@@ -364,11 +367,12 @@ void init_tc_p2p(fmmpc_handle &H) {
   H.tcp.smem = smem;
 }
 
-// TF32 hi/lo weight strips of the right-hand side r (FP64), for run_p2p_tc.
-int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s) {
+// TF32 hi/lo weight strips of the right-hand side r (FP64), for run_p2p_tc, and the FP32 weight image.
+int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s, float *wimg) {
   const Geo &g = H.g;
   const int64_t total = (int64_t)g.n * g.n * nrhs;
-  k_tc_strips<<<nblk(total), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, total, r, H.tcp.ahi, H.tcp.alo);
+  k_tc_strips<<<nblk(total), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, total, r, H.tcp.ahi, H.tcp.alo,
+                                          wimg, g.npad, g.pad);
   FMMPC_LAUNCH_CHECK();
   return 1;
 }
