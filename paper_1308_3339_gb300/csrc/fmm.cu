@@ -30,6 +30,13 @@ namespace {
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// 1/k! for k <= 20, evaluated at compile time (unrolled loops fold it to a constant)
+__host__ __device__ constexpr double inv_fact_d(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return 1.0 / f;
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -81,17 +88,17 @@ __device__ __forceinline__ void p2m_warp(const R *__restrict__ W, int npad, int 
     cpx<R> pw = z;
     acc[0].re += w;
 #pragma unroll
-    for (int k = 1; k < P; ++k) {
-      const R s = -w / R(k);
-      acc[k].re = fma(s, pw.re, acc[k].re);
-      acc[k].im = fma(s, pw.im, acc[k].im);
+    for (int k = 1; k < P; ++k) {  // sum w z^k here; the -1/k is applied once per leaf below
+      acc[k].re = fma(w, pw.re, acc[k].re);
+      acc[k].im = fma(w, pw.im, acc[k].im);
       pw = pw * z;
     }
   }
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    acc[k].re = warp_sum(acc[k].re);
-    acc[k].im = warp_sum(acc[k].im);
+    const R sk = k == 0 ? R(1) : R(-1) / R(k);
+    acc[k].re = sk * warp_sum(acc[k].re);
+    acc[k].im = sk * warp_sum(acc[k].im);
   }
 }
 
@@ -257,12 +264,8 @@ __device__ __forceinline__ void m2l_accum(cpx<R> (&H)[P], const cpx<R> *__restri
 #pragma unroll
   for (int j = 2; j < 2 * P; ++j) I[j] = R(j - 1) * (I[j - 1] * inv);
   cpx<R> a[P];
-  R invf = 1;
 #pragma unroll
-  for (int k = 1; k < P; ++k) {
-    a[k] = invf * m[k];
-    invf = invf / R(k);
-  }
+  for (int k = 1; k < P; ++k) a[k] = R(inv_fact_d(k - 1)) * m[k];  // m_k / (k-1)!
   const R lz = R(0.5) * dev_log<R>(z.re * z.re + z.im * z.im) + lnrho;
   const R az = atan2(z.im, z.re);
   H[0].re += m[0].re * lz - m[0].im * az;
@@ -468,11 +471,62 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
 }
 
 // Boundary trees, one block per side: P2M of each leaf run from its element densities
-// (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run,
-// with a barrier between levels.
+// (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run, with
+// a barrier between levels.  The side's whole tree (2^(L+1) - 1 runs) and its M2M matrices
+// stay in shared memory; the result is written out once.
 template <typename R, int P>
 __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, Mats<R> mt,
                                                  cpx<R> *__restrict__ Mb) {
+  extern __shared__ __align__(16) unsigned char bnd_smem[];
+  cpx<R> *T2 = reinterpret_cast<cpx<R> *>(bnd_smem);  // [2 children][P][P]
+  cpx<R> *S = T2 + 2 * P * P;                          // [level l: 2^l runs][P], level 0 first
+  const int side = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L;
+  const R h = (R)g.h;
+  for (int t = threadIdx.x; t < 2 * P * P; t += blockDim.x) T2[t] = mt.bm2m[(int64_t)side * 2 * P * P + t];
+  const int nleafrun = 1 << L;
+  cpx<R> *SL = S + (int64_t)(nleafrun - 1) * P;
+  for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
+    const int k = t / P, nn = t % P;
+    const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
+    const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+    cpx<R> acc = mk<R>(0, 0);
+    for (int e = 0; e < m; ++e) {
+      const R qe = (R)qr[e] * h;
+      acc.re = fma(qe, B[e * P].re, acc.re);
+      acc.im = fma(qe, B[e * P].im, acc.im);
+    }
+    SL[t] = acc;
+  }
+  __syncthreads();
+  for (int l = L - 1; l >= 0; --l) {
+    const cpx<R> *Sc = S + (int64_t)((1 << (l + 1)) - 1) * P;
+    cpx<R> *Sp = S + (int64_t)((1 << l) - 1) * P;
+    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) {
+      const int k = t / P, nn = t % P;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int j = 0; j < 2; ++j) {
+        const cpx<R> *Mc = Sc + (2 * k + j) * P;
+        const cpx<R> *T = T2 + (j * P + nn) * P;
+        for (int kk = 0; kk <= nn; ++kk) cmac(acc, T[kk], Mc[kk]);
+      }
+      Sp[t] = acc;
+    }
+    __syncthreads();
+  }
+  cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
+  for (int l = 0; l <= L; ++l) {
+    const cpx<R> *Sl = S + (int64_t)((1 << l) - 1) * P;
+    cpx<R> *Ml = M + (blevel_offset(l) + ((int64_t)side << l)) * P;
+    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) Ml[t] = Sl[t];
+  }
+}
+
+// The same pass through global memory, for trees whose levels do not fit in shared memory
+// (FP64 at the largest depths).
+template <typename R, int P>
+__global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restrict__ q, Mats<R> mt,
+                                                   cpx<R> *__restrict__ Mb) {
   const int side = blockIdx.x, rhs = blockIdx.y;
   const int n = g.n, m = g.m, L = g.L;
   cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
@@ -483,7 +537,7 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
     const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
     cpx<R> acc = mk<R>(0, 0);
     for (int e = 0; e < m; ++e) {
-      const R qe = (R)(qr[e] * g.h);
+      const R qe = (R)qr[e] * (R)g.h;
       acc.re = fma(qe, B[e * P].re, acc.re);
       acc.im = fma(qe, B[e * P].im, acc.im);
     }
@@ -505,13 +559,47 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
   }
 }
 
+template <typename R, int P>
+size_t bnd_up_smem(int L) {
+  return sizeof(cpx<R>) * ((size_t)2 * P * P + (size_t)((1 << (L + 1)) - 1) * P);
+}
+
 // ------------------------------------------------------------------ collocation points
+// Set-up for the single-precision forms: the near-field log kernel between each collocation
+// point and the nodes of its near volume leaves, formed in FP64 and stored FP32.  Warp per
+// point; layout [boundary leaf: pfirst m m^2][point in leaf][near leaf][node].
+__global__ void k_colloc_mat(Geo g, const int32_t *__restrict__ pfirst, const int32_t *__restrict__ psrc,
+                             float *__restrict__ Kc) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)g.NG) return;
+  const int ge = (int)wid, n = g.n, m = g.m, L = g.L;
+  const int side = ge / n, along = ge % n;
+  const int64_t bl = ((int64_t)side << L) + along / m;
+  const int64_t numc = (2 * (int64_t)along + 1) * (n + 1);
+  const int c_near = pfirst[bl + 1] - pfirst[bl];
+  const int64_t kbase = ((int64_t)pfirst[bl] * m + (int64_t)(along % m) * c_near) * (m * m);
+  for (int e0 = pfirst[bl]; e0 < pfirst[bl + 1]; ++e0) {
+    int a, b;
+    morton_decode((uint32_t)psrc[e0], a, b);
+    float *kr = Kc + kbase + (int64_t)(e0 - pfirst[bl]) * (m * m);
+    for (int t = lane; t < m * m; t += 32) {
+      const int i = a * m + t % m, j = b * m + t / m;
+      int u, d;
+      side_coords(side, n + 1, i + 1, j + 1, u, d);
+      const double ds = (double)(numc - 2 * (int64_t)u * n) / (2.0 * n);
+      kr[t] = (float)(0.5 * log(ds * ds + (double)d * (double)d));
+    }
+  }
+}
+
+
 // (V r)(y_m) = -(1/2pi)[ Re sum_n Lt_n zt^n  +  sum_{near nodes} w_j ln|y_m - x_j| ].
 // Warp per (collocation point, rhs); requires L < 32.
 template <typename R>
 __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<R> *__restrict__ Lb,
                          const int32_t *__restrict__ pfirst, const int32_t *__restrict__ psrc,
-                         double *__restrict__ vcol) {
+                         double *__restrict__ vcol, const float *__restrict__ Kc) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (int64_t)g.NG * nrhs) return;
@@ -524,9 +612,36 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   const R inv2n = R(1) / (R)(2 * n);
   const int64_t numc = (2 * (int64_t)along + 1) * (n + 1);
   R acc = 0;
+  // precomputed (single-precision forms): Kc[(pfirst m + ip c) m^2 + el m^2 + t] = ln|y - x_t|
+  const int c_near = pfirst[bl + 1] - pfirst[bl];
+  const int64_t kbase = ((int64_t)pfirst[bl] * m + (int64_t)(along % m) * c_near) * (m * m);
+  bool done_near = false;
+  if constexpr (std::is_same<R, float>::value) {
+    if (Kc && m == 8 && (g.pad & 3) == 0 && (g.npad & 3) == 0) {
+      // 16 lanes per near leaf, 4 consecutive nodes of a leaf row per lane (float4)
+      const float4 *k4 = reinterpret_cast<const float4 *>(Kc + kbase);
+      for (int it = lane; it < c_near * 16; it += 32) {
+        const int el = it >> 4, t4 = it & 15;
+        int a, b;
+        morton_decode((uint32_t)psrc[pfirst[bl] + el], a, b);
+        const int row = b * 8 + (t4 >> 1), col = a * 8 + (t4 & 1) * 4;
+        const float4 wv = *reinterpret_cast<const float4 *>(W + (int64_t)(row + g.pad) * g.npad + col + g.pad);
+        const float4 kv = k4[it];
+        acc += wv.x * kv.x + wv.y * kv.y + wv.z * kv.z + wv.w * kv.w;
+      }
+      done_near = true;
+    }
+  }
+  if (!done_near)
   for (int e0 = pfirst[bl]; e0 < pfirst[bl + 1]; ++e0) {
     int a, b;
     morton_decode((uint32_t)psrc[e0], a, b);
+    if (Kc) {
+      const float *kr = Kc + kbase + (int64_t)(e0 - pfirst[bl]) * (m * m);
+      for (int t = lane; t < m * m; t += 32)
+        acc += W[(int64_t)(b * m + t / m + g.pad) * g.npad + a * m + t % m + g.pad] * (R)kr[t];
+      continue;
+    }
     for (int t = lane; t < m * m; t += 32) {
       const int i = a * m + t % m, j = b * m + t / m;
       int u, d;
@@ -543,10 +658,11 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   if (lane <= L) {
     const int l = lane, nl = n >> l;
     const int64_t id = ((int64_t)side << l) + along / nl;
-    const double off = ((n + 1.0) / n) * ((along % nl) + 0.5 - 0.5 * nl) / nl;
-    double ex, ey;
-    side_dir(side, ex, ey);
-    const cpx<R> z = mk<R>((R)(off * ex), (R)(off * ey));
+    // offset of the point from the run centre, in run units: (n+1)/n (j + 1/2 - nl/2) / nl
+    const R off = (R)(n + 1) * ((R)(along % nl) + R(0.5) - R(0.5) * (R)nl) / ((R)n * (R)nl);
+    const R ex = (side == 0) ? R(1) : (side == 2 ? R(-1) : R(0));
+    const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
+    const cpx<R> z = mk<R>(off * ex, off * ey);
     const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
     cpx<R> v = mk<R>(0, 0);
     for (int kk = p - 1; kk >= 0; --kk) v = v * z + Lc[kk];
@@ -673,6 +789,70 @@ __global__ void __launch_bounds__(256) k_bnd_near(Geo g, int64_t nbnear, int nrh
     R s = 0;
     for (int q2 = 0; q2 < ngrp; ++q2) s += red[q2 * mm + threadIdx.x];
     phib[((int64_t)rhs * nbnear + slot) * mm + threadIdx.x] = s;
+  }
+}
+
+// The same integrals formed once at set-up (FP64, stored FP32) for the single-precision
+// forms: K[(first[slot] m + idx) m^2 + t] = h int_{element idx} ln|x_t - y| ds, so each apply
+// is a product with q instead of ~5e6 log/atan2 evaluations at 1024^2.
+__global__ void __launch_bounds__(256) k_bnd_near_mat(Geo g, int64_t nbnear, const int32_t *__restrict__ leaf,
+                                                      const int32_t *__restrict__ first,
+                                                      const int32_t *__restrict__ src, float *__restrict__ K) {
+  const int slot = blockIdx.x;
+  const int n = g.n, m = g.m, L = g.L, mm = m * m;
+  const int ngrp = blockDim.x / mm;
+  const int t = threadIdx.x % mm, grp = threadIdx.x / mm;
+  if (grp >= ngrp) return;
+  int a, b;
+  morton_decode((uint32_t)leaf[slot], a, b);
+  const double ell = (n + 1.0) / n;
+  const int x = a * m + t % m + 1, y = b * m + t / m + 1;
+  const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
+  for (int idx = grp; idx < cnt; idx += ngrp) {
+    const int bl = src[f0 + idx / m], e = idx % m;
+    const int side = bl >> L;
+    const int64_t kk = bl & ((int64_t(1) << L) - 1);
+    int u, d;
+    side_coords(side, n + 1, x, y, u, d);
+    const int64_t num = (kk * m + e) * (int64_t)(n + 1) - (int64_t)u * n;
+    K[((int64_t)f0 * m + idx) * mm + t] = (float)(g.h * seg_log_int<double>((double)num / n, ell, (double)d));
+  }
+}
+
+// Apply of the precomputed integrals: block per (slot, rhs), 16 groups of 16 threads; a
+// thread takes 4 consecutive nodes (float4) of every 16th element; partials meet in shared
+// memory.  Requires m = 8 (64 nodes per leaf).
+__global__ void __launch_bounds__(256) k_bnd_near_k(Geo g, int64_t nbnear, int nrhs, const int32_t *__restrict__ first,
+                                                    const int32_t *__restrict__ src, const float *__restrict__ K,
+                                                    const double *__restrict__ q, float *__restrict__ phib) {
+  __shared__ float4 red[16][16];
+  const int slot = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L;
+  const int t4 = threadIdx.x & 15, grp = threadIdx.x >> 4;
+  const double *qr = q + (int64_t)rhs * g.NG;
+  const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
+  const float4 *K4 = reinterpret_cast<const float4 *>(K) + (int64_t)f0 * m * 16;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int idx = grp; idx < cnt; idx += 16) {
+    const int bl = src[f0 + idx / m], e = idx % m;
+    const int64_t kk = bl & ((int64_t(1) << L) - 1);
+    const float qe = (float)qr[(bl >> L) * n + kk * m + e];
+    const float4 kv = K4[(int64_t)idx * 16 + t4];
+    acc.x = fmaf(kv.x, qe, acc.x);
+    acc.y = fmaf(kv.y, qe, acc.y);
+    acc.z = fmaf(kv.z, qe, acc.z);
+    acc.w = fmaf(kv.w, qe, acc.w);
+  }
+  red[grp][t4] = acc;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int tt = threadIdx.x >> 2, c = threadIdx.x & 3;
+    float sacc = 0.f;
+    for (int q2 = 0; q2 < 16; ++q2) {
+      const float4 v = red[q2][tt];
+      sacc += c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+    }
+    phib[((int64_t)rhs * nbnear + slot) * 64 + threadIdx.x] = sacc;
   }
 }
 
@@ -1027,7 +1207,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
                                                               Ls.vbb_src, Mv, Lb);
     k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, 0, Mv, Mb, Lv, Lb);
     k_colloc<R><<<nblk((int64_t)g.NG * nrhs * 32, 128), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
-                                                                   H.fb.vcol);
+                                                                   H.fb.vcol, H.fb.kcol);
     FMMPC_LAUNCH_CHECK();
     launches += 3;
     if (part == PART_VCOL) {
@@ -1048,7 +1228,19 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(4);
-    k_bnd_up<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, H.fb.q, mt, Mb);
+    {
+      const size_t sm = bnd_up_smem<R, P>(g.L);
+      static int maxsm = 0;
+      static bool raised[2][17] = {};
+      bool &done = raised[std::is_same<R, double>::value ? 1 : 0][P];
+      if (!done) {
+        FMMPC_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+        FMMPC_CUDA(cudaFuncSetAttribute(k_bnd_up<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        done = true;
+      }
+      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, H.fb.q, mt, Mb);
+      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, H.fb.q, mt, Mb);
+    }
     FMMPC_LAUNCH_CHECK();
     ++launches;
   }
@@ -1076,8 +1268,12 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   launches += run_l2l<R, P>(H, nrhs, s);
   if (with_bnd && Ls.nbnear > 0) {
     mark(8);
-    k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
-                                                                 Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
+    if (std::is_same<R, float>::value && H.fb.knear && g.m == 8)
+      k_bnd_near_k<<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_first, Ls.pbv_src,
+                                                                   H.fb.knear, H.fb.q, (float *)H.fb.phib);
+    else
+      k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
+                                                                   Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
     FMMPC_LAUNCH_CHECK();
     ++launches;
   }
@@ -1231,6 +1427,19 @@ void init_fmm(fmmpc_handle &H) {
   } else {
     set_p2p_smem_limit<float>();
     alloc_fmm<float>(H);
+    // near-boundary operators formed once (the geometry is fixed): element integrals at the
+    // nodes of volume leaves next to the boundary, and the log kernel at collocation points
+    const int64_t nent = H.lists.n_p2p_vb * (int64_t)H.g.m * H.g.m * H.g.m;
+    if (nent > 0 && H.lists.nbnear > 0) {
+      H.fb.knear = H.pool.get<float>(nent);
+      H.fb.kcol = H.pool.get<float>(nent);
+      k_bnd_near_mat<<<(unsigned)H.lists.nbnear, 256, 0, H.stream>>>(H.g, H.lists.nbnear, H.lists.pbv_leaf,
+                                                                    H.lists.pbv_first, H.lists.pbv_src, H.fb.knear);
+      k_colloc_mat<<<nblk((int64_t)H.g.NG * 32, 128), 128, 0, H.stream>>>(H.g, H.lists.pvb_first, H.lists.pvb_src,
+                                                                         H.fb.kcol);
+      FMMPC_LAUNCH_CHECK();
+      FMMPC_CUDA(cudaStreamSynchronize(H.stream));
+    }
   }
   FMMPC_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_in, cudaEventDisableTiming));

@@ -31,6 +31,8 @@ struct FmmBufs {
   double *vcol = nullptr;    // [nrhs][NG] V r at collocation points
   double *q = nullptr;       // [nrhs][NG] BEM density
   double *vt = nullptr;      // [nrhs][NG] side-DFT of vcol for the block-circulant apply
+  float *knear = nullptr;    // near-boundary element integrals (single-precision forms)
+  float *kcol = nullptr;     // collocation-point near-field log kernel (single-precision forms)
 };
 
 // tensor-core lattice P2P (p2p_tc.cu)

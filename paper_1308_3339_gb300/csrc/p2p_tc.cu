@@ -61,23 +61,47 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.  The
-// same pass writes the FP32 zero-padded weight image the other stages read (w, npad, pad).
-__global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int64_t total, const double *__restrict__ r,
+// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.  Thread
+// per (rhs, leaf, node row of the leaf): it reads the row's 8 weights, writes their two
+// 32-byte pieces of the leaf's swizzled 128-byte rows (hi, lo) and the same 8 weights of the
+// FP32 zero-padded weight image the other stages read (w, npad, pad).  Leaves are the
+// fastest index, so reads and writes of neighbouring threads are contiguous.
+__global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int nrhs, const double *__restrict__ r,
                             float *__restrict__ ahi, float *__restrict__ alo, float *__restrict__ wimg, int npad,
                             int pad) {
+  const int NL = n / 8;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int64_t N = (int64_t)n * n;
-  const int64_t rhs = t / N, q = t - rhs * N;
-  const int i = (int)(q % n), j = (int)(q / n);
-  wimg[rhs * npad * (int64_t)npad + (int64_t)(j + pad) * npad + i + pad] = (float)(h2 * r[t]);
-  const int X = i / 8 + R, Y = j / 8 + R, k = (j % 8) * 8 + (i % 8), kk = k % 32;
-  const int64_t idx = (((rhs * NLY + Y) * 2 + k / 32) * NLX + X) * 32 + (((kk / 4) ^ (X & 7)) * 4) + (kk % 4);
-  const double w = h2 * r[t];
-  const float hi = tf32_round((float)w);
-  ahi[idx] = hi;
-  alo[idx] = tf32_round((float)(w - (double)hi));
+  if (t >= (int64_t)nrhs * NL * NL * 8) return;
+  const int Xl = (int)(t % NL);
+  const int64_t rest = t / NL;
+  const int jr = (int)(rest % 8);  // node row of the leaf: K half jr / 4, row jj = jr % 4 in it
+  const int64_t rest2 = rest / 8;
+  const int Yl = (int)(rest2 % NL);
+  const int64_t rhs = rest2 / NL;
+  const int kh = jr >> 2, jj = jr & 3;
+  const int X = Xl + R, Y = Yl + R;
+  const int64_t rowoff = (((rhs * NLY + Y) * 2 + kh) * NLX + X) * 32;
+  float4 *hrow = reinterpret_cast<float4 *>(ahi + rowoff), *lrow = reinterpret_cast<float4 *>(alo + rowoff);
+  const int j = 8 * Yl + jr, i0 = 8 * Xl;
+  const double *src = r + rhs * (int64_t)n * n + (int64_t)j * n + i0;
+  float w[8], hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double wd = h2 * src[q];
+    w[q] = (float)wd;
+    hi[q] = tf32_round(w[q]);
+    lo[q] = tf32_round((float)(wd - (double)hi[q]));
+  }
+  // k = 32 kh + 8 jj + q: chunk c = 2 jj + q / 4 of the K half, stored at c ^ (X & 7)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = 2 * jj + h;
+    hrow[c ^ (X & 7)] = make_float4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
+    lrow[c ^ (X & 7)] = make_float4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+  }
+  float *wr = wimg + rhs * (int64_t)npad * npad + (int64_t)(j + pad) * npad + i0 + pad;
+  reinterpret_cast<float4 *>(wr)[0] = make_float4(w[0], w[1], w[2], w[3]);
+  reinterpret_cast<float4 *>(wr)[1] = make_float4(w[4], w[5], w[6], w[7]);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
@@ -370,9 +394,9 @@ void init_tc_p2p(fmmpc_handle &H) {
 // TF32 hi/lo weight strips of the right-hand side r (FP64), for run_p2p_tc, and the FP32 weight image.
 int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s, float *wimg) {
   const Geo &g = H.g;
-  const int64_t total = (int64_t)g.n * g.n * nrhs;
-  k_tc_strips<<<nblk(total), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, total, r, H.tcp.ahi, H.tcp.alo,
-                                          wimg, g.npad, g.pad);
+  const int64_t threads = (int64_t)nrhs * (g.n / 8) * (g.n / 8) * 8;
+  k_tc_strips<<<nblk(threads), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, nrhs, r, H.tcp.ahi, H.tcp.alo,
+                                            wimg, g.npad, g.pad);
   FMMPC_LAUNCH_CHECK();
   return 1;
 }
