@@ -179,7 +179,9 @@ int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 int fmmpc_set_graphs(fmmpc_handle *h, int32_t on);
 
 /* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream.
- * fmmpc_set_timing(h, 1) creates the events and turns recording on (0 turns it off).
+ * fmmpc_set_timing(h, 1) creates the events and turns recording on for every stage; 2
+ * records only the four events around the M2L (stage 5) and P2P (stage 9) kernels, so the
+ * rest of the apply runs without event records; 0 turns recording off.
  * fmmpc_get_timing synchronises the stream and writes the durations in milliseconds of
  * the stages of the last apply into ms[0 .. min(cap, count)), *count = 11 stages:
  *  0 weight image, 1 P2M + M2M (Sec. 5.3 items 1-2), 2 collocation pass (M2L to boundary

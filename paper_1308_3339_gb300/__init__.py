@@ -91,8 +91,10 @@ class FmmPreconditioner:
     def set_graphs(self, on: bool = True):
         check(self.lib.fmmpc_set_graphs(self._h, 1 if on else 0), self._h)
 
-    def set_timing(self, on: bool = True):
-        check(self.lib.fmmpc_set_timing(self._h, 1 if on else 0), self._h)
+    def set_timing(self, on=True):
+        """True / 1: every stage; 2: only the M2L and P2P kernels; False / 0: off."""
+        mode = 0 if on is False else (1 if on is True else int(on))
+        check(self.lib.fmmpc_set_timing(self._h, mode), self._h)
 
     def stage_times(self) -> dict:
         """Stage durations (ms) of the last apply, from CUDA events on the handle stream."""

@@ -369,7 +369,8 @@ int fmmpc_set_timing(fmmpc_handle *h, int32_t on) {
   return guarded(h, [&] {
     if (on && !h->ev[0])
       for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k) FMMPC_CUDA(cudaEventCreate(&h->ev[k]));
-    h->timing = on != 0;
+    require(on >= 0 && on <= 2, "set_timing: mode must be 0, 1 or 2");
+    h->timing = on;
     return FMMPC_OK;
   });
 }
@@ -381,6 +382,14 @@ int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count) {
     FMMPC_CUDA(cudaStreamSynchronize(h->stream));
     const int ns = fmmpc_handle::NSTAGE;
     *count = ns;
+    if (h->timing == 2) {  // only M2L (5 -> 6) and P2P (9 -> 10)
+      for (int k = 0; k < ns && k < cap; ++k) ms[k] = 0.0f;
+      const int pairs[2][2] = {{5, 6}, {9, 10}};
+      for (auto &pr : pairs)
+        if (pr[0] < cap && h->stage_hit[pr[0]] && h->stage_hit[pr[1]])
+          FMMPC_CUDA(cudaEventElapsedTime(&ms[pr[0]], h->ev[pr[0]], h->ev[pr[1]]));
+      return FMMPC_OK;
+    }
     for (int k = 0; k < ns && k < cap; ++k) {
       ms[k] = 0.0f;
       if (!h->stage_hit[k]) continue;

@@ -1,11 +1,13 @@
 // Boundary-element set-up (Sec. 4.3): constant elements, no nodes at the corners, 4n
 // equal elements on the square, collocation at their midpoints.  The single-layer
 // matrix S_mk = int_{Gamma_k} G(y_m, y) dGamma (left side of Eq. e:ubound) is assembled in
-// FP64 from the closed-form element integral (Sec. 4.2) and inverted once, in place, by
-// Gauss-Jordan elimination with partial pivoting, so each apply needs one FP64
-// matrix-vector product for q.  The square's 90-degree rotation symmetry makes S (and its
-// inverse) block circulant over the four sides; only the first block row is kept.
+// FP64 from the closed-form element integral (Sec. 4.2).  The square's 90-degree rotation
+// symmetry makes S block circulant over the four sides, so a 4-point DFT over the side
+// index splits it into three n x n blocks (one complex); each is inverted once by
+// Gauss-Jordan elimination with partial pivoting, and the apply works in that basis.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "handle.cuh"
 
@@ -131,30 +133,43 @@ __global__ void k_swap_cols(int N, double *__restrict__ A, int c1, int c2) {
   row[c2] = t;
 }
 
-// T[m] = [C0+C1+C2+C3 | C0-C1+C2-C3 | C0-C2 | C1-C3][m] from the first n rows of the inverse
-__global__ void k_bem_dft(int n, const double *__restrict__ A, double *__restrict__ T) {
+// From the first block row of S (n x 4n): S^0 and S^2 (n x n) and the real form of S^1,
+// E = [[S0 - S2, -(S1 - S3)], [S1 - S3, S0 - S2]] (2n x 2n).
+__global__ void k_bem_blocks(int n, const double *__restrict__ S, double *__restrict__ B0, double *__restrict__ B2,
+                             double *__restrict__ E) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
   const int64_t m = t / n;
   const int k = (int)(t % n);
-  const double *row = A + m * 4 * n;
-  const double c0 = row[k], c1 = row[n + k], c2 = row[2 * n + k], c3 = row[3 * n + k];
-  double *o = T + m * 4 * n;
-  o[k] = (c0 + c2) + (c1 + c3);
-  o[n + k] = (c0 + c2) - (c1 + c3);
-  o[2 * n + k] = c0 - c2;
-  o[3 * n + k] = c1 - c3;
+  const double *row = S + m * 4 * n;
+  const double s0 = row[k], s1 = row[n + k], s2 = row[2 * n + k], s3 = row[3 * n + k];
+  B0[m * n + k] = (s0 + s2) + (s1 + s3);
+  B2[m * n + k] = (s0 + s2) - (s1 + s3);
+  const double re = s0 - s2, im = s1 - s3;
+  E[m * 2 * n + k] = re;
+  E[m * 2 * n + n + k] = -im;
+  E[(m + n) * 2 * n + k] = im;
+  E[(m + n) * 2 * n + n + k] = re;
 }
 
-}  // namespace
+// T[m] = [inv(S^0) | inv(S^2) | A | B][m] with A + i B = inv(S^1): A, B from the left
+// column blocks of inv(E).
+__global__ void k_bem_pack(int n, const double *__restrict__ B0, const double *__restrict__ B2,
+                           const double *__restrict__ E, double *__restrict__ T) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int64_t m = t / n;
+  const int k = (int)(t % n);
+  double *o = T + m * 4 * n;
+  o[k] = B0[m * n + k];
+  o[n + k] = B2[m * n + k];
+  o[2 * n + k] = E[m * 2 * n + k];
+  o[3 * n + k] = E[(m + n) * 2 * n + k];
+}
 
-void init_bem(fmmpc_handle &H, DevPool &tmp) {
-  const Geo &g = H.g;
-  const int N = g.NG;
-  cudaStream_t s = H.stream;
-  double *A = tmp.get<double>((size_t)N * N);  // full matrix, inverted in place
-  k_bem_S<<<nblk((int64_t)N * N), 256, 0, s>>>(g.n, g.h, g.lnh, A);
-  FMMPC_LAUNCH_CHECK();
+// In-place Gauss-Jordan inverse of the N x N matrix A (row-major, device) with partial
+// pivoting; returns the smallest pivot magnitude (0 for a singular matrix).
+double gj_invert(double *A, int N, cudaStream_t s, DevPool &tmp) {
   int *piv = tmp.get<int>(N);
   double *pinv = tmp.get<double>(1), *pabs = tmp.get<double>(N), *col = tmp.get<double>(N);
   for (int k = 0; k < N; ++k) {
@@ -171,15 +186,37 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   FMMPC_CUDA(cudaStreamSynchronize(s));
   double amin = ha[0];
   for (int k = 0; k < N; ++k) amin = std::min(amin, ha[k]);
-  if (!(amin > 0.0)) throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
   for (int k = N - 1; k >= 0; --k)
     if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, A, k, hp[k]);
   FMMPC_LAUNCH_CHECK();
-  // the inverse is block circulant in the four sides (90-degree rotation of the square):
-  // keep its first block row [C0 | C1 | C2 | C3] (n x 4n), stored as its side-DFT
-  // [C0+C1+C2+C3 | C0-C1+C2-C3 | C0-C2 | C1-C3] for the apply
-  H.Sinv = H.pool.get<double>((size_t)g.n * N);
-  k_bem_dft<<<nblk((int64_t)g.n * g.n), 256, 0, s>>>(g.n, A, H.Sinv);
+  return amin;
+}
+
+}  // namespace
+
+void init_bem(fmmpc_handle &H, DevPool &tmp) {
+  // S is block circulant in the four sides (the 90-degree rotation of the square maps
+  // element (s, k) to (s+1, k)), so a 4-point DFT over the side index block-diagonalises
+  // it: with S_d = S[(0, .), (d, .)], S^0 = S0+S1+S2+S3, S^2 = S0-S1+S2-S3 (real) and
+  // S^1 = (S0 - S2) + i (S1 - S3).  The apply needs exactly the inverses of these blocks,
+  // [inv(S^0) | inv(S^2) | Re inv(S^1) | Im inv(S^1)] per row, so only the first block row
+  // of S is assembled and three n x n systems are inverted (the complex one through its
+  // 2n x 2n real form [[Re, -Im], [Im, Re]], whose inverse is [[A, -B], [B, A]]).
+  const Geo &g = H.g;
+  const int n = g.n, N = g.NG;
+  cudaStream_t s = H.stream;
+  double *S = tmp.get<double>((size_t)n * N);  // first block row, n x 4n
+  k_bem_S<<<nblk((int64_t)n * N), 256, 0, s>>>(n, g.h, g.lnh, S);
+  FMMPC_LAUNCH_CHECK();
+  double *B0 = tmp.get<double>((size_t)n * n), *B2 = tmp.get<double>((size_t)n * n);
+  double *E = tmp.get<double>((size_t)4 * n * n);
+  k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, S, B0, B2, E);
+  FMMPC_LAUNCH_CHECK();
+  const double a0 = gj_invert(B0, n, s, tmp), a2 = gj_invert(B2, n, s, tmp), a1 = gj_invert(E, 2 * n, s, tmp);
+  if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
+    throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
+  H.Sinv = H.pool.get<double>((size_t)n * N);
+  k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, E, H.Sinv);
   FMMPC_LAUNCH_CHECK();
   FMMPC_CUDA(cudaStreamSynchronize(s));
 }

@@ -1166,13 +1166,20 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   int cur = -1;
   auto mark = [&](int stage) {
     if (!H.timing) return;
+    if (H.timing == 2) {  // events only around the M2L (5 -> 6) and P2P (9 -> 10) stages
+      if (stage == 5 || stage == 6 || stage == 9 || stage == 10) {
+        FMMPC_CUDA(cudaEventRecordWithFlags(H.ev[stage], s, cudaEventRecordExternal));
+        H.stage_hit[stage] = true;
+      }
+      return;
+    }
     // external record nodes keep the events timeable when the apply is captured in a graph
     FMMPC_CUDA(cudaEventRecordWithFlags(H.ev[stage], s, cudaEventRecordExternal));
     if (cur >= 0) H.stage_hit[cur] = true;
     cur = stage;
   };
   auto mark_end = [&]() {
-    if (!H.timing) return;
+    if (!H.timing || H.timing == 2) return;
     FMMPC_CUDA(cudaEventRecordWithFlags(H.ev[fmmpc_handle::NSTAGE], s, cudaEventRecordExternal));
     if (cur >= 0) H.stage_hit[cur] = true;
   };

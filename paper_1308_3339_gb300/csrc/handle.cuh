@@ -64,7 +64,7 @@ struct GraphEntry {
   const double *r;
   double *out;
   int nrhs;
-  bool timing;
+  int timing;
   cudaGraphExec_t exec;
   uint64_t last;
 };
@@ -104,7 +104,7 @@ struct fmmpc_handle {
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
   static constexpr int NSTAGE = 11;
-  bool timing = false;
+  int timing = 0;  // 0 off, 1 every stage, 2 only the M2L and P2P kernels (four events)
   cudaEvent_t ev[NSTAGE + 1] = {};
   bool stage_hit[NSTAGE] = {};
   double t_setup_ms = 0.0;
