@@ -20,6 +20,7 @@
 #include <complex>
 #include <mutex>
 
+#include <set>
 #include <type_traits>
 
 #include "handle.cuh"
@@ -965,7 +966,7 @@ template <typename R, int M>
 __global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, int nrhs, int do_bnd,
                             const cpx<R> *__restrict__ Lv, const R *__restrict__ phib,
                             const int32_t *__restrict__ bslot, double *__restrict__ out,
-                            const double *__restrict__ near2) {
+                            const float *__restrict__ near1, const float *__restrict__ near2) {
   const int64_t nleaf = int64_t(1) << (2 * L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nleaf * M * nrhs) return;
@@ -991,11 +992,22 @@ __global__ void k_far_final(int n, int L, int p, int64_t ncell, int64_t nbnear, 
   }
   const int64_t off = (int64_t)rhs * n * n + (int64_t)(gy * M + ty) * n + gx * M;
   double *o = out + off;
+  if (near1) {
+    // tensor-core near field: the two raw halves and the far term meet in FP64 (they often
+    // cancel) -- one add and one fused multiply-add per node
 #pragma unroll
-  for (int q = 0; q < M; ++q) {
-    double v = (double)acc[q].re;
-    if (pb) v += (double)pb[q];
-    o[q] += v * NEG_INV_2PI + (near2 ? near2[off + q] : 0.0);
+    for (int q = 0; q < M; ++q) {
+      float v = (float)acc[q].re;
+      if (pb) v += (float)pb[q];
+      o[q] = fma((double)near1[off + q] + (double)near2[off + q], NEG_INV_2PI, (double)(v * (float)NEG_INV_2PI));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      double v = (double)acc[q].re;
+      if (pb) v += (double)pb[q];
+      o[q] += v * NEG_INV_2PI;
+    }
   }
 }
 
@@ -1071,15 +1083,15 @@ void run_p2p(fmmpc_handle &H, const void *table, double *out, int nrhs, cudaStre
 
 template <typename R>
 void run_far_final(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s,
-                   const double *near2 = nullptr) {
+                   const float *near1 = nullptr, const float *near2 = nullptr) {
   const Geo &g = H.g;
   const int64_t tasks = g.nleaf * g.m * nrhs;
   const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
   const R *pb = (const R *)H.fb.phib;
   switch (g.m) {
-    case 4: k_far_final<R, 4><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
-    case 8: k_far_final<R, 8><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
-    default: k_far_final<R, 16><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near2); break;
+    case 4: k_far_final<R, 4><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 8: k_far_final<R, 8><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    default: k_far_final<R, 16><<<nblk(tasks, 128), 128, 0, s>>>(g.n, g.L, g.p, g.ncell, H.lists.nbnear, nrhs, do_bnd, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
   }
   FMMPC_LAUNCH_CHECK();
 }
@@ -1288,7 +1300,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   if (tc) {
     launches += run_p2p_tc(H, false, out, nrhs, s);
     mark(10);
-    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s, H.tcp.near2);
+    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s, H.tcp.near1, H.tcp.near2);
   } else {
     run_p2p<R>(H, H.fb.table, out, nrhs, s);  // the CUDA-core kernel also evaluates L2P and the sum
     ++launches;

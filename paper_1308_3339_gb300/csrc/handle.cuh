@@ -41,7 +41,7 @@ struct TcP2P {
   int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, nofs = 0, smem = 0, usplit = 0;
   int row_oy[33] = {}, row_q0[33] = {}, row_q1[33] = {}, row_ox0[33] = {};
   float *ahi = nullptr, *alo = nullptr, *bmat = nullptr, *bmat_lnh = nullptr;
-  double *near2 = nullptr;  // second half of the near field, added by L2P
+  float *near1 = nullptr, *near2 = nullptr;  // the two halves of the near-field sum, FP32 images
   int *err = nullptr;
 };
 

@@ -18,7 +18,7 @@
 // commit-to-barrier round trip is longer than two groups of MMAs).  Each tile's 74 groups
 // are split between two CTAs (37 each; the second writes a scratch image that the L2P pass
 // adds), and two CTAs share an SM, so one's copies and barrier round trips overlap the
-// other's MMAs.
+// other's MMAs.  Both halves are written as FP32 images of the raw sums.
 //
 // Data: per padded leaf row and K half, each leaf's 32 weights are one 128-byte row in the
 // 128-byte swizzle (chunk c of leaf X at position c ^ (X % 8)), leaves contiguous, so the
@@ -49,7 +49,7 @@ constexpr int TC_MAXROWS = 33;
 struct TcArgs {
   const float *ahi, *alo;  // [nrhs][NLY][K half][NLX][32], swizzled per leaf
   const float *bmat;       // [nofs][K half][hi, lo][64][32], swizzled per row t
-  double *out, *out2;  // first and second half of the stencil (grid z = 2 rhs + half)
+  float *out1, *out2;  // near-field sums (unscaled), first and second half of the stencil (z = 2 rhs + half)
   int *err;
   int n, R, NLX, NLY, NS, nrows, nofs, npass, usplit;
   int row_oy[TC_MAXROWS], row_q0[TC_MAXROWS], row_q1[TC_MAXROWS], row_ox0[TC_MAXROWS];
@@ -86,11 +86,10 @@ __global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int nrhs,
   const double *src = r + rhs * (int64_t)n * n + (int64_t)j * n + i0;
   float w[8], hi[8], lo[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double wd = h2 * src[q];
-    w[q] = (float)wd;
+  for (int q = 0; q < 8; ++q) {  // one rounding of the FP64 product (as the weight image
+    w[q] = (float)(h2 * src[q]);   // of the other engine); hi + lo is that FP32 value
     hi[q] = tf32_round(w[q]);
-    lo[q] = tf32_round((float)(wd - (double)hi[q]));
+    lo[q] = tf32_round(w[q] - hi[q]);
   }
   // k = 32 kh + 8 jj + q: chunk c = 2 jj + q / 4 of the K half, stored at c ^ (X & 7)
 #pragma unroll
@@ -259,16 +258,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
     }
     if (ok && !abort_flag) {
       const int X = lx0 + 32 * qd + lane;
-      double *o = (half ? a.out2 : a.out) + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
-      const double sc = -1.0 / (2.0 * PI);
+      // the half's sum as accumulated (FP32, unscaled): the -1/(2 pi) and the sum of the two
+      // halves are applied once, in FP64, where the near field meets the far field
+      float *o = (half ? a.out2 : a.out1) + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
 #pragma unroll
       for (int tr = 0; tr < 8; ++tr) {
-        double2 *orow = reinterpret_cast<double2 *>(o + (int64_t)tr * a.n);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int t0 = 8 * tr + 2 * c;
-          orow[c] = make_double2(sc * (double)sum[t0], sc * (double)sum[t0 + 1]);
-        }
+        float4 *orow = reinterpret_cast<float4 *>(o + (int64_t)tr * a.n);
+        orow[0] = make_float4(sum[8 * tr], sum[8 * tr + 1], sum[8 * tr + 2], sum[8 * tr + 3]);
+        orow[1] = make_float4(sum[8 * tr + 4], sum[8 * tr + 5], sum[8 * tr + 6], sum[8 * tr + 7]);
       }
     }
   }
@@ -289,9 +286,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
   }
 }
 
-__global__ void k_add_near2(int64_t total, const double *__restrict__ b, double *__restrict__ a) {
+__global__ void k_near_combine(int64_t total, const float *__restrict__ a, const float *__restrict__ b,
+                               double *__restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < total) a[t] += b[t];
+  if (t < total) out[t] = ((double)a[t] + (double)b[t]) * NEG_INV_2PI;
 }
 
 float tf32_round_host(double v) {
@@ -383,7 +381,8 @@ void init_tc_p2p(fmmpc_handle &H) {
     }
     H.tcp.usplit = best;
   }
-  H.tcp.near2 = H.pool.get<double>((size_t)H.nrhs_max * g.n * g.n);
+  H.tcp.near1 = H.pool.get<float>((size_t)H.nrhs_max * g.n * g.n);
+  H.tcp.near2 = H.pool.get<float>((size_t)H.nrhs_max * g.n * g.n);
   H.tcp.err = H.pool.get<int>(1);
   FMMPC_CUDA(cudaMemsetAsync(H.tcp.err, 0, sizeof(int), H.stream));
   const int smem = 4 * ((H.tcp.NS * 128 + 1023) & ~1023) + TC_NB * TC_BGRP + 1024;  // + alignment slack
@@ -408,7 +407,8 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
   a.ahi = H.tcp.ahi;
   a.alo = H.tcp.alo;
   a.bmat = with_lnh ? H.tcp.bmat_lnh : H.tcp.bmat;
-  a.out = out;
+  a.out1 = H.tcp.near1;
+  (void)out;
   a.err = H.tcp.err;
   a.n = g.n;
   a.R = g.R;
@@ -432,10 +432,10 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
   return 1;
 }
 
-// out += the second half of the near field (PART_NEAR, where no L2P pass follows).
+// out = the two halves of the near field (PART_NEAR, where no L2P pass follows).
 int add_near2(fmmpc_handle &H, double *out, int nrhs, cudaStream_t s) {
   const int64_t total = (int64_t)H.g.n * H.g.n * nrhs;
-  k_add_near2<<<nblk(total), 256, 0, s>>>(total, H.tcp.near2, out);
+  k_near_combine<<<nblk(total), 256, 0, s>>>(total, H.tcp.near1, H.tcp.near2, out);
   FMMPC_LAUNCH_CHECK();
   return 1;
 }
