@@ -50,13 +50,15 @@ struct TcM2L {
   bool enabled = false;
   int kind = 0;  // 0 TF32, 1 BF16
   int nsplit = 0;  // leading multipoles split hi + lo
-  int ntiles = 0, stage_bytes = 0, smem = 0, nofs_total = 0;
-  int ngroups[4] = {}, goff[4] = {}, ooff[4] = {};
+  int width = 32;  // outputs per target class (N = 4 width)
+  int ntiles = 0, smem = 0, nofs_total = 0;  // nofs_total: shifts
+  int nparts = 1, gpart[3] = {}, gpart_sh[3] = {};
   int64_t rows_per_rhs = 0;
   int64_t lev_row0[24] = {};
   int lev_P[24] = {};
   unsigned char *img = nullptr, *bmat = nullptr;
-  int4 *tiles = nullptr, *groups = nullptr;
+  int2 *tiles = nullptr;
+  int4 *groups = nullptr;
   int *dxs = nullptr, *err = nullptr;
 };
 

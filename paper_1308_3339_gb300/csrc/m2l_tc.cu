@@ -9,26 +9,32 @@
 //   C_o[0][0] = log o, C_o[0][k] = o^-k, C_o[n][0] = (-1)^(n+1) / (n o^n),
 //   C_o[n][k] = (-1)^n (n+k-1)! / (n! (k-1)! o^(n+k)),  L~_0 += ln(rho) M~_0.
 // Written as real 2p x 2p blocks, one level's M2L is a lattice convolution of the
-// multipole image with 140 fixed matrices.  The image of each level is split into its four
+// multipole image with fixed matrices.  The image of each level is split into its four
 // parity sub-images, each zero-padded by 4 cells and flattened with row pitch P = S + 8
-// (S = 2^(l-1) cells), so that for a target class and an offset the sources of 128
-// consecutive flattened targets are 128 consecutive rows of one sub-image, shifted by
-// dy P + dx.  One CTA takes such a tile of targets (M = 128) and sweeps its class's offsets,
-// D[t][u] += sum_v X[t + shift][v] B_o[u][v] with K = 2p real inputs and N = 32 outputs: 2p
-// real parts of L~ plus the two sums of M~_0 that carry the ln rho term.  Padding targets are
-// computed and dropped.  The low-order terms dominate the translated
-// field and meets the large log o + ln rho, so their products are split hi + lo in the
-// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded input x rounded
-// matrix, input residual x rounded matrix, rounded input x matrix residual.
+// (S = 2^(l-1) cells).  Target (i, j) of parity class c = (cx, cy) and offset o take source
+// 2 (i, j) + c - o, which lies in sub-image ((cx - ox) & 1, (cy - oy) & 1) at (i + dx, j + dy)
+// with (dx, dy) = floor((c - o) / 2): the same target position in all four classes reads
+// the same source row for a shift (source parity, dx, dy), each class through its own
+// offset.  So one CTA takes 128 consecutive flattened target positions (M = 128) of all
+// four classes and sweeps the 124 shifts, D[t][32 c + u] += sum_v X[t + dy P + dx][v] B_s[32 c + u][v],
+// with the four classes' matrices stacked along N = 128 (zero rows where a class has no
+// offset for the shift), K = the multipole inputs.  Per class the 32 outputs are the 2p
+// real parts of L~ and, in outputs 30 and 31, the two sums of M~_0 that carry ln rho.
+// Padding targets are computed and dropped.  The low-order terms dominate the translated
+// field and meet the large log o + ln rho, so their products are split hi + lo in the
+// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded
+// input x rounded matrix, input residual x rounded matrix, rounded input x matrix residual.
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
-// descriptor offset.  Offsets are grouped by (source parity, dy); one 144-row window of the
-// source sub-image serves every dx of a group.  Warp 0 streams window + B groups through
-// two stages (two CTAs share an SM, so their copy and MMA round trips overlap), warp 1
-// issues the MMAs, one fresh TMEM accumulator per group (four in
-// flight), and warps 2-5 drain each into Kahan-compensated FP32 sums: one long chain of
-// MMAs would drift with the tensor core's truncating adds (~2^-24 of the partial per MMA).
+// descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
+// source sub-image serves every dx of a group.  Warp 0 streams windows and per-shift B
+// blocks through separate rings, warp 1 issues the MMAs, one fresh 128-column TMEM
+// accumulator per group (four in flight), and warps 2-9 add each into FP32 sums: one long
+// chain of MMAs would drift with the tensor core's truncating adds (~2^-24 of the partial
+// per MMA).  When a level has too few tiles to fill the GPU, each tile's groups are split
+// into two parts run by two CTAs, which add into zeroed L~.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -47,26 +53,36 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 constexpr int M2L_WROWS = 144;                  // window rows (128 targets + 2 x 4 shift + alignment)
 constexpr int M2L_WBYTES = M2L_WROWS * 128;     // 18 KB
-constexpr int M2L_BBYTES = 32 * 128;            // one offset's B operand: 32 outputs x 128 B
-constexpr int M2L_NSTG = 2;                     // stages per CTA (two CTAs per SM)
-constexpr int M2L_NACC = 4;                     // TMEM accumulators (32 columns each) in flight
-constexpr int M2L_THREADS = 192;
+constexpr int M2L_NWIN = 2;                     // window slots
+constexpr int M2L_NACC = 4;                     // TMEM accumulators in flight (128-column stride)
+constexpr int M2L_NGR = 16;                     // group barriers (> B slots, > M2L_NACC)
+constexpr int M2L_EPI_WARPS = 8;
+constexpr int M2L_THREADS = 64 + 32 * M2L_EPI_WARPS;
 constexpr int M2L_TAIL = 256;                   // zero rows after each sub-image (window overrun)
-constexpr int M2L_MAXGRP = 128, M2L_MAXOFS = 225;  // per class: (source parity, dy) groups, offsets
+constexpr int M2L_MAXGRP = 64, M2L_MAXSH = 255;  // per part: (source parity, dy) groups, shifts
+// W outputs per class (2p real parts of L~, the two M~_0 sums in the last two): N = 4 W;
+// one shift's B block is N rows of 128 bytes; as many B slots as fit beside the windows
+template <int W>
+struct M2lShape {
+  static constexpr int N = 4 * W;
+  static constexpr int BBYTES = N * 128;
+  static constexpr int NB = W == 24 ? 14 : 11;
+  static constexpr int SMEM = M2L_NWIN * M2L_WBYTES + NB * BBYTES + 1024;
+};
 
 struct M2lArgs {
   const unsigned char *img;     // [nrhs][rows_per_rhs][128 B]
-  const unsigned char *bmat;    // [class][offset][32][128 B]
-  const int4 *tiles;            // (level, class, f0, -)
-  const int4 *groups;           // [class][group]: (source parity, dy, first offset, count)
-  const int *dxs;               // [class][offset]: dx of the offset
+  const unsigned char *bmat;    // [shift][4 W][128 B]
+  const int2 *tiles;            // (level, f0)
+  const int4 *groups;           // (source parity, dy, first shift, count), by (source parity, dy)
+  const int *dxs;               // [shift]: dx of the shift
   cpx<float> *Lv;               // [nrhs][ncell][p]
   int *err;
   int64_t rows_per_rhs, ncell;
   int64_t lev_row0[24];         // first image row of level l (parity 0)
   int lev_P[24];
-  int ngroups[4], goff[4], ooff[4], nofs[4];
-  int p, n, stage_bytes, nks, nsplit;
+  int gpart[3], gpart_sh[3];    // groups and shifts of each part
+  int p, n, nks, nsplit, nparts;
 };
 
 __device__ __forceinline__ int floor8(int x) { return x & ~7; }
@@ -98,7 +114,8 @@ __device__ __forceinline__ float m2l_input(const cpx<float> *M, int v, int p, in
 }
 
 // Multipole image rows: thread per (rhs, cell at level >= 2, 16-byte chunk).  Also clears
-// the local expansions of levels 0 and 1, which have no M2L sources.
+// the local expansions of levels 0 and 1, which have no M2L sources, and those of every
+// level when the M2L is split into parts that add.
 template <int KIND>
 __global__ void k_m2l_pack(M2lArgs a, int nrhs, int64_t ncell_lo, int64_t ncell_hi, const cpx<float> *__restrict__ Mv) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,6 +137,11 @@ __global__ void k_m2l_pack(M2lArgs a, int nrhs, int64_t ncell_lo, int64_t ncell_
   const int64_t f = (int64_t)((y >> 1) + 4) * P + (x >> 1) + 4;
   const int64_t row = rhs * a.rows_per_rhs + a.lev_row0[l] + (int64_t)q * ((int64_t)P * P + M2L_TAIL) + f;
   const cpx<float> *M = Mv + (rhs * a.ncell + gidx) * a.p;
+  if (a.nparts > 1) {  // the M2L parts add into L~
+    cpx<float> *Lc = a.Lv + (rhs * a.ncell + gidx) * a.p;
+    if (chunk < a.p) Lc[chunk] = mk<float>(0.f, 0.f);
+    if (chunk + 8 < a.p) Lc[chunk + 8] = mk<float>(0.f, 0.f);
+  }
   uint32_t w[4];
   if (KIND == 0) {
 #pragma unroll
@@ -136,59 +158,106 @@ __global__ void k_m2l_pack(M2lArgs a, int nrhs, int64_t ncell_lo, int64_t ncell_
   *dst = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
+// L~ of target (i, j) of class c at level l from its W outputs t[0 .. W): 2p real parts,
+// and in the last two the sums of Re M~_0 and Im M~_0 that carry the ln rho term of L~_0.
+template <int W>
+__device__ __forceinline__ void m2l_store(const M2lArgs &a, const float *t, int l, int c, int i, int j, int rhs,
+                                          float lnrho) {
+  const int x = 2 * i + (c & 1), y = 2 * j + (c >> 1);
+  const int64_t gidx = level_offset(l) + morton_encode((uint32_t)x, (uint32_t)y);
+  cpx<float> *L = a.Lv + ((int64_t)rhs * a.ncell + gidx) * a.p;
+  const float l0r = t[0] + lnrho * t[W - 2], l0i = t[1] + lnrho * t[W - 1];
+  if (a.nparts == 1) {
+    L[0] = mk<float>(l0r, l0i);
+#pragma unroll
+    for (int nn = 1; nn < W / 2 - 1; ++nn)
+      if (nn < a.p) L[nn] = mk<float>(t[2 * nn], t[2 * nn + 1]);
+  } else {
+    // two parts add onto zeros: (0 + a) + b = (0 + b) + a, so the order of the two atomic
+    // adds does not change the result
+    float2 *L2 = reinterpret_cast<float2 *>(L);
+    atomicAdd(L2, make_float2(l0r, l0i));
+#pragma unroll
+    for (int nn = 1; nn < W / 2 - 1; ++nn)
+      if (nn < a.p) atomicAdd(L2 + nn, make_float2(t[2 * nn], t[2 * nn + 1]));
+  }
+}
+
+template <int KIND, int W>
+__global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
+  using SH = M2lShape<W>;
+  constexpr int N = SH::N, NB = SH::NB, BBYTES = SH::BBYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t full[M2L_NSTG], empty[M2L_NSTG], acc_full[M2L_NACC], acc_empty[M2L_NACC], done;
+  // wfull / bfull: a window / one shift's B block landed; gdone (ring of M2L_NGR groups):
+  // the group's MMAs completed (one commit), which frees its window slot, its B slots and
+  // its accumulator
+  __shared__ uint64_t wfull[M2L_NWIN], bfull[NB], gdone[M2L_NGR], acc_empty[M2L_NACC], done;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag, used;
-  __shared__ int4 sgrp[M2L_MAXGRP];  // the class's groups and offsets, off the issue path
-  __shared__ int sdx[M2L_MAXOFS];
+  __shared__ int abort_flag, w_used, b_used;
+  __shared__ int4 sgrp[M2L_MAXGRP];  // this part's groups and shifts, off the issue path
+  __shared__ int sdx[M2L_MAXSH];
+  __shared__ unsigned char sgof[M2L_MAXSH];  // group of each shift of the part
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
-  const int4 tile = a.tiles[blockIdx.x];
-  const int l = tile.x, c = tile.y, f0 = tile.z, rhs = blockIdx.y;
+  unsigned char *wbuf = smem, *bbuf = smem + M2L_NWIN * M2L_WBYTES;
+  const int2 tile = a.tiles[blockIdx.x];
+  const int l = tile.x, f0 = tile.y, part = blockIdx.y, rhs = blockIdx.z;
   const int P = a.lev_P[l];
-  const int ng = a.ngroups[c];
-  for (int i = tid; i < ng; i += blockDim.x) sgrp[i] = a.groups[a.goff[c] + i];
-  for (int i = tid; i < a.nofs[c]; i += blockDim.x) sdx[i] = a.dxs[a.ooff[c] + i];
-  const int4 *grp = sgrp;
+  const int g0 = a.gpart[part], ng = a.gpart[part + 1] - g0;
+  const int sh0 = a.gpart_sh[part], nsh = a.gpart_sh[part + 1] - sh0;
+  for (int i = tid; i < ng; i += blockDim.x) {
+    const int4 g = a.groups[g0 + i];
+    sgrp[i] = g;
+    for (int k = 0; k < g.w; ++k) sgof[g.z - sh0 + k] = (unsigned char)i;
+  }
+  for (int i = tid; i < nsh; i += blockDim.x) sdx[i] = a.dxs[sh0 + i];
   if (tid == 0) {
-    for (int s = 0; s < M2L_NSTG; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
-    }
-    for (int b = 0; b < M2L_NACC; ++b) {
-      tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], 4);
-    }
+    for (int s = 0; s < M2L_NWIN; ++s) tc::mbar_init(&wfull[s], 1);
+    for (int s = 0; s < NB; ++s) tc::mbar_init(&bfull[s], 1);
+    for (int s = 0; s < M2L_NGR; ++s) tc::mbar_init(&gdone[s], 1);
+    for (int b = 0; b < M2L_NACC; ++b) tc::mbar_init(&acc_empty[b], M2L_EPI_WARPS);
     tc::mbar_init(&done, 1);
     tc::mbar_init_fence();
     abort_flag = 0;
-    used = 0;
+    w_used = b_used = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 32 * M2L_NACC);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 128 * M2L_NACC);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  int issued = 0;
+  int w_issued = 0, b_issued = 0;
   if (warp == 0) {
     if (lane == 0) {
-      // producer: per group, the source window and the group's B operands into one stage
+      // producer: per group its source window into window slot gi % M2L_NWIN (free once
+      // group gi - M2L_NWIN is done), then per shift its B block (the four classes'
+      // translation matrices stacked along N) into B slot b % NB (free once the group
+      // holding shift b - NB is done); groups complete in order
       bool ok = true;
-      for (int gi = 0; gi < ng && !abort_flag; ++gi) {
-        const int s = gi % M2L_NSTG;
-        if (gi >= M2L_NSTG && !tc::mbar_wait(&empty[s], ((gi / M2L_NSTG) - 1) & 1, &abort_flag)) { ok = false; break; }
-        const int4 g = grp[gi];  // (source parity, dy, first, count)
-        const int ws = floor8(f0 + g.y * P - 4);
+      int known = -1;  // groups known to be done: 0 .. known
+      auto wait_done = [&](int gq) -> bool {
+        if (gq <= known) return true;
+        if (!tc::mbar_wait(&gdone[gq % M2L_NGR], (gq / M2L_NGR) & 1, &abort_flag)) return false;
+        known = gq;
+        return true;
+      };
+      for (int gi = 0; gi < ng && ok && !abort_flag; ++gi) {
+        const int4 g = sgrp[gi];  // (source parity, dy, first shift, count)
+        if (!wait_done(gi - M2L_NWIN)) { ok = false; break; }
+        const int w0 = floor8(f0 + g.y * P - 4);
         const unsigned char *src = a.img + ((int64_t)rhs * a.rows_per_rhs + a.lev_row0[l] +
-                                            (int64_t)g.x * ((int64_t)P * P + M2L_TAIL) + ws) * 128;
-        unsigned char *st = smem + s * a.stage_bytes;
-        tc::mbar_expect_tx(&full[s], M2L_WBYTES + g.w * M2L_BBYTES);
-        tc::bulk_g2s(st, src, M2L_WBYTES, &full[s]);
-        tc::bulk_g2s(st + M2L_WBYTES, a.bmat + ((int64_t)a.ooff[c] + g.z) * M2L_BBYTES, g.w * M2L_BBYTES, &full[s]);
-        issued = gi + 1;
+                                            (int64_t)g.x * ((int64_t)P * P + M2L_TAIL) + w0) * 128;
+        const int ws = gi % M2L_NWIN;
+        tc::mbar_expect_tx(&wfull[ws], M2L_WBYTES);
+        tc::bulk_g2s(wbuf + ws * M2L_WBYTES, src, M2L_WBYTES, &wfull[ws]);
+        w_issued = gi + 1;
+        for (int k = 0; k < g.w; ++k) {
+          const int b = b_issued, bs = b % NB;
+          if (b >= NB && !wait_done(sgof[b - NB])) { ok = false; break; }
+          tc::mbar_expect_tx(&bfull[bs], BBYTES);
+          tc::bulk_g2s(bbuf + bs * BBYTES, a.bmat + (int64_t)(g.z + k) * BBYTES, BBYTES, &bfull[bs]);
+          b_issued = b + 1;
+        }
       }
       if (!ok) {
         abort_flag = 1;
@@ -197,30 +266,35 @@ __global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: one fresh accumulator per group; one commit per group (the epilogue,
-      // which waits for the same completion, releases the stage)
-      const uint32_t idesc = KIND == 0 ? tc::idesc_tf32(128, 32)
-                                       : ((1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24));
+      // MMA issuer: per group one fresh accumulator and one commit; per shift M = 128
+      // targets, N = 4 classes x W outputs
+      const uint32_t idesc = KIND == 0 ? tc::idesc_tf32(128, N)
+                                       : ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                          ((128u >> 4) << 24));
       const int nks = a.nks;  // K steps of 32 bytes (8 TF32 or 16 BF16 inputs each)
       bool ok = true;
-      for (int gi = 0; gi < ng; ++gi) {
-        const int s = gi % M2L_NSTG, ab = gi % M2L_NACC;
-        if (!tc::mbar_wait(&full[s], (gi / M2L_NSTG) & 1, &abort_flag)) { ok = false; break; }
-        used = gi + 1;
+      int b = 0;
+      for (int gi = 0; gi < ng && ok; ++gi) {
+        const int ab = gi % M2L_NACC, ws = gi % M2L_NWIN;
+        if (!tc::mbar_wait(&wfull[ws], (gi / M2L_NWIN) & 1, &abort_flag)) { ok = false; break; }
+        w_used = gi + 1;
         if (gi >= M2L_NACC && !tc::mbar_wait(&acc_empty[ab], ((gi / M2L_NACC) - 1) & 1, &abort_flag)) {
           ok = false;
           break;
         }
-        tc::fence_after();
-        const int4 g = grp[gi];
-        const int ws = floor8(f0 + g.y * P - 4);
-        const uint32_t st = tc::smem_addr(smem + s * a.stage_bytes);
-        const uint32_t d = tmem + 32 * ab;
+        const int4 g = sgrp[gi];
+        const int w0 = floor8(f0 + g.y * P - 4);
+        const uint32_t wst = tc::smem_addr(wbuf + ws * M2L_WBYTES);
+        const uint32_t d = tmem + 128 * ab;
         uint32_t acc = 0;
-        for (int k = 0; k < g.w; ++k) {
-          const int dx = sdx[g.z + k];
-          const uint32_t arow = st + (uint32_t)((f0 + g.y * P + dx - ws) * 128);
-          const uint32_t brow = st + M2L_WBYTES + k * M2L_BBYTES;
+        for (int k = 0; k < g.w; ++k, ++b) {
+          const int bs = b % NB;
+          if (!tc::mbar_wait(&bfull[bs], (b / NB) & 1, &abort_flag)) { ok = false; break; }
+          b_used = b + 1;
+          tc::fence_after();
+          const int dx = sdx[g.z - sh0 + k];
+          const uint32_t arow = wst + (uint32_t)((f0 + g.y * P + dx - w0) * 128);
+          const uint32_t brow = tc::smem_addr(bbuf + bs * BBYTES);
           for (int ks = 0; ks < nks; ++ks) {
             const uint64_t ad = tc::desc_sw128(arow + 32 * ks), bd = tc::desc_sw128(brow + 32 * ks);
             if (KIND == 0) {
@@ -234,7 +308,8 @@ __global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
             acc = 1;
           }
         }
-        tc::commit(&acc_full[ab]);
+        if (!ok) break;
+        tc::commit(&gdone[gi % M2L_NGR]);
       }
       if (!ok) {
         abort_flag = 1;
@@ -243,28 +318,29 @@ __global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
       tc::commit(&done);
     }
   } else {
-    // epilogue: drain each group's accumulator into FP32 sums (Kahan), one target per thread
-    const int qd = warp & 3;
-    float sum[32], cmp[32];
+    // epilogue: warps 2-9; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one target each) and
+    // the 2W columns of classes 2h, 2h + 1, h = (w - 2) / 4, in loads of 16 columns; each
+    // group's accumulator is added into plain FP32 sums (a group is at most a few dozen
+    // MMAs, so the tensor core's truncating adds stay near 2^-24 relative)
+    const int qd = warp & 3, h = (warp - 2) >> 2;
+    float sum[2 * W];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) sum[i] = cmp[i] = 0.0f;
+    for (int i = 0; i < 2 * W; ++i) sum[i] = 0.0f;
     bool ok = true;
     for (int gi = 0; gi < ng; ++gi) {
       const int ab = gi % M2L_NACC;
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[ab], (gi / M2L_NACC) & 1, &abort_flag))) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&gdone[gi % M2L_NGR], (gi / M2L_NGR) & 1, &abort_flag))) {
         ok = false;
         break;
       }
       tc::fence_after();
-      if (warp == 2 && lane == 0) tc::mbar_arrive(&empty[gi % M2L_NSTG]);  // the group's MMAs are done
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 32 * ab, v);
+      const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 128 * ab + 2 * W * h;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float y = v[i] - cmp[i];
-        const float t = sum[i] + y;
-        cmp[i] = (t - sum[i]) - y;
-        sum[i] = t;
+      for (int q = 0; q < 2 * W / 16; ++q) {
+        float v[16];
+        tc::tmem_ld16(ta + 16 * q, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sum[16 * q + i] += v[i];
       }
       tc::fence_before();
       __syncwarp();
@@ -278,23 +354,9 @@ __global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
     const int S = P - 8;
     const int i = f % P - 4, j = f / P - 4;
     if (ok && !abort_flag && i >= 0 && i < S && j >= 0 && j < S) {
-      const int x = 2 * i + (c & 1), y = 2 * j + (c >> 1);
-      const int64_t gidx = level_offset(l) + morton_encode((uint32_t)x, (uint32_t)y);
-      cpx<float> *L = a.Lv + ((int64_t)rhs * a.ncell + gidx) * a.p;
       const float lnrho = logf((float)(a.n >> l));
-      float tot[32];
-#pragma unroll
-      for (int u = 0; u < 32; ++u) tot[u] = sum[u] - cmp[u];
-      float m0r = 0.f, m0i = 0.f;  // the sums of M~_0 in outputs 2p, 2p + 1 (p <= 15)
-#pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        if (u == 2 * a.p) m0r = tot[u];
-        if (u == 2 * a.p + 1) m0i = tot[u];
-      }
-      L[0] = mk<float>(tot[0] + lnrho * m0r, tot[1] + lnrho * m0i);
-#pragma unroll
-      for (int nn = 1; nn < 16; ++nn)
-        if (nn < a.p) L[nn] = mk<float>(tot[2 * nn], tot[2 * nn + 1]);
+      m2l_store<W>(a, sum, l, 2 * h, i, j, rhs, lnrho);
+      m2l_store<W>(a, sum + W, l, 2 * h + 1, i, j, rhs, lnrho);
     }
   }
   __syncwarp();
@@ -302,12 +364,14 @@ __global__ void __launch_bounds__(M2L_THREADS, 2) k_m2l_tc(M2lArgs a) {
   if (!finished && lane == 0) atomicOr(a.err, 4);
   tc::fence_before();
   __syncthreads();
-  if (abort_flag && warp == 0 && lane == 0)
-    for (int u = used; u < issued; ++u) tc::mbar_wait(&full[u % M2L_NSTG], (u / M2L_NSTG) & 1, nullptr);
+  if (abort_flag && warp == 0 && lane == 0) {  // copies still in flight land before the block exits
+    for (int u = w_used; u < w_issued; ++u) tc::mbar_wait(&wfull[u % M2L_NWIN], (u / M2L_NWIN) & 1, nullptr);
+    for (int u = b_used; u < b_issued; ++u) tc::mbar_wait(&bfull[u % NB], (u / NB) & 1, nullptr);
+  }
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, 32 * M2L_NACC);
+    tc::tmem_dealloc(tmem, 128 * M2L_NACC);
   }
 }
 
@@ -395,6 +459,7 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   const Geo &g = H.g;
   const int L = g.L, p = g.p;
   T.kind = (H.prec == FMMPC_PREC_MIXED_TF32) ? 0 : 1;
+  T.width = (2 * p + 2 <= 24) ? 24 : 32;  // outputs per class
   // hi/lo splits of the leading multipoles in the spare K columns (24 for TF32, 32 for BF16)
   // K capacity: TF32 32 inputs (4 steps of 8, one 128-byte row); BF16 48 (3 steps of 16)
   const int kcap = T.kind == 0 ? 32 : 48;
@@ -413,97 +478,37 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   FMMPC_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, H.stream));
   FMMPC_CUDA(cudaStreamSynchronize(H.stream));
   if (herr) throw Error(FMMPC_ERR_INVALID, "tensor-core M2L: the M2L lists are not translation invariant");
-  // per class: offsets sorted by (source parity, dy, dx), grouped by (source parity, dy)
-  std::vector<int4> groups;
-  std::vector<int> dxs;
-  std::vector<std::pair<int, int>> ofs_all;  // (ox, oy) in class order
-  int maxcnt = 1;
+  // shifts (source parity, dy, dx) with the offset each class translates over it, grouped
+  // by (source parity, dy) and sorted by dx: target (i, j) of class c = (cx, cy) takes
+  // source cell 2 (i, j) + (cx, cy) - o, which sits in source parity sub-image
+  // ((cx - ox) & 1, (cy - oy) & 1) at (i + dx, j + dy), dx = floor((cx - ox) / 2)
+  std::map<std::pair<int, int>, std::map<int, std::array<int, 4>>> bykey;  // (sp, dy) -> dx -> offset per class
   for (int c = 0; c < 4; ++c) {
     const int cx = c & 1, cy = c >> 1;
-    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> bykey;  // (sp, dy) -> (dx, idx)
     for (int oy = -7; oy <= 7; ++oy)
       for (int ox = -7; ox <= 7; ++ox) {
         if (!tab[c * 225 + (oy + 7) * 15 + ox + 7]) continue;
         const int spx = (cx - ox) & 1, spy = (cy - oy) & 1;
         const int dx = (cx - ox - spx) / 2, dy = (cy - oy - spy) / 2;
-        bykey[{spx + 2 * spy, dy}].push_back({dx, (oy + 7) * 15 + ox + 7});
+        auto &row = bykey[{spx + 2 * spy, dy}];
+        if (!row.count(dx)) row[dx] = {-1, -1, -1, -1};
+        row[dx][c] = (oy + 7) * 15 + ox + 7;
       }
-    T.goff[c] = (int)groups.size();
-    T.ooff[c] = (int)dxs.size();
-    int first = 0;
-    for (auto &kv : bykey) {
-      auto v = kv.second;
-      std::sort(v.begin(), v.end());
-      groups.push_back(make_int4(kv.first.first, kv.first.second, first, (int)v.size()));
-      for (auto &e : v) {
-        dxs.push_back(e.first);
-        ofs_all.push_back({e.second % 15 - 7, e.second / 15 - 7});
-      }
-      first += (int)v.size();
-      maxcnt = std::max(maxcnt, (int)v.size());
+  }
+  std::vector<int4> groups;
+  std::vector<int> dxs;
+  std::vector<std::array<int, 4>> shift_ofs;
+  for (auto &kv : bykey) {
+    groups.push_back(make_int4(kv.first.first, kv.first.second, (int)dxs.size(), (int)kv.second.size()));
+    for (auto &e : kv.second) {
+      dxs.push_back(e.first);
+      shift_ofs.push_back(e.second);
     }
-    T.ngroups[c] = (int)groups.size() - T.goff[c];
   }
-  T.nofs_total = (int)dxs.size();
-  for (int c = 0; c < 4; ++c)
-    if (T.ngroups[c] > M2L_MAXGRP) throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L: too many offset groups");
-  // B operands: rows u (2p outputs, then sum Re M0, sum Im M0), columns v (2p inputs)
-  std::vector<unsigned char> B((size_t)T.nofs_total * M2L_BBYTES, 0);
-  std::vector<double> fact(2 * p + 2, 1.0);
-  for (int i = 1; i < (int)fact.size(); ++i) fact[i] = fact[i - 1] * i;
-  for (int q = 0; q < T.nofs_total; ++q) {
-    const std::complex<double> o((double)ofs_all[q].first, (double)ofs_all[q].second);
-    std::vector<std::complex<double>> C((size_t)p * p);
-    for (int nn = 0; nn < p; ++nn)
-      for (int k = 0; k < p; ++k) {
-        std::complex<double> cv;
-        if (nn == 0 && k == 0) cv = std::log(o);
-        else if (nn == 0) cv = 1.0 / std::pow(o, k);
-        else if (k == 0) cv = ((nn % 2) ? 1.0 : -1.0) / ((double)nn * std::pow(o, nn));
-        else cv = ((nn % 2) ? -1.0 : 1.0) * fact[nn + k - 1] / (fact[nn] * fact[k - 1]) / std::pow(o, nn + k);
-        C[(size_t)nn * p + k] = cv;
-      }
-    auto Breal = [&](int u, int v) -> double {  // real form of C_o, plus the two M~_0 sum rows
-      if (u >= 2 * p) return (u - 2 * p == v) ? 1.0 : 0.0;
-      const std::complex<double> cv = C[(size_t)(u / 2) * p + v / 2];
-      if ((u & 1) == 0) return (v & 1) ? -cv.imag() : cv.real();
-      return (v & 1) ? cv.real() : cv.imag();
-    };
-    auto put = [&](int u, int v, double val) {
-      unsigned char *row = B.data() + (size_t)q * M2L_BBYTES + (size_t)u * 128;
-      if (T.kind == 0) {
-        const int ch = v / 4, e = v % 4;
-        const float f = tf32_round_host_m2l(val);
-        std::memcpy(row + ((ch ^ (u & 7)) * 16) + 4 * e, &f, 4);
-      } else {
-        const int ch = v / 8, e = v % 8;
-        const uint16_t b = bf16_round_host(val);
-        std::memcpy(row + ((ch ^ (u & 7)) * 16) + 2 * e, &b, 2);
-      }
-    };
-    for (int nn = 0; nn < p; ++nn)
-      for (int k = 0; k < p; ++k) {
-        const std::complex<double> cv = C[(size_t)nn * p + k];
-        put(2 * nn, 2 * k, cv.real());
-        put(2 * nn, 2 * k + 1, -cv.imag());
-        put(2 * nn + 1, 2 * k, cv.imag());
-        put(2 * nn + 1, 2 * k + 1, cv.real());
-      }
-    put(2 * p, 0, 1.0);
-    put(2 * p + 1, 1, 1.0);
-    // split columns: residual inputs meet the rounded column, rounded inputs the column residual
-    for (int j = 0; j < T.nsplit; ++j)
-      for (int u = 0; u < 2 * p + 2; ++u)
-        for (int e = 0; e < 2; ++e) {
-          const double full = Breal(u, 2 * j + e);
-          const double hi = T.kind == 0 ? (double)tf32_round_host_m2l(full) : bf16_value(bf16_round_host(full));
-          put(u, 2 * p + 4 * j + e, full);
-          put(u, 2 * p + 4 * j + 2 + e, full - hi);
-        }
-  }
-  // images and tiles
+  const int nshift = (int)dxs.size(), ngrp = (int)groups.size();
+  // images and tiles (128 consecutive flattened targets of one level, all four classes)
   int64_t rows = 0;
-  std::vector<int4> tiles;
+  std::vector<int2> tiles;
   for (int l = 0; l < 24; ++l) {
     T.lev_row0[l] = 0;
     T.lev_P[l] = 0;
@@ -514,30 +519,114 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
     T.lev_row0[l] = rows;
     rows += 4 * ((int64_t)P * P + M2L_TAIL);
     const int fs = 4 * P + 4, fe = (S + 3) * P + S + 3;
-    for (int c = 0; c < 4; ++c)
-      for (int f0 = fs; f0 <= fe; f0 += 128) tiles.push_back(make_int4(l, c, f0, 0));
+    for (int f0 = fs; f0 <= fe; f0 += 128) tiles.push_back(make_int2(l, f0));
   }
   T.rows_per_rhs = rows;
   T.ntiles = (int)tiles.size();
-  T.stage_bytes = (M2L_WBYTES + maxcnt * M2L_BBYTES + 1023) & ~1023;
-  T.smem = M2L_NSTG * T.stage_bytes + 1024;
+  // with few tiles per right-hand side, each tile's groups are split into two parts of about
+  // equal shift counts (two CTAs); the choice depends on the geometry only, so a batch and
+  // its single right-hand sides take the same sums
+  int nsm = 0;
+  FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
+  T.nparts = (2 * T.ntiles <= nsm && ngrp >= 2) ? 2 : 1;
+  T.gpart[0] = 0;
+  T.gpart[T.nparts] = ngrp;
+  if (T.nparts == 2) {
+    int best = 1, bestd = 1 << 30;
+    for (int k = 1; k < ngrp; ++k) {
+      const int d = std::abs(2 * groups[k].z - nshift);
+      if (d < bestd) bestd = d, best = k;
+    }
+    T.gpart[1] = best;
+  }
+  for (int q = 0; q <= T.nparts; ++q) T.gpart_sh[q] = T.gpart[q] < ngrp ? groups[T.gpart[q]].z : nshift;
+  int maxcnt = 0;
+  for (auto &gr : groups) maxcnt = std::max(maxcnt, gr.w);
+  for (int q = 0; q < T.nparts; ++q)
+    if (T.gpart[q + 1] - T.gpart[q] > M2L_MAXGRP || T.gpart_sh[q + 1] - T.gpart_sh[q] > M2L_MAXSH ||
+        maxcnt > (T.width == 24 ? M2lShape<24>::NB : M2lShape<32>::NB))
+      throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L: too many shifts");
+  T.nofs_total = nshift;
+  // B operands, one 4W x 128-byte block per shift: row W c + u is output u of class c
+  // (2p real parts of L~; in W - 2, W - 1 the sums of Re M~_0 and Im M~_0), zero where class c has no
+  // offset for the shift; column v is input v of the multipole image row
+  const int W = T.width, bbytes = 4 * W * 128;
+  std::vector<unsigned char> B((size_t)nshift * bbytes, 0);
+  std::vector<double> fact(2 * p + 2, 1.0);
+  for (int i = 1; i < (int)fact.size(); ++i) fact[i] = fact[i - 1] * i;
+  for (int q = 0; q < nshift; ++q)
+    for (int c = 0; c < 4; ++c) {
+      const int oi = shift_ofs[q][c];
+      if (oi < 0) continue;
+      const std::complex<double> o((double)(oi % 15 - 7), (double)(oi / 15 - 7));
+      std::vector<std::complex<double>> C((size_t)p * p);
+      for (int nn = 0; nn < p; ++nn)
+        for (int k = 0; k < p; ++k) {
+          std::complex<double> cv;
+          if (nn == 0 && k == 0) cv = std::log(o);
+          else if (nn == 0) cv = 1.0 / std::pow(o, k);
+          else if (k == 0) cv = ((nn % 2) ? 1.0 : -1.0) / ((double)nn * std::pow(o, nn));
+          else cv = ((nn % 2) ? -1.0 : 1.0) * fact[nn + k - 1] / (fact[nn] * fact[k - 1]) / std::pow(o, nn + k);
+          C[(size_t)nn * p + k] = cv;
+        }
+      auto Breal = [&](int u, int v) -> double {  // real form of C_o, plus the two M~_0 sum rows
+        if (u >= W - 2) return (u - (W - 2) == v) ? 1.0 : 0.0;
+        const std::complex<double> cv = C[(size_t)(u / 2) * p + v / 2];
+        if ((u & 1) == 0) return (v & 1) ? -cv.imag() : cv.real();
+        return (v & 1) ? cv.real() : cv.imag();
+      };
+      auto put = [&](int u, int v, double val) {
+        const int n = W * c + u;
+        unsigned char *row = B.data() + (size_t)q * bbytes + (size_t)n * 128;
+        if (T.kind == 0) {
+          const int ch = v / 4, e = v % 4;
+          const float f = tf32_round_host_m2l(val);
+          std::memcpy(row + ((ch ^ (n & 7)) * 16) + 4 * e, &f, 4);
+        } else {
+          const int ch = v / 8, e = v % 8;
+          const uint16_t b = bf16_round_host(val);
+          std::memcpy(row + ((ch ^ (n & 7)) * 16) + 2 * e, &b, 2);
+        }
+      };
+      std::vector<int> outs;  // 2p real parts of L~, the two M~_0 sums in outputs W - 2, W - 1
+      for (int u = 0; u < 2 * p; ++u) outs.push_back(u);
+      outs.push_back(W - 2);
+      outs.push_back(W - 1);
+      for (int u : outs)
+        for (int v = 0; v < 2 * p; ++v) put(u, v, Breal(u, v));
+      // split columns: residual inputs meet the rounded column, rounded inputs the column residual
+      for (int j = 0; j < T.nsplit; ++j)
+        for (int u : outs)
+          for (int e = 0; e < 2; ++e) {
+            const double full = Breal(u, 2 * j + e);
+            const double hi = T.kind == 0 ? (double)tf32_round_host_m2l(full) : bf16_value(bf16_round_host(full));
+            put(u, 2 * p + 4 * j + e, full);
+            put(u, 2 * p + 4 * j + 2 + e, full - hi);
+          }
+    }
+  T.smem = W == 24 ? M2lShape<24>::SMEM : M2lShape<32>::SMEM;
   int maxsm = 0;
   FMMPC_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
-  if (T.smem + 2048 > maxsm) throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L: offset groups too large");
+  if (T.smem + 8192 > maxsm) throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L: not enough shared memory");
   T.img = H.pool.get<unsigned char>((size_t)H.nrhs_max * rows * 128);
   FMMPC_CUDA(cudaMemsetAsync(T.img, 0, (size_t)H.nrhs_max * rows * 128, H.stream));
   T.bmat = H.pool.get<unsigned char>(B.size());
-  T.tiles = H.pool.get<int4>(tiles.size());
+  T.tiles = H.pool.get<int2>(tiles.size());
   T.groups = H.pool.get<int4>(groups.size());
   T.dxs = H.pool.get<int>(dxs.size());
   T.err = H.pool.get<int>(1);
   FMMPC_CUDA(cudaMemcpyAsync(T.bmat, B.data(), B.size(), cudaMemcpyHostToDevice, H.stream));
-  FMMPC_CUDA(cudaMemcpyAsync(T.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, H.stream));
+  FMMPC_CUDA(cudaMemcpyAsync(T.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, H.stream));
   FMMPC_CUDA(cudaMemcpyAsync(T.groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice, H.stream));
   FMMPC_CUDA(cudaMemcpyAsync(T.dxs, dxs.data(), sizeof(int) * dxs.size(), cudaMemcpyHostToDevice, H.stream));
   FMMPC_CUDA(cudaMemsetAsync(T.err, 0, sizeof(int), H.stream));
-  FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
-  FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
+  if (W == 24) {
+    FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<0, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
+    FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<1, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
+  } else {
+    FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
+    FMMPC_CUDA(cudaFuncSetAttribute(k_m2l_tc<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, T.smem));
+  }
   FMMPC_CUDA(cudaStreamSynchronize(H.stream));
   T.enabled = true;
 }
@@ -560,16 +649,14 @@ int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t
     a.lev_row0[l] = T.lev_row0[l];
     a.lev_P[l] = T.lev_P[l];
   }
-  for (int c = 0; c < 4; ++c) {
-    a.ngroups[c] = T.ngroups[c];
-    a.goff[c] = T.goff[c];
-    a.ooff[c] = T.ooff[c];
-    a.nofs[c] = (c < 3 ? T.ooff[c + 1] : T.nofs_total) - T.ooff[c];
+  for (int q = 0; q < 3; ++q) {
+    a.gpart[q] = T.gpart[q];
+    a.gpart_sh[q] = T.gpart_sh[q];
   }
   a.p = g.p;
   a.n = g.n;
-  a.stage_bytes = T.stage_bytes;
   a.nsplit = T.nsplit;
+  a.nparts = T.nparts;
   a.nks = T.kind == 0 ? (2 * g.p + 4 * T.nsplit + 7) / 8 : (2 * g.p + 4 * T.nsplit + 15) / 16;
   const int64_t lo = level_offset(2), hi = level_offset(g.L + 1);
   const int64_t threads = std::max<int64_t>((int64_t)nrhs * (hi - lo) * 8, (int64_t)nrhs * lo * g.p);
@@ -577,9 +664,14 @@ int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t
   if (T.kind == 0) k_m2l_pack<0><<<nblk(threads), 256, 0, s>>>(a, nrhs, lo, hi, M);
   else k_m2l_pack<1><<<nblk(threads), 256, 0, s>>>(a, nrhs, lo, hi, M);
   FMMPC_LAUNCH_CHECK();
-  dim3 grid((unsigned)T.ntiles, (unsigned)nrhs);
-  if (T.kind == 0) k_m2l_tc<0><<<grid, M2L_THREADS, T.smem, s>>>(a);
-  else k_m2l_tc<1><<<grid, M2L_THREADS, T.smem, s>>>(a);
+  dim3 grid((unsigned)T.ntiles, (unsigned)T.nparts, (unsigned)nrhs);
+  if (T.width == 24) {
+    if (T.kind == 0) k_m2l_tc<0, 24><<<grid, M2L_THREADS, T.smem, s>>>(a);
+    else k_m2l_tc<1, 24><<<grid, M2L_THREADS, T.smem, s>>>(a);
+  } else {
+    if (T.kind == 0) k_m2l_tc<0, 32><<<grid, M2L_THREADS, T.smem, s>>>(a);
+    else k_m2l_tc<1, 32><<<grid, M2L_THREADS, T.smem, s>>>(a);
+  }
   FMMPC_LAUNCH_CHECK();
   return 2;
 }
