@@ -194,6 +194,18 @@ double gj_invert(double *A, int N, cudaStream_t s, DevPool &tmp) {
 
 }  // namespace
 
+namespace {
+// x = hi + lo, hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_split_f2(int64_t total, const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const double v = x[t];
+  const float h = (float)v;
+  hi[t] = h;
+  lo[t] = (float)(v - (double)h);
+}
+}  // namespace
+
 void init_bem(fmmpc_handle &H, DevPool &tmp) {
   // S is block circulant in the four sides (the 90-degree rotation of the square maps
   // element (s, k) to (s+1, k)), so a 4-point DFT over the side index block-diagonalises
@@ -218,6 +230,12 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   H.Sinv = H.pool.get<double>((size_t)n * N);
   k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, E, H.Sinv);
   FMMPC_LAUNCH_CHECK();
+  if (H.prec != FMMPC_PREC_FP64) {  // the single-precision forms apply it in two-word FP32
+    H.Sinv_hi = H.pool.get<float>((size_t)n * N);
+    H.Sinv_lo = H.pool.get<float>((size_t)n * N);
+    k_split_f2<<<nblk((int64_t)n * N), 256, 0, s>>>((int64_t)n * N, H.Sinv, H.Sinv_hi, H.Sinv_lo);
+    FMMPC_LAUNCH_CHECK();
+  }
   FMMPC_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -115,36 +115,126 @@ __device__ __forceinline__ cpx<R> m2m_row(const cpx<R> *__restrict__ T, const cp
   return acc;
 }
 
-// P2M for a 4x4 block of leaves (one warp each) fused with the two M2M levels above it.
+// k M2M levels (item 2) over the 4^k consecutive (Morton) cells of level l held in
+// buf[0 .. 4^k), the first of them cell c0: each level's parents overwrite buf[0 ..) and
+// are written to M.  Per output the sum over the four children is split into per-child
+// partial sums (at most P terms) run by separate threads, then added in child order.
 template <typename R, int P>
-__global__ void __launch_bounds__(512) k_upward_fused(Geo g, const R *__restrict__ wpad,
-                                                      const cpx<R> *__restrict__ vm2m, cpx<R> *__restrict__ Mv) {
-  __shared__ cpx<R> sl[16][P], sp[4][P], sT[4 * P * P];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+__device__ __forceinline__ void m2m_levels_smem(const cpx<R> *sT, cpx<R> (*buf)[P], cpx<R> (*part)[P], cpx<R> *M,
+                                                int l, uint32_t c0, int k, int tid, int nthr) {
+  for (int lev = 1; lev <= k; ++lev) {
+    const int npar = 1 << (2 * (k - lev));
+    for (int t = tid; t < 4 * npar * P; t += nthr) {  // (parent, child q, output n)
+      const int ch = t / P, q = ch & 3, n = t % P;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int kk = 0; kk <= n; ++kk) cmac(acc, sT[(q * P + n) * P + kk], buf[ch][kk]);
+      part[ch][n] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < npar * P; t += nthr) {
+      const int pc = t / P, n = t % P;
+      const cpx<R> v = part[4 * pc][n] + part[4 * pc + 1][n] + part[4 * pc + 2][n] + part[4 * pc + 3][n];
+      buf[pc][n] = v;
+      M[(level_offset(l - lev) + (c0 >> (2 * lev)) + pc) * P + n] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// The whole upward pass of the volume tree in one launch.  Block (b, rhs) takes the 4x4
+// Morton block b of leaves (MS x MS nodes each): P2M (item 1; Mt_0 = sum w_j,
+// Mt_k = -sum w_j zt_j^k / k; 16 threads per leaf, each summing every 16th node with all
+// its loads issued first, then a shuffle reduction), then M2M (item 2) to the 4 parents and
+// to cell b of level L - 2.  Above that, M2M proceeds up to three levels at a time: the
+// last of the blocks that complete a Morton group of 4^k cells (an atomic count per group,
+// reset by that block) computes the k levels above it.  Any block that does a step
+// computes the same sums, so the result does not depend on which block it is.
+template <typename R, int P, int MS>
+__global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict__ wpad, const cpx<R> *__restrict__ vm2m,
+                                                     cpx<R> *__restrict__ Mv, int *__restrict__ counter, int64_t ncount) {
+  // three-level steps need 64 cells in shared memory; two-level steps where that would not fit
+  constexpr int NBUF = sizeof(cpx<R>) * P * (4 * P + 128) <= 45000 ? 64 : 16, MAXSTEP = NBUF == 64 ? 3 : 2;
+  __shared__ cpx<R> sT[4 * P * P], buf[NBUF][P], part[NBUF][P];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   const int rhs = blockIdx.y;
   const uint32_t blk = blockIdx.x;
-  for (int i = tid; i < 4 * P * P; i += blockDim.x) sT[i] = vm2m[i];
+  for (int i = tid; i < 4 * P * P; i += nthr) sT[i] = vm2m[i];
   cpx<R> *M = Mv + (int64_t)rhs * g.ncell * P;
   {
-    cpx<R> acc[P];
-    p2m_warp<R, P>(wpad + (int64_t)rhs * g.npad * g.npad, g.npad, g.pad, g.m, 16 * blk + w, lane, acc);
-    if (lane == 0) {
+    constexpr int NP = (MS * MS + 15) / 16;  // nodes per thread
+    const int leaf = tid >> 4, c = tid & 15;
+    const uint32_t lc = 16 * blk + leaf;
+    int a, b;
+    morton_decode(lc, a, b);
+    const R half = R(0.5) * (MS - 1), invm = R(1) / MS;
+    const R *W = wpad + (int64_t)rhs * g.npad * g.npad + (int64_t)(b * MS + g.pad) * g.npad + a * MS + g.pad;
+    R w[NP];
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        sl[w][k] = acc[k];
-        M[(level_offset(g.L) + 16 * blk + w) * P + k] = acc[k];
+    for (int e = 0; e < NP; ++e) {
+      const int pt = c + 16 * e;
+      w[e] = pt < MS * MS ? W[(int64_t)(pt / MS) * g.npad + pt % MS] : R(0);
+    }
+    cpx<R> acc[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc[k] = mk<R>(0, 0);
+#pragma unroll
+    for (int e = 0; e < NP; ++e) {
+      const int pt = c + 16 * e;
+      const cpx<R> z = mk<R>((pt % MS - half) * invm, (pt / MS - half) * invm);
+      cpx<R> pw = z;
+      acc[0].re += w[e];
+#pragma unroll
+      for (int k = 1; k < P; ++k) {
+        acc[k].re = fma(w[e], pw.re, acc[k].re);
+        acc[k].im = fma(w[e], pw.im, acc[k].im);
+        pw = pw * z;
       }
     }
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
+        acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
+      }
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if ((k & 15) == c) {
+        const R sk = k == 0 ? R(1) : R(-1) / R(k);
+        const cpx<R> v = mk<R>(sk * acc[k].re, sk * acc[k].im);
+        buf[leaf][k] = v;
+        M[(level_offset(g.L) + lc) * P + k] = v;
+      }
   }
   __syncthreads();
-  if (tid < 4 * P) {
-    const int pi = tid / P, n = tid % P;
-    const cpx<R> v = m2m_row<R, P>(sT, sl[4 * pi], sl[4 * pi + 1], sl[4 * pi + 2], sl[4 * pi + 3], n);
-    sp[pi][n] = v;
-    M[(level_offset(g.L - 1) + 4 * blk + pi) * P + n] = v;
+  m2m_levels_smem<R, P>(sT, buf, part, M, g.L, 16 * blk, 2, tid, nthr);
+  int l = g.L - 2;
+  uint32_t cell = blk;
+  while (l > 0) {
+    const int step = l < MAXSTEP ? l : MAXSTEP, pl = l - step;
+    const uint32_t pc = cell >> (2 * step);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      int *ctr = counter + (int64_t)rhs * ncount + level_offset(pl) + pc;
+      s_last = atomicAdd(ctr, 1) == (1 << (2 * step)) - 1;
+      if (s_last) *ctr = 0;  // ready for the next launch
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nch = 1 << (2 * step);
+    const uint32_t c0 = pc << (2 * step);
+    for (int i = tid; i < nch * P; i += nthr) {
+      const R *src = reinterpret_cast<const R *>(M + (level_offset(l) + c0 + i / P) * P + i % P);
+      buf[i / P][i % P] = mk<R>(__ldcg(src), __ldcg(src + 1));
+    }
+    __syncthreads();
+    m2m_levels_smem<R, P>(sT, buf, part, M, l, c0, step, tid, nthr);
+    l = pl;
+    cell = pc;
   }
-  __syncthreads();
-  if (tid < P) M[(level_offset(g.L - 2) + blk) * P + tid] = m2m_row<R, P>(sT, sp[0], sp[1], sp[2], sp[3], tid);
 }
 
 // M2M levels lfrom down to lto (thread per parent coefficient).  One level: a grid of
@@ -192,28 +282,6 @@ __global__ void k_l2l_levels(int lfrom, int lto, int64_t ncell, int nrhs, const 
     }
     if (!single) __syncthreads();
   }
-}
-
-// Two M2M levels in one block: 16 cells of level lc (a 4x4 Morton block) -> 4 parents ->
-// 1 grandparent, with the intermediate parents kept in shared memory.
-template <typename R, int P>
-__global__ void __launch_bounds__(256) k_m2m_2levels(int lc, int64_t ncell, const cpx<R> *__restrict__ vm2m,
-                                                     cpx<R> *__restrict__ Mv) {
-  __shared__ cpx<R> sc[16][P], sp[4][P], sT[4 * P * P];
-  const int tid = threadIdx.x, rhs = blockIdx.y;
-  const uint32_t blk = blockIdx.x;
-  cpx<R> *M = Mv + (int64_t)rhs * ncell * P;
-  for (int i = tid; i < 4 * P * P; i += blockDim.x) sT[i] = vm2m[i];
-  for (int i = tid; i < 16 * P; i += blockDim.x) sc[i / P][i % P] = M[(level_offset(lc) + 16 * blk) * P + i];
-  __syncthreads();
-  if (tid < 4 * P) {
-    const int pi = tid / P, n = tid % P;
-    const cpx<R> v = m2m_row<R, P>(sT, sc[4 * pi], sc[4 * pi + 1], sc[4 * pi + 2], sc[4 * pi + 3], n);
-    sp[pi][n] = v;
-    M[(level_offset(lc - 1) + 4 * blk + pi) * P + n] = v;
-  }
-  __syncthreads();
-  if (tid < P) M[(level_offset(lc - 2) + blk) * P + tid] = m2m_row<R, P>(sT, sp[0], sp[1], sp[2], sp[3], tid);
 }
 
 // Two L2L levels in one block: a cell of level lp adds into its 4 children and their 16
@@ -742,6 +810,119 @@ __global__ void __launch_bounds__(256) k_bem_apply(int n, int nrhs, const double
   }
 }
 
+// Two-word FP32 arithmetic for the BEM apply of the single-precision forms (FP64 is scarce
+// on this GPU): a value x is carried as hi + lo, hi = fl32(x), lo = fl32(x - hi).
+// s + c += p with Knuth's TwoSum (the rounding error of s + p goes into c).
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float p) {
+  const float t = s + p, bb = t - s;
+  c += (s - (t - bb)) + (p - bb);
+  s = t;
+}
+// s + c += (ah + al)(bh + bl): the product ah bh split exactly by an FMA, the cross terms
+// into c (the dot product of Ogita, Rump and Oishi, "Dot2", with the operands' low words).
+__device__ __forceinline__ void dot2_mac(float &s, float &c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = fmaf(ah, bh, -p);
+  two_sum_acc(s, c, p);
+  c = fmaf(al, bh, fmaf(ah, bl, c + e));
+}
+
+// vt (the side DFT of V r at the collocation points, as k_bem_vt) as hi and lo words.
+__global__ void k_bem_vt_f2(int n, int nrhs, const double *__restrict__ vcol, float *__restrict__ vh,
+                            float *__restrict__ vl) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * n) return;
+  const int64_t rr = t / n;
+  const int k = (int)(t % n);
+  const double *v = vcol + rr * 4 * n;
+  const double v0 = v[k], v1 = v[n + k], v2 = v[2 * n + k], v3 = v[3 * n + k];
+  const double o[4] = {(v0 + v2) + (v1 + v3), (v0 + v2) - (v1 + v3), v0 - v2, v1 - v3};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float hi = (float)o[j];
+    vh[rr * 4 * n + j * n + k] = hi;
+    vl[rr * 4 * n + j * n + k] = (float)(o[j] - (double)hi);
+  }
+}
+
+// The BEM apply of k_bem_apply in two-word FP32 arithmetic: block per row m of
+// T = [C^0 | C^2 | A | B], each thread a strided share of the row, RB right-hand sides per
+// pass over it; the partial two-word sums are combined with TwoSum (warp shuffles, then
+// across the 8 warps) and converted to FP64 once per row and right-hand side.
+template <int RB>
+__global__ void __launch_bounds__(256) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
+                                                      const float *__restrict__ Tl, const float *__restrict__ vh,
+                                                      const float *__restrict__ vl, double *__restrict__ q) {
+  __shared__ float rs[8][RB][4], rc[8][RB][4];
+  __shared__ double tot[RB][4];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int mrow = blockIdx.x;
+  const int NG = 4 * n;
+  const float *th = Th + (int64_t)mrow * NG, *tl = Tl + (int64_t)mrow * NG;
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    float sa[RB][4], ca[RB][4];
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+#pragma unroll
+      for (int g = 0; g < 4; ++g) sa[j][g] = ca[j][g] = 0.f;
+#pragma unroll 4
+    for (int k = tid; k < n; k += 256) {
+      const float c0h = th[k], c2h = th[n + k], cah = th[2 * n + k], cbh = th[3 * n + k];
+      const float c0l = tl[k], c2l = tl[n + k], cal = tl[2 * n + k], cbl = tl[3 * n + k];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        if (r0 + j < nrhs) {
+          const float *xh = vh + (int64_t)(r0 + j) * NG, *xl = vl + (int64_t)(r0 + j) * NG;
+          const float v0h = xh[k], v2h = xh[n + k], ah = xh[2 * n + k], bh = xh[3 * n + k];
+          const float v0l = xl[k], v2l = xl[n + k], al = xl[2 * n + k], bl = xl[3 * n + k];
+          dot2_mac(sa[j][0], ca[j][0], c0h, c0l, v0h, v0l);
+          dot2_mac(sa[j][1], ca[j][1], c2h, c2l, v2h, v2l);
+          dot2_mac(sa[j][2], ca[j][2], cah, cal, ah, al);  // re = A a + B b
+          dot2_mac(sa[j][2], ca[j][2], cbh, cbl, bh, bl);
+          dot2_mac(sa[j][3], ca[j][3], cbh, cbl, ah, al);  // im = B a - A b
+          dot2_mac(sa[j][3], ca[j][3], -cah, -cal, bh, bl);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float s2 = __shfl_xor_sync(0xffffffffu, sa[j][g], o), c2 = __shfl_xor_sync(0xffffffffu, ca[j][g], o);
+          two_sum_acc(sa[j][g], ca[j][g], s2);
+          ca[j][g] += c2;
+        }
+        if (lane == 0) {
+          rs[w][j][g] = sa[j][g];
+          rc[w][j][g] = ca[j][g];
+        }
+      }
+    __syncthreads();
+    if (tid < RB * 4) {
+      const int j = tid >> 2, g = tid & 3;
+      float s0 = rs[0][j][g], c0 = rc[0][j][g];
+      for (int ww = 1; ww < 8; ++ww) {
+        two_sum_acc(s0, c0, rs[ww][j][g]);
+        c0 += rc[ww][j][g];
+      }
+      tot[j][g] = (double)s0 + (double)c0;
+    }
+    __syncthreads();
+    if (tid < RB && r0 + tid < nrhs) {
+      const int j = tid;
+      const double P0 = tot[j][0], P2 = tot[j][1], R = tot[j][2], I = tot[j][3];
+      double *qr = q + (int64_t)(r0 + j) * NG;
+      qr[mrow] = -0.25 * (P0 + P2 + 2.0 * R);
+      qr[n + mrow] = -0.25 * (P0 - P2 - 2.0 * I);
+      qr[2 * n + mrow] = -0.25 * (P0 + P2 - 2.0 * R);
+      qr[3 * n + mrow] = -0.25 * (P0 - P2 + 2.0 * I);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ near boundary field
 // int over an element of ln|x - y| ds (node units), stable closed form:
 // with s1 = (a - x).t, s2 = s1 + l, d = (x - a).n, A_i = s_i^2 + d^2,
@@ -960,6 +1141,131 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_p2p(P2PArgs<R> 
   for (int t = 0; t < M; ++t) o[t] = ((double)sum[t] - (double)comp[t]) * NEG_INV_2PI;
 }
 
+// FP32 -> FP64 by the IEEE-754 field layout (exponent bias 127 -> 1023) on the integer
+// units; zeros included, the subnormal / infinite / NaN cases through the conversion unit.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)((uint64_t)u << 32));
+  if (e == 0 || e == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                                          ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
+// -(1/2pi) (a + b) + u, u = v (float)(-1/2pi): a + b exactly as a two-word sum (Knuth's
+// TwoSum), times -1/(2pi) held as two floats (the product's error word from an FMA, as in
+// Dekker's product), u added with TwoSum, and the two words converted to FP64 and added.
+__device__ __forceinline__ double near_far_sum(float a, float b, float v) {
+  constexpr float c_hi = (float)NEG_INV_2PI;
+  constexpr float c_lo = (float)(NEG_INV_2PI - (double)c_hi);
+  const float s = a + b, bb = s - a, s_lo = (a - (s - bb)) + (b - bb);
+  const float p = __fmul_rn(s, c_hi);  // rounded products, never fused into the sums below
+  const float p_lo = fmaf(s, c_hi, -p) + fmaf(s, c_lo, s_lo * c_hi);
+  const float u = __fmul_rn(v, c_hi);
+  const float r = p + u, rb = r - p, r_lo = ((p - (r - rb)) + (u - rb)) + p_lo;
+  return f32_to_f64_bits(r) + f32_to_f64_bits(r_lo);
+}
+
+// The whole downward pass of the volume tree, L2L (item 4) and L2P (item 5), in one launch,
+// with the final sum z = -(1/2pi) (near field + far field + near-boundary correction).
+// Block (b, rhs) takes the 4x4 Morton block b of leaves (cell b of level L - 2): it first
+// forms the complete local expansion of each of its ancestors from the root down (its own
+// copy: L(cell) = L_M2L(cell) + L2L(L(parent)), at most P terms per output), then those of
+// cell b, its 4 children and the 16 leaves, and evaluates each leaf expansion at the leaf's
+// nodes (NPT consecutive nodes of one row per thread, so a warp writes whole row segments).
+template <typename R, int P, int M>
+__global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_bnd, int64_t nbnear,
+                                                       const cpx<R> *__restrict__ vl2l, const cpx<R> *__restrict__ Lv,
+                                                       const R *__restrict__ phib, const int32_t *__restrict__ bslot,
+                                                       double *__restrict__ out, const float *__restrict__ near1,
+                                                       const float *__restrict__ near2) {
+  __shared__ cpx<R> sS[4 * P * P], sanc[24][P], s1[4][P], s2[16][P];
+  const int tid = threadIdx.x, nthr = blockDim.x, rhs = blockIdx.y;
+  const uint32_t blk = blockIdx.x;
+  const int L = g.L;
+  const cpx<R> *Lr = Lv + (int64_t)rhs * g.ncell * P;
+  // every value the block needs, loaded at once: the translation matrices, the M2L parts of
+  // the ancestors (levels 0 .. L - 2), of the 4 children and of the 16 leaves
+  for (int i = tid; i < 4 * P * P; i += nthr) sS[i] = vl2l[i];
+  for (int i = tid; i < (L - 1) * P; i += nthr) {
+    const int l = i / P, n = i % P;
+    sanc[l][n] = Lr[(level_offset(l) + (blk >> (2 * (L - 2 - l)))) * P + n];
+  }
+  for (int i = tid; i < 4 * P; i += nthr) s1[i / P][i % P] = Lr[(level_offset(L - 1) + 4 * blk) * P + i];
+  for (int i = tid; i < 16 * P; i += nthr) s2[i / P][i % P] = Lr[(level_offset(L) + 16 * blk) * P + i];
+  __syncthreads();
+  // complete local expansions down the ancestor chain, in place: sanc[l] += L2L(sanc[l - 1])
+  for (int l = 1; l <= L - 2; ++l) {
+    const int q = (blk >> (2 * (L - 2 - l))) & 3;
+    cpx<R> acc = mk<R>(0, 0);
+    if (tid < P) {
+      const int n = tid;
+      acc = sanc[l][n];
+      for (int k = n; k < P; ++k) cmac(acc, sS[(q * P + n) * P + k], sanc[l - 1][k]);
+    }
+    __syncthreads();
+    if (tid < P) sanc[l][tid] = acc;
+    __syncthreads();
+  }
+  const cpx<R> *cur = sanc[L - 2];
+  cpx<R> v1 = mk<R>(0, 0), v2 = mk<R>(0, 0);
+  if (tid < 4 * P) {
+    const int q = tid / P, n = tid % P;
+    v1 = s1[q][n];
+    for (int k = n; k < P; ++k) cmac(v1, sS[(q * P + n) * P + k], cur[k]);
+  }
+  __syncthreads();
+  if (tid < 4 * P) s1[tid / P][tid % P] = v1;
+  __syncthreads();
+  if (tid < 16 * P) {
+    const int lf = tid / P, n = tid % P, q = lf & 3;
+    v2 = s2[lf][n];
+    for (int k = n; k < P; ++k) cmac(v2, sS[(q * P + n) * P + k], s1[lf >> 2][k]);
+  }
+  __syncthreads();
+  if (tid < 16 * P) s2[tid / P][tid % P] = v2;
+  __syncthreads();
+  constexpr int NPT = M * M / 16;  // nodes per thread: (4M)^2 nodes over 256 threads
+  const int e0 = tid * NPT, y = e0 / (4 * M), x0 = e0 % (4 * M);
+  const int lf = (int)morton_encode((uint32_t)(x0 / M), (uint32_t)(y / M));
+  const int tx0 = x0 % M, ty = y % M;
+  int bx, by;
+  morton_decode(blk, bx, by);
+  const int64_t off = (int64_t)rhs * g.n * g.n + (int64_t)(by * 4 * M + y) * g.n + bx * 4 * M + x0;
+  const R *pb = nullptr;
+  if (do_bnd) {
+    const int slot = bslot[16 * (int64_t)blk + lf];
+    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M + tx0;
+  }
+  const R zy = (ty - R(0.5) * (M - 1)) / M;
+  cpx<R> acc[NPT];
+#pragma unroll
+  for (int e = 0; e < NPT; ++e) acc[e] = mk<R>(0, 0);
+  for (int k = P - 1; k >= 0; --k) {
+    const cpx<R> Lk = s2[lf][k];
+#pragma unroll
+    for (int e = 0; e < NPT; ++e) acc[e] = acc[e] * mk<R>((tx0 + e - R(0.5) * (M - 1)) / M, zy) + Lk;
+  }
+  double *o = out + off;
+  if (near1) {
+    // tensor-core near field: the two raw halves often cancel, so they are added exactly
+    // and scaled by -1/(2 pi) in two-word FP32 arithmetic, the far term added, and the
+    // two-word result converted to FP64 with one FP64 addition (FP64 is scarce here)
+#pragma unroll
+    for (int e = 0; e < NPT; ++e) {
+      float v = (float)acc[e].re;
+      if (pb) v += (float)pb[e];
+      o[e] = near_far_sum(near1[off + e], near2[off + e], v);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NPT; ++e) {
+      double v = (double)acc[e].re;
+      if (pb) v += (double)pb[e];
+      o[e] += v * NEG_INV_2PI;
+    }
+  }
+}
+
 // z += -(1/2pi) (L2P of the leaf local expansion + near-boundary element integrals).
 // Thread per (leaf, row of m targets, rhs).
 template <typename R, int M>
@@ -1108,36 +1414,28 @@ Mats<R> mats_of(fmmpc_handle &H) {
   return mt;
 }
 
-// Upward pass of the volume tree: P2M fused with two M2M levels, then two M2M levels per
-// launch (one for a last odd level).
+// Upward pass of the volume tree: one launch for L >= 2 (P2M, then every M2M level).
 template <typename R, int P>
 int run_upward(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   const Geo &g = H.g;
   const R *wpad = (const R *)H.fb.wpad;
   cpx<R> *Mv = (cpx<R> *)H.fb.Mv;
   Mats<R> mt = mats_of<R>(H);
-  int launches = 0;
-  int lc;  // level whose cells are complete
   if (g.L >= 2) {
-    k_upward_fused<R, P><<<dim3((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs), 512, 0, s>>>(g, wpad, mt.vm2m, Mv);
-    lc = g.L - 2;
-  } else {
-    k_p2m_small<R, P><<<1, 256, 0, s>>>(g, nrhs, wpad, Mv);
-    lc = g.L;
+    const dim3 grid((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs);
+    switch (g.m) {
+      case 4: k_upward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, wpad, mt.vm2m, Mv, H.fb.up_count, H.fb.up_ncount); break;
+      case 8: k_upward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, wpad, mt.vm2m, Mv, H.fb.up_count, H.fb.up_ncount); break;
+      case 16: k_upward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, wpad, mt.vm2m, Mv, H.fb.up_count, H.fb.up_ncount); break;
+      default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
+    }
+    FMMPC_LAUNCH_CHECK();
+    return 1;
   }
-  ++launches;
+  k_p2m_small<R, P><<<1, 256, 0, s>>>(g, nrhs, wpad, Mv);
+  if (g.L == 1) k_m2m_levels<R, P><<<1, 256, 0, s>>>(0, 0, g.ncell, nrhs, mt.vm2m, Mv);
   FMMPC_LAUNCH_CHECK();
-  while (lc >= 2) {
-    k_m2m_2levels<R, P><<<dim3((unsigned)(int64_t(1) << (2 * (lc - 2))), nrhs), 256, 0, s>>>(lc, g.ncell, mt.vm2m, Mv);
-    lc -= 2;
-    ++launches;
-  }
-  if (lc == 1) {
-    k_m2m_levels<R, P><<<1, 256, 0, s>>>(0, 0, g.ncell, nrhs, mt.vm2m, Mv);
-    ++launches;
-  }
-  FMMPC_LAUNCH_CHECK();
-  return launches;
+  return g.L == 1 ? 2 : 1;
 }
 
 // Downward pass: two L2L levels per launch from the root (one for a last odd level).
@@ -1161,6 +1459,25 @@ int run_l2l(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   FMMPC_LAUNCH_CHECK();
   return launches;
 }
+
+// L2L and L2P with the final sum in one launch (L >= 2).
+template <typename R, int P>
+void run_downward(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s, const float *near1 = nullptr,
+                  const float *near2 = nullptr) {
+  const Geo &g = H.g;
+  const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
+  const R *pb = (const R *)H.fb.phib;
+  const cpx<R> *vl2l = mats_of<R>(H).vl2l;
+  const dim3 grid((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs);
+  switch (g.m) {
+    case 4: k_downward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 8: k_downward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 16: k_downward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
+  }
+  FMMPC_LAUNCH_CHECK();
+}
+
 
 template <typename R, int P>
 void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
@@ -1236,8 +1553,14 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(3);
-    k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
-    k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv, H.fb.vt, H.fb.q);
+    if (H.Sinv_hi && H.fb.vt_hi) {
+      k_bem_vt_f2<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt_hi, H.fb.vt_lo);
+      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      else k_bem_apply_f2<1><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+    } else {
+      k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
+      k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv, H.fb.vt, H.fb.q);
+    }
     FMMPC_LAUNCH_CHECK();
     launches += 2;
     if (part == PART_Q) {
@@ -1284,7 +1607,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   FMMPC_LAUNCH_CHECK();
   launches += 1;
   mark(7);
-  launches += run_l2l<R, P>(H, nrhs, s);
+  if (g.L < 2) launches += run_l2l<R, P>(H, nrhs, s);  // else L2L runs with L2P below
   if (with_bnd && Ls.nbnear > 0) {
     mark(8);
     if (std::is_same<R, float>::value && H.fb.knear && g.m == 8)
@@ -1297,15 +1620,19 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     ++launches;
   }
   mark(9);
+  const int do_bnd = (with_bnd && Ls.nbnear > 0) ? 1 : 0;
+  const float *n1 = nullptr, *n2 = nullptr;
   if (tc) {
     launches += run_p2p_tc(H, false, out, nrhs, s);
-    mark(10);
-    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s, H.tcp.near1, H.tcp.near2);
+    n1 = H.tcp.near1;
+    n2 = H.tcp.near2;
   } else {
-    run_p2p<R>(H, H.fb.table, out, nrhs, s);  // the CUDA-core kernel also evaluates L2P and the sum
+    run_p2p<R>(H, H.fb.table, out, nrhs, s);  // writes the near field into out
     ++launches;
-    run_far_final<R>(H, out, nrhs, (with_bnd && Ls.nbnear > 0) ? 1 : 0, s);
   }
+  mark(10);
+  if (g.L >= 2) run_downward<R, P>(H, out, nrhs, do_bnd, s, n1, n2);
+  else run_far_final<R>(H, out, nrhs, do_bnd, s, n1, n2);
   ++launches;
   mark_end();
   H.launches = launches;
@@ -1382,6 +1709,9 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.wpad = H.pool.get<R>((size_t)nr * g.npad * g.npad);
   FMMPC_CUDA(cudaMemsetAsync(H.fb.wpad, 0, sizeof(R) * (size_t)nr * g.npad * g.npad, H.stream));
   H.fb.Mv = H.pool.get<cpx<R>>((size_t)nr * g.ncell * g.p);
+  H.fb.up_ncount = std::max<int64_t>(1, level_offset(std::max(g.L - 3, 1)));
+  H.fb.up_count = H.pool.get<int>((size_t)nr * H.fb.up_ncount);
+  FMMPC_CUDA(cudaMemsetAsync(H.fb.up_count, 0, sizeof(int) * (size_t)nr * H.fb.up_ncount, H.stream));
   H.fb.Lv = H.pool.get<cpx<R>>((size_t)nr * g.ncell * g.p);
   H.fb.Mb = H.pool.get<cpx<R>>((size_t)nr * g.nbcell * g.p);
   H.fb.Lb = H.pool.get<cpx<R>>((size_t)nr * g.nbcell * g.p);
@@ -1389,6 +1719,10 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.vcol = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.vt = H.pool.get<double>((size_t)nr * g.NG);
+  if (std::is_same<R, float>::value) {  // two-word FP32 BEM apply
+    H.fb.vt_hi = H.pool.get<float>((size_t)nr * g.NG);
+    H.fb.vt_lo = H.pool.get<float>((size_t)nr * g.NG);
+  }
   std::vector<cpx<R>> mats;
   build_mats<R>(H, mats);
   H.fb.mats = H.pool.get<cpx<R>>(mats.size());

@@ -31,8 +31,11 @@ struct FmmBufs {
   double *vcol = nullptr;    // [nrhs][NG] V r at collocation points
   double *q = nullptr;       // [nrhs][NG] BEM density
   double *vt = nullptr;      // [nrhs][NG] side-DFT of vcol for the block-circulant apply
+  float *vt_hi = nullptr, *vt_lo = nullptr;  // the same as two FP32 words (single-precision forms)
   float *knear = nullptr;    // near-boundary element integrals (single-precision forms)
   float *kcol = nullptr;     // collocation-point near-field log kernel (single-precision forms)
+  int *up_count = nullptr;   // [nrhs][up_ncount] upward-pass arrival counts (zero between launches)
+  int64_t up_ncount = 0;
 };
 
 // tensor-core lattice P2P (p2p_tc.cu)
@@ -98,6 +101,7 @@ struct fmmpc_handle {
   fmmpc::Lists lists{};
   fmmpc::FmmBufs fb{};
   double *Sinv = nullptr;   // [n][4n] first block row of the FP64 inverse of the single-layer matrix
+  float *Sinv_hi = nullptr, *Sinv_lo = nullptr;  // the same as two FP32 words (single-precision forms)
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
   fmmpc::TcP2P tcp{};
