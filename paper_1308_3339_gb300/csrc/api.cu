@@ -125,6 +125,9 @@ void release(fmmpc_handle *h) {
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
   if (h->gev_out) cudaEventDestroy(h->gev_out);
+  if (h->sstream) cudaStreamDestroy(h->sstream);
+  for (auto e : h->sev)
+    if (e) cudaEventDestroy(e);
   for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k)
     if (h->ev[k]) cudaEventDestroy(h->ev[k]);
   if (h->kw.hbuf) cudaFreeHost(h->kw.hbuf);

@@ -1479,6 +1479,21 @@ void run_downward(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream
 }
 
 
+// Near-boundary correction phib at the nodes of the leaves next to the boundary.
+template <typename R>
+int run_bnd_near(fmmpc_handle &H, int nrhs, cudaStream_t s) {
+  const Geo &g = H.g;
+  const Lists &Ls = H.lists;
+  if (std::is_same<R, float>::value && H.fb.knear && g.m == 8)
+    k_bnd_near_k<<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_first, Ls.pbv_src,
+                                                                 H.fb.knear, H.fb.q, (float *)H.fb.phib);
+  else
+    k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
+                                                                 Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
+  FMMPC_LAUNCH_CHECK();
+  return 1;
+}
+
 template <typename R, int P>
 void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
   const Geo &g = H.g;
@@ -1535,8 +1550,25 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     return;
   }
   const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q;
+  // The tensor-core near field and volume M2L do not depend on the boundary chain
+  // (collocation values, BEM density, boundary tree, near-boundary correction): for the
+  // full apply without stage timing they run on a second stream, forked after the weights
+  // and after the upward pass and joined before the boundary-to-volume M2L.
+  const bool side = tc && part == PART_FULL && H.timing == 0 && H.sstream;
+  const bool m2l_side = side && std::is_same<R, float>::value && H.tcm.enabled;
+  cudaStream_t ss = H.sstream;
+  if (side) {
+    FMMPC_CUDA(cudaEventRecord(H.sev[0], s));
+    FMMPC_CUDA(cudaStreamWaitEvent(ss, H.sev[0], 0));
+    launches += run_p2p_tc(H, false, out, nrhs, ss);
+  }
   mark(1);
   launches += run_upward<R, P>(H, nrhs, s);
+  if (m2l_side) {
+    FMMPC_CUDA(cudaEventRecord(H.sev[1], s));
+    FMMPC_CUDA(cudaStreamWaitEvent(ss, H.sev[1], 0));
+    launches += run_m2l_tc(H, Mv, Lv, nrhs, ss);
+  }
   if (with_bnd) {
     mark(2);
     k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbb_first,
@@ -1586,10 +1618,15 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     FMMPC_LAUNCH_CHECK();
     ++launches;
   }
+  if (side) {
+    if (with_bnd && Ls.nbnear > 0) launches += run_bnd_near<R>(H, nrhs, s);
+    FMMPC_CUDA(cudaEventRecord(H.sev[2], ss));
+    FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[2], 0));
+  }
   mark(5);
   if (std::is_same<R, float>::value && H.tcm.enabled) {
     // volume-to-volume M2L on the tensor cores (mixed forms); boundary sources added after
-    launches += run_m2l_tc(H, Mv, Lv, nrhs, s);
+    if (!m2l_side) launches += run_m2l_tc(H, Mv, Lv, nrhs, s);
     mark(6);
     if (with_bnd && Ls.n_vbv_cells > 0) {
       k_m2l_vbv<R, P><<<nblk(Ls.n_vbv_cells * nrhs * 8), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbv_first,
@@ -1608,22 +1645,15 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   launches += 1;
   mark(7);
   if (g.L < 2) launches += run_l2l<R, P>(H, nrhs, s);  // else L2L runs with L2P below
-  if (with_bnd && Ls.nbnear > 0) {
+  if (!side && with_bnd && Ls.nbnear > 0) {
     mark(8);
-    if (std::is_same<R, float>::value && H.fb.knear && g.m == 8)
-      k_bnd_near_k<<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_first, Ls.pbv_src,
-                                                                   H.fb.knear, H.fb.q, (float *)H.fb.phib);
-    else
-      k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
-                                                                   Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
-    FMMPC_LAUNCH_CHECK();
-    ++launches;
+    launches += run_bnd_near<R>(H, nrhs, s);
   }
   mark(9);
   const int do_bnd = (with_bnd && Ls.nbnear > 0) ? 1 : 0;
   const float *n1 = nullptr, *n2 = nullptr;
   if (tc) {
-    launches += run_p2p_tc(H, false, out, nrhs, s);
+    if (!side) launches += run_p2p_tc(H, false, out, nrhs, s);
     n1 = H.tcp.near1;
     n2 = H.tcp.near2;
   } else {
@@ -1797,6 +1827,8 @@ void init_fmm(fmmpc_handle &H) {
   FMMPC_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_in, cudaEventDisableTiming));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_out, cudaEventDisableTiming));
+  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream, cudaStreamNonBlocking));
+  for (auto &e : H.sev) FMMPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 namespace {

@@ -118,6 +118,8 @@ struct fmmpc_handle {
   bool graphs = true;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  cudaStream_t sstream = nullptr;  // second stream of the full apply (near field, volume M2L)
+  cudaEvent_t sev[3] = {};         // fork after the weights, fork after the upward pass, join
   std::vector<fmmpc::GraphEntry> gcache;
   uint64_t gclock = 0;
 };
