@@ -472,7 +472,7 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
 template <typename R, int P>
 __global__ void k_m2l_bnd(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs,
                           const int32_t *__restrict__ first, const int32_t *__restrict__ src,
-                          const cpx<R> *__restrict__ Mv, cpx<R> *__restrict__ Lb) {
+                          const cpx<R> *__restrict__ Mv, cpx<R> *__restrict__ Lb, double lnh) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= nbcell * nrhs) return;
@@ -500,6 +500,9 @@ __global__ void k_m2l_bnd(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs,
                     mk<R>((R)((double)(BX - X) * scale), (R)((double)(BY - Y) * scale)), lnrho);
   }
   m2l_finish<R, P>(H, lane, Lb + (int64_t)rhs * nbcell * P + gb * P, 0);
+  // the four side roots also take the ln h part of G times the total volume weight
+  if (gb < 4 && lane == 0)
+    Lb[(int64_t)rhs * nbcell * P + gb * P].re += (R)(lnh * (double)Mv[(int64_t)rhs * ncell * P].re);
 }
 
 // ------------------------------------------------------------------ root constants
@@ -1174,7 +1177,9 @@ __device__ __forceinline__ double near_far_sum(float a, float b, float v) {
 // nodes (NPT consecutive nodes of one row per thread, so a warp writes whole row segments).
 template <typename R, int P, int M>
 __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_bnd, int64_t nbnear,
-                                                       const cpx<R> *__restrict__ vl2l, const cpx<R> *__restrict__ Lv,
+                                                       const cpx<R> *__restrict__ Mv, const cpx<R> *__restrict__ Mb,
+                                                       int with_bnd_w, const cpx<R> *__restrict__ vl2l,
+                                                       const cpx<R> *__restrict__ Lv,
                                                        const R *__restrict__ phib, const int32_t *__restrict__ bslot,
                                                        double *__restrict__ out, const float *__restrict__ near1,
                                                        const float *__restrict__ near2) {
@@ -1192,6 +1197,12 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   }
   for (int i = tid; i < 4 * P; i += nthr) s1[i / P][i % P] = Lr[(level_offset(L - 1) + 4 * blk) * P + i];
   for (int i = tid; i < 16 * P; i += nthr) s2[i / P][i % P] = Lr[(level_offset(L) + 16 * blk) * P + i];
+  if (tid == 0) {  // the root also takes ln h times the total weight (volume, and boundary if present)
+    double W = (double)Mv[(int64_t)rhs * g.ncell * P].re;
+    if (with_bnd_w)
+      for (int sd = 0; sd < 4; ++sd) W += (double)Mb[((int64_t)rhs * g.nbcell + sd) * P].re;
+    sanc[0][0].re = sanc[0][0].re + (R)(g.lnh * W);
+  }
   __syncthreads();
   // complete local expansions down the ancestor chain, in place: sanc[l] += L2L(sanc[l - 1])
   for (int l = 1; l <= L - 2; ++l) {
@@ -1460,19 +1471,21 @@ int run_l2l(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   return launches;
 }
 
-// L2L and L2P with the final sum in one launch (L >= 2).
+// L2L and L2P with the final sum in one launch (L >= 2); with_bnd_w: the root constant
+// includes the boundary weight.
 template <typename R, int P>
-void run_downward(fmmpc_handle &H, double *out, int nrhs, int do_bnd, cudaStream_t s, const float *near1 = nullptr,
-                  const float *near2 = nullptr) {
+void run_downward(fmmpc_handle &H, double *out, int nrhs, int do_bnd, int with_bnd_w, cudaStream_t s,
+                  const float *near1 = nullptr, const float *near2 = nullptr) {
   const Geo &g = H.g;
+  const cpx<R> *Mv = (const cpx<R> *)H.fb.Mv, *Mb = (const cpx<R> *)H.fb.Mb;
   const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
   const R *pb = (const R *)H.fb.phib;
   const cpx<R> *vl2l = mats_of<R>(H).vl2l;
   const dim3 grid((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs);
   switch (g.m) {
-    case 4: k_downward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
-    case 8: k_downward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
-    case 16: k_downward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 4: k_downward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 8: k_downward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 16: k_downward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
     default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
   }
   FMMPC_LAUNCH_CHECK();
@@ -1572,12 +1585,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   if (with_bnd) {
     mark(2);
     k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbb_first,
-                                                              Ls.vbb_src, Mv, Lb);
-    k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, 0, Mv, Mb, Lv, Lb);
+                                                              Ls.vbb_src, Mv, Lb, g.lnh);
     k_colloc<R><<<nblk((int64_t)g.NG * nrhs * 32, 128), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
                                                                    H.fb.vcol, H.fb.kcol);
     FMMPC_LAUNCH_CHECK();
-    launches += 3;
+    launches += 2;
     if (part == PART_VCOL) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.vcol, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
@@ -1601,6 +1613,12 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       H.launches = launches;
       return;
     }
+    if (side && Ls.nbnear > 0) {  // the near-boundary correction needs only q: a third stream
+      FMMPC_CUDA(cudaEventRecord(H.sev[3], s));
+      FMMPC_CUDA(cudaStreamWaitEvent(H.sstream2, H.sev[3], 0));
+      launches += run_bnd_near<R>(H, nrhs, H.sstream2);
+      FMMPC_CUDA(cudaEventRecord(H.sev[4], H.sstream2));
+    }
     mark(4);
     {
       const size_t sm = bnd_up_smem<R, P>(g.L);
@@ -1619,7 +1637,6 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     ++launches;
   }
   if (side) {
-    if (with_bnd && Ls.nbnear > 0) launches += run_bnd_near<R>(H, nrhs, s);
     FMMPC_CUDA(cudaEventRecord(H.sev[2], ss));
     FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[2], 0));
   }
@@ -1640,9 +1657,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
                                                              Mv, Mb, Lv);
     ++launches;
   }
-  k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);
-  FMMPC_LAUNCH_CHECK();
-  launches += 1;
+  if (g.L < 2) {  // else the downward kernel adds the root constant
+    k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);
+    FMMPC_LAUNCH_CHECK();
+    launches += 1;
+  }
   mark(7);
   if (g.L < 2) launches += run_l2l<R, P>(H, nrhs, s);  // else L2L runs with L2P below
   if (!side && with_bnd && Ls.nbnear > 0) {
@@ -1660,8 +1679,9 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     run_p2p<R>(H, H.fb.table, out, nrhs, s);  // writes the near field into out
     ++launches;
   }
+  if (side && Ls.nbnear > 0) FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[4], 0));
   mark(10);
-  if (g.L >= 2) run_downward<R, P>(H, out, nrhs, do_bnd, s, n1, n2);
+  if (g.L >= 2) run_downward<R, P>(H, out, nrhs, do_bnd, with_bnd ? 1 : 0, s, n1, n2);
   else run_far_final<R>(H, out, nrhs, do_bnd, s, n1, n2);
   ++launches;
   mark_end();
@@ -1828,6 +1848,7 @@ void init_fmm(fmmpc_handle &H) {
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_in, cudaEventDisableTiming));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_out, cudaEventDisableTiming));
   FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream, cudaStreamNonBlocking));
+  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream2, cudaStreamNonBlocking));
   for (auto &e : H.sev) FMMPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 

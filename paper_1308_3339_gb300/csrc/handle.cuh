@@ -118,8 +118,9 @@ struct fmmpc_handle {
   bool graphs = true;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
-  cudaStream_t sstream = nullptr;  // second stream of the full apply (near field, volume M2L)
-  cudaEvent_t sev[3] = {};         // fork after the weights, fork after the upward pass, join
+  cudaStream_t sstream = nullptr;   // second stream of the full apply (near field, volume M2L)
+  cudaStream_t sstream2 = nullptr;  // third stream (near-boundary correction)
+  cudaEvent_t sev[5] = {};  // forks after the weights, the upward pass and the BEM solve; two joins
   std::vector<fmmpc::GraphEntry> gcache;
   uint64_t gclock = 0;
 };
