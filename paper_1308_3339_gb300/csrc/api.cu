@@ -127,6 +127,7 @@ void release(fmmpc_handle *h) {
   if (h->gev_out) cudaEventDestroy(h->gev_out);
   if (h->sstream) cudaStreamDestroy(h->sstream);
   if (h->sstream2) cudaStreamDestroy(h->sstream2);
+  if (h->sstream3) cudaStreamDestroy(h->sstream3);
   for (auto e : h->sev)
     if (e) cudaEventDestroy(e);
   for (int k = 0; k <= fmmpc_handle::NSTAGE; ++k)

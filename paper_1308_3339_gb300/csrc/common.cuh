@@ -209,6 +209,7 @@ struct Lists {
   int32_t *vbv_src = nullptr;     // boundary cell id at that level
   int32_t *vbv_cells = nullptr;   // [n_vbv_cells] volume cells whose vbv list is not empty
   int64_t n_vbv_cells = 0;
+  int32_t *vbv_slot = nullptr;    // [ncell] index in vbv_cells, -1 for cells without boundary sources
   int32_t *vbb_first = nullptr;   // [nbcell+1] by boundary target: volume sources (pass A)
   int32_t *vbb_src = nullptr;     // volume Morton index at that level
   int32_t *pvb_first = nullptr;   // [nbleaf+1] by boundary leaf: near volume leaves (pass A)

@@ -420,10 +420,12 @@ __global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, in
 // Boundary sources added to volume locals, for the cells that have them (cells[0, ntgt)):
 // eight lanes per (cell, rhs), four cells per warp, a segmented shuffle reduction, and
 // L += (-1)^n/n! H_n (deterministic: no atomics).  The lists average ~8 sources per cell.
+// With Lsep the result is written there instead ([rhs][index in cells][P]), for the
+// downward pass to add, so that this pass need not wait for the volume M2L.
 template <typename R, int P>
 __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, const int32_t *__restrict__ bfirst,
                           const int32_t *__restrict__ bsrc, const cpx<R> *__restrict__ Mb, cpx<R> *__restrict__ Lv,
-                          const int32_t *__restrict__ cells, int64_t ntgt) {
+                          const int32_t *__restrict__ cells, int64_t ntgt, cpx<R> *__restrict__ Lsep = nullptr) {
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const int sub = threadIdx.x & 7;
   const bool active = grp < ntgt * nrhs;
@@ -454,7 +456,7 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
     }
   }
   R f = 1;
-  cpx<R> *out = Lv + (int64_t)rhs * ncell * P + gidx * P;
+  cpx<R> *out = Lsep ? Lsep + ((int64_t)rhs * ntgt + gg % ntgt) * P : Lv + (int64_t)rhs * ncell * P + gidx * P;
 #pragma unroll
   for (int n = 0; n < P; ++n) {
     if (n > 0) f = -f / R(n);
@@ -464,7 +466,7 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (active && sub == 0) out[n] = out[n] + mk(f * re, f * im);
+    if (active && sub == 0) out[n] = Lsep ? mk(f * re, f * im) : out[n] + mk(f * re, f * im);
   }
 }
 
@@ -1179,7 +1181,8 @@ template <typename R, int P, int M>
 __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_bnd, int64_t nbnear,
                                                        const cpx<R> *__restrict__ Mv, const cpx<R> *__restrict__ Mb,
                                                        int with_bnd_w, const cpx<R> *__restrict__ vl2l,
-                                                       const cpx<R> *__restrict__ Lv,
+                                                       const cpx<R> *__restrict__ Lv, const int32_t *__restrict__ vslot,
+                                                       const cpx<R> *__restrict__ Lsep, int64_t nsep,
                                                        const R *__restrict__ phib, const int32_t *__restrict__ bslot,
                                                        double *__restrict__ out, const float *__restrict__ near1,
                                                        const float *__restrict__ near2) {
@@ -1191,12 +1194,21 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   // every value the block needs, loaded at once: the translation matrices, the M2L parts of
   // the ancestors (levels 0 .. L - 2), of the 4 children and of the 16 leaves
   for (int i = tid; i < 4 * P * P; i += nthr) sS[i] = vl2l[i];
+  // L of cell c (global index), coefficient n, with the boundary-source part kept apart
+  auto lval = [&](int64_t c, int n) -> cpx<R> {
+    cpx<R> v = Lr[c * P + n];
+    if (vslot) {
+      const int sl = vslot[c];
+      if (sl >= 0) v = v + Lsep[((int64_t)rhs * nsep + sl) * P + n];
+    }
+    return v;
+  };
   for (int i = tid; i < (L - 1) * P; i += nthr) {
     const int l = i / P, n = i % P;
-    sanc[l][n] = Lr[(level_offset(l) + (blk >> (2 * (L - 2 - l)))) * P + n];
+    sanc[l][n] = lval(level_offset(l) + (blk >> (2 * (L - 2 - l))), n);
   }
-  for (int i = tid; i < 4 * P; i += nthr) s1[i / P][i % P] = Lr[(level_offset(L - 1) + 4 * blk) * P + i];
-  for (int i = tid; i < 16 * P; i += nthr) s2[i / P][i % P] = Lr[(level_offset(L) + 16 * blk) * P + i];
+  for (int i = tid; i < 4 * P; i += nthr) s1[i / P][i % P] = lval(level_offset(L - 1) + 4 * blk + i / P, i % P);
+  for (int i = tid; i < 16 * P; i += nthr) s2[i / P][i % P] = lval(level_offset(L) + 16 * blk + i / P, i % P);
   if (tid == 0) {  // the root also takes ln h times the total weight (volume, and boundary if present)
     double W = (double)Mv[(int64_t)rhs * g.ncell * P].re;
     if (with_bnd_w)
@@ -1475,17 +1487,20 @@ int run_l2l(fmmpc_handle &H, int nrhs, cudaStream_t s) {
 // includes the boundary weight.
 template <typename R, int P>
 void run_downward(fmmpc_handle &H, double *out, int nrhs, int do_bnd, int with_bnd_w, cudaStream_t s,
-                  const float *near1 = nullptr, const float *near2 = nullptr) {
+                  const float *near1 = nullptr, const float *near2 = nullptr, bool sep = false) {
   const Geo &g = H.g;
+  const int32_t *vslot = sep ? H.lists.vbv_slot : nullptr;
+  const cpx<R> *Lsep = (const cpx<R> *)H.fb.Lvb;
+  const int64_t nsep = H.lists.n_vbv_cells;
   const cpx<R> *Mv = (const cpx<R> *)H.fb.Mv, *Mb = (const cpx<R> *)H.fb.Mb;
   const cpx<R> *Lv = (const cpx<R> *)H.fb.Lv;
   const R *pb = (const R *)H.fb.phib;
   const cpx<R> *vl2l = mats_of<R>(H).vl2l;
   const dim3 grid((unsigned)(int64_t(1) << (2 * (g.L - 2))), nrhs);
   switch (g.m) {
-    case 4: k_downward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
-    case 8: k_downward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
-    case 16: k_downward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 4: k_downward_tree<R, P, 4><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, vslot, Lsep, nsep, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 8: k_downward_tree<R, P, 8><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, vslot, Lsep, nsep, pb, H.lists.leaf_bslot, out, near1, near2); break;
+    case 16: k_downward_tree<R, P, 16><<<grid, 256, 0, s>>>(g, nrhs, do_bnd, H.lists.nbnear, Mv, Mb, with_bnd_w, vl2l, Lv, vslot, Lsep, nsep, pb, H.lists.leaf_bslot, out, near1, near2); break;
     default: throw Error(FMMPC_ERR_UNSUPPORTED, "leaf side must be 4, 8 or 16");
   }
   FMMPC_LAUNCH_CHECK();
@@ -1577,10 +1592,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   }
   mark(1);
   launches += run_upward<R, P>(H, nrhs, s);
-  if (m2l_side) {
+  if (m2l_side) {  // its own stream, so that it need not wait for the near field
     FMMPC_CUDA(cudaEventRecord(H.sev[1], s));
-    FMMPC_CUDA(cudaStreamWaitEvent(ss, H.sev[1], 0));
-    launches += run_m2l_tc(H, Mv, Lv, nrhs, ss);
+    FMMPC_CUDA(cudaStreamWaitEvent(H.sstream3, H.sev[1], 0));
+    launches += run_m2l_tc(H, Mv, Lv, nrhs, H.sstream3);
+    FMMPC_CUDA(cudaEventRecord(H.sev[5], H.sstream3));
   }
   if (with_bnd) {
     mark(2);
@@ -1636,21 +1652,28 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     FMMPC_LAUNCH_CHECK();
     ++launches;
   }
+  // with the tensor-core M2L (L >= 2) the boundary-source part of the volume locals is kept
+  // apart for the downward pass to add, so it can run while the volume M2L still runs
+  const bool vbv_sep = std::is_same<R, float>::value && H.tcm.enabled && with_bnd && Ls.n_vbv_cells > 0;
+  auto run_vbv_sep = [&]() {
+    k_m2l_vbv<R, P><<<nblk(Ls.n_vbv_cells * nrhs * 8), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbv_first,
+                                                                     Ls.vbv_src, Mb, Lv, Ls.vbv_cells,
+                                                                     Ls.n_vbv_cells, (cpx<R> *)H.fb.Lvb);
+    FMMPC_LAUNCH_CHECK();
+    ++launches;
+  };
   if (side) {
+    if (vbv_sep) run_vbv_sep();
     FMMPC_CUDA(cudaEventRecord(H.sev[2], ss));
     FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[2], 0));
+    if (m2l_side) FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[5], 0));
   }
   mark(5);
   if (std::is_same<R, float>::value && H.tcm.enabled) {
     // volume-to-volume M2L on the tensor cores (mixed forms); boundary sources added after
     if (!m2l_side) launches += run_m2l_tc(H, Mv, Lv, nrhs, s);
     mark(6);
-    if (with_bnd && Ls.n_vbv_cells > 0) {
-      k_m2l_vbv<R, P><<<nblk(Ls.n_vbv_cells * nrhs * 8), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbv_first,
-                                                                       Ls.vbv_src, Mb, Lv, Ls.vbv_cells,
-                                                                       Ls.n_vbv_cells);
-      ++launches;
-    }
+    if (vbv_sep && !side) run_vbv_sep();
   } else {
     k_m2l_vol<R, P><<<nblk(g.ncell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, 1, with_bnd ? 1 : 0, 0,
                                                              Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src,
@@ -1681,7 +1704,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   }
   if (side && Ls.nbnear > 0) FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[4], 0));
   mark(10);
-  if (g.L >= 2) run_downward<R, P>(H, out, nrhs, do_bnd, with_bnd ? 1 : 0, s, n1, n2);
+  if (g.L >= 2) run_downward<R, P>(H, out, nrhs, do_bnd, with_bnd ? 1 : 0, s, n1, n2, vbv_sep);
   else run_far_final<R>(H, out, nrhs, do_bnd, s, n1, n2);
   ++launches;
   mark_end();
@@ -1769,6 +1792,7 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.vcol = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.vt = H.pool.get<double>((size_t)nr * g.NG);
+  H.fb.Lvb = H.pool.get<cpx<R>>((size_t)nr * std::max<int64_t>(1, H.lists.n_vbv_cells) * g.p);
   if (std::is_same<R, float>::value) {  // two-word FP32 BEM apply
     H.fb.vt_hi = H.pool.get<float>((size_t)nr * g.NG);
     H.fb.vt_lo = H.pool.get<float>((size_t)nr * g.NG);
@@ -1849,6 +1873,7 @@ void init_fmm(fmmpc_handle &H) {
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_out, cudaEventDisableTiming));
   FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream, cudaStreamNonBlocking));
   FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream2, cudaStreamNonBlocking));
+  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream3, cudaStreamNonBlocking));
   for (auto &e : H.sev) FMMPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 

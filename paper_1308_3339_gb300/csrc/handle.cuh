@@ -34,6 +34,7 @@ struct FmmBufs {
   float *vt_hi = nullptr, *vt_lo = nullptr;  // the same as two FP32 words (single-precision forms)
   float *knear = nullptr;    // near-boundary element integrals (single-precision forms)
   float *kcol = nullptr;     // collocation-point near-field log kernel (single-precision forms)
+  void *Lvb = nullptr;       // [nrhs][n_vbv_cells][p] boundary-source part of L of those cells
   int *up_count = nullptr;   // [nrhs][up_ncount] upward-pass arrival counts (zero between launches)
   int64_t up_ncount = 0;
 };
@@ -120,7 +121,8 @@ struct fmmpc_handle {
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaStream_t sstream = nullptr;   // second stream of the full apply (near field, volume M2L)
   cudaStream_t sstream2 = nullptr;  // third stream (near-boundary correction)
-  cudaEvent_t sev[5] = {};  // forks after the weights, the upward pass and the BEM solve; two joins
+  cudaStream_t sstream3 = nullptr;  // fourth stream (volume M2L)
+  cudaEvent_t sev[6] = {};  // forks after the weights, the upward pass and the BEM solve; three joins
   std::vector<fmmpc::GraphEntry> gcache;
   uint64_t gclock = 0;
 };

@@ -292,6 +292,10 @@ void build_lists(const Geo &g, Lists &Ls, Stencil &st, cudaStream_t s, DevPool &
     Ls.vbv_cells = pool.get<int32_t>(cells.size() + 1);
     if (!cells.empty())
       FMMPC_CUDA(cudaMemcpyAsync(Ls.vbv_cells, cells.data(), sizeof(int32_t) * cells.size(), cudaMemcpyHostToDevice, s));
+    std::vector<int32_t> slot(g.ncell, -1);  // cell -> its index in vbv_cells
+    for (size_t i = 0; i < cells.size(); ++i) slot[cells[i]] = (int32_t)i;
+    Ls.vbv_slot = pool.get<int32_t>(g.ncell);
+    FMMPC_CUDA(cudaMemcpyAsync(Ls.vbv_slot, slot.data(), sizeof(int32_t) * g.ncell, cudaMemcpyHostToDevice, s));
     FMMPC_CUDA(cudaStreamSynchronize(s));
   }
   // regroup the volume-boundary lists by boundary target for the collocation pass
