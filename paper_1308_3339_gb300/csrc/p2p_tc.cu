@@ -66,7 +66,38 @@ __device__ __forceinline__ float tf32_round(float x) {
 // 32-byte pieces of the leaf's swizzled 128-byte rows (hi, lo) and the same 8 weights of the
 // FP32 zero-padded weight image the other stages read (w, npad, pad).  Leaves are the
 // fastest index, so reads and writes of neighbouring threads are contiguous.
-__global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int nrhs, const double *__restrict__ r,
+// h^2 as two FP32 words for the weight product
+inline float h2_hi(double h) { return (float)(h * h); }
+inline float h2_lo(double h) { return (float)(h * h - (double)(float)(h * h)); }
+
+// x = hi + lo, hi = fl32(x) rounded to nearest even and lo = fl32(x - hi), from the IEEE-754
+// fields on the integer units (FP64 arithmetic is scarce on this GPU); |x| outside
+// [2^-100, 2^101) goes through the conversion unit.  (Below about 2^-100 the error words of
+// the product below lose bits as FP32 subnormals; the weights are far above that.)
+__device__ __forceinline__ void f64_to_f32x2(double x, float &hi, float &lo) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7ffu;
+  const uint64_t m = u & 0xfffffffffffffull;
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  if (e >= 923u && e <= 1123u) {
+    uint32_t f = sign | ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint32_t rest = (uint32_t)(m & 0x1fffffffu);  // the 29 bits below FP32 precision
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (f & 1u));
+    f += up ? 1u : 0u;  // a carry out of the mantissa moves into the exponent, as it should
+    hi = __uint_as_float(f);
+    const int32_t rr = (int32_t)rest - (up ? 0x20000000 : 0);  // x - hi in units of 2^(e - 1075)
+    const float mag = __int2float_rn(rr) * 0x1p-29f * __uint_as_float((e - 1046u + 127u) << 23);
+    lo = sign ? -mag : mag;
+  } else if (e == 0 && m == 0) {
+    hi = lo = __uint_as_float(sign);
+  } else {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  }
+}
+
+__global__ void k_tc_strips(int n, int R, int NLX, int NLY, float h2_hi, float h2_lo, int nrhs,
+                            const double *__restrict__ r,
                             float *__restrict__ ahi, float *__restrict__ alo, float *__restrict__ wimg, int npad,
                             int pad) {
   const int NL = n / 8;
@@ -86,8 +117,15 @@ __global__ void k_tc_strips(int n, int R, int NLX, int NLY, double h2, int nrhs,
   const double *src = r + rhs * (int64_t)n * n + (int64_t)j * n + i0;
   float w[8], hi[8], lo[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {  // one rounding of the FP64 product (as the weight image
-    w[q] = (float)(h2 * src[q]);   // of the other engine); hi + lo is that FP32 value
+  for (int q = 0; q < 8; ++q) {
+    // w = fl32(h^2 r) rounded once from a two-word FP32 product (h^2 and r each as hi + lo,
+    // the product of the high words split exactly by an FMA): the FP32 value the other
+    // engine's weight image holds, but for exact near-ties; then hi + lo TF32 words of w
+    float xh, xl;
+    f64_to_f32x2(src[q], xh, xl);
+    const float p = __fmul_rn(xh, h2_hi);
+    const float t = fmaf(xh, h2_lo, fmaf(xl, h2_hi, fmaf(xh, h2_hi, -p)));
+    w[q] = p + t;
     hi[q] = tf32_round(w[q]);
     lo[q] = tf32_round(w[q] - hi[q]);
   }
@@ -394,7 +432,7 @@ void init_tc_p2p(fmmpc_handle &H) {
 int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s, float *wimg) {
   const Geo &g = H.g;
   const int64_t threads = (int64_t)nrhs * (g.n / 8) * (g.n / 8) * 8;
-  k_tc_strips<<<nblk(threads), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, g.h * g.h, nrhs, r, H.tcp.ahi, H.tcp.alo,
+  k_tc_strips<<<nblk(threads), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, h2_hi(g.h), h2_lo(g.h), nrhs, r, H.tcp.ahi, H.tcp.alo,
                                             wimg, g.npad, g.pad);
   FMMPC_LAUNCH_CHECK();
   return 1;
