@@ -214,16 +214,18 @@ __global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict_
   while (l > 0) {
     const int step = l < MAXSTEP ? l : MAXSTEP, pl = l - step;
     const uint32_t pc = cell >> (2 * step);
-    __threadfence();
     __syncthreads();
     if (tid == 0) {
+      __threadfence();  // after the barrier, one fence makes the whole block's writes visible
       int *ctr = counter + (int64_t)rhs * ncount + level_offset(pl) + pc;
       s_last = atomicAdd(ctr, 1) == (1 << (2 * step)) - 1;
-      if (s_last) *ctr = 0;  // ready for the next launch
+      if (s_last) {
+        *ctr = 0;  // ready for the next launch
+        __threadfence();
+      }
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const int nch = 1 << (2 * step);
     const uint32_t c0 = pc << (2 * step);
     for (int i = tid; i < nch * P; i += nthr) {
@@ -855,7 +857,7 @@ __global__ void k_bem_vt_f2(int n, int nrhs, const double *__restrict__ vcol, fl
 // pass over it; the partial two-word sums are combined with TwoSum (warp shuffles, then
 // across the 8 warps) and converted to FP64 once per row and right-hand side.
 template <int RB>
-__global__ void __launch_bounds__(256) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
+__global__ void __launch_bounds__(256, RB == 1 ? 3 : 2) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
                                                       const float *__restrict__ Tl, const float *__restrict__ vh,
                                                       const float *__restrict__ vl, double *__restrict__ q) {
   __shared__ float rs[8][RB][4], rc[8][RB][4];
