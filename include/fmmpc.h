@@ -174,22 +174,28 @@ int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 
 /* on = 1 (the default): fmmpc_apply records its kernels once per distinct (r, z, n_rhs)
  * into a CUDA graph on an internal stream and replays it (ordered after and before the
- * handle's stream with events); on = 0: launches the kernels one by one.  fmmpc_solve
- * follows its own opts.use_graphs instead.  Up to 64 graphs are kept per handle. */
+ * handle's stream with events); on = 0: launches the kernels one by one.  Either way,
+ * with stage timing off, the full apply runs the tensor-core near field, the volume M2L
+ * and the near-boundary correction on three further internal streams, forked and joined
+ * with events, so they overlap the boundary chain; the result is the same bit for bit as
+ * with the stages in order on one stream.  fmmpc_solve follows its own opts.use_graphs
+ * instead.  Up to 64 graphs are kept per handle. */
 int fmmpc_set_graphs(fmmpc_handle *h, int32_t on);
 
-/* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream.
+/* Per-stage timing of fmmpc_apply with CUDA events recorded on the handle's stream; with
+ * timing on, the apply runs its stages in order on that one stream (no overlap).
  * fmmpc_set_timing(h, 1) creates the events and turns recording on for every stage; 2
  * records only the four events around the M2L (stage 5) and P2P (stage 9) kernels, so the
  * rest of the apply runs without event records; 0 turns recording off.
  * fmmpc_get_timing synchronises the stream and writes the durations in milliseconds of
  * the stages of the last apply into ms[0 .. min(cap, count)), *count = 11 stages:
  *  0 weight image, 1 P2M + M2M (Sec. 5.3 items 1-2), 2 collocation pass (M2L to boundary
- *  cells, local expansions and near field at the collocation points), 3 BEM solve (FP64),
- *  4 boundary multipoles, 5 M2L (item 3; with the tensor-core M2L its volume part only),
- *  6 boundary-source M2L added after the tensor-core M2L, 7 L2L (item 4), 8 near-boundary
- *  element integrals, 9 P2P near field (item 5, Eq. e:volume_integral; with the CUDA-core
- *  engine this stage also holds L2P and the sum), 10 L2P + sum (tensor-core engine).
+ *  cells, local expansions and near field at the collocation points), 3 BEM solve (FP64,
+ *  or two-word FP32 in the single-precision forms), 4 boundary multipoles, 5 M2L (item 3;
+ *  with the tensor-core M2L its volume part only), 6 boundary-source M2L with the
+ *  tensor-core M2L (kept apart, added by the downward pass), 7 L2L (item 4; only for trees
+ *  of fewer than three levels, else part of stage 10), 8 near-boundary element integrals,
+ *  9 P2P near field (item 5, Eq. e:volume_integral), 10 L2L + L2P + the final sum.
  * A stage that did not run reports 0.  Errors: _INVALID if timing is off. */
 int fmmpc_set_timing(fmmpc_handle *h, int32_t on);
 int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);

@@ -3,7 +3,8 @@
 // Pass A (volume sources w = h^2 r):  P2M at the leaves, M2M up the quadtree (Sec. 5.3
 //   items 1-2); M2L from volume cells into the boundary cells, L2L along each side, L2P
 //   plus the near field at the collocation points: (V r)(y_m), the right-hand side of
-//   Eq. e:ubound with z = 0 on Gamma.  q = S^{-1}(-(V r)|_Gamma) in FP64 (Sec. 4.3).
+//   Eq. e:ubound with z = 0 on Gamma.  q = S^{-1}(-(V r)|_Gamma) in FP64, or in two-word
+//   FP32 in the single-precision forms (Sec. 4.3).
 // Pass B: boundary elements carrying q become sources (exact segment multipoles), M2M up
 //   the boundary trees; M2L over volume and boundary sources into the volume locals
 //   (item 3), L2L down (item 4); the lattice near field (P2P), L2P (item 5) and the
@@ -15,6 +16,10 @@
 // two nodes depends only on their integer offset, so P2P is a block convolution of the
 // weight image with a table of ln|d| over the stencil of leaf offsets that the dual tree
 // traversal produced.
+//
+// Without stage timing the full apply forks the tensor-core near field, the volume M2L and
+// the near-boundary correction onto streams of their own; they overlap the boundary chain
+// (collocation values, BEM density, boundary tree) and join before the downward pass.
 #include <algorithm>
 #include <cmath>
 #include <complex>
