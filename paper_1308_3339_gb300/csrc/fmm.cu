@@ -291,35 +291,6 @@ __global__ void k_l2l_levels(int lfrom, int lto, int64_t ncell, int nrhs, const 
   }
 }
 
-// Two L2L levels in one block: a cell of level lp adds into its 4 children and their 16
-// children, with the updated children kept in shared memory.
-template <typename R, int P>
-__global__ void __launch_bounds__(256) k_l2l_2levels(int lp, int64_t ncell, const cpx<R> *__restrict__ vl2l,
-                                                     cpx<R> *__restrict__ Lv) {
-  __shared__ cpx<R> spar[P], sc[4][P], sS[4 * P * P];
-  const int tid = threadIdx.x, rhs = blockIdx.y;
-  const uint32_t c = blockIdx.x;
-  cpx<R> *L = Lv + (int64_t)rhs * ncell * P;
-  for (int i = tid; i < 4 * P * P; i += blockDim.x) sS[i] = vl2l[i];
-  if (tid < P) spar[tid] = L[(level_offset(lp) + c) * P + tid];
-  __syncthreads();
-  if (tid < 4 * P) {
-    const int ch = tid / P, n = tid % P;
-    cpx<R> acc = L[(level_offset(lp + 1) + 4 * c + ch) * P + n];
-    for (int k = n; k < P; ++k) cmac(acc, sS[(ch * P + n) * P + k], spar[k]);
-    sc[ch][n] = acc;
-    L[(level_offset(lp + 1) + 4 * c + ch) * P + n] = acc;
-  }
-  __syncthreads();
-  for (int t = tid; t < 16 * P; t += blockDim.x) {
-    const int g = t / P, n = t % P, par = g >> 2, ch = g & 3;
-    cpx<R> *dst = L + (level_offset(lp + 2) + 16 * c + g) * P + n;
-    cpx<R> acc = *dst;
-    for (int k = n; k < P; ++k) cmac(acc, sS[(ch * P + n) * P + k], sc[par][k]);
-    *dst = acc;
-  }
-}
-
 // ------------------------------------------------------------------ M2L (item 3)
 // With zt = (c_target - c_source)/rho (same level), the scaled M2L reads
 //   Lt_0 = Mt_0 (log zt + ln rho) + sum_k Mt_k zt^-k
@@ -535,11 +506,6 @@ __global__ void k_root_const(int p, int64_t ncell, int64_t nbcell, int nrhs, dou
 }
 
 // ------------------------------------------------------------------ boundary geometry
-__device__ __forceinline__ void side_dir(int side, double &ex, double &ey) {
-  ex = (side == 0) ? 1.0 : (side == 2 ? -1.0 : 0.0);
-  ey = (side == 1) ? 1.0 : (side == 3 ? -1.0 : 0.0);
-}
-
 // Along-side coordinate u and signed normal offset d of node coordinates (x, y): for an
 // element starting at arclength t_a, s1 = t_a - u and d = (x - a).n_outward (Sec. 4.3).
 __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int &u, int &d) {
@@ -1468,20 +1434,15 @@ int run_upward(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   return g.L == 1 ? 2 : 1;
 }
 
-// Downward pass: two L2L levels per launch from the root (one for a last odd level).
+// Downward pass for trees of depth L < 2 (one launch per level; deeper trees use the
+// one-launch downward kernel).
 template <typename R, int P>
 int run_l2l(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   const Geo &g = H.g;
   cpx<R> *Lv = (cpx<R> *)H.fb.Lv;
   Mats<R> mt = mats_of<R>(H);
   int launches = 0;
-  int lp = 0;
-  while (lp + 2 <= g.L) {
-    k_l2l_2levels<R, P><<<dim3((unsigned)(int64_t(1) << (2 * lp)), nrhs), 256, 0, s>>>(lp, g.ncell, mt.vl2l, Lv);
-    lp += 2;
-    ++launches;
-  }
-  if (lp < g.L) {
+  for (int lp = 0; lp < g.L; ++lp) {
     const int64_t tasks = (int64_t(1) << (2 * (lp + 1))) * P * nrhs;
     k_l2l_levels<R, P><<<nblk(tasks), 256, 0, s>>>(lp, lp + 1, g.ncell, nrhs, mt.vl2l, Lv);
     ++launches;
