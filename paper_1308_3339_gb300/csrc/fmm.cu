@@ -328,6 +328,37 @@ __device__ __forceinline__ void m2l_accum(cpx<R> (&H)[P], const cpx<R> *__restri
 }
 
 // warp-reduce H, scale by (-1)^n/n!, then store (add = 0) or accumulate (add = 1)
+// Offset between a volume and a boundary cell centre in cell units, d * scale with
+// scale = 1 / (rho 2^(L+1)) and d an integer in those fine units.  When the scale is a power
+// of two and |d| < 2^24 the FP32 product is exact and equals the FP64 one rounded to FP32,
+// so the single-precision forms take it without FP64 instructions (scarce on this GPU).
+struct OffsetScale {
+  double s64;
+  float s32;
+  bool exact32;
+};
+__device__ __forceinline__ OffsetScale offset_scale(int rho, int L) {
+  const int64_t v = (int64_t)rho << (L + 1);
+  OffsetScale o;
+  if ((v & (v - 1)) == 0) {  // 1 / 2^k from the exponent field, no division
+    const int k = 63 - __clzll(v);
+    o.s64 = __longlong_as_double((long long)(1023 - k) << 52);
+    o.exact32 = k < 126;
+    o.s32 = o.exact32 ? __int_as_float((127 - k) << 23) : 0.f;
+  } else {
+    o.s64 = 1.0 / (double)v;
+    o.s32 = 0.f;
+    o.exact32 = false;
+  }
+  return o;
+}
+template <typename R>
+__device__ __forceinline__ R scaled_offset(int64_t d, const OffsetScale &o) {
+  if (std::is_same<R, float>::value && o.exact32 && d > -(int64_t(1) << 24) && d < (int64_t(1) << 24))
+    return (R)((float)d * o.s32);
+  return (R)((double)d * o.s64);
+}
+
 template <typename R, int P>
 __device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__restrict__ out, int add) {
   R f = 1;
@@ -382,14 +413,14 @@ __global__ void k_m2l_vol(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, in
     vol_geom(gd, l, c, X, Y, sw);
     X <<= gd.L;
     Y <<= gd.L;
-    const double scale = 1.0 / ((double)rho * (double)(int64_t(1) << (gd.L + 1)));
+    const OffsetScale scale = offset_scale(rho, gd.L);
     const cpx<R> *MB = Mb + (int64_t)rhs * nbcell * P + blevel_offset(l) * P;
     for (int e = bfirst[gidx] + lane; e < bfirst[gidx + 1]; e += 32) {
       const uint32_t b = (uint32_t)bsrc[e];
       int64_t BX, BY, bs;
       bnd_geom(gd, l, b, BX, BY, bs);
       m2l_accum<R, P>(H, MB + (int64_t)b * P,
-                      mk<R>((R)((double)(X - BX) * scale), (R)((double)(Y - BY) * scale)), lnrho);
+                      mk<R>(scaled_offset<R>(X - BX, scale), scaled_offset<R>(Y - BY, scale)), lnrho);
     }
   }
   m2l_finish<R, P>(H, lane, Lv + (int64_t)rhs * ncell * P + gidx * P, add);
@@ -423,14 +454,14 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
     vol_geom(gd, l, c, X, Y, sw);
     X <<= gd.L;
     Y <<= gd.L;
-    const double scale = 1.0 / ((double)rho * (double)(int64_t(1) << (gd.L + 1)));
+    const OffsetScale scale = offset_scale(rho, gd.L);
     const cpx<R> *MB = Mb + (int64_t)rhs * nbcell * P + blevel_offset(l) * P;
     for (int e = bfirst[gidx] + sub; e < bfirst[gidx + 1]; e += 8) {
       const uint32_t b = (uint32_t)bsrc[e];
       int64_t BX, BY, bs;
       bnd_geom(gd, l, b, BX, BY, bs);
       m2l_accum<R, P>(H, MB + (int64_t)b * P,
-                      mk<R>((R)((double)(X - BX) * scale), (R)((double)(Y - BY) * scale)), lnrho);
+                      mk<R>(scaled_offset<R>(X - BX, scale), scaled_offset<R>(Y - BY, scale)), lnrho);
     }
   }
   R f = 1;
@@ -465,7 +496,7 @@ __global__ void k_m2l_bnd(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs,
   const R lnrho = dev_log<R>((R)rho);
   int64_t BX, BY, bs;
   bnd_geom(gd, l, b, BX, BY, bs);
-  const double scale = 1.0 / ((double)rho * (double)(int64_t(1) << (gd.L + 1)));
+  const OffsetScale scale = offset_scale(rho, gd.L);
   cpx<R> H[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) H[k] = mk<R>(0, 0);
@@ -477,7 +508,7 @@ __global__ void k_m2l_bnd(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs,
     X <<= gd.L;
     Y <<= gd.L;
     m2l_accum<R, P>(H, M + (int64_t)v * P,
-                    mk<R>((R)((double)(BX - X) * scale), (R)((double)(BY - Y) * scale)), lnrho);
+                    mk<R>(scaled_offset<R>(BX - X, scale), scaled_offset<R>(BY - Y, scale)), lnrho);
   }
   m2l_finish<R, P>(H, lane, Lb + (int64_t)rhs * nbcell * P + gb * P, 0);
   // the four side roots also take the ln h part of G times the total volume weight
@@ -646,14 +677,14 @@ __global__ void k_colloc_mat(Geo g, const int32_t *__restrict__ pfirst, const in
 template <typename R>
 __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<R> *__restrict__ Lb,
                          const int32_t *__restrict__ pfirst, const int32_t *__restrict__ psrc,
-                         double *__restrict__ vcol, const float *__restrict__ Kc) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                         double *__restrict__ vcol, const float *__restrict__ Kc, float *__restrict__ vt_hi,
+                         float *__restrict__ vt_lo) {
+  // block (rhs, along): warp w takes the collocation point `along` of side w
+  __shared__ double sv[4];
   const int lane = threadIdx.x & 31;
-  if (wid >= (int64_t)g.NG * nrhs) return;
-  const int rhs = (int)(wid / g.NG);
-  const int ge = (int)(wid % g.NG);
+  const int rhs = (int)(blockIdx.x / g.n), along = (int)(blockIdx.x % g.n), side = threadIdx.x >> 5;
   const int n = g.n, m = g.m, L = g.L, p = g.p;
-  const int side = ge / n, along = ge % n;
+  const int ge = side * n + along;
   const int64_t bl = ((int64_t)side << L) + along / m;
   const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
   const R inv2n = R(1) / (R)(2 * n);
@@ -716,7 +747,24 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
     far = v.re;
   }
   far = warp_sum(far);
-  if (lane == 0) vcol[(int64_t)rhs * g.NG + ge] = ((double)acc + (double)far) * NEG_INV_2PI;
+  const double v = ((double)acc + (double)far) * NEG_INV_2PI;
+  if (lane == 0) {
+    vcol[(int64_t)rhs * g.NG + ge] = v;
+    sv[side] = v;
+  }
+  if (vt_hi) {
+    // the side DFT of the four values (as k_bem_vt) as FP32 hi + lo words for the BEM apply
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      const int j = threadIdx.x;
+      const double o = j == 0 ? (sv[0] + sv[2]) + (sv[1] + sv[3])
+                     : j == 1 ? (sv[0] + sv[2]) - (sv[1] + sv[3])
+                     : j == 2 ? sv[0] - sv[2] : sv[1] - sv[3];
+      const float hi = (float)o;
+      vt_hi[(int64_t)rhs * g.NG + j * n + along] = hi;
+      vt_lo[(int64_t)rhs * g.NG + j * n + along] = (float)(o - (double)hi);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ BEM solve (FP64)
@@ -803,24 +851,6 @@ __device__ __forceinline__ void dot2_mac(float &s, float &c, float ah, float al,
   const float e = fmaf(ah, bh, -p);
   two_sum_acc(s, c, p);
   c = fmaf(al, bh, fmaf(ah, bl, c + e));
-}
-
-// vt (the side DFT of V r at the collocation points, as k_bem_vt) as hi and lo words.
-__global__ void k_bem_vt_f2(int n, int nrhs, const double *__restrict__ vcol, float *__restrict__ vh,
-                            float *__restrict__ vl) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nrhs * n) return;
-  const int64_t rr = t / n;
-  const int k = (int)(t % n);
-  const double *v = vcol + rr * 4 * n;
-  const double v0 = v[k], v1 = v[n + k], v2 = v[2 * n + k], v3 = v[3 * n + k];
-  const double o[4] = {(v0 + v2) + (v1 + v3), (v0 + v2) - (v1 + v3), v0 - v2, v1 - v3};
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float hi = (float)o[j];
-    vh[rr * 4 * n + j * n + k] = hi;
-    vl[rr * 4 * n + j * n + k] = (float)(o[j] - (double)hi);
-  }
 }
 
 // The BEM apply of k_bem_apply in two-word FP32 arithmetic: block per row m of
@@ -1570,8 +1600,10 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     mark(2);
     k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbb_first,
                                                               Ls.vbb_src, Mv, Lb, g.lnh);
-    k_colloc<R><<<nblk((int64_t)g.NG * nrhs * 32, 128), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
-                                                                   H.fb.vcol, H.fb.kcol);
+    const bool vt_f2 = H.Sinv_hi && H.fb.vt_hi;  // the side DFT for the two-word BEM apply, fused
+    k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
+                                                               H.fb.vcol, H.fb.kcol, vt_f2 ? H.fb.vt_hi : nullptr,
+                                                               vt_f2 ? H.fb.vt_lo : nullptr);
     FMMPC_LAUNCH_CHECK();
     launches += 2;
     if (part == PART_VCOL) {
@@ -1581,8 +1613,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(3);
-    if (H.Sinv_hi && H.fb.vt_hi) {
-      k_bem_vt_f2<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt_hi, H.fb.vt_lo);
+    if (H.Sinv_hi && H.fb.vt_hi) {  // vt_hi / vt_lo came with the collocation values
       if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
       else k_bem_apply_f2<1><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
     } else {
@@ -1590,7 +1621,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv, H.fb.vt, H.fb.q);
     }
     FMMPC_LAUNCH_CHECK();
-    launches += 2;
+    launches += (H.Sinv_hi && H.fb.vt_hi) ? 1 : 2;
     if (part == PART_Q) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.q, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
