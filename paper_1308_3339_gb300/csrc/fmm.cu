@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict_
                                                      cpx<R> *__restrict__ Mv, int *__restrict__ counter, int64_t ncount) {
   // three-level steps need 64 cells in shared memory; two-level steps where that would not fit
   constexpr int NBUF = sizeof(cpx<R>) * P * (4 * P + 128) <= 45000 ? 64 : 16, MAXSTEP = NBUF == 64 ? 3 : 2;
-  __shared__ cpx<R> sT[4 * P * P], buf[NBUF][P], part[NBUF][P];
+  // z^k of each node position in a leaf (the same for every leaf), where it fits
+  constexpr bool ZTAB = sizeof(cpx<R>) * MS * MS * P <= 16384;
+  constexpr int ZN = ZTAB ? MS * MS : 1;
+  __shared__ cpx<R> sT[4 * P * P], buf[NBUF][P], part[NBUF][P], zt[ZN][P];
   __shared__ int s_last;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rhs = blockIdx.y;
@@ -180,20 +183,41 @@ __global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict_
       const int pt = c + 16 * e;
       w[e] = pt < MS * MS ? W[(int64_t)(pt / MS) * g.npad + pt % MS] : R(0);
     }
+    if (ZTAB) {  // the same chain of products as below, so the same values
+      for (int pt = tid; pt < ZN; pt += nthr) {
+        const cpx<R> z = mk<R>((pt % MS - half) * invm, (pt / MS - half) * invm);
+        cpx<R> pw = z;
+        for (int k = 1; k < P; ++k) {
+          zt[pt][k] = pw;
+          pw = pw * z;
+        }
+      }
+      __syncthreads();
+    }
     cpx<R> acc[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = mk<R>(0, 0);
 #pragma unroll
     for (int e = 0; e < NP; ++e) {
       const int pt = c + 16 * e;
-      const cpx<R> z = mk<R>((pt % MS - half) * invm, (pt / MS - half) * invm);
-      cpx<R> pw = z;
       acc[0].re += w[e];
+      if (ZTAB) {
+        const int ptc = pt < ZN ? pt : 0;  // w[e] is 0 past the leaf
 #pragma unroll
-      for (int k = 1; k < P; ++k) {
-        acc[k].re = fma(w[e], pw.re, acc[k].re);
-        acc[k].im = fma(w[e], pw.im, acc[k].im);
-        pw = pw * z;
+        for (int k = 1; k < P; ++k) {
+          const cpx<R> zk = zt[ptc][k];
+          acc[k].re = fma(w[e], zk.re, acc[k].re);
+          acc[k].im = fma(w[e], zk.im, acc[k].im);
+        }
+      } else {
+        const cpx<R> z = mk<R>((pt % MS - half) * invm, (pt / MS - half) * invm);
+        cpx<R> pw = z;
+#pragma unroll
+        for (int k = 1; k < P; ++k) {
+          acc[k].re = fma(w[e], pw.re, acc[k].re);
+          acc[k].im = fma(w[e], pw.im, acc[k].im);
+          pw = pw * z;
+        }
       }
     }
 #pragma unroll
