@@ -16,10 +16,11 @@
 // with (dx, dy) = floor((c - o) / 2): the same target position in all four classes reads
 // the same source row for a shift (source parity, dx, dy), each class through its own
 // offset.  So one CTA takes 128 consecutive flattened target positions (M = 128) of all
-// four classes and sweeps the 124 shifts, D[t][32 c + u] += sum_v X[t + dy P + dx][v] B_s[32 c + u][v],
-// with the four classes' matrices stacked along N = 128 (zero rows where a class has no
-// offset for the shift), K = the multipole inputs.  Per class the 32 outputs are the 2p
-// real parts of L~ and, in outputs 30 and 31, the two sums of M~_0 that carry ln rho.
+// four classes and sweeps the 124 shifts, D[t][W c + u] += sum_v X[t + dy P + dx][v] B_s[W c + u][v],
+// with the four classes' matrices stacked along N = 4 W (zero rows where a class has no
+// offset for the shift), K = the multipole inputs.  Per class the W outputs (W = 24 for
+// p <= 11, else 32) are the 2p real parts of L~ and, in outputs W - 2 and W - 1, the two
+// sums of M~_0 that carry ln rho.
 // Padding targets are computed and dropped.  The low-order terms dominate the translated
 // field and meet the large log o + ln rho, so their products are split hi + lo in the
 // spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded
@@ -448,7 +449,7 @@ float tf32_round_host_m2l(double v) {
 }  // namespace
 
 bool tc_m2l_eligible(const fmmpc_handle &H) {
-  // N = 32 outputs hold 2p + 2; K (32 TF32 or BF16 inputs per 128-byte row) holds 2p
+  // W <= 32 outputs per class hold 2p + 2; K (32 TF32 or BF16 inputs per 128-byte row) holds 2p
   return (H.prec == FMMPC_PREC_MIXED_BF16 || H.prec == FMMPC_PREC_MIXED_TF32) && H.g.L >= 2 && 2 * H.g.p + 2 <= 32;
 }
 
