@@ -65,7 +65,8 @@ typedef struct {
   double x0, y0, x1, y1;
 } fmmpc_grid;
 
-/* p: expansion order, coefficients n = 0..p-1 (Sec. 5.3), 2 <= p <= 20.
+/* p: expansion order, coefficients n = 0..p-1 (Sec. 5.3); p must be one of 4, 6, 8, 10, 12, 16
+ *   (the kernels are compiled for these orders; any other value is rejected with _INVALID).
  * leaf_max: the tree splits a cell at its centre lines while it holds more than leaf_max
  *   nodes (Sec. 5.1); the grid must stay divisible down to the leaf (nx = m 2^L) and the
  *   leaf side m must be 4, 8 or 16.
@@ -220,13 +221,17 @@ int fmmpc_get_timing(fmmpc_handle *h, float *ms, int32_t cap, int32_t *count);
  * n = 1024 with 8x8 leaves and theta = 0.4 is the largest grid that fits.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls
+ * with that device current, and so does the first call after the device's context was made
+ * anew (cudaDeviceReset reloads the module); make those calls before any stream capture.
+ * All calls
  * share the one array and it keeps the last call's contents; each call rewrites the table
  * and the whole padded image, so nothing stale is read.  Calls that overlap on the GPU
  * (on different streams, or from several host threads) race on the array and must be
  * serialised by the caller.  No cudaMalloc, cudaFree or allocating library routine is
- * called.  Errors: _INVALID (arguments, size), _UNSUPPORTED (theta), _CUDA; message via
- * fmmpc_last_error(NULL).  The paper has no counterpart of this entry point. */
+ * called; the kernel's shared-memory limit is raised when this call needs more, never
+ * lowered.  Errors: _INVALID (arguments, size), _UNSUPPORTED (theta so small that the stencil
+ * radius passes 15 leaves, or a source tile beyond one block's shared memory; both found
+ * before any GPU work is queued), _CUDA; message via fmmpc_last_error(NULL).  The paper has no counterpart of this entry point. */
 int fmmpc_near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta,
                              const double *r_dev, double *out_dev, void *stream);
 

@@ -3,29 +3,43 @@
 FmmSolve.apply(f, P, opts) runs the FMM-preconditioned Krylov solve of the 5-point system
 (fmmpc_solve).  Its backward is the adjoint solve A^{-T} g; the 5-point matrix with zero
 Dirichlet values is symmetric, so that is the same preconditioned solve applied to the
-incoming gradient.  Both passes run entirely in libfmmpc.
+incoming gradient.  Both passes run entirely in libfmmpc.  A solve of either pass that stops
+at maxit above rtol (or meets a NaN) raises FmmpcError with its status and residual, so a
+gradient is never returned from an unconverged adjoint solve.
 """
 from __future__ import annotations
 
 import torch
+
+from ._lib import FmmpcError
 
 __all__ = ["FmmSolve", "fmm_solve"]
 
 _DEFAULTS = dict(method="fgmres", restart=30, maxit=200, rtol=1e-10, use_graphs=1)
 
 
+def _checked_solve(P, rhs, opts, what):
+    u, info = P.solve(rhs, raise_on_fail=False, **opts)
+    if info["status"] != 0:
+        raise FmmpcError(info["status"], f"{what} solve did not converge: {info['iters']} iterations, "
+                                         f"relative residual {info['rel_res']:.3e} > rtol {opts['rtol']:.1e}")
+    return u, info
+
+
 class FmmSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, P, opts):
         o = dict(_DEFAULTS, **(opts or {}))
-        u, info = P.solve(f.detach().contiguous(), **o)
+        o.pop("raise_on_fail", None)
+        u, info = _checked_solve(P, f.detach().contiguous(), o, "forward")
         ctx.P, ctx.opts = P, o
         ctx.info = info
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
-        g, info = ctx.P.solve(grad_u.detach().contiguous(), **ctx.opts)
+        g, info = _checked_solve(ctx.P, grad_u.detach().contiguous(), ctx.opts, "adjoint")
+        ctx.info_backward = info
         return g, None, None
 
 

@@ -1993,32 +1993,74 @@ static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
 
 namespace {
 
-// Device address of g_noalloc_scratch for the current device, resolved once per device.
+// Identity of the current CUDA context (unique for the life of the process), through the
+// driver's cuCtxGetId reached via the runtime's entry-point query; 0 if unavailable.
+unsigned long long current_ctx_id() {
+  using ctx_id_fn = int (*)(void *, unsigned long long *);
+  static ctx_id_fn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<ctx_id_fn>(f);
+  }();
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_noalloc_scratch, resolved once per device and context: a context
+// made anew (after cudaDeviceReset) reloads the module, and the array may then sit at a
+// different address, so the cached address is taken again when the context id changes.
 cudaError_t noalloc_scratch(float **out) {
   static std::mutex mu;
   static float *ptr[NOALLOC_MAX_DEVICES] = {};
+  static unsigned long long ctx[NOALLOC_MAX_DEVICES] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
-  if (!ptr[dev]) {
+  const unsigned long long id = current_ctx_id();  // 0: no current context yet, or no query
+  if (!ptr[dev] || id == 0 || id != ctx[dev]) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the primary context current if needed
     if (e != cudaSuccess) return e;
     ptr[dev] = static_cast<float *>(p);
+    ctx[dev] = id ? id : current_ctx_id();
   }
   *out = ptr[dev];
   return cudaSuccess;
 }
 
+// Dynamic shared memory the near-field kernel of leaf side M may take on this device (the
+// per-block opt-in maximum minus its static use).
 template <int M>
-cudaError_t noalloc_launch(const P2PArgs<float> &a, int L, cudaStream_t s) {
+cudaError_t noalloc_smem_cap(size_t *cap) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_p2p<float, M>);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  *cap = (size_t)optin - fa.sharedSizeBytes;
+  return cudaSuccess;
+}
+
+// The attribute is per function and shared with the handle-based near field, so it is only
+// ever raised, never set below what another caller configured.
+template <int M>
+cudaError_t noalloc_launch(const P2PArgs<float> &a, int L, size_t smem, cudaStream_t s) {
   const int side = 1 << L;
   dim3 grid(side / a.tile_x, side / a.tile_y, 1);
-  const size_t smem = ((size_t)a.HY * a.HX + (size_t)(a.Rn + 1) * a.TS) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_p2p<float, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_p2p<float, M>);
   if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes < smem) {
+    e = cudaFuncSetAttribute(k_p2p<float, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   k_p2p<float, M><<<grid, a.tile_x * a.tile_y * M, smem, s>>>(a);
   return cudaPeekAtLastError();
 }
@@ -2063,8 +2105,19 @@ int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, c
   const int64_t need = tab_floats + (int64_t)npad * npad;
   if (need > NOALLOC_FLOATS)
     return set_global_error(FMMPC_ERR_INVALID, "near_field_noalloc: grid too large for the 16 MiB static scratch (n = 1024 with 8x8 leaves and theta 0.4 is the largest such grid)");
+  const int sidel = 1 << L;
+  int tx = (m == 16) ? 4 : 8, ty = (m == 4) ? 8 : 4;
+  tx = std::min(tx, sidel);
+  ty = std::min(ty, sidel);
+  const int HX = (tx + 2 * R) * m, HY = (ty + 2 * R) * m;
+  const size_t smem = ((size_t)HY * HX + (size_t)(Rn + 1) * TS) * sizeof(float);
+  size_t cap = 0;
+  cudaError_t e = (m == 4) ? noalloc_smem_cap<4>(&cap) : (m == 8) ? noalloc_smem_cap<8>(&cap) : noalloc_smem_cap<16>(&cap);
+  if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
+  if (smem > cap)  // checked before any work is queued
+    return set_global_error(FMMPC_ERR_UNSUPPORTED, "near_field_noalloc: the source tile of this theta and leaf size does not fit in one block's shared memory");
   float *scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
   cudaStream_t s = (cudaStream_t)stream;
   const double h = side / (n + 1);
@@ -2073,20 +2126,16 @@ int near_field_noalloc(int32_t n, double side, int32_t leaf_max, double theta, c
   k_noalloc_image<<<(unsigned)(((int64_t)npad * npad + 255) / 256), 256, 0, s>>>(img, n, npad, pad, h * h, r_dev);
   e = cudaPeekAtLastError();
   if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
-  const int sidel = 1 << L;
-  int tx = (m == 16) ? 4 : 8, ty = (m == 4) ? 8 : 4;
-  tx = std::min(tx, sidel);
-  ty = std::min(ty, sidel);
   P2PArgs<float> a{};
   a.wpad = img; a.table = tab; a.out = out_dev;
   a.n = n; a.npad = npad; a.L = L; a.R_ = R; a.Rn = Rn;
-  a.HX = (tx + 2 * R) * m; a.HY = (ty + 2 * R) * m; a.TS = TS; a.c0 = c0;
+  a.HX = HX; a.HY = HY; a.TS = TS; a.c0 = c0;
   a.tile_x = tx; a.tile_y = ty; a.nrhs = 1;
   a.st = st;
   switch (m) {
-    case 4: e = noalloc_launch<4>(a, L, s); break;
-    case 8: e = noalloc_launch<8>(a, L, s); break;
-    default: e = noalloc_launch<16>(a, L, s); break;
+    case 4: e = noalloc_launch<4>(a, L, smem, s); break;
+    case 8: e = noalloc_launch<8>(a, L, smem, s); break;
+    default: e = noalloc_launch<16>(a, L, smem, s); break;
   }
   if (e != cudaSuccess) return set_global_error(FMMPC_ERR_CUDA, cudaGetErrorString(e));
   return FMMPC_OK;
