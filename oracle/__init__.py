@@ -70,6 +70,8 @@ def _lib():
     L.orc_seg_int_dlog.restype = d
     L.orc_elements.argtypes = [i, d, d, d] + [vp] * 6
     L.orc_bem_matrices.argtypes = [i, d, d, d, vp, vp]
+    L.orc_bem_rows.argtypes = [i, d, d, d, i, vp, vp, vp]
+    L.orc_layers_at.argtypes = [i, d, d, d, vp, vp, i, vp, vp, vp, vp]
     L.orc_lu.argtypes = [i, vp, vp]
     L.orc_lu.restype = i
     L.orc_lu_solve.argtypes = [i, vp, vp, vp]
@@ -210,6 +212,26 @@ def bem_matrices(n, x0, y0, side):
     S = np.empty((NG, NG)); K = np.empty((NG, NG))
     _lib().orc_bem_matrices(n, x0, y0, side, _p(S), _p(K))
     return S, K
+
+
+def bem_rows(n, x0, y0, side, rows):
+    """Rows of the single- and double-layer matrices (Sec. 4.3) at collocation indices rows."""
+    rows = np.ascontiguousarray(rows, np.int32)
+    NG = 4 * n
+    S = np.empty((rows.size, NG)); K = np.empty((rows.size, NG))
+    _lib().orc_bem_rows(n, x0, y0, side, rows.size, _p(rows), _p(S), _p(K))
+    return S, K
+
+
+def layers_at(n, x0, y0, side, tx, ty, q=None, mu=None):
+    """Single-layer (density q) and double-layer (density mu) potentials of constant
+    elements at targets (tx, ty) off the boundary: the boundary terms of Eq. e:uinter."""
+    tx = np.ascontiguousarray(tx, np.float64); ty = np.ascontiguousarray(ty, np.float64)
+    qq = None if q is None else np.ascontiguousarray(q, np.float64)
+    mm = None if mu is None else np.ascontiguousarray(mu, np.float64)
+    sl, dl = np.zeros(tx.size), np.zeros(tx.size)
+    _lib().orc_layers_at(n, x0, y0, side, _p(qq), _p(mm), tx.size, _p(tx), _p(ty), _p(sl), _p(dl))
+    return sl, dl
 
 
 # ---------------------------------------------------------------- tree (Sec. 5.1)

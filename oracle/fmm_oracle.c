@@ -337,6 +337,50 @@ void orc_bem_matrices(int n, double x0, double y0, double side, double *S, doubl
   free(ax);
 }
 
+/* Selected rows of the two matrices of orc_bem_matrices: S[r][k] and K[r][k] for the
+ * collocation indices rows[0..nr), each row N_G long (NULL skips a matrix).  Used to check
+ * the boundary system S q = -(V r)|_Gamma of Eq. e:ubound at sampled collocation points of
+ * grids whose full N_G x N_G matrices are too large to form. */
+void orc_bem_rows(int n, double x0, double y0, double side, int nr, const int32_t *rows, double *S,
+                  double *K) {
+  const int NG = 4 * n;
+  double *ax = malloc(sizeof(double) * NG * 6);
+  double *ay = ax + NG, *bx = ay + NG, *by = bx + NG, *cx = by + NG, *cy = cx + NG;
+  orc_elements(n, x0, y0, side, ax, ay, bx, by, cx, cy);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < nr; ++t) {
+    const int m = rows[t];
+    for (int k = 0; k < NG; ++k) {
+      if (S) S[(int64_t)t * NG + k] = -orc_seg_int_log(cx[m], cy[m], ax[k], ay[k], bx[k], by[k]) / (2.0 * PI_);
+      if (K) K[(int64_t)t * NG + k] = -orc_seg_int_dlog(cx[m], cy[m], ax[k], ay[k], bx[k], by[k]) / (2.0 * PI_);
+    }
+  }
+  free(ax);
+}
+
+/* Boundary-layer potentials of constant-element densities at targets off the boundary
+ * (the two boundary integrals of Eq. e:uinter): sl[t] = sum_k q_k int_{Gamma_k} G(x_t, y)
+ * dGamma_y and dl[t] = sum_k mu_k int_{Gamma_k} dG/dn_y(x_t, y) dGamma_y, with
+ * G = -(1/2pi) ln|x - y|; q or mu NULL skips that sum. */
+void orc_layers_at(int n, double x0, double y0, double side, const double *q, const double *mu, int nt,
+                   const double *tx, const double *ty, double *sl, double *dl) {
+  const int NG = 4 * n;
+  double *ax = malloc(sizeof(double) * NG * 6);
+  double *ay = ax + NG, *bx = ay + NG, *by = bx + NG, *cx = by + NG, *cy = cx + NG;
+  orc_elements(n, x0, y0, side, ax, ay, bx, by, cx, cy);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < nt; ++t) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < NG; ++k) {
+      if (q) a += q[k] * orc_seg_int_log(tx[t], ty[t], ax[k], ay[k], bx[k], by[k]);
+      if (mu) b += mu[k] * orc_seg_int_dlog(tx[t], ty[t], ax[k], ay[k], bx[k], by[k]);
+    }
+    if (sl) sl[t] = -a / (2.0 * PI_);
+    if (dl) dl[t] = -b / (2.0 * PI_);
+  }
+  free(ax);
+}
+
 /* Dense LU with partial pivoting (Doolittle), in place; piv[i] = row swapped with i.
  * Returns 0, or 1 if a pivot is exactly zero. */
 int orc_lu(int N, double *A, int32_t *piv) {

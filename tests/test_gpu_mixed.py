@@ -5,22 +5,25 @@ Error bars.  Rounding both operands of an M2L product to TF32 (unit roundoff 2^-
 BF16 (2^-9) perturbs it by about sqrt(2) u.  The leading multipoles and their translation
 columns are split hi + lo in the spare K columns (M~_0..2 for TF32, M~_0..6 for BF16), so
 only the small high-order terms carry u; the far field is a fraction of z, and the error
-of z stays below u.  The gates are u itself: 5e-4 for TF32 and 2e-3 for BF16 (the BF16 bar
-against the direct sum).  Measured at 1024^2: 2.5e-6 (TF32) and 4.6e-5 (BF16).  The Krylov
-recurrences stay FP64, so a solve still reaches its relative residual and the oracle's
-solution.
+of z stays well below u.  The contract bars are 1e-5 (TF32, the FP32 gate) and 2e-3 (BF16
+against the direct sum); the gates below sit at about ten times the errors measured on
+GB300 (relative L2 and worst node, max|a - b| / max|b|), so a regression of the hi + lo
+splitting or of one class's translation block fails them long before the contract bar.
+The Krylov recurrences stay FP64, so a solve still reaches its relative residual and the
+oracle's solution.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import synth_inputs as S
-from conftest import rel_l2
+from conftest import check_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"mixed_tf32": 5e-4, "mixed_bf16": 2e-3}
+# (relative L2, worst node) gates of z against the FP64 FMM and the direct sum
+TOL = {"mixed_tf32": (3e-5, 3e-5), "mixed_bf16": (5e-4, 5e-4)}
 KIND = {"mixed_tf32": 1, "mixed_bf16": 2}
 
 
@@ -53,7 +56,7 @@ def test_mixed_apply_matches_fp64_fmm(prec, n):
     z = host(P.apply(dev(r)))
     assert P.query("device_errors") == 0
     ref = O.Problem(n, p=10).apply(r, "fmm", stages=True)["z"]
-    assert rel_l2(z, ref) < TOL[prec]
+    check_close(f"{prec} z n={n} vs oracle fmm", z, ref, *TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
@@ -63,7 +66,7 @@ def test_mixed_apply_matches_direct_sum(prec):
     P = gpu(n, p=10, precision=prec)
     z = host(P.apply(dev(r)))
     ref = O.Problem(n, p=10).apply(r, "direct")
-    assert rel_l2(z, ref) < TOL[prec]
+    check_close(f"{prec} z n=128 vs oracle direct", z, ref, *TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
@@ -73,8 +76,8 @@ def test_mixed_tensor_core_m2l_is_close_to_fp32_m2l(prec):
     r = dev(S.random_field(n, 8))
     z = host(gpu(n, p=10, precision=prec).apply(r))
     z32 = host(gpu(n, p=10, precision="fp32").apply(r))
-    assert rel_l2(z, z32) < TOL[prec]
-    assert rel_l2(z, z32) > 0  # the tensor-core path did run
+    e2, _ = check_close(f"{prec} z vs fp32 z n=512", z, z32, *TOL[prec])
+    assert e2 > 0  # the tensor-core path did run
 
 
 def test_mixed_multi_rhs_equals_single_rhs():
@@ -83,7 +86,7 @@ def test_mixed_multi_rhs_equals_single_rhs():
     P = gpu(n, p=10, n_rhs=k, precision="mixed_bf16")
     zb = host(P.apply(dev(rs)))
     for i in range(k):
-        assert rel_l2(zb[i], host(P.apply(dev(rs[i])))) < 1e-6
+        check_close(f"bf16 multi-rhs z[{i}] vs single", zb[i], host(P.apply(dev(rs[i]))), 1e-6, 1e-6)
     assert P.query("device_errors") == 0
 
 
@@ -98,17 +101,34 @@ def test_mixed_fgmres_matches_oracle_solve(prec):
     _, it_o, _, _ = O.Problem(n, p=8).solve(f, "fgmres", 30, 100, 1e-8, "fmm")
     assert info["status"] == 0 and info["rel_res"] <= 1e-8
     assert abs(info["iters"] - it_o) <= 1
-    assert rel_l2(host(x), (2 * np.pi ** 2 / lam) * u) < 1e-7
+    check_close(f"{prec} fgmres solution vs closed form n=64", host(x), (2 * np.pi ** 2 / lam) * u, 1e-7, 1e-7)
 
 
-def test_mixed_bf16_solve_1024_matches_oracle_solution():
-    # 1e-10 on both sides: at 1024^2 (condition number ~4e5) a relative residual of 1e-12 is
-    # at the FP64 floor of b - A u whatever the preconditioner
+@pytest.fixture(scope="module")
+def oracle_1024_solve():
+    """The oracle's FGMRES(30) solve of the 1024^2 Gaussian-mixture problem at 1e-10 and at
+    1e-8 (iteration counts of both), FP64 FMM preconditioner."""
     n = 1024
     f = S.gaussian_mixture(n, 0)
-    P = gpu(n, p=10, precision="mixed_bf16")
+    R = O.Problem(n, p=10)
+    xo, it10, _, _ = R.solve(f, "fgmres", 30, 200, 1e-10, "fmm")
+    _, it8, _, _ = R.solve(f, "fgmres", 30, 200, 1e-8, "fmm")
+    return f, xo, it10, it8
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_mixed_solve_1024_matches_oracle_solution(prec, oracle_1024_solve):
+    # 1e-10 on both sides: at 1024^2 (condition number ~4e5) a relative residual of 1e-12 is
+    # at the FP64 floor of b - A u whatever the preconditioner.  Iterations within +-1 of the
+    # oracle's at 1e-10 and at the headline 1e-8.
+    n = 1024
+    f, xo, it10, it8 = oracle_1024_solve
+    P = gpu(n, p=10, precision=prec)
     x, info = P.solve(dev(f), rtol=1e-10)
-    xo, it_o, _, _ = O.Problem(n, p=10).solve(f, "fgmres", 30, 200, 1e-10, "fmm")
     assert info["status"] == 0
-    assert abs(info["iters"] - it_o) <= 2
-    assert rel_l2(host(x), xo) < 1e-8
+    print(f"ITERS {prec} n=1024 rtol=1e-10: gpu {info['iters']} oracle {it10}", flush=True)
+    assert abs(info["iters"] - it10) <= 1
+    check_close(f"{prec} fgmres solution n=1024 vs oracle", host(x), xo, 1e-8, 1e-8)
+    _, info8 = P.solve(dev(f), rtol=1e-8)
+    print(f"ITERS {prec} n=1024 rtol=1e-8: gpu {info8['iters']} oracle {it8}", flush=True)
+    assert info8["status"] == 0 and abs(info8["iters"] - it8) <= 1

@@ -4,13 +4,15 @@ Bars: integer work (Morton keys, permutation, cell ranges, interaction lists) bi
 FP64 FMM within 1e-11 of the oracle FMM (same lists and p, different rounding order);
 FP32 FMM within 1e-5 relative L2 (single-precision near field with Kahan partial sums
 over ~2400 terms and FP32 expansions give ~1e-7..1e-6; 1e-5 is the FP32 accuracy gate).
+Every floating-point comparison also bounds the worst node, max|a - b| / max|b| (max_rel),
+at the same bar: a slip confined to the boundary band or one leaf shows there first.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import synth_inputs as S
-from conftest import rel_l2
+from conftest import check_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,7 +41,8 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,leaf_max", [(8, 64), (16, 64), (64, 64), (64, 16), (128, 256), (256, 64)])
+@pytest.mark.parametrize("n,leaf_max", [(8, 64), (16, 64), (64, 64), (64, 16), (128, 256), (256, 64),
+                                        (1024, 64), (512, 16), (1024, 256)])
 def test_tree_and_lists_bit_exact(n, leaf_max):
     P = gpu(n, p=8, leaf_max=leaf_max)
     R = O.Problem(n, p=8, leaf_max=leaf_max)
@@ -60,11 +63,13 @@ def test_apply_stages_match_oracle(prec, tol, n, leaf_max, p):
     P = gpu(n, p=p, leaf_max=leaf_max, precision=prec)
     ref = O.Problem(n, p=p, leaf_max=leaf_max).apply(r, "fmm", stages=True)
     rd = dev(r)
-    assert rel_l2(host(P.apply_part("near", rd)), ref["near"]) < tol
-    assert rel_l2(host(P.apply_part("vr", rd)), ref["vr"]) < tol
-    assert rel_l2(host(P.apply_part("vcol", rd))[0], ref["vr_col"]) < tol
-    assert rel_l2(host(P.apply_part("q", rd))[0], ref["q"]) < 10 * tol
-    assert rel_l2(host(P.apply(rd)), ref["z"]) < tol
+    tag = f"{prec} n={n} leaf={leaf_max} p={p}"
+    check_close(f"near {tag}", host(P.apply_part("near", rd)), ref["near"], tol, tol)
+    check_close(f"vr {tag}", host(P.apply_part("vr", rd)), ref["vr"], tol, tol)
+    check_close(f"vcol {tag}", host(P.apply_part("vcol", rd))[0], ref["vr_col"], tol, tol)
+    # q = S^{-1}(-(V r)|_Gamma): the first-kind BEM system amplifies the collocation error
+    check_close(f"q {tag}", host(P.apply_part("q", rd))[0], ref["q"], 10 * tol, 10 * tol)
+    check_close(f"z {tag}", host(P.apply(rd)), ref["z"], tol, tol)
 
 
 def test_fp32_volume_fmm_vs_direct_sum():
@@ -73,7 +78,7 @@ def test_fp32_volume_fmm_vs_direct_sum():
     r = S.gaussian_mixture(n, 4)
     P = gpu(n, p=10)
     vr = host(P.apply_part("vr", dev(r)))
-    assert rel_l2(vr, O.direct_V(n, 0, 0, 1, r)) < 1e-5
+    check_close("vr fp32 vs direct n=128", vr, O.direct_V(n, 0, 0, 1, r), 1e-5, 1e-5)
 
 
 def test_multi_rhs_equals_single_rhs():
@@ -83,7 +88,7 @@ def test_multi_rhs_equals_single_rhs():
     zb = host(P.apply(dev(rs)))
     for i in range(k):
         zi = host(P.apply(dev(rs[i])))
-        assert rel_l2(zb[i], zi) < 1e-6
+        check_close(f"multi-rhs z[{i}] vs single", zb[i], zi, 1e-6, 1e-6)
 
 
 def test_tensor_core_near_field_multi_rhs_matches_single_rhs():
@@ -110,7 +115,7 @@ def test_spmv_matches_oracle():
     n = 64
     x = S.random_field(n, 5)
     P = gpu(n, p=8)
-    assert rel_l2(host(P.spmv(dev(x))), O.spmv5(n, 1 / 65, x)) < 1e-14
+    check_close("spmv5", host(P.spmv(dev(x))), O.spmv5(n, 1 / 65, x), 1e-14, 1e-14)
 
 
 def test_apply_host_matches_device():
@@ -134,7 +139,7 @@ def test_solve_matches_oracle_and_closed_form(method, prec):
     _, it_o, rr_o, conv_o = O.Problem(n, p=8).solve(f, method, 30, 100, 1e-8, "fmm")
     assert info["status"] == 0 and info["rel_res"] <= 1e-8
     assert abs(info["iters"] - it_o) <= 1
-    assert rel_l2(host(x), uh) < 1e-8 * 10
+    check_close(f"{method} {prec} solution vs closed form", host(x), uh, 1e-7, 1e-7)
 
 
 def test_solve_gaussian_mixture_fp64_vs_oracle():
@@ -145,7 +150,7 @@ def test_solve_gaussian_mixture_fp64_vs_oracle():
     R = O.Problem(n, p=10)
     xo, it_o, rr_o, _ = R.solve(f, "fgmres", 30, 200, 1e-13, "fmm")
     assert info["status"] == 0
-    assert rel_l2(host(x), xo) < 1e-9
+    check_close("fp64 fgmres solution vs oracle n=128", host(x), xo, 1e-9, 1e-9)
 
 
 def test_inhomogeneous_dirichlet_quadratic_is_exact():
@@ -155,7 +160,7 @@ def test_inhomogeneous_dirichlet_quadratic_is_exact():
     g = S.boundary_values(n, lambda x, y: x * x + y * y, -1.0, -1.0, 2.0)
     P = gpu(n, p=10, x0=-1.0, y0=-1.0, side=2.0)
     x, info = P.solve(dev(-4.0 * np.ones(n * n)), g=dev(g), rtol=1e-12, maxit=100)
-    assert rel_l2(host(x), X ** 2 + Y ** 2) < 1e-10
+    check_close("x^2+y^2 inhomogeneous", host(x), X ** 2 + Y ** 2, 1e-10, 1e-10)
 
 
 def test_not_converged_status_and_error_codes():
@@ -176,10 +181,10 @@ def test_full_size_1024_apply_matches_oracle_and_direct_sum():
     rd = dev(r)
     z = host(P.apply(rd))
     zo = O.Problem(n, p=10).apply(r, "fmm")
-    assert rel_l2(z, zo) < 1e-5
+    check_close("z fp32 n=1024 vs oracle fmm", z, zo, 1e-5, 1e-5)
     idx = np.random.default_rng(0).choice(n * n, 192, replace=False).astype(np.int32)
     vr = host(P.apply_part("vr", rd))[idx]
-    assert rel_l2(vr, O.direct_V_nodes(n, 0.0, 0.0, 1.0, r, idx)) < 1e-5
+    check_close("vr fp32 n=1024 vs direct (192 nodes)", vr, O.direct_V_nodes(n, 0.0, 0.0, 1.0, r, idx), 1e-5, 1e-5)
 
 
 def test_graph_replay_matches_direct_launches():
@@ -212,6 +217,6 @@ def test_tensor_core_near_field_matches_oracle(seed, kind):
     # hi*hi MMAs, so the tensor core's truncating adds cost ~4 * 2^-24 of a group's partial;
     # the 74 partials per tile are summed in FP32 with Kahan compensation, and the TF32
     # splits leave ~2^-22 per product: ~1e-7 in all, bounded here by 1e-6.
-    assert rel_l2(near_tc, ref["near"]) < 1e-6
-    assert rel_l2(z_tc, ref["z"]) < FP32_TOL
-    assert rel_l2(z_tc, z_simt) < 1e-6
+    check_close(f"tc near n=1024 {kind}", near_tc, ref["near"], 1e-6, 1e-6)
+    check_close(f"tc z n=1024 {kind}", z_tc, ref["z"], FP32_TOL, FP32_TOL)
+    check_close(f"tc z vs simt z n=1024 {kind}", z_tc, z_simt, 1e-6, 1e-6)

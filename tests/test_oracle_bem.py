@@ -145,3 +145,77 @@ def test_fmm_and_direct_preconditioners_give_same_iterations():
     _, it1, rr1, c1 = P.solve(f, "fgmres", rtol=1e-8, prec="fmm")
     _, it2, rr2, c2 = P.solve(f, "fgmres", rtol=1e-8, prec="direct")
     assert c1 and c2 and abs(it1 - it2) <= 1
+
+
+def _element_quadrature(n, x0, y0, side, tx, ty, dens, kind, k=48):
+    """sum_k dens_k int_{Gamma_k} K(x_t, y) dGamma by Gauss-Legendre on every element, in
+    numpy (no oracle code): kind 'sl' K = G = -(1/2pi) ln r, kind 'dl' K = dG/dn_y."""
+    ax, ay, bx, by, _, _ = O.elements(n, x0, y0, side)
+    t, w = np.polynomial.legendre.leggauss(k)
+    out = np.zeros(len(tx))
+    for e in range(4 * n):
+        a, b = np.array([ax[e], ay[e]]), np.array([bx[e], by[e]])
+        L = np.linalg.norm(b - a)
+        tan = (b - a) / L
+        nrm = np.array([tan[1], -tan[0]])
+        pts = a[None, :] + (t[:, None] + 1) / 2 * (b - a)[None, :]
+        d = np.stack([tx, ty], 1)[:, None, :] - pts[None, :, :]
+        r2 = np.sum(d * d, axis=2)
+        val = -0.5 * np.log(r2) / (2 * np.pi) if kind == "sl" else (d @ nrm) / r2 / (2 * np.pi)
+        out += dens[e] * L / 2 * (val @ w)
+    return out
+
+
+def test_bem_rows_match_quadrature_and_gauss_identity():
+    # rows of S and K at sampled collocation points (the sampled-row check of the boundary
+    # system at grids too large for the full matrices): entries of elements at least two
+    # away from the collocation point against Gauss-Legendre quadrature; every row of K
+    # sums to -1/2 (Gauss's identity for a point on a smooth part of Gamma)
+    n, x0, y0, side = 16, -1.0, -1.0, 2.0
+    rows = np.array([0, 5, 17, 40, 63], np.int32)
+    Sr, Kr = O.bem_rows(n, x0, y0, side, rows)
+    _, _, _, _, cx, cy = O.elements(n, x0, y0, side)
+    for i, m in enumerate(rows):
+        for k in range(4 * n):
+            if min(abs(k - m), 4 * n - abs(k - m)) < 2:
+                continue
+            e = np.zeros(4 * n)
+            e[k] = 1.0
+            s_ref = _element_quadrature(n, x0, y0, side, cx[m:m + 1], cy[m:m + 1], e, "sl")[0]
+            assert abs(Sr[i, k] - s_ref) < 1e-10
+        assert abs(Kr[i].sum() + 0.5) < 1e-12
+
+
+def test_layer_potentials_at_interior_points():
+    # single and double layer at interior targets against element-wise quadrature; the
+    # double layer of a unit density is -1 inside (Gauss's identity)
+    n, x0, y0, side = 8, 0.0, 0.0, 1.0
+    rng = np.random.default_rng(3)
+    tx, ty = rng.uniform(0.15, 0.85, 20), rng.uniform(0.15, 0.85, 20)
+    q, mu = rng.standard_normal(4 * n), rng.standard_normal(4 * n)
+    sl, dl = O.layers_at(n, x0, y0, side, tx, ty, q=q, mu=mu)
+    assert np.max(np.abs(sl - _element_quadrature(n, x0, y0, side, tx, ty, q, "sl"))) < 1e-12
+    assert np.max(np.abs(dl - _element_quadrature(n, x0, y0, side, tx, ty, mu, "dl"))) < 1e-12
+    _, one = O.layers_at(n, x0, y0, side, tx, ty, mu=np.ones(4 * n))
+    assert np.max(np.abs(one + 1.0)) < 1e-12
+
+
+def test_green_representation_of_a_harmonic_function():
+    # Eq. e:uinter with f = 0: u(x) = int_Gamma du/dn G - int_Gamma u dG/dn for harmonic u.
+    # Constant elements at midpoint values are first-order accurate: the error falls ~2x
+    # per halving of the element length.
+    x0, y0, side = -1.0, -1.0, 2.0
+    u = lambda x, y: 2 * (1 + y) / ((3 + x) ** 2 + (1 + y) ** 2)  # Table t:p2's solution
+    def dudn(x, y, nx, ny, e=1e-6):
+        return ((u(x + e * nx, y + e * ny) - u(x - e * nx, y - e * ny)) / (2 * e))
+    tx, ty = np.array([0.1, -0.4, 0.5]), np.array([0.2, 0.3, -0.5])
+    errs = []
+    for n in (16, 32, 64):
+        ax, ay, bx, by, cx, cy = O.elements(n, x0, y0, side)
+        tl = np.stack([bx - ax, by - ay], 1)
+        tl /= np.linalg.norm(tl, axis=1)[:, None]
+        q = dudn(cx, cy, tl[:, 1], -tl[:, 0])
+        sl, dl = O.layers_at(n, x0, y0, side, tx, ty, q=q, mu=u(cx, cy))
+        errs.append(np.max(np.abs(sl - dl - u(tx, ty))))
+    assert errs[-1] < 2e-3
+    assert errs[0] / errs[1] > 1.6 and errs[1] / errs[2] > 1.6
