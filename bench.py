@@ -54,7 +54,11 @@ def parse():
                     help="FMM form of the headline apply (FP64 Krylov in every form)")
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    return ap.parse_args()
+    ap.add_argument("--configs", default="c1,c3,c4,c5",
+                    help="further workloads timed after the headline (comma list of c1,c3,c4,c5; '' for none)")
+    a = ap.parse_args()
+    a.configs = [c for c in a.configs.split(",") if c]
+    return a
 
 
 def workload(args):
@@ -218,14 +222,14 @@ def load_peaks():
         return None
 
 
-def rooflines(P, stage_ms):
+def rooflines(P, stage_ms, nrhs=1):
     """Roofline of the P2P (tensor cores) and M2L (FP32 CUDA cores) kernels from their
     live CUDA-event times; the dominant one (larger time) is reported as `roofline`."""
     m = P.query("leaf_side")
     pk = load_peaks()
     out = {}
     # P2P: one FMA (2 flops) per source-target pair of the near-field lists
-    pairs = P.query("n_p2p") * m ** 4
+    pairs = P.query("n_p2p") * m ** 4 * nrhs
     t = stage_ms["p2p"]
     if P.query("tc_p2p"):
         if pk:
@@ -248,7 +252,7 @@ def rooflines(P, stage_ms):
     t = stage_ms["m2l"]
     tcm = P.query("tc_m2l")
     if tcm:
-        pairs_m = P.query("n_m2l")  # volume pairs; boundary sources run in stage m2l_bnd
+        pairs_m = P.query("n_m2l") * nrhs  # volume pairs; boundary sources run in stage m2l_bnd
         if tcm == 2:
             peak = pk["bf16_tflops"] if pk else 1900.0
             src = "measured bf16 burst" if pk else "fallback bf16 1.9 PFLOP/s"
@@ -259,7 +263,7 @@ def rooflines(P, stage_ms):
                       "achieved": 8.0 * p * p * pairs_m / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                       "peak_source": src, "work": f"{pairs_m} pairs/launch x 8p^2 flop (p={p})", "launch_ms": t}
     else:
-        m2l_pairs = P.query("n_m2l") + P.query("n_m2l_vb")
+        m2l_pairs = (P.query("n_m2l") + P.query("n_m2l_vb")) * nrhs
         peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         out["m2l"] = {"bound": "alu", "kernel": "k_m2l_vol (+ k_root_const, 1 block)",
                       "achieved": 8.0 * p * p * m2l_pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -273,19 +277,175 @@ def rooflines(P, stage_ms):
     return out[dom], out
 
 
-def time_solves(P, fd, reps, rtol=1e-8, graphs=1):
+def time_solves(P, fd, reps, rtol=1e-8, graphs=2, **kw):
+    """Median wall time of P.solve (host clock around the call, device synchronised on
+    both sides: the solve returns after its convergence test) after one warm-up solve."""
     import torch
-    P.solve(fd, rtol=rtol, use_graphs=graphs)  # warm-up (workspace, graphs)
+    P.solve(fd, rtol=rtol, use_graphs=graphs, **kw)  # warm-up (workspace, graphs)
     out = []
     for _ in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        u, info = P.solve(fd, rtol=rtol, use_graphs=graphs)
+        u, info = P.solve(fd, rtol=rtol, use_graphs=graphs, **kw)
         torch.cuda.synchronize()
         out.append((time.perf_counter() - t0) * 1e3)
         last = info
     return {"ms": float(np.median(out)), "iters": last["iters"], "rel_res": last["rel_res"],
-            "status": last["status"]}
+            "status": last["status"], "mode": {0: "host loop", 1: "host loop + apply graphs",
+                                                2: "one graph (device-side convergence)"}[graphs]}
+
+
+def time_apply(P, r, z, flush, reps=10):
+    """Mean CUDA-event time of one apply (L2 flushed before each) on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(reps + 3):
+        flush.zero_()
+        e0.record(stream)
+        P.apply(r, out=z)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def bench_c1(args, flush):
+    """64 x 64, manufactured sin solution, p = 8, GMRES(30) to 1e-8 (FGMRES in the single-
+    precision forms, whose preconditioner is not exactly linear)."""
+    import torch
+    import synth_inputs as S
+    from paper_1308_3339_gb300 import FmmPreconditioner
+    n = 64
+    f, _ = S.manufactured_sin(n)
+    fd = torch.tensor(f, dtype=torch.float64, device="cuda")
+    out = {}
+    for form in ("mixed_tf32", "fp32", "fp64"):
+        P = FmmPreconditioner(n, p=8, precision=form)
+        method = "gmres" if form == "fp64" else "fgmres"
+        out[form] = {"method": method, "apply_ms": time_apply(P, fd, torch.empty_like(fd), flush),
+                     **time_solves(P, fd, 5, method=method)}
+        P.close()
+    return {"workload": "poisson-fd 64x64 manufactured sin, p=8, leaf 8x8, theta 0.4", **out}
+
+
+def bench_c3(args, flush):
+    """4096 x 4096 x 32 right-hand sides, p = 10: apply points/s (N R / t) and FGMRES(15)
+    time to 1e-8 in the mixed TF32 and plain FP32 forms; M2L roofline of the 32-RHS apply."""
+    import torch
+    import synth_inputs as S
+    from paper_1308_3339_gb300 import FmmPreconditioner
+    n, R = 4096, 32
+    rs = torch.tensor(np.stack([S.gaussian_mixture(n, k) for k in range(R)]), dtype=torch.float64, device="cuda")
+    z = torch.empty_like(rs)
+    out = {"workload": "poisson-fd 4096x4096 x 32 rhs gaussian-mixture(16), p=10, FGMRES(15) to 1e-8"}
+    for form in ("mixed_tf32", "fp32"):
+        t0 = time.perf_counter()
+        P = FmmPreconditioner(n, p=10, precision=form, n_rhs=R)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        ta = time_apply(P, rs, z, flush, reps=5)
+        P.set_timing(2)
+        P.apply(rs, out=z)
+        st = P.stage_times()
+        P.set_timing(0)
+        _, allr = rooflines(P, st, nrhs=R)
+        rec = {"setup_ms": setup_ms, "apply_ms": ta, "points_per_s": n * n * R / (ta * 1e-3)}
+        for k in ("m2l", "p2p"):
+            rec[f"{k}_roofline"] = {q: allr[k][q] for q in ("kernel", "achieved", "peak", "unit", "frac", "launch_ms",
+                                                            "work")}
+        rec.update(time_solves(P, rs, 1, restart=15))
+        out[form] = rec
+        P.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_c4(args, flush):
+    """64 problems of sides drawn from {128, ..., 2048} (seed 0), each its own Gaussian
+    mixture (seed 1000 + k): one graph solving all of them side by side (FGMRES(30) to
+    1e-8) against the sum of the same problems solved one at a time."""
+    import torch
+    import synth_inputs as S
+    from paper_1308_3339_gb300 import FmmBatch, FmmPreconditioner
+    sides = [int(v) for v in S.batched_sides(0, 64)]
+    fs = [torch.tensor(S.gaussian_mixture(n, 1000 + k), dtype=torch.float64, device="cuda")
+          for k, n in enumerate(sides)]
+    out = {"workload": "64 poisson-fd problems, sides from {128,256,512,1024,2048} (seed 0), p=10",
+           "nodes": int(sum(n * n for n in sides))}
+    for form in ("mixed_tf32", "fp32"):
+        t0 = time.perf_counter()
+        B = FmmBatch(sides, p=10, precision=form)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        B.solve(fs, rtol=1e-8)  # warm-up: workspace and the batch graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        us, infos = B.solve(fs, rtol=1e-8)
+        torch.cuda.synchronize()
+        t_batch = (time.perf_counter() - t0) * 1e3
+        B.close()
+        t_single = 0.0
+        for k, n in enumerate(sides):
+            P = FmmPreconditioner(n, p=10, precision=form)
+            P.solve(fs[k], rtol=1e-8)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.solve(fs[k], rtol=1e-8)
+            torch.cuda.synchronize()
+            t_single += (time.perf_counter() - t0) * 1e3
+            P.close()
+        out[form] = {"setup_ms": setup_ms, "batched_ms": t_batch, "sum_single_ms": t_single,
+                     "speedup": t_single / t_batch, "max_iters": max(i["iters"] for i in infos),
+                     "all_converged": all(i["status"] == 0 for i in infos)}
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_c5(args, flush):
+    """Source inversion at 2048 x 2048: gradient of ||u(f) - u_obs||^2 through the adjoint
+    FMM-preconditioned solve (forward + backward time), and a central-difference check of
+    the gradient along one random direction (GPU only)."""
+    import torch
+    import synth_inputs as S
+    from paper_1308_3339_gb300 import FmmPreconditioner
+    from paper_1308_3339_gb300.autograd import fmm_solve
+    n = 2048
+    P = FmmPreconditioner(n, p=10, precision="mixed_tf32")
+    f_true = torch.tensor(S.gaussian_mixture(n, 3), dtype=torch.float64, device="cuda")
+    u_true, _ = P.solve(f_true, rtol=1e-10)
+    noise = torch.tensor(np.random.default_rng(7).normal(0.0, 0.01, n * n), device="cuda")
+    u_obs = u_true + noise
+    f0 = torch.zeros(n * n, dtype=torch.float64, device="cuda", requires_grad=True)
+
+    def loss(f):
+        return ((fmm_solve(f, P, rtol=1e-10) - u_obs) ** 2).sum()
+
+    loss(f0).backward()  # warm-up
+    f0.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = loss(f0)
+    torch.cuda.synchronize()
+    t_fwd = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t_bwd = (time.perf_counter() - t0) * 1e3
+    g = f0.grad.detach()
+    d = torch.tensor(np.random.default_rng(1).standard_normal(n * n), device="cuda")
+    d /= d.norm()
+    delta = 1e-2
+    with torch.no_grad():
+        fd = (loss(f0 + delta * d) - loss(f0 - delta * d)).item() / (2 * delta)
+    gd = float(g @ d)
+    P.close()
+    return {"workload": "source inversion 2048x2048, loss ||u(f)-u_obs||^2, f0 = 0, mixed TF32, rtol 1e-10",
+            "forward_ms": t_fwd, "backward_ms": t_bwd,
+            "fd_check": {"directional_grad": gd, "central_difference": fd,
+                         "rel_err": abs(fd - gd) / max(abs(fd), 1e-300)}}
 
 
 def run_ours(args):
@@ -372,28 +532,36 @@ def run_ours(args):
 
     tts = None
     if not args.no_tts:
+        # every form timed the same way: applies replayed from their graphs, solves as one
+        # graph each, so the forms differ only in their arithmetic
         P.set_timing(False)
         tts = {}
         for form in ("mixed_tf32", "mixed_bf16", "fp32", "fp64"):
+            t0 = time.perf_counter()
             Pf = P if form == args.precision else FmmPreconditioner(n, p=args.p, leaf_max=args.leaf,
                                                                      theta=args.theta, precision=form)
-            graphs = 1 if form.startswith("mixed") else 0  # the plain forms replay no graphs
-            Pf.set_graphs(bool(graphs))
-            ta = []
-            for i in range(13):
-                flush.zero_()
-                e0.record(stream)
-                Pf.apply(r, out=z)
-                e1.record(stream)
-                e1.synchronize()
-                if i >= 3:
-                    ta.append(e0.elapsed_time(e1))
-            tts[form] = {"apply_ms": float(np.mean(ta)), "graphs": bool(graphs),
-                         **time_solves(Pf, r, 3 if graphs else 2, graphs=graphs)}
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3 if Pf is not P else None
+            Pf.set_graphs(True)
+            tts[form] = {"apply_ms": time_apply(Pf, r, z, flush), **time_solves(Pf, r, 3 if form != "fp64" else 2)}
+            _, inf = Pf.solve(r, rtol=1e-8)
+            tts[form]["t_setup_ms"] = inf["t_setup_ms"]
+            if form == args.precision:
+                tts[form]["host_loop"] = time_solves(Pf, r, 3, graphs=1)
+                tts[form]["solve_over_iters_x_apply"] = tts[form]["ms"] / (tts[form]["iters"] * tts[form]["apply_ms"])
             if Pf is not P:
                 Pf.close()
-            else:
-                Pf.set_graphs(True)
+
+    configs = {}
+    for name, fn in (("c1", bench_c1), ("c3", bench_c3), ("c4", bench_c4), ("c5", bench_c5)):
+        if name in args.configs and world == 1:
+            t0 = time.perf_counter()
+            try:
+                configs[name] = fn(args, flush)
+            except Exception as e:  # reported, not hidden: the line says which config failed
+                configs[name] = {"error": f"{type(e).__name__}: {e}"}
+            configs[name]["bench_wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -406,7 +574,7 @@ def run_ours(args):
                 "config": workload(args), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(launches * args.steps), "roofline": roofline, "rooflines": all_rooflines,
                 "cpu_baseline": cpu,
-                "time_to_solution": tts, "stage_ms": stage_ms, "timed_wall_s": wall}
+                "time_to_solution": tts, "stage_ms": stage_ms, "timed_wall_s": wall, "configs": configs}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -86,7 +86,16 @@ typedef struct {
 /* method: FMMPC_CG | FMMPC_GMRES | FMMPC_FGMRES; restart: Krylov basis size m of
  * (F)GMRES(m); maxit: cap on preconditioner applications; rtol: stop when the relative
  * residual ||b - A u|| / ||b|| <= rtol (Sec. 6 stops at a relative-residual drop).
- * use_graphs: 1 = replay the preconditioner through a captured CUDA graph. */
+ * use_graphs: how the iteration is driven.
+ *   0: a host loop; every kernel launched one by one, and the host reads the Hessenberg
+ *      column (or the CG scalars) after every step to decide convergence.
+ *   1: the same host loop, each preconditioner application replayed from its CUDA graph.
+ *   2: the whole solve is one CUDA graph launched once: set-up, a conditional WHILE node
+ *      whose body is one Arnoldi step (or one CG iteration), and the final true residual.
+ *      The Givens rotations, the residual estimate, the convergence decision and the back
+ *      substitution run on the device and set the loop's condition; the loop is bounded by
+ *      maxit.  The host waits once, for the report.  Graphs are kept per (method, restart,
+ *      n_rhs, g present) and rebuilt when the workspace grows. */
 typedef struct {
   int32_t method;
   int32_t restart;

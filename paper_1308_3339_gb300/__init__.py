@@ -137,8 +137,10 @@ class FmmPreconditioner:
         return out
 
     def solve(self, f, g=None, u0=None, method="fgmres", restart=30, maxit=200, rtol=1e-8,
-              use_graphs=0, raise_on_fail=True):
-        """Krylov solve of A u = f (+ boundary values g); returns (u, info dict)."""
+              use_graphs=2, raise_on_fail=True):
+        """Krylov solve of A u = f (+ boundary values g); returns (u, info dict).
+        use_graphs: 2 the whole solve as one CUDA graph (device-side convergence), 1 a host
+        loop replaying the preconditioner's graph, 0 a host loop of single launches."""
         import torch
         k = self._vec(f)
         u = torch.zeros_like(f) if u0 is None else u0.clone()

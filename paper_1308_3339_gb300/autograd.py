@@ -15,7 +15,7 @@ from ._lib import FmmpcError
 
 __all__ = ["FmmSolve", "fmm_solve"]
 
-_DEFAULTS = dict(method="fgmres", restart=30, maxit=200, rtol=1e-10, use_graphs=1)
+_DEFAULTS = dict(method="fgmres", restart=30, maxit=200, rtol=1e-10, use_graphs=2)
 
 
 def _checked_solve(P, rhs, opts, what):

@@ -122,6 +122,8 @@ void release(fmmpc_handle *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (auto &e : h->gcache) cudaGraphExecDestroy(e.exec);
+  clear_solve_graphs(*h);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
   if (h->gev_out) cudaEventDestroy(h->gev_out);
@@ -360,6 +362,7 @@ int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine) {
   h->p2p_engine = engine;
   for (auto &e : h->gcache) cudaGraphExecDestroy(e.exec);  // captured graphs used the old engine
   h->gcache.clear();
+  clear_solve_graphs(*h);
   return FMMPC_OK;
 }
 

@@ -1952,6 +1952,10 @@ void apply_graph(fmmpc_handle &H, const double *r, double *out, int nrhs) {
 
 }  // namespace
 
+void apply_fmm_eager(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
+  apply_direct(H, part, r, out, nrhs);
+}
+
 void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs) {
   if (part == PART_FULL && H.graphs) apply_graph(H, r, out, nrhs);
   else apply_direct(H, part, r, out, nrhs);

@@ -79,11 +79,24 @@ struct KrylovWs {
   int64_t cap_vecs = 0;   // vectors of N*nrhs doubles allocated in V (and Z)
   double *V = nullptr, *Z = nullptr;
   double *w = nullptr, *t = nullptr, *b = nullptr, *x = nullptr, *r = nullptr;
-  double *dots = nullptr;  // [nrhs][MAXDOT]
+  double *fin = nullptr, *gin = nullptr, *zin = nullptr;  // graph solves: f, g, z_j
+  double *dots = nullptr;  // [4][nrhs][MAXDOT]
   double *part = nullptr;  // block partials
   double *scal = nullptr;  // per-rhs scalars on device
   double *hbuf = nullptr;  // pinned host mirror
   int *mask = nullptr;     // [nrhs] active right-hand sides
+  // device-resident state of the graph solves (krylov.cu)
+  int *g_ctl = nullptr, *g_done = nullptr, *g_iters = nullptr;
+  double *g_H = nullptr, *g_cs = nullptr, *g_sn = nullptr, *g_g = nullptr, *g_bn = nullptr, *g_rel = nullptr,
+         *g_sc = nullptr, *g_rtol = nullptr;
+};
+
+// An instantiated whole-solve graph (krylov.cu), keyed by method, restart, right-hand
+// sides, boundary data present, and the number of problems it solves side by side.
+struct SolveGraph {
+  int method, m, nrhs, has_g, nprob;
+  cudaGraphExec_t exec;
+  std::vector<uint64_t> gens;  // workspace generation of every member handle when built
 };
 
 }  // namespace fmmpc
@@ -125,10 +138,22 @@ struct fmmpc_handle {
   cudaEvent_t sev[6] = {};  // forks after the weights, the upward pass and the BEM solve; three joins
   std::vector<fmmpc::GraphEntry> gcache;
   uint64_t gclock = 0;
+  // whole-solve graphs (device-resident Krylov loop) and the stream they are captured on
+  std::vector<fmmpc::SolveGraph> sgraphs;
+  cudaStream_t cstream = nullptr;
+  uint64_t ws_gen = 0;  // bumped whenever the Krylov workspace is reallocated
 };
 
 namespace fmmpc {
 void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs);
+// the apply's kernels issued on H.stream one by one (no graph of its own; used inside captures)
+void apply_fmm_eager(fmmpc_handle &H, int part, const double *r, double *out, int nrhs);
+void clear_solve_graphs(fmmpc_handle &H);
+int solve_graphed(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs, const fmmpc_solve_opts &o,
+                  fmmpc_solve_info &info);
+cudaGraphExec_t solve_graph(std::vector<fmmpc_handle *> &hs, int method, int m, int nrhs, bool has_g);
+int solve_batched_graphed(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,
+                          double *const *u, const fmmpc_solve_opts &o, fmmpc_solve_info *infos);
 void init_fmm(fmmpc_handle &H);
 void init_bem(fmmpc_handle &H, DevPool &tmp);
 void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs);

@@ -209,6 +209,8 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
   const int64_t N = (int64_t)H.g.n * H.g.n * H.nrhs_max;
   if (k.cap_vecs >= nvec && (!flexible || k.Z)) return;
   FMMPC_CUDA(cudaStreamSynchronize(H.stream));
+  clear_solve_graphs(H);  // they hold the old workspace addresses
+  ++H.ws_gen;             // and so do batch graphs kept by another handle
   if (k.hbuf) cudaFreeHost(k.hbuf);
   H.kpool.release();
   k = KrylovWs{};
@@ -219,7 +221,23 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
   k.b = H.kpool.get<double>(N);
   k.r = H.kpool.get<double>(N);
   k.x = H.kpool.get<double>(N);
-  k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
+  k.fin = H.kpool.get<double>(N);
+  k.zin = H.kpool.get<double>(N);
+  k.gin = H.kpool.get<double>((size_t)4 * H.g.n * H.nrhs_max);
+  const int nr = H.nrhs_max;
+  k.g_ctl = H.kpool.get<int>(16);
+  k.g_done = H.kpool.get<int>(nr);
+  k.g_iters = H.kpool.get<int>(nr);
+  k.g_H = H.kpool.get<double>((size_t)nr * (MAXJ + 1) * MAXJ);
+  k.g_cs = H.kpool.get<double>((size_t)nr * MAXJ);
+  k.g_sn = H.kpool.get<double>((size_t)nr * MAXJ);
+  k.g_g = H.kpool.get<double>((size_t)nr * (MAXJ + 1));
+  k.g_bn = H.kpool.get<double>(nr);
+  k.g_rel = H.kpool.get<double>(nr);
+  k.g_sc = H.kpool.get<double>(nr);
+  k.g_rtol = H.kpool.get<double>(1);
+  FMMPC_CUDA(cudaMemsetAsync(k.g_ctl, 0, sizeof(int) * 16, H.stream));
+  k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 4);
   k.part = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * RED_BLOCKS);
   k.scal = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
   FMMPC_CUDA(cudaMallocHost(&k.hbuf, sizeof(double) * H.nrhs_max * MAXJ * 8));
@@ -497,14 +515,19 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
     bool saved;
     ~GraphsGuard() { H.graphs = saved; }
   } guard{H, H.graphs};
-  H.graphs = o.use_graphs != 0;
+  require(o.use_graphs >= 0 && o.use_graphs <= 2, "use_graphs must be 0, 1 or 2");
+  H.graphs = o.use_graphs == 1;
   Ctx c{H, (int64_t)H.g.n * H.g.n, nrhs, H.stream};
   const int64_t NR = c.N * nrhs;
-  k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(H.g.n, 1.0 / (H.g.h * H.g.h), NR, f, g, H.kw.b);
-  FMMPC_LAUNCH_CHECK();
   int st;
-  if (o.method == FMMPC_CG) st = pcg(c, o.maxit, o.rtol, H.kw.b, u, info);
-  else st = gmres(c, o.method == FMMPC_FGMRES, m, o.maxit, o.rtol, H.kw.b, u, info);
+  if (o.use_graphs == 2) {
+    st = solve_graphed(H, f, g, u, nrhs, o, info);  // one graph, device-side convergence
+  } else {
+    k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(H.g.n, 1.0 / (H.g.h * H.g.h), NR, f, g, H.kw.b);
+    FMMPC_LAUNCH_CHECK();
+    if (o.method == FMMPC_CG) st = pcg(c, o.maxit, o.rtol, H.kw.b, u, info);
+    else st = gmres(c, o.method == FMMPC_FGMRES, m, o.maxit, o.rtol, H.kw.b, u, info);
+  }
   FMMPC_CUDA(cudaStreamSynchronize(c.s));
   info.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   info.t_setup_ms = H.t_setup_ms;
@@ -550,8 +573,15 @@ int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const
   require(o.maxit >= 1 && o.rtol > 0.0, "maxit >= 1 and rtol > 0 required");
   const int m = std::min(o.restart, o.maxit);
   require(m >= 1 && m < MAXJ, "restart must be in [1, 63]");
+  require(o.use_graphs >= 0 && o.use_graphs <= 2, "use_graphs must be 0, 1 or 2");
   const int np = (int)hs.size();
   auto t0 = std::chrono::steady_clock::now();
+  if (o.use_graphs == 2) {
+    const int rc = solve_batched_graphed(hs, f, gb, u, o, infos);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int p = 0; infos && p < np; ++p) infos[p].t_solve_ms = ms;
+    return rc;
+  }
   std::vector<BatchState> st(np);
   std::vector<bool> saved_graphs(np);
   for (int p = 0; p < np; ++p) {
@@ -709,6 +739,696 @@ int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const
     }
     if (status != FMMPC_OK && worst == FMMPC_OK) worst = status;
     hs[p]->graphs = saved_graphs[p];
+  }
+  return worst;
+}
+
+}  // namespace fmmpc
+
+// ====================================================================== graph-resident solves
+// The whole Krylov solve as one CUDA graph: set-up nodes, then a conditional WHILE node whose
+// body is one Arnoldi step (FGMRES/GMRES) or one CG iteration, and final nodes that recompute
+// the true residual.  The Hessenberg column, the Givens rotations, the residual estimate, the
+// convergence decision and (at the end of a cycle) the back substitution run on the device
+// in one small kernel, which also sets the conditions of the loop and of the end-of-cycle
+// IF node, so no step waits for the host: the host launches the graph once and reads the
+// report when it has finished.  Orthogonalisation is classical Gram-Schmidt applied twice
+// (CGS2) at every step.  The loop is bounded: every pass counts one preconditioner
+// application and the loop stops at maxit, on a NaN, or when every right-hand side meets
+// rtol.  Vector indices that depend on the step (V_j, Z_j, the number of basis vectors) are
+// read by the kernels from the device control block.
+namespace fmmpc {
+
+namespace {
+
+// control block (ints)
+enum {
+  KC_J = 0,       // step index within the current cycle
+  KC_IT = 1,      // preconditioner applications so far (the loop's bound)
+  KC_CYC = 2,     // 1: this step ended the cycle
+  KC_DONE = 3,    // 1: every right-hand side met rtol (true residual)
+  KC_NAN = 4,     // 1: a NaN or Inf met in a residual
+  KC_MAXIT = 5,   // cap on KC_IT (set by the host before each launch)
+  KC_JCNT = 6,    // basis vectors of the cycle that just ended
+  KC_CONT = 7,    // value given to the loop condition
+  KC_COUNT = 8
+};
+
+__global__ void k_gcopy_col(const int *__restrict__ ctl, int64_t NR, const double *__restrict__ base, int64_t vs,
+                            double *__restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < NR) dst[t] = base[(int64_t)ctl[KC_J] * vs + t];
+}
+
+// y = A x (5-point) and, if Zb, Z_j = x
+__global__ void k_gspmv_store(const int *__restrict__ ctl, int n, double s, int64_t total, const double *__restrict__ x,
+                              double *__restrict__ y, double *__restrict__ Zb, int64_t vs) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t N = (int64_t)n * n;
+  const int64_t k = t % N;
+  const int i = (int)(k % n), j = (int)(k / n);
+  const double xc = x[t];
+  double v = 4.0 * xc;
+  if (i > 0) v -= x[t - 1];
+  if (i < n - 1) v -= x[t + 1];
+  if (j > 0) v -= x[t - n];
+  if (j < n - 1) v -= x[t + n];
+  y[t] = s * v;
+  if (Zb) Zb[(int64_t)ctl[KC_J] * vs + t] = xc;
+}
+
+// partial[rhs][i][blk] = slice sums of <V_i[rhs], w[rhs]> for i <= ctl[KC_J]
+__global__ void k_gmdot_partial(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V, int64_t vs,
+                                const double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double red[RED_THREADS / 32][8];
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double *wr = w + (int64_t)rhs * N;
+  const int nv = ctl[KC_J] + 1;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+      const double wk = wr[k];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q < nv) acc[q] = fma(V[(int64_t)(i0 + q) * vs + (int64_t)rhs * N + k], wk, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nv) {
+      double sum = 0.0;
+      for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
+      part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// out[rhs][i] = sum of the block partials for i <= ctl[KC_J]; acc[rhs][i] += the same
+__global__ void k_gmdot_final(const int *__restrict__ ctl, int nblocks, const double *__restrict__ part,
+                              double *__restrict__ out, double *__restrict__ acc) {
+  const int rhs = blockIdx.x, lane = threadIdx.x & 31;
+  const int nv = ctl[KC_J] + 1;
+  for (int i = threadIdx.x >> 5; i < nv; i += blockDim.x >> 5) {
+    const double *pp = part + ((int64_t)rhs * MAXJ + i) * nblocks;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += pp[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      out[rhs * MAXJ + i] = s;
+      if (acc) acc[rhs * MAXJ + i] += s;
+    }
+  }
+}
+
+// w[rhs] -= sum_{i <= j} c[rhs][i] V_i[rhs]; with part, also slice sums of the new |w|^2
+__global__ void k_gmupdate(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V, int64_t vs,
+                           const double *__restrict__ c, double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double red[RED_THREADS / 32];
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nv = ctl[KC_J] + 1;
+  double *wr = w + (int64_t)rhs * N;
+  const double *cr = c + rhs * MAXJ;
+  double sq = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    double v = wr[k];
+    for (int i = 0; i < nv; ++i) v = fma(-cr[i], V[(int64_t)i * vs + (int64_t)rhs * N + k], v);
+    wr[k] = v;
+    sq = fma(v, v, sq);
+  }
+  if (!part) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) red[wid] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) t += red[q];
+    part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// x[rhs] += sum_{i < ctl[KC_JCNT]} y[rhs][i] Z_i[rhs]
+__global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ Z, int64_t vs,
+                         const double *__restrict__ y, double *__restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int rhs = (int)(t / N), nv = ctl[KC_JCNT];
+  double v = x[t];
+  for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
+  x[t] = v;
+}
+
+// V_{ctl[KC_J]}[rhs] = sc[rhs] w[rhs]
+__global__ void k_gscale_col(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ sc,
+                             const double *__restrict__ w, double *__restrict__ V, int64_t vs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  V[(int64_t)ctl[KC_J] * vs + t] = sc[t / N] * w[t];
+}
+
+// Per-right-hand-side state of the graph-resident (F)GMRES.
+struct GmState {
+  double *Hm;    // [nrhs][(MAXJ + 1) MAXJ], entry (i, j) at i MAXJ + j (rotated)
+  double *cs, *sn;  // [nrhs][MAXJ]
+  double *g;     // [nrhs][MAXJ + 1]
+  double *bn;    // [nrhs] ||b|| (1 where b = 0)
+  double *rel;   // [nrhs] final true relative residual
+  double *sc;    // [nrhs] scale of the next basis vector (0 for a finished right-hand side)
+  double *rtol;  // [1]
+  int *done, *iters;  // [nrhs]
+};
+
+__global__ void k_ginit(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots) {
+  const int r = threadIdx.x;
+  if (r < nrhs) {
+    const double b = sqrt(fmax(0.0, dots[r * MAXJ]));
+    st.bn[r] = b > 0.0 ? b : 1.0;
+    st.iters[r] = 0;
+    st.done[r] = 0;
+  }
+  if (r == 0) {
+    ctl[KC_J] = 0;
+    ctl[KC_IT] = 0;
+    ctl[KC_CYC] = 0;
+    ctl[KC_DONE] = 0;
+    ctl[KC_NAN] = 0;
+    ctl[KC_JCNT] = 0;
+  }
+}
+
+// Start of a cycle from the true residual r (|r|^2 in dots[rhs][0]): per right-hand side
+// done = |r| / |b| <= rtol, g = (|r|, 0, ...), scale 1/|r| of V_0 (0 when done); j = 0.
+__global__ void k_grestart(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots) {
+  __shared__ int s_all, s_nan;
+  const int r = threadIdx.x;
+  if (r == 0) { s_all = 1; s_nan = 0; }
+  __syncthreads();
+  if (r < nrhs) {
+    const double beta = sqrt(fmax(0.0, dots[r * MAXJ]));
+    const double rtol = st.rtol[0];
+    if (!isfinite(beta) || !isfinite(dots[r * MAXJ])) atomicOr(&s_nan, 1);
+    const int d = (beta / st.bn[r] <= rtol) ? 1 : 0;
+    st.done[r] = d;
+    double *g = st.g + r * (MAXJ + 1);
+    for (int i = 0; i <= MAXJ; ++i) g[i] = 0.0;
+    g[0] = d ? 0.0 : beta;
+    st.sc[r] = (d || beta == 0.0) ? 0.0 : 1.0 / beta;
+    if (!d) atomicAnd(&s_all, 0);
+  }
+  __syncthreads();
+  if (r == 0) {
+    ctl[KC_J] = 0;
+    ctl[KC_DONE] = s_all;
+    ctl[KC_NAN] |= s_nan;
+  }
+}
+
+// End of an Arnoldi step: Hessenberg column j from the CGS2 coefficients h (hsum) and
+// |w| (wsq), the previous rotations, a new rotation, the residual estimate |g_{j+1}| / |b|,
+// the scale of V_{j+1}; the cycle ends when every right-hand side is within rtol (or has
+// a zero |w|), at j + 1 = m, at maxit, or on a NaN; then y from the triangular system.
+// Sets the condition of the end-of-cycle IF node.
+__global__ void k_gtail(int *__restrict__ ctl, GmState st, int nrhs, int m, const double *__restrict__ hsum,
+                        const double *__restrict__ wsq, double *__restrict__ y, cudaGraphConditionalHandle if_end) {
+  __shared__ int s_ok, s_nan, s_cyc;
+  const int r = threadIdx.x;
+  const int j = ctl[KC_J], it = ctl[KC_IT] + 1;
+  if (r == 0) { s_ok = 1; s_nan = 0; }
+  __syncthreads();
+  if (r < nrhs) {
+    double *Hr = st.Hm + (int64_t)r * (MAXJ + 1) * MAXJ;
+    double *cs = st.cs + r * MAXJ, *sn = st.sn + r * MAXJ, *g = st.g + r * (MAXJ + 1);
+    for (int i = 0; i <= j; ++i) Hr[i * MAXJ + j] = hsum[r * MAXJ + i];
+    const double hn = sqrt(fmax(0.0, wsq[r * MAXJ]));
+    Hr[(j + 1) * MAXJ + j] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = Hr[i * MAXJ + j], b = Hr[(i + 1) * MAXJ + j];
+      Hr[i * MAXJ + j] = cs[i] * a + sn[i] * b;
+      Hr[(i + 1) * MAXJ + j] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = Hr[j * MAXJ + j], b = Hr[(j + 1) * MAXJ + j], rr = hypot(a, b);
+    if (rr == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+    else { cs[j] = a / rr; sn[j] = b / rr; }
+    Hr[j * MAXJ + j] = rr;
+    Hr[(j + 1) * MAXJ + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const double est = fabs(g[j + 1]) / st.bn[r];
+    if (!isfinite(est)) atomicOr(&s_nan, 1);
+    const int done = st.done[r];
+    if (!done) st.iters[r] = it;
+    const bool ok = done || est <= st.rtol[0] || hn == 0.0;
+    if (!ok) atomicAnd(&s_ok, 0);
+    st.sc[r] = (hn > 0.0 && !done) ? 1.0 / hn : 0.0;
+  }
+  __syncthreads();
+  if (r == 0) {
+    const int cyc = (s_ok || s_nan || j + 1 >= m || it >= ctl[KC_MAXIT]) ? 1 : 0;
+    s_cyc = cyc;
+    ctl[KC_IT] = it;
+    ctl[KC_CYC] = cyc;
+    ctl[KC_JCNT] = j + 1;
+    ctl[KC_J] = j + 1;
+    ctl[KC_NAN] |= s_nan;
+    cudaGraphSetConditional(if_end, (unsigned)cyc);
+  }
+  __syncthreads();
+  if (s_cyc && r < nrhs) {  // back substitution (zeros for a finished right-hand side)
+    const double *Hr = st.Hm + (int64_t)r * (MAXJ + 1) * MAXJ;
+    const double *g = st.g + r * (MAXJ + 1);
+    double *yr = y + r * MAXJ;
+    const int jn = j + 1;
+    for (int i = 0; i < MAXJ; ++i) yr[i] = 0.0;
+    if (!st.done[r])
+      for (int i = jn - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int k = i + 1; k < jn; ++k) acc -= Hr[i * MAXJ + k] * yr[k];
+        yr[i] = (Hr[i * MAXJ + i] != 0.0) ? acc / Hr[i * MAXJ + i] : 0.0;
+      }
+  }
+}
+
+// Condition of the loop: continue while some right-hand side is above rtol, no NaN was met
+// and fewer than maxit preconditioner applications ran.
+__global__ void k_gcond(int *__restrict__ ctl, cudaGraphConditionalHandle loop) {
+  const int cont = (!ctl[KC_DONE] && !ctl[KC_NAN] && ctl[KC_IT] < ctl[KC_MAXIT]) ? 1 : 0;
+  ctl[KC_CONT] = cont;
+  cudaGraphSetConditional(loop, (unsigned)cont);
+}
+
+// Final report: true relative residual per right-hand side.
+__global__ void k_gfinal(GmState st, int nrhs, const double *__restrict__ dots) {
+  const int r = threadIdx.x;
+  if (r < nrhs) st.rel[r] = sqrt(fmax(0.0, dots[r * MAXJ])) / st.bn[r];
+}
+
+// ---- CG (Sec. 3.1) with per-right-hand-side masks
+// alpha = <r, z> / <p, A p> (0 when done or p A p = 0)
+__global__ void k_cg_alpha(GmState st, int nrhs, const double *__restrict__ rz, const double *__restrict__ pq) {
+  const int r = threadIdx.x;
+  if (r < nrhs) {
+    const double d = pq[r * MAXJ];
+    st.sc[r] = (st.done[r] || d == 0.0) ? 0.0 : rz[r * MAXJ] / d;
+  }
+}
+
+// after x += alpha p, r -= alpha q: |r|^2 in dots; done; iterations; the IF condition of
+// the second half of the iteration (preconditioner, beta, p) is "some right-hand side runs"
+__global__ void k_cg_check(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots,
+                           cudaGraphConditionalHandle if_more) {
+  __shared__ int s_all, s_nan;
+  const int r = threadIdx.x;
+  const int it = ctl[KC_IT] + 1;
+  if (r == 0) { s_all = 1; s_nan = 0; }
+  __syncthreads();
+  if (r < nrhs) {
+    const double rn = sqrt(fmax(0.0, dots[r * MAXJ]));
+    if (!isfinite(rn)) atomicOr(&s_nan, 1);
+    if (!st.done[r]) st.iters[r] = it;
+    const int d = st.done[r] || rn / st.bn[r] <= st.rtol[0];
+    st.done[r] = d;
+    if (!d) atomicAnd(&s_all, 0);
+  }
+  __syncthreads();
+  if (r == 0) {
+    ctl[KC_IT] = it;
+    ctl[KC_DONE] = s_all;
+    ctl[KC_NAN] |= s_nan;
+    const int more = (!s_all && !s_nan && it < ctl[KC_MAXIT]) ? 1 : 0;
+    cudaGraphSetConditional(if_more, (unsigned)more);
+  }
+}
+
+// beta = <r, z>_new / <r, z>_old (0 when done); rz_old = rz_new
+__global__ void k_cg_beta(GmState st, int nrhs, const double *__restrict__ rz_new, double *__restrict__ rz_old) {
+  const int r = threadIdx.x;
+  if (r < nrhs) {
+    const double o = rz_old[r * MAXJ], nw = rz_new[r * MAXJ];
+    st.sc[r] = (st.done[r] || o == 0.0) ? 0.0 : nw / o;
+    rz_old[r * MAXJ] = nw;
+  }
+}
+
+__global__ void k_cg_init(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots) {
+  const int r = threadIdx.x;
+  __shared__ int s_all;
+  if (r == 0) s_all = 1;
+  __syncthreads();
+  if (r < nrhs) {
+    const double rn = sqrt(fmax(0.0, dots[r * MAXJ]));
+    const int d = rn / st.bn[r] <= st.rtol[0];
+    st.done[r] = d;
+    if (!d) atomicAnd(&s_all, 0);
+  }
+  __syncthreads();
+  if (r == 0) ctl[KC_DONE] = s_all;
+}
+
+__global__ void k_copy(int64_t total, const double *__restrict__ a, double *__restrict__ b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) b[t] = a[t];
+}
+
+// Captures the work fn() issues on H.stream into `graph` after the nodes deps (H.stream is
+// the capture stream meanwhile; the preconditioner's internal streams join it by events)
+// and returns the capture's last nodes, the dependencies of whatever follows.
+template <typename F>
+std::vector<cudaGraphNode_t> capture_into(fmmpc_handle &H, cudaStream_t cs, cudaGraph_t graph,
+                                          const std::vector<cudaGraphNode_t> &deps, F &&fn) {
+  cudaStream_t user = H.stream;
+  const int timing = H.timing;
+  H.stream = cs;
+  H.timing = 0;
+  std::vector<cudaGraphNode_t> out;
+  FMMPC_CUDA(cudaStreamBeginCaptureToGraph(cs, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                           cudaStreamCaptureModeThreadLocal));
+  try {
+    fn();
+    cudaStreamCaptureStatus st{};
+    const cudaGraphNode_t *d = nullptr;
+    size_t nd = 0;
+    FMMPC_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd));
+    out.assign(d, d + nd);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    H.stream = user;
+    H.timing = timing;
+    throw;
+  }
+  H.stream = user;
+  H.timing = timing;
+  cudaGraph_t g = nullptr;
+  FMMPC_CUDA(cudaStreamEndCapture(cs, &g));
+  return out;
+}
+
+cudaGraphNode_t add_conditional(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps,
+                                cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t n = nullptr;
+  FMMPC_CUDA(cudaGraphAddNode(&n, parent, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+  *body = p.conditional.phGraph_out[0];
+  return n;
+}
+
+GmState gm_state(KrylovWs &K) {
+  return GmState{K.g_H, K.g_cs, K.g_sn, K.g_g, K.g_bn, K.g_rel, K.g_sc, K.g_rtol, K.g_done, K.g_iters};
+}
+
+// norms |v[rhs]|^2 into dots[rhs][0] (captured)
+void gnorm2(Ctx &c, const double *v) {
+  dim3 grid(RED_BLOCKS, c.nrhs);
+  k_mdot_partial<<<grid, RED_THREADS, 0, c.H.stream>>>(c.N, 1, v, 0, v, c.H.kw.part, 0);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, RED_BLOCKS, c.H.kw.part, c.H.kw.dots, nullptr, 0);
+  FMMPC_LAUNCH_CHECK();
+}
+
+// <a, b> into out[rhs][0] (captured)
+void gdot(Ctx &c, const double *a, const double *b, double *out) {
+  dim3 grid(RED_BLOCKS, c.nrhs);
+  k_mdot_partial<<<grid, RED_THREADS, 0, c.H.stream>>>(c.N, 1, a, 0, b, c.H.kw.part, 0);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, RED_BLOCKS, c.H.kw.part, out, nullptr, 0);
+  FMMPC_LAUNCH_CHECK();
+}
+
+// Builds one problem's chain [set-up] -> WHILE [step (-> IF cycle end)] -> [final] into
+// graph G.  Solves A u = b for the handle's internal vectors: b is folded from K.fin
+// (and K.gin), the iterate is K.x.
+void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bool has_g) {
+  KrylovWs &K = H.kw;
+  if (!H.cstream) FMMPC_CUDA(cudaStreamCreateWithFlags(&H.cstream, cudaStreamNonBlocking));
+  cudaStream_t cs = H.cstream;
+  const int64_t N = (int64_t)H.g.n * H.g.n, NR = N * nrhs, vs = N * H.nrhs_max;
+  const double s = 1.0 / (H.g.h * H.g.h);
+  const bool flexible = method == FMMPC_FGMRES;
+  GmState st = gm_state(K);
+  int *ctl = K.g_ctl;
+  cudaGraphConditionalHandle hloop;
+  FMMPC_CUDA(cudaGraphConditionalHandleCreate(&hloop, G, 0, cudaGraphCondAssignDefault));
+  Ctx c{H, N, nrhs, cs};
+  auto precond = [&](const double *in, double *out) { apply_fmm_eager(H, PART_FULL, in, out, nrhs); };
+  auto residual_c = [&](const double *b, const double *x, double *r) {
+    k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, x, r);
+    k_resid<<<nblk(NR), 256, 0, H.stream>>>(NR, b, r);
+    FMMPC_LAUNCH_CHECK();
+  };
+  // ---- set-up
+  const std::vector<cudaGraphNode_t> none;
+  auto f_init = capture_into(H, cs, G, none, [&] {
+    c.s = H.stream;
+    k_fold_rhs<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, K.fin, has_g ? K.gin : nullptr, K.b);
+    gnorm2(c, K.b);
+    k_ginit<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
+    residual_c(K.b, K.x, K.r);
+    gnorm2(c, K.r);
+    if (method == FMMPC_CG) {
+      k_cg_init<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
+      precond(K.r, K.w);
+      k_copy<<<nblk(NR), 256, 0, H.stream>>>(NR, K.w, K.V);  // p = z
+      gdot(c, K.r, K.w, K.dots + (size_t)nrhs * MAXJ);     // <r, z> in the second dots block
+    } else {
+      k_grestart<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
+      k_scale<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, K.r, K.V);
+    }
+    k_gcond<<<1, 1, 0, H.stream>>>(ctl, hloop);
+    FMMPC_LAUNCH_CHECK();
+  });
+  cudaGraph_t body = nullptr;
+  cudaGraphNode_t n_loop = add_conditional(G, f_init, hloop, cudaGraphCondTypeWhile, &body);
+  cudaGraphConditionalHandle hif;
+  FMMPC_CUDA(cudaGraphConditionalHandleCreate(&hif, body, 0, 0));
+  double *hsum = K.dots + (size_t)nrhs * MAXJ, *wsq = K.scal + (size_t)nrhs * MAXJ;
+  std::vector<cudaGraphNode_t> f_step;
+  cudaGraph_t ifb = nullptr;
+  if (method == FMMPC_CG) {
+    // p in V_0, q in t, z in w; <r, z> of the last iteration in the second dots block
+    double *p = K.V, *q = K.t, *z = K.w, *rz_old = K.dots + (size_t)nrhs * MAXJ;
+    double *pq = K.dots + (size_t)2 * nrhs * MAXJ;
+    f_step = capture_into(H, cs, body, none, [&] {
+      c.s = H.stream;
+      k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, p, q);
+      gdot(c, p, q, pq);
+      k_cg_alpha<<<1, 64, 0, H.stream>>>(st, nrhs, rz_old, pq);
+      k_cg_xr<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, p, q, K.x, K.r);
+      gnorm2(c, K.r);
+      k_cg_check<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots, hif);
+      FMMPC_LAUNCH_CHECK();
+    });
+    cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
+    capture_into(H, cs, ifb, none, [&] {
+      c.s = H.stream;
+      precond(K.r, z);
+      gdot(c, K.r, z, K.dots);
+      k_cg_beta<<<1, 64, 0, H.stream>>>(st, nrhs, K.dots, rz_old);
+      k_cg_p<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, z, p);
+      FMMPC_LAUNCH_CHECK();
+    });
+    capture_into(H, cs, body, {n_if}, [&] {
+      k_gcond<<<1, 1, 0, H.stream>>>(ctl, hloop);
+      FMMPC_LAUNCH_CHECK();
+    });
+  } else {
+    f_step = capture_into(H, cs, body, none, [&] {
+      c.s = H.stream;
+      k_gcopy_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, NR, K.V, vs, K.t);  // v_j into a fixed buffer
+      precond(K.t, K.zin);
+      k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, H.g.n, s, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
+      FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nrhs * MAXJ, H.stream));
+      dim3 grid(RED_BLOCKS, nrhs);
+      for (int pass = 0; pass < 2; ++pass) {
+        k_gmdot_partial<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part);
+        k_gmdot_final<<<nrhs, 256, 0, H.stream>>>(ctl, RED_BLOCKS, K.part, K.dots, hsum);
+        k_gmupdate<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, pass ? K.part : nullptr);
+      }
+      k_mdot_final<<<dim3(nrhs, 1), 256, 0, H.stream>>>(1, RED_BLOCKS, K.part, wsq, nullptr, 0);
+      k_gtail<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, m, hsum, wsq, K.scal, hif);
+      k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs);
+      FMMPC_LAUNCH_CHECK();
+    });
+    cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
+    capture_into(H, cs, ifb, none, [&] {
+      c.s = H.stream;
+      if (flexible) {
+        k_gmaxpy<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.Z, vs, K.scal, K.x);
+      } else {
+        FMMPC_CUDA(cudaMemsetAsync(K.t, 0, sizeof(double) * NR, H.stream));
+        k_gmaxpy<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.V, vs, K.scal, K.t);
+        precond(K.t, K.w);
+        k_add<<<nblk(NR), 256, 0, H.stream>>>(NR, K.w, K.x);
+      }
+      residual_c(K.b, K.x, K.r);
+      gnorm2(c, K.r);
+      k_grestart<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
+      k_scale<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, K.r, K.V);
+      FMMPC_LAUNCH_CHECK();
+    });
+    capture_into(H, cs, body, {n_if}, [&] {
+      k_gcond<<<1, 1, 0, H.stream>>>(ctl, hloop);
+      FMMPC_LAUNCH_CHECK();
+    });
+  }
+  // ---- final: the true residual
+  capture_into(H, cs, G, {n_loop}, [&] {
+    c.s = H.stream;
+    residual_c(K.b, K.x, K.r);
+    gnorm2(c, K.r);
+    k_gfinal<<<1, 64, 0, H.stream>>>(st, nrhs, K.dots);
+    FMMPC_LAUNCH_CHECK();
+  });
+}
+
+}  // namespace
+
+void clear_solve_graphs(fmmpc_handle &H) {
+  for (auto &e : H.sgraphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  H.sgraphs.clear();
+}
+
+// The graph of (method, m, nrhs, has_g) for the handles hs (one chain each, side by side in
+// one graph), built and instantiated on first use and kept by the first handle.
+cudaGraphExec_t solve_graph(std::vector<fmmpc_handle *> &hs, int method, int m, int nrhs, bool has_g) {
+  fmmpc_handle &H0 = *hs[0];
+  std::vector<uint64_t> gens;
+  for (auto *h : hs) gens.push_back(h->ws_gen);
+  for (auto it = H0.sgraphs.begin(); it != H0.sgraphs.end(); ++it)
+    if (it->method == method && it->m == m && it->nrhs == nrhs && it->has_g == (int)has_g &&
+        it->nprob == (int)hs.size()) {
+      if (it->gens == gens) return it->exec;
+      cudaGraphExecDestroy(it->exec);  // a member's workspace moved since it was built
+      H0.sgraphs.erase(it);
+      break;
+    }
+  cudaGraph_t G = nullptr;
+  FMMPC_CUDA(cudaGraphCreate(&G, 0));
+  try {
+    for (auto *h : hs) build_chain(*h, G, method, m, nrhs, has_g);
+  } catch (...) {
+    cudaGraphDestroy(G);
+    throw;
+  }
+  SolveGraph e{method, m, nrhs, (int)has_g, (int)hs.size(), nullptr, gens};
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, G, 0);
+  cudaGraphDestroy(G);
+  FMMPC_CUDA(ie);
+  H0.sgraphs.push_back(e);
+  return e.exec;
+}
+
+// Solve through the graph: inputs copied into the handle's vectors, one launch, the report
+// read back once.
+int solve_graphed(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs, const fmmpc_solve_opts &o,
+                  fmmpc_solve_info &info) {
+  const int m = (o.method == FMMPC_CG) ? 1 : std::min(o.restart, o.maxit);
+  KrylovWs &K = H.kw;
+  const int64_t N = (int64_t)H.g.n * H.g.n, NR = N * nrhs;
+  std::vector<fmmpc_handle *> hs{&H};
+  cudaGraphExec_t ex = solve_graph(hs, o.method, m, nrhs, g != nullptr);
+  cudaStream_t s = H.stream;
+  FMMPC_CUDA(cudaMemcpyAsync(K.fin, f, sizeof(double) * NR, cudaMemcpyDeviceToDevice, s));
+  if (g) FMMPC_CUDA(cudaMemcpyAsync(K.gin, g, sizeof(double) * 4 * H.g.n * nrhs, cudaMemcpyDeviceToDevice, s));
+  FMMPC_CUDA(cudaMemcpyAsync(K.x, u, sizeof(double) * NR, cudaMemcpyDeviceToDevice, s));
+  int *hc = reinterpret_cast<int *>(K.hbuf);
+  double *hp = K.hbuf + 8;
+  hc[0] = o.maxit;
+  hp[0] = o.rtol;
+  FMMPC_CUDA(cudaMemcpyAsync(K.g_ctl + KC_MAXIT, hc, sizeof(int), cudaMemcpyHostToDevice, s));
+  FMMPC_CUDA(cudaMemcpyAsync(K.g_rtol, hp, sizeof(double), cudaMemcpyHostToDevice, s));
+  FMMPC_CUDA(cudaGraphLaunch(ex, s));
+  FMMPC_CUDA(cudaMemcpyAsync(u, K.x, sizeof(double) * NR, cudaMemcpyDeviceToDevice, s));
+  double *hrel = K.hbuf + 16;
+  int *hit = reinterpret_cast<int *>(K.hbuf + 16 + MAXJ), *hctl = hit + MAXJ;
+  FMMPC_CUDA(cudaMemcpyAsync(hrel, K.g_rel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaMemcpyAsync(hit, K.g_iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaMemcpyAsync(hctl, K.g_ctl, sizeof(int) * KC_COUNT, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaStreamSynchronize(s));
+  double worst = 0.0;
+  int status = FMMPC_OK;
+  info.iters = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    if (!std::isfinite(hrel[r])) status = FMMPC_ERR_NAN;
+    worst = std::max(worst, hrel[r]);
+    info.iters = std::max(info.iters, hit[r]);
+  }
+  if (hctl[KC_NAN]) status = FMMPC_ERR_NAN;
+  if (status == FMMPC_OK && worst > o.rtol) status = FMMPC_ERR_NOT_CONVERGED;
+  info.rel_res = worst;
+  return status;
+}
+
+// Independent problems solved by one graph: one chain per problem side by side (each with
+// its own WHILE loop, so a problem stops at its own convergence), launched once on the
+// first problem's stream after every problem's inputs are in place.
+int solve_batched_graphed(std::vector<fmmpc_handle *> &hs, const double *const *f, const double *const *gb,
+                          double *const *u, const fmmpc_solve_opts &o, fmmpc_solve_info *infos) {
+  const int m = std::min(o.restart, o.maxit);
+  const int np = (int)hs.size();
+  bool has_g = false;
+  for (int p = 0; p < np && gb; ++p) has_g = has_g || gb[p] != nullptr;
+  for (auto *h : hs) ensure_ws(*h, m + 1, true);
+  cudaGraphExec_t ex = solve_graph(hs, FMMPC_FGMRES, m, 1, has_g);
+  fmmpc_handle &H0 = *hs[0];
+  cudaStream_t s0 = H0.stream;
+  for (int p = 0; p < np; ++p) {
+    fmmpc_handle &H = *hs[p];
+    KrylovWs &K = H.kw;
+    const int64_t N = (int64_t)H.g.n * H.g.n;
+    FMMPC_CUDA(cudaMemcpyAsync(K.fin, f[p], sizeof(double) * N, cudaMemcpyDeviceToDevice, s0));
+    if (has_g) {
+      if (gb[p]) FMMPC_CUDA(cudaMemcpyAsync(K.gin, gb[p], sizeof(double) * 4 * H.g.n, cudaMemcpyDeviceToDevice, s0));
+      else FMMPC_CUDA(cudaMemsetAsync(K.gin, 0, sizeof(double) * 4 * H.g.n, s0));
+    }
+    FMMPC_CUDA(cudaMemcpyAsync(K.x, u[p], sizeof(double) * N, cudaMemcpyDeviceToDevice, s0));
+    int *hc = reinterpret_cast<int *>(K.hbuf);
+    double *hp = K.hbuf + 8;
+    hc[0] = o.maxit;
+    hp[0] = o.rtol;
+    FMMPC_CUDA(cudaMemcpyAsync(K.g_ctl + KC_MAXIT, hc, sizeof(int), cudaMemcpyHostToDevice, s0));
+    FMMPC_CUDA(cudaMemcpyAsync(K.g_rtol, hp, sizeof(double), cudaMemcpyHostToDevice, s0));
+  }
+  FMMPC_CUDA(cudaGraphLaunch(ex, s0));
+  for (int p = 0; p < np; ++p) {
+    fmmpc_handle &H = *hs[p];
+    KrylovWs &K = H.kw;
+    const int64_t N = (int64_t)H.g.n * H.g.n;
+    FMMPC_CUDA(cudaMemcpyAsync(u[p], K.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s0));
+    FMMPC_CUDA(cudaMemcpyAsync(K.hbuf + 16, K.g_rel, sizeof(double), cudaMemcpyDeviceToHost, s0));
+    FMMPC_CUDA(cudaMemcpyAsync(K.hbuf + 17, K.g_iters, sizeof(int), cudaMemcpyDeviceToHost, s0));
+    FMMPC_CUDA(cudaMemcpyAsync(K.hbuf + 18, K.g_ctl, sizeof(int) * KC_COUNT, cudaMemcpyDeviceToHost, s0));
+  }
+  FMMPC_CUDA(cudaStreamSynchronize(s0));
+  int worst = FMMPC_OK;
+  for (int p = 0; p < np; ++p) {
+    KrylovWs &K = hs[p]->kw;
+    const double rel = K.hbuf[16];
+    const int iters = *reinterpret_cast<int *>(K.hbuf + 17);
+    const int *hctl = reinterpret_cast<int *>(K.hbuf + 18);
+    int status = FMMPC_OK;
+    if (!std::isfinite(rel) || hctl[KC_NAN]) status = FMMPC_ERR_NAN;
+    else if (rel > o.rtol) status = FMMPC_ERR_NOT_CONVERGED;
+    if (infos) {
+      infos[p].iters = iters;
+      infos[p].rel_res = rel;
+      infos[p].t_setup_ms = hs[p]->t_setup_ms;
+      infos[p].status = status;
+    }
+    if (status != FMMPC_OK && worst == FMMPC_OK) worst = status;
   }
   return worst;
 }

@@ -41,7 +41,7 @@ def test_batched_solve_matches_individual_solves():
         check_close(f"batched problem {k} (n={n}) vs single", ub, u1.cpu().numpy(), 1e-7, 1e-7)
         # against the FP64 oracle solved tightly
         xo, *_ = O.Problem(n, p=10).solve(S.gaussian_mixture(n, 1000 + k), "fgmres", rtol=1e-13, prec="fmm")
-        check_close(f"batched problem {k} (n={n}) vs oracle", ub, xo, 1e-6, 1e-6)
+        check_close(f"batched problem {k} (n={n}) vs oracle", ub, xo, 5e-8, 5e-8)  # measured <= 5.5e-9
 
 
 def test_autotune_meets_gate_and_reports_all_candidates():

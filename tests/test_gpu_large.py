@@ -61,7 +61,7 @@ def test_4096_with_32_right_hand_sides():
         check_close(f"C3 vcol rhs{k} (64 points) vs direct", vcol[rows],
                     O.direct_V_at(n, 0.0, 0.0, 1.0, rs[k], cx[rows], cy[rows]), 1e-5, 1e-5)
         # S q + vcol = 0 at the sampled rows, relative to |vcol|
-        check_close(f"C3 BEM system rhs{k} (64 rows)", Srows @ q, -vcol[rows], 1e-8, 1e-8)
+        check_close(f"C3 BEM system rhs{k} (64 rows)", Srows @ q, -vcol[rows], 1e-10, 1e-10)  # measured 4e-12
         sel = np.concatenate([idx, band])
         zk = z[k].cpu().numpy()[sel]
         sl, _ = O.layers_at(n, 0.0, 0.0, 1.0, (sel % n + 1) * h, (sel // n + 1) * h, q=q)
@@ -92,5 +92,5 @@ def test_64_uneven_problems_batched():
     xo, *_ = O.Problem(sides[k], p=10).solve(S.gaussian_mixture(sides[k], 1000 + k), "fgmres", rtol=1e-12,
                                               prec="fmm")
     # ours stops at 1e-8, the oracle at 1e-12
-    check_close(f"C4 problem {k} vs oracle", us[k].cpu().numpy(), xo, 1e-6, 1e-6)
+    check_close(f"C4 problem {k} vs oracle", us[k].cpu().numpy(), xo, 5e-8, 5e-8)
     B.close()

