@@ -143,7 +143,8 @@ int fmmpc_apply_host(fmmpc_handle *h, const double *r_host, double *z_host, int3
 int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double *out_dev,
                      int32_t n_rhs);
 
-/* y = A x, the 5-point operator with zero boundary values (Eq. e:axb). */
+/* y = A x with zero boundary values: the operator chosen by fmmpc_set_operator (the
+ * five-point stencil of Eq. e:axb by default). */
 int fmmpc_spmv(fmmpc_handle *h, const double *x_dev, double *y_dev, int32_t n_rhs);
 
 /* Krylov solve of A u = b with b = f + (boundary values g of the stencil neighbours)/h^2
@@ -181,6 +182,28 @@ int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
  * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision; three TF32 products
  * per pair, FP32-accurate in every single-precision form), 1 the CUDA-core kernel. */
 int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
+
+/* Operator of the Krylov solves, fmmpc_spmv and the right-hand side folding (the
+ * preconditioner stays the constant-coefficient FMM-BEM P of the handle):
+ *  FMMPC_OP_FD5 (default): the five-point stencil (1/h^2)(4 u_ij - neighbours), Eq. e:axb.
+ *  FMMPC_OP_FD5_VAR: -div(a grad u) (Sec. 2.1 Eq. e:p with a variable diffusion
+ *    coefficient, Sec. 4.4 and Sec. 6.4), five-point flux form: the coefficient of the face
+ *    between two nodes is the mean of a at the two nodes.  a_dev: FP64 device array of
+ *    (n+2)^2 values at the nodes of the full grid including the boundary ring, row-major,
+ *    interior node (i, j) at (j+1)(n+2) + (i+1); copied by the call (the caller keeps
+ *    ownership).  Boundary data g enters through the face coefficient.  Sec. 6.4
+ *    preconditions this operator with the constant-coefficient P, as here.
+ *  FMMPC_OP_Q1: the Q1 bilinear finite-element stiffness of -lap, the paper's
+ *    discretisation (Sec. 6.1): 8/3 on the diagonal, -1/3 for the eight neighbours; the
+ *    right-hand side is the lumped load b = h^2 f; the preconditioner acts on M^{-1} r, M
+ *    the consistent Q1 mass matrix (the finite-element function of the residual), through
+ *    tridiagonal solves along the rows and columns.  Boundary data is rejected (_INVALID):
+ *    the nine-point stencil would need the corner values.
+ * a_dev is ignored unless op = FMMPC_OP_FD5_VAR.  Errors: _INVALID. */
+#define FMMPC_OP_FD5 0
+#define FMMPC_OP_FD5_VAR 1
+#define FMMPC_OP_Q1 2
+int fmmpc_set_operator(fmmpc_handle *h, int32_t op, const double *a_dev);
 
 /* on = 1 (the default): fmmpc_apply records its kernels once per distinct (r, z, n_rhs)
  * into a CUDA graph on an internal stream and replays it (ordered after and before the

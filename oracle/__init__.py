@@ -52,6 +52,13 @@ def _lib():
     L.orc_threads.restype = i
     L.orc_spmv5.argtypes = [i, d, vp, vp]
     L.orc_fold_rhs.argtypes = [i, d, vp, vp, vp]
+    L.orc_spmv5_var.argtypes = [i, d, vp, vp, vp]
+    L.orc_fold_rhs_var.argtypes = [i, d, vp, vp, vp, vp]
+    L.orc_spmv_q1.argtypes = [i, vp, vp]
+    L.orc_q1_load.argtypes = [i, d, vp, vp]
+    L.orc_q1_mass_solve.argtypes = [i, d, vp, vp]
+    L.orc_set_operator.argtypes = [vp, i, vp]
+    L.orc_set_operator.restype = i
     L.orc_self_constant.restype = d
     L.orc_direct_V.argtypes = [i, d, d, d, vp, vp]
     L.orc_direct_V_at.argtypes = [i, d, d, d, vp, i, vp, vp, vp]
@@ -117,6 +124,50 @@ def fold_rhs(n: int, h: float, f: np.ndarray, g: np.ndarray | None) -> np.ndarra
     b = np.empty_like(f)
     _lib().orc_fold_rhs(n, h, _p(f), _p(gg), _p(b))
     return b
+
+
+def spmv5_var(n: int, h: float, a: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """A x for -div(a grad u), five-point flux form (Sec. 4.4, Sec. 6.4); a at the
+    (n+2)^2 nodes of the full grid."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    assert a.size == (n + 2) ** 2
+    y = np.empty_like(x)
+    _lib().orc_spmv5_var(n, h, _p(a), _p(x), _p(y))
+    return y
+
+
+def fold_rhs_var(n, h, a, f, g):
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    b = np.empty_like(f)
+    _lib().orc_fold_rhs_var(n, h, _p(a), _p(f), _p(gg), _p(b))
+    return b
+
+
+def spmv_q1(n: int, x: np.ndarray) -> np.ndarray:
+    """A x for the Q1 stiffness of -lap on the uniform grid (Sec. 6.1), zero Dirichlet."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    y = np.empty_like(x)
+    _lib().orc_spmv_q1(n, _p(x), _p(y))
+    return y
+
+
+def q1_load(n, h, f):
+    """Lumped Q1 load vector b = h^2 f."""
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+    b = np.empty_like(f)
+    _lib().orc_q1_load(n, h, _p(f), _p(b))
+    return b
+
+
+def q1_mass_solve(n, h, r):
+    """c with M c = r, M the consistent Q1 mass matrix of the interior nodes."""
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+    c = np.empty_like(r)
+    _lib().orc_q1_mass_solve(n, h, _p(r), _p(c))
+    return c
 
 
 def self_constant() -> float:
@@ -273,6 +324,16 @@ class Problem:
         if getattr(self, "_h", None):
             _lib().orc_destroy(self._h)
             self._h = None
+
+    def set_operator(self, op, a=None):
+        """Operator of later solves: "fd5" (Eq. e:axb), "fd5_var" with coefficient a at the
+        (n+2)^2 full-grid nodes (Sec. 6.4), or "q1" (Sec. 6.1; the preconditioner then acts
+        on M^{-1} r, M the consistent Q1 mass matrix)."""
+        code = {"fd5": 0, "fd5_var": 1, "q1": 2}[op]
+        aa = None if a is None else np.ascontiguousarray(a, np.float64).reshape(-1)
+        if _lib().orc_set_operator(self._h, code, _p(aa)):
+            raise ValueError("oracle: bad operator")
+        self._a = aa
 
     def export(self, what):
         N = self.n * self.n

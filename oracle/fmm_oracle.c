@@ -83,6 +83,104 @@ void orc_fold_rhs(int n, double h, const double *f, const double *g, double *b) 
 }
 
 /* ======================================================================== */
+/* 1b. Variable diffusion coefficient (Sec. 4.4; the problem of Sec. 6.4,    */
+/*     -div(a grad u) = f with a = 1 + mu sin(m pi x) sin(n pi y)).          */
+/*     Five-point flux form: the coefficient of the face between two nodes   */
+/*     is the mean of a at the two nodes; a is given at the (n+2)^2 nodes of  */
+/*     the full grid, boundary ring included, row-major, node (i, j) of the   */
+/*     interior at full index (j+1)(n+2) + (i+1).                             */
+/* ======================================================================== */
+
+void orc_spmv5_var(int n, double h, const double *a, const double *x, double *y) {
+  const double s = 1.0 / (h * h);
+  const int W = n + 2;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const int ic = (j + 1) * W + (i + 1);
+      const double aE = 0.5 * (a[ic] + a[ic + 1]), aW = 0.5 * (a[ic] + a[ic - 1]);
+      const double aN = 0.5 * (a[ic] + a[ic + W]), aS = 0.5 * (a[ic] + a[ic - W]);
+      double v = (aE + aW + aN + aS) * x[j * n + i];
+      if (i > 0) v -= aW * x[j * n + i - 1];
+      if (i < n - 1) v -= aE * x[j * n + i + 1];
+      if (j > 0) v -= aS * x[(j - 1) * n + i];
+      if (j < n - 1) v -= aN * x[(j + 1) * n + i];
+      y[j * n + i] = s * v;
+    }
+}
+
+/* b = f + (1/h^2) a_face g at the boundary neighbours (layout of g as in orc_fold_rhs). */
+void orc_fold_rhs_var(int n, double h, const double *a, const double *f, const double *g, double *b) {
+  const double s = 1.0 / (h * h);
+  const int W = n + 2;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const int ic = (j + 1) * W + (i + 1);
+      double v = f[j * n + i];
+      if (g) {
+        if (j == 0) v += s * 0.5 * (a[ic] + a[ic - W]) * g[i];
+        if (i == n - 1) v += s * 0.5 * (a[ic] + a[ic + 1]) * g[n + j];
+        if (j == n - 1) v += s * 0.5 * (a[ic] + a[ic + W]) * g[2 * n + (n - 1 - i)];
+        if (i == 0) v += s * 0.5 * (a[ic] + a[ic - 1]) * g[3 * n + (n - 1 - j)];
+      }
+      b[j * n + i] = v;
+    }
+}
+
+/* ======================================================================== */
+/* 1c. Q1 bilinear finite elements, the paper's discretisation (Sec. 6.1),   */
+/*     on the uniform square grid with zero Dirichlet values: the stiffness   */
+/*     of -lap sums the element integrals of grad phi_i . grad phi_j over the */
+/*     four elements around node i, giving 8/3 on the diagonal and -1/3 for   */
+/*     each of the eight neighbours (independent of h in two dimensions).     */
+/*     Load vector: the lumped Q1 mass, b_i = h^2 f_i (exact for the constant */
+/*     f of Table t:p1).                                                      */
+/* ======================================================================== */
+
+void orc_spmv_q1(int n, const double *x, double *y) {
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      double v = (8.0 / 3.0) * x[j * n + i];
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (dx == 0 && dy == 0) continue;
+          const int ii = i + dx, jj = j + dy;
+          if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
+          v -= (1.0 / 3.0) * x[jj * n + ii];
+        }
+      y[j * n + i] = v;
+    }
+}
+
+void orc_q1_load(int n, double h, const double *f, double *b) {
+  for (int k = 0; k < n * n; ++k) b[k] = h * h * f[k];
+}
+
+/* The FMM-BEM preconditioner inverts the continuous operator, so on a Q1 residual r (a
+ * functional, r_i = int r phi_i) it acts on the finite-element function whose coefficients
+ * solve M c = r, M the consistent Q1 mass matrix of the interior nodes.  On the uniform grid
+ * M = h^2 (M1 (x) M1) with M1 = tridiag(1, 4, 1)/6, so c follows from tridiagonal solves
+ * along every row and then every column (Thomas algorithm). */
+static void tridiag_141_solve(int n, double *x, int stride, double *cp) {
+  /* (1/6) tridiag(1, 4, 1) y = x, in place, elements x[k stride] */
+  double prev = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double den = 4.0 / 6.0 - (k ? (1.0 / 6.0) * cp[k - 1] : 0.0);
+    cp[k] = (1.0 / 6.0) / den;
+    prev = (x[(int64_t)k * stride] - (k ? (1.0 / 6.0) * prev : 0.0)) / den;
+    x[(int64_t)k * stride] = prev;
+  }
+  for (int k = n - 2; k >= 0; --k) x[(int64_t)k * stride] -= cp[k] * x[(int64_t)(k + 1) * stride];
+}
+
+void orc_q1_mass_solve(int n, double h, const double *r, double *c) {
+  double *cp = malloc(sizeof(double) * n);
+  for (int k = 0; k < n * n; ++k) c[k] = r[k] / (h * h);
+  for (int j = 0; j < n; ++j) tridiag_141_solve(n, c + (int64_t)j * n, 1, cp);  /* rows */
+  for (int i = 0; i < n; ++i) tridiag_141_solve(n, c + i, n, cp);              /* columns */
+  free(cp);
+}
+
+/* ======================================================================== */
 /* 2. Green's function and the volume operator (Sec. 4.2 Eq. eq:green,       */
 /*    Sec. 5.1 Eq. e:volume_integral).                                        */
 /*    (V r)_i = sum_j h^2 r_j G_ij,  G_ij = -(1/2pi) ln|x_i - x_j|.           */
@@ -518,6 +616,11 @@ typedef struct {
   double *LU;
   int32_t *piv;
   int lu_ok;
+  /* operator of the Krylov solves: 0 five-point (Eq. e:axb), 1 five-point with the
+   * variable coefficient acoef (Sec. 6.4), 2 Q1 stiffness (Sec. 6.1), whose residuals
+   * the preconditioner takes through the inverse Q1 mass matrix (orc_q1_mass_solve) */
+  int op;
+  double *acoef;
 } orc_prob;
 
 static int64_t lev_off(int l) { return ((((int64_t)1) << (2 * l)) - 1) / 3; }
@@ -676,6 +779,8 @@ orc_prob *orc_create(int n, double x0, double y0, double side, int leaf_max, int
   P->piv = malloc(sizeof(int32_t) * NG);
   orc_bem_matrices(n, x0, y0, side, P->LU, NULL);
   P->lu_ok = (orc_lu(NG, P->LU, P->piv) == 0);
+  P->op = 0;
+  P->acoef = NULL;
   return P;
 }
 
@@ -684,7 +789,7 @@ void orc_destroy(orc_prob *P) {
   free(P->keys); free(P->perm); free(P->cell_start);
   free(P->m2l.v); free(P->p2p.v); free(P->m2l_vb.v); free(P->p2p_vb.v);
   free(P->m2l_first); free(P->p2p_first); free(P->vb_first); free(P->pvb_first);
-  free(P->eax); free(P->LU); free(P->piv);
+  free(P->eax); free(P->LU); free(P->piv); free(P->acoef);
   free(P);
 }
 
@@ -979,14 +1084,42 @@ static double dot(int N, const double *a, const double *b) {
   return s;
 }
 
+/* Selects the operator of later solves (op 0, 1 with the (n+2)^2 coefficient a, or 2). */
+int orc_set_operator(orc_prob *P, int op, const double *a) {
+  if (op < 0 || op > 2 || (op == 1 && !a)) return 1;
+  free(P->acoef);
+  P->acoef = NULL;
+  if (op == 1) {
+    const size_t na = (size_t)(P->n + 2) * (P->n + 2);
+    P->acoef = malloc(sizeof(double) * na);
+    memcpy(P->acoef, a, sizeof(double) * na);
+  }
+  P->op = op;
+  return 0;
+}
+
+static void op_apply(orc_prob *P, const double *x, double *y) {
+  if (P->op == 1) orc_spmv5_var(P->n, P->h, P->acoef, x, y);
+  else if (P->op == 2) orc_spmv_q1(P->n, x, y);
+  else orc_spmv5(P->n, P->h, x, y);
+}
+
 static void prec_apply(orc_prob *P, int prec, const double *r, double *z) {
-  if (prec == 0) memcpy(z, r, sizeof(double) * P->N);
-  else orc_apply(P, prec == 1 ? 0 : 1, r, z, NULL, NULL, NULL, NULL, NULL);
+  if (prec == 0) {
+    memcpy(z, r, sizeof(double) * P->N);
+  } else if (P->op == 2) {  /* Q1: the preconditioner acts on the function M^{-1} r */
+    double *c = malloc(sizeof(double) * P->N);
+    orc_q1_mass_solve(P->n, P->h, r, c);
+    orc_apply(P, prec == 1 ? 0 : 1, c, z, NULL, NULL, NULL, NULL, NULL);
+    free(c);
+  } else {
+    orc_apply(P, prec == 1 ? 0 : 1, r, z, NULL, NULL, NULL, NULL, NULL);
+  }
 }
 
 static double true_relres(orc_prob *P, const double *b, const double *x, double bn) {
   double *t = malloc(sizeof(double) * P->N);
-  orc_spmv5(P->n, P->h, x, t);
+  op_apply(P, x, t);
   for (int i = 0; i < P->N; ++i) t[i] = b[i] - t[i];
   double r = sqrt(dot(P->N, t, t)) / bn;
   free(t);
@@ -998,7 +1131,7 @@ static int solve_cg(orc_prob *P, int prec, int maxit, double rtol, const double 
   const int N = P->N;
   double *r = malloc(sizeof(double) * N * 4), *zz = r + N, *pp = zz + N, *qq = pp + N;
   double bn = sqrt(dot(N, b, b));
-  orc_spmv5(P->n, P->h, x, r);
+  op_apply(P, x, r);
   for (int i = 0; i < N; ++i) r[i] = b[i] - r[i];
   int it = 0, conv = 0;
   if (hist) hist[0] = sqrt(dot(N, r, r)) / bn;
@@ -1007,7 +1140,7 @@ static int solve_cg(orc_prob *P, int prec, int maxit, double rtol, const double 
   memcpy(pp, zz, sizeof(double) * N);
   double rz = dot(N, r, zz);
   while (!conv && it < maxit) {
-    orc_spmv5(P->n, P->h, pp, qq);
+    op_apply(P, pp, qq);
     double alpha = rz / dot(N, pp, qq);
     for (int i = 0; i < N; ++i) { x[i] += alpha * pp[i]; r[i] -= alpha * qq[i]; }
     ++it;
@@ -1038,7 +1171,7 @@ static int solve_gmres(orc_prob *P, int flexible, int prec, int restart, int max
   int it = 0, conv = 0;
   if (hist) hist[0] = 1.0;
   for (;;) {
-    orc_spmv5(P->n, P->h, x, w);
+    op_apply(P, x, w);
     for (int i = 0; i < N; ++i) w[i] = b[i] - w[i];
     double beta = sqrt(dot(N, w, w));
     if (beta / bn <= rtol) { conv = 1; break; }
@@ -1050,7 +1183,7 @@ static int solve_gmres(orc_prob *P, int flexible, int prec, int restart, int max
     for (; j < m && it < maxit; ++j) {
       double *zj = flexible ? Z + (int64_t)j * N : Z;
       prec_apply(P, prec, V + (int64_t)j * N, zj);
-      orc_spmv5(P->n, P->h, zj, w);
+      op_apply(P, zj, w);
       for (int i = 0; i <= j; ++i) { /* modified Gram-Schmidt */
         double hij = dot(N, w, V + (int64_t)i * N);
         H[i * m + j] = hij;

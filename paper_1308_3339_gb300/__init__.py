@@ -88,6 +88,12 @@ class FmmPreconditioner:
         """Near-field engine: "tc" (tensor cores where the grid allows it) or "simt"."""
         check(self.lib.fmmpc_set_p2p_engine(self._h, {"tc": 0, "simt": 1}[engine]), self._h)
 
+    def set_operator(self, op: str = "fd5", a=None):
+        """Operator of the solves (fmmpc_set_operator): "fd5", "fd5_var" with the diffusion
+        coefficient a (float64 CUDA tensor of (n+2)^2 full-grid node values), or "q1"."""
+        ap = C.c_void_p(0) if a is None else _ptr(a)
+        check(self.lib.fmmpc_set_operator(self._h, _lib.OPERATOR[op], ap), self._h)
+
     def set_graphs(self, on: bool = True):
         check(self.lib.fmmpc_set_graphs(self._h, 1 if on else 0), self._h)
 

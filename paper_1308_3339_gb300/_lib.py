@@ -16,6 +16,7 @@ ERRORS = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "NAN", 
 PREC = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_tf32": 3}
 METHOD = {"cg": 0, "gmres": 1, "fgmres": 2}
 PART = {"full": 0, "vr": 1, "near": 2, "vcol": 3, "q": 4}
+OPERATOR = {"fd5": 0, "fd5_var": 1, "q1": 2}
 QUERY = {"L": 0, "leaf_side": 1, "n_m2l": 2, "n_p2p": 3, "n_m2l_vb": 4, "n_p2p_vb": 5, "NG": 6,
          "n_cell": 7, "N": 8, "stencil": 9, "launches": 10, "device_bytes": 11, "device_errors": 12,
          "tc_p2p": 13, "tc_m2l": 14}
@@ -64,6 +65,7 @@ SIGNATURES = {
     "fmmpc_query": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "fmmpc_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
     "fmmpc_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fmmpc_set_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fmmpc_set_p2p_engine": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),

@@ -366,6 +366,36 @@ int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine) {
   return FMMPC_OK;
 }
 
+int fmmpc_set_operator(fmmpc_handle *h, int32_t op, const double *a_dev) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(op >= FMMPC_OP_FD5 && op <= FMMPC_OP_Q1, "set_operator: unknown operator");
+    require(op != FMMPC_OP_FD5_VAR || a_dev, "set_operator: the variable-coefficient operator needs a");
+    const int n = h->g.n;
+    if (op == FMMPC_OP_FD5_VAR) {
+      const size_t na = (size_t)(n + 2) * (n + 2);
+      if (!h->acoef) h->acoef = h->pool.get<double>(na);
+      FMMPC_CUDA(cudaMemcpyAsync(h->acoef, a_dev, sizeof(double) * na, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (op == FMMPC_OP_Q1 && !h->q1tab) {
+      // Thomas coefficients of (1/6) tridiag(1, 4, 1): cp[k] and 1 / (pivot k)
+      std::vector<double> t(2 * (size_t)n);
+      double cprev = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double den = 4.0 / 6.0 - (k ? cprev / 6.0 : 0.0);
+        t[n + k] = 1.0 / den;
+        cprev = t[k] = (1.0 / 6.0) / den;
+      }
+      h->q1tab = h->pool.get<double>(t.size());
+      FMMPC_CUDA(cudaMemcpyAsync(h->q1tab, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, h->stream));
+      FMMPC_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    h->op = op;
+    clear_solve_graphs(*h);  // they hold the previous operator
+    return FMMPC_OK;
+  });
+}
+
 int fmmpc_set_graphs(fmmpc_handle *h, int32_t on) {
   if (!h) return FMMPC_ERR_INVALID;
   h->graphs = on != 0;

@@ -121,6 +121,10 @@ struct fmmpc_handle {
   fmmpc::TcP2P tcp{};
   fmmpc::TcM2L tcm{};
   int p2p_engine = 0;       // 0: tensor cores where eligible, 1: CUDA cores
+  // operator of the Krylov solves (fmmpc_set_operator): 0 five-point, 1 five-point with the
+  // coefficient acoef [(n+2)^2], 2 Q1 stiffness (q1tab: Thomas coefficients of the mass solve)
+  int op = 0;
+  double *acoef = nullptr, *q1tab = nullptr;
   int64_t launches = 0;     // kernel launches of the last apply
   // optional per-stage CUDA-event timing of the apply (fmmpc_set_timing)
   static constexpr int NSTAGE = 11;
@@ -149,6 +153,8 @@ void apply_fmm(fmmpc_handle &H, int part, const double *r, double *out, int nrhs
 // the apply's kernels issued on H.stream one by one (no graph of its own; used inside captures)
 void apply_fmm_eager(fmmpc_handle &H, int part, const double *r, double *out, int nrhs);
 void clear_solve_graphs(fmmpc_handle &H);
+void precond_op(fmmpc_handle &H, const double *r, double *z, double *scratch, int nrhs, bool in_capture);
+void q1_mass_solve(fmmpc_handle &H, const double *r, double *c, int nrhs);
 int solve_graphed(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs, const fmmpc_solve_opts &o,
                   fmmpc_solve_info &info);
 cudaGraphExec_t solve_graph(std::vector<fmmpc_handle *> &hs, int method, int m, int nrhs, bool has_g);

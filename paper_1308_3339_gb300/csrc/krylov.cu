@@ -21,38 +21,118 @@ constexpr int MAXJ = 64;         // largest Krylov basis handled by the fused ke
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-__global__ void k_spmv5(int n, double s, int64_t total, const double *__restrict__ x,
-                        double *__restrict__ y) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
+// The operator A of the solves (fmmpc_set_operator), zero Dirichlet values outside the
+// n x n block: 0 the five-point stencil (1/h^2)(4 u - neighbours) of Eq. e:axb; 1 the
+// five-point flux form of -div(a grad u) (Sec. 4.4, Sec. 6.4), the coefficient of a face
+// the mean of a at its two nodes, a at the (n+2)^2 nodes of the full grid; 2 the Q1
+// stiffness of -lap (Sec. 6.1), 8/3 on the diagonal and -1/3 for the eight neighbours.
+struct OpDev {
+  int op, n;
+  double s;          // 1/h^2
+  const double *a;   // op 1: [(n+2)^2] coefficient
+};
+
+OpDev op_of(const fmmpc_handle &H) { return OpDev{H.op, H.g.n, 1.0 / (H.g.h * H.g.h), H.acoef}; }
+
+__device__ __forceinline__ double op_at(const OpDev &o, const double *__restrict__ x, int64_t t) {
+  const int n = o.n;
   const int64_t N = (int64_t)n * n;
   const int64_t k = t % N;
   const int i = (int)(k % n), j = (int)(k / n);
+  if (o.op == 2) {
+    double nb = 0.0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (dx == 0 && dy == 0) continue;
+        const int ii = i + dx, jj = j + dy;
+        if (ii >= 0 && ii < n && jj >= 0 && jj < n) nb += x[t + (int64_t)dy * n + dx];
+      }
+    return (8.0 / 3.0) * x[t] - (1.0 / 3.0) * nb;
+  }
+  if (o.op == 1) {
+    const int W = n + 2;
+    const int64_t I = (int64_t)(j + 1) * W + (i + 1);
+    const double ac = o.a[I];
+    const double aE = 0.5 * (ac + o.a[I + 1]), aW = 0.5 * (ac + o.a[I - 1]);
+    const double aN = 0.5 * (ac + o.a[I + W]), aS = 0.5 * (ac + o.a[I - W]);
+    double v = (aE + aW + aN + aS) * x[t];
+    if (i > 0) v -= aW * x[t - 1];
+    if (i < n - 1) v -= aE * x[t + 1];
+    if (j > 0) v -= aS * x[t - n];
+    if (j < n - 1) v -= aN * x[t + n];
+    return o.s * v;
+  }
   double v = 4.0 * x[t];
   if (i > 0) v -= x[t - 1];
   if (i < n - 1) v -= x[t + 1];
   if (j > 0) v -= x[t - n];
   if (j < n - 1) v -= x[t + n];
-  y[t] = s * v;
+  return o.s * v;
 }
 
-// b = f + g / h^2 at the stencil neighbours outside the interior block (Eq. e:pbound)
-__global__ void k_fold_rhs(int n, double s, int64_t total, const double *__restrict__ f,
-                           const double *__restrict__ g, double *__restrict__ b) {
+__global__ void k_spmv5(OpDev o, int64_t total, const double *__restrict__ x, double *__restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) y[t] = op_at(o, x, t);
+}
+
+// Right-hand side of A u = b: op 0, b = f + g / h^2 at the stencil neighbours outside the
+// interior block (Eq. e:pbound); op 1, the same with the face coefficient; op 2, the lumped
+// Q1 load b = h^2 f (boundary data is rejected on the host for op 2).
+__global__ void k_fold_rhs(OpDev o, int64_t total, const double *__restrict__ f, const double *__restrict__ g,
+                           double *__restrict__ b) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
+  const int n = o.n;
+  const double s = o.s;
   const int64_t N = (int64_t)n * n;
   const int64_t rhs = t / N, k = t % N;
   const int i = (int)(k % n), j = (int)(k / n);
+  if (o.op == 2) {
+    b[t] = f[t] / s;
+    return;
+  }
   double v = f[t];
   if (g) {
     const double *gg = g + rhs * 4 * n;
-    if (j == 0) v += s * gg[i];
-    if (i == n - 1) v += s * gg[n + j];
-    if (j == n - 1) v += s * gg[2 * n + (n - 1 - i)];
-    if (i == 0) v += s * gg[3 * n + (n - 1 - j)];
+    double fe = 1.0, fw = 1.0, fn = 1.0, fs = 1.0;  // face coefficients toward the boundary
+    if (o.op == 1) {
+      const int W = n + 2;
+      const int64_t I = (int64_t)(j + 1) * W + (i + 1);
+      fe = 0.5 * (o.a[I] + o.a[I + 1]);
+      fw = 0.5 * (o.a[I] + o.a[I - 1]);
+      fn = 0.5 * (o.a[I] + o.a[I + W]);
+      fs = 0.5 * (o.a[I] + o.a[I - W]);
+    }
+    if (j == 0) v += s * fs * gg[i];
+    if (i == n - 1) v += s * fe * gg[n + j];
+    if (j == n - 1) v += s * fn * gg[2 * n + (n - 1 - i)];
+    if (i == 0) v += s * fw * gg[3 * n + (n - 1 - j)];
   }
   b[t] = v;
+}
+
+// Solves with (1/6) tridiag(1, 4, 1) along every row (cols = 0) or column (cols = 1) of every
+// right-hand side: dst = scale * src on the way (src may alias dst).  cp[k], iden[k]: the
+// Thomas coefficients of the constant matrix, formed once on the host.
+__global__ void k_mass_sweep(int n, int nrhs, int cols, double scale, const double *__restrict__ src,
+                             double *__restrict__ dst, const double *__restrict__ cp,
+                             const double *__restrict__ iden) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * n) return;
+  const int64_t N = (int64_t)n * n;
+  const int64_t rhs = t / n, line = t % n;
+  const int64_t base = rhs * N + (cols ? line : line * n), st = cols ? n : 1;
+  double y = 0.0;
+  for (int k = 0; k < n; ++k) {
+    y = (scale * src[base + k * st] - (1.0 / 6.0) * y) * iden[k];
+    dst[base + k * st] = y;
+  }
+  for (int k = n - 2; k >= 0; --k) {
+    y = dst[base + k * st] - cp[k] * y;
+    dst[base + k * st] = y;
+  }
 }
 
 // partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
@@ -197,6 +277,33 @@ __global__ void k_cg_p(int64_t N, int nrhs, const double *__restrict__ beta, con
   p[t] = fma(beta[t / N], p[t], z[t]);
 }
 
+}  // namespace
+
+// c = M^{-1} r for the consistent Q1 mass matrix M = h^2 (M1 (x) M1) of the interior nodes:
+// tridiagonal solves along every row, then every column (the preconditioner of the Q1
+// operator acts on the finite-element function of the residual, Sec. 6.1).
+void q1_mass_solve(fmmpc_handle &H, const double *r, double *c, int nrhs) {
+  const int n = H.g.n;
+  const double h = H.g.h;
+  k_mass_sweep<<<nblk((int64_t)nrhs * n), 256, 0, H.stream>>>(n, nrhs, 0, 1.0 / (h * h), r, c, H.q1tab, H.q1tab + n);
+  k_mass_sweep<<<nblk((int64_t)nrhs * n), 256, 0, H.stream>>>(n, nrhs, 1, 1.0, c, c, H.q1tab, H.q1tab + n);
+  FMMPC_LAUNCH_CHECK();
+}
+
+// z = P^{-1} r; with the Q1 operator, P^{-1} M^{-1} r through scratch (which may alias r when
+// r is not needed afterwards).  in_capture: the apply's kernels go into the stream being
+// captured instead of its own graph.
+void precond_op(fmmpc_handle &H, const double *r, double *z, double *scratch, int nrhs, bool in_capture) {
+  if (H.op == 2) {
+    q1_mass_solve(H, r, scratch, nrhs);
+    r = scratch;
+  }
+  if (in_capture) apply_fmm_eager(H, PART_FULL, r, z, nrhs);
+  else apply_fmm(H, PART_FULL, r, z, nrhs);
+}
+
+namespace {
+
 struct Ctx {
   fmmpc_handle &H;
   int64_t N;
@@ -268,7 +375,7 @@ void to_host(Ctx &c, const double *d, size_t count) {
   FMMPC_CUDA(cudaStreamSynchronize(c.s));
 }
 
-void precond(Ctx &c, const double *in, double *out) { apply_fmm(c.H, PART_FULL, in, out, c.nrhs); }
+void precond(Ctx &c, const double *in, double *out) { precond_op(c.H, in, out, c.H.kw.zin, c.nrhs, false); }
 
 void residual(Ctx &c, const double *b, const double *x, double *r) {
   spmv5(c.H, x, r, c.nrhs);
@@ -498,7 +605,7 @@ int pcg(Ctx &c, int maxit, double rtol, const double *b, double *x, fmmpc_solve_
 
 void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs) {
   const int64_t total = (int64_t)H.g.n * H.g.n * nrhs;
-  k_spmv5<<<nblk(total), 256, 0, H.stream>>>(H.g.n, 1.0 / (H.g.h * H.g.h), total, x, y);
+  k_spmv5<<<nblk(total), 256, 0, H.stream>>>(op_of(H), total, x, y);
   FMMPC_LAUNCH_CHECK();
 }
 
@@ -516,6 +623,7 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
     ~GraphsGuard() { H.graphs = saved; }
   } guard{H, H.graphs};
   require(o.use_graphs >= 0 && o.use_graphs <= 2, "use_graphs must be 0, 1 or 2");
+  require(!(g && H.op == 2), "boundary data is not supported with the Q1 operator (its stencil needs the corners)");
   H.graphs = o.use_graphs == 1;
   Ctx c{H, (int64_t)H.g.n * H.g.n, nrhs, H.stream};
   const int64_t NR = c.N * nrhs;
@@ -523,7 +631,7 @@ int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs
   if (o.use_graphs == 2) {
     st = solve_graphed(H, f, g, u, nrhs, o, info);  // one graph, device-side convergence
   } else {
-    k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(H.g.n, 1.0 / (H.g.h * H.g.h), NR, f, g, H.kw.b);
+    k_fold_rhs<<<nblk(NR), 256, 0, c.s>>>(op_of(H), NR, f, g, H.kw.b);
     FMMPC_LAUNCH_CHECK();
     if (o.method == FMMPC_CG) st = pcg(c, o.maxit, o.rtol, H.kw.b, u, info);
     else st = gmres(c, o.method == FMMPC_FGMRES, m, o.maxit, o.rtol, H.kw.b, u, info);
@@ -590,7 +698,8 @@ int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const
     H.graphs = o.use_graphs != 0;
     ensure_ws(H, m + 1, true);
     const int64_t N = (int64_t)H.g.n * H.g.n;
-    k_fold_rhs<<<nblk(N), 256, 0, H.stream>>>(H.g.n, 1.0 / (H.g.h * H.g.h), N, f[p], gb ? gb[p] : nullptr, H.kw.b);
+    require(!(gb && gb[p]) || H.op != 2, "boundary data is not supported with the Q1 operator");
+    k_fold_rhs<<<nblk(N), 256, 0, H.stream>>>(op_of(H), N, f[p], gb ? gb[p] : nullptr, H.kw.b);
     FMMPC_LAUNCH_CHECK();
     norm2_async(H, H.kw.b, H.kw.dots, 0);
     BatchState &s = st[p];
@@ -648,7 +757,7 @@ int solve_batched(std::vector<fmmpc_handle *> &hs, const double *const *f, const
         const int64_t N = (int64_t)H.g.n * H.g.n, vs = N * H.nrhs_max;
         Ctx c{H, N, 1, H.stream};
         double *vj = H.kw.V + (int64_t)s.j * vs, *zj = H.kw.Z + (int64_t)s.j * vs;
-        apply_fmm(H, PART_FULL, vj, zj, 1);
+        precond_op(H, vj, zj, H.kw.zin, 1, false);
         spmv5(H, zj, H.kw.w, 1);
         double *d1 = H.kw.dots, *hsum = H.kw.dots + MAXJ;
         FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * MAXJ, H.stream));
@@ -780,22 +889,13 @@ __global__ void k_gcopy_col(const int *__restrict__ ctl, int64_t NR, const doubl
   if (t < NR) dst[t] = base[(int64_t)ctl[KC_J] * vs + t];
 }
 
-// y = A x (5-point) and, if Zb, Z_j = x
-__global__ void k_gspmv_store(const int *__restrict__ ctl, int n, double s, int64_t total, const double *__restrict__ x,
+// y = A x and, if Zb, Z_j = x
+__global__ void k_gspmv_store(const int *__restrict__ ctl, OpDev o, int64_t total, const double *__restrict__ x,
                               double *__restrict__ y, double *__restrict__ Zb, int64_t vs) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
-  const int64_t N = (int64_t)n * n;
-  const int64_t k = t % N;
-  const int i = (int)(k % n), j = (int)(k / n);
-  const double xc = x[t];
-  double v = 4.0 * xc;
-  if (i > 0) v -= x[t - 1];
-  if (i < n - 1) v -= x[t + 1];
-  if (j > 0) v -= x[t - n];
-  if (j < n - 1) v -= x[t + n];
-  y[t] = s * v;
-  if (Zb) Zb[(int64_t)ctl[KC_J] * vs + t] = xc;
+  y[t] = op_at(o, x, t);
+  if (Zb) Zb[(int64_t)ctl[KC_J] * vs + t] = x[t];
 }
 
 // partial[rhs][i][blk] = slice sums of <V_i[rhs], w[rhs]> for i <= ctl[KC_J]
@@ -1182,9 +1282,12 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
   cudaGraphConditionalHandle hloop;
   FMMPC_CUDA(cudaGraphConditionalHandleCreate(&hloop, G, 0, cudaGraphCondAssignDefault));
   Ctx c{H, N, nrhs, cs};
-  auto precond = [&](const double *in, double *out) { apply_fmm_eager(H, PART_FULL, in, out, nrhs); };
+  const OpDev od = op_of(H);
+  auto precond = [&](const double *in, double *out, double *scratch) {
+    precond_op(H, in, out, scratch, nrhs, true);
+  };
   auto residual_c = [&](const double *b, const double *x, double *r) {
-    k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, x, r);
+    k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(od, NR, x, r);
     k_resid<<<nblk(NR), 256, 0, H.stream>>>(NR, b, r);
     FMMPC_LAUNCH_CHECK();
   };
@@ -1192,14 +1295,14 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
   const std::vector<cudaGraphNode_t> none;
   auto f_init = capture_into(H, cs, G, none, [&] {
     c.s = H.stream;
-    k_fold_rhs<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, K.fin, has_g ? K.gin : nullptr, K.b);
+    k_fold_rhs<<<nblk(NR), 256, 0, H.stream>>>(od, NR, K.fin, has_g ? K.gin : nullptr, K.b);
     gnorm2(c, K.b);
     k_ginit<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
     residual_c(K.b, K.x, K.r);
     gnorm2(c, K.r);
     if (method == FMMPC_CG) {
       k_cg_init<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
-      precond(K.r, K.w);
+      precond(K.r, K.w, K.zin);
       k_copy<<<nblk(NR), 256, 0, H.stream>>>(NR, K.w, K.V);  // p = z
       gdot(c, K.r, K.w, K.dots + (size_t)nrhs * MAXJ);     // <r, z> in the second dots block
     } else {
@@ -1222,7 +1325,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     double *pq = K.dots + (size_t)2 * nrhs * MAXJ;
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
-      k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(H.g.n, s, NR, p, q);
+      k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(od, NR, p, q);
       gdot(c, p, q, pq);
       k_cg_alpha<<<1, 64, 0, H.stream>>>(st, nrhs, rz_old, pq);
       k_cg_xr<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, p, q, K.x, K.r);
@@ -1233,7 +1336,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
     capture_into(H, cs, ifb, none, [&] {
       c.s = H.stream;
-      precond(K.r, z);
+      precond(K.r, z, K.zin);
       gdot(c, K.r, z, K.dots);
       k_cg_beta<<<1, 64, 0, H.stream>>>(st, nrhs, K.dots, rz_old);
       k_cg_p<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, z, p);
@@ -1247,8 +1350,8 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
       k_gcopy_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, NR, K.V, vs, K.t);  // v_j into a fixed buffer
-      precond(K.t, K.zin);
-      k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, H.g.n, s, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
+      precond(K.t, K.zin, K.t);
+      k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, od, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
       FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nrhs * MAXJ, H.stream));
       dim3 grid(RED_BLOCKS, nrhs);
       for (int pass = 0; pass < 2; ++pass) {
@@ -1269,7 +1372,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       } else {
         FMMPC_CUDA(cudaMemsetAsync(K.t, 0, sizeof(double) * NR, H.stream));
         k_gmaxpy<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.V, vs, K.scal, K.t);
-        precond(K.t, K.w);
+        precond(K.t, K.w, K.t);
         k_add<<<nblk(NR), 256, 0, H.stream>>>(NR, K.w, K.x);
       }
       residual_c(K.b, K.x, K.r);

@@ -15,6 +15,8 @@ Recipes:
 * ``batched_sides``: grid sides of the 64 uneven problems,
   ``default_rng(0).choice([128, 256, 512, 1024, 2048], 64)``.
 * ``random_field``: i.i.d. N(0,1) node values (parity tests).
+* ``diffusion_coefficient``: a = 1 + mu sin(m pi x) sin(k pi y) at the (n+2)^2 nodes of the
+  full grid, boundary ring included (the variable-coefficient problems).
 """
 from __future__ import annotations
 
@@ -73,3 +75,13 @@ def boundary_values(n: int, fn, x0: float = 0.0, y0: float = 0.0, side: float = 
     top = fn(x0 + t[::-1], np.full(n, y1))
     left = fn(np.full(n, x0), y0 + t[::-1])
     return np.concatenate([bottom, right, top, left])
+
+
+def diffusion_coefficient(n: int, mu: float, m: int, k: int, x0: float = 0.0, y0: float = 0.0,
+                          side: float = 1.0) -> np.ndarray:
+    """a = 1 + mu sin(m pi x) sin(k pi y) at the (n+2)^2 full-grid nodes, row-major, so that
+    interior node (i, j) sits at (j+1)(n+2) + (i+1)."""
+    h = side / (n + 1)
+    t = np.arange(n + 2) * h
+    X, Y = np.meshgrid(x0 + t, y0 + t)
+    return (1.0 + mu * np.sin(m * np.pi * X) * np.sin(k * np.pi * Y)).ravel()
