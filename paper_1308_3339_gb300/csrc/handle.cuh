@@ -87,6 +87,7 @@ struct KrylovWs {
   int *mask = nullptr;     // [nrhs] active right-hand sides
   // device-resident state of the graph solves (krylov.cu)
   int *g_ctl = nullptr, *g_done = nullptr, *g_iters = nullptr;
+  int *g_cnt = nullptr;  // [nrhs] arrival counters of the fused reductions (zero between launches)
   double *g_H = nullptr, *g_cs = nullptr, *g_sn = nullptr, *g_g = nullptr, *g_bn = nullptr, *g_rel = nullptr,
          *g_sc = nullptr, *g_rtol = nullptr;
 };

@@ -343,7 +343,9 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
   k.g_rel = H.kpool.get<double>(nr);
   k.g_sc = H.kpool.get<double>(nr);
   k.g_rtol = H.kpool.get<double>(1);
+  k.g_cnt = H.kpool.get<int>(nr);
   FMMPC_CUDA(cudaMemsetAsync(k.g_ctl, 0, sizeof(int) * 16, H.stream));
+  FMMPC_CUDA(cudaMemsetAsync(k.g_cnt, 0, sizeof(int) * nr, H.stream));
   k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 4);
   k.part = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * RED_BLOCKS);
   k.scal = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
@@ -883,12 +885,6 @@ enum {
   KC_COUNT = 8
 };
 
-__global__ void k_gcopy_col(const int *__restrict__ ctl, int64_t NR, const double *__restrict__ base, int64_t vs,
-                            double *__restrict__ dst) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < NR) dst[t] = base[(int64_t)ctl[KC_J] * vs + t];
-}
-
 // y = A x and, if Zb, Z_j = x
 __global__ void k_gspmv_store(const int *__restrict__ ctl, OpDev o, int64_t total, const double *__restrict__ x,
                               double *__restrict__ y, double *__restrict__ Zb, int64_t vs) {
@@ -989,12 +985,94 @@ __global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const
   x[t] = v;
 }
 
-// V_{ctl[KC_J]}[rhs] = sc[rhs] w[rhs]
+// V_{ctl[KC_J]}[rhs] = sc[rhs] w[rhs], and the same into t2 (the next preconditioner input)
 __global__ void k_gscale_col(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ sc,
-                             const double *__restrict__ w, double *__restrict__ V, int64_t vs) {
+                             const double *__restrict__ w, double *__restrict__ V, int64_t vs, double *__restrict__ t2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  V[(int64_t)ctl[KC_J] * vs + t] = sc[t / N] * w[t];
+  const double v = sc[t / N] * w[t];
+  V[(int64_t)ctl[KC_J] * vs + t] = v;
+  if (t2) t2[t] = v;
+}
+
+// One pass of classical Gram-Schmidt over the basis V_0 .. V_j (j = ctl[KC_J], at most 31)
+// fused with the reduction it needs, per right-hand side (grid y):
+//   MODE 0: d = V^T w;                      out = d, hsum = d
+//   MODE 1: w -= V c (c = the first pass);  out = V^T w (new w), hsum += out
+//   MODE 2: w -= V c (c = the second pass); out[0] = |w|^2
+// Every block writes its slice sums to part; the last block to arrive (counter cnt[rhs])
+// adds them in a fixed order, so the result does not depend on the arrival order.
+template <int MODE>
+__global__ void __launch_bounds__(RED_THREADS) k_gcgs(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
+                                                      int64_t vs, double *__restrict__ w, const double *__restrict__ c,
+                                                      double *__restrict__ part, int *__restrict__ cnt,
+                                                      double *__restrict__ out, double *__restrict__ hsum) {
+  constexpr int NV = 32;
+  __shared__ double red[RED_THREADS / 32][NV];
+  __shared__ double cs[NV];
+  __shared__ int last;
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nv = ctl[KC_J] + 1;
+  const int nout = MODE == 2 ? 1 : nv;
+  if (MODE != 0 && threadIdx.x < NV) cs[threadIdx.x] = threadIdx.x < nv ? c[rhs * MAXJ + threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  const double *Vr = V + (int64_t)rhs * N;
+  double *wr = w + (int64_t)rhs * N;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    double vv[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) vv[q] = q < nv ? Vr[(int64_t)q * vs + k] : 0.0;
+    double x = wr[k];
+    if (MODE != 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) x = fma(-cs[q], vv[q], x);
+      wr[k] = x;
+    }
+    if (MODE == 2) {
+      acc[0] = fma(x, x, acc[0]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] = fma(vv[q], x, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (q < nout) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nout) {
+    double sum = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
+    part[((int64_t)rhs * MAXJ + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&cnt[rhs], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = wid; i < nout; i += RED_THREADS / 32) {
+    const double *pp = part + ((int64_t)rhs * MAXJ + i) * gridDim.x;
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(pp + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      out[rhs * MAXJ + i] = s;
+      if (MODE == 0) hsum[rhs * MAXJ + i] = s;
+      if (MODE == 1) hsum[rhs * MAXJ + i] += s;
+    }
+  }
+  if (threadIdx.x == 0) cnt[rhs] = 0;
 }
 
 // Per-right-hand-side state of the graph-resident (F)GMRES.
@@ -1307,7 +1385,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       gdot(c, K.r, K.w, K.dots + (size_t)nrhs * MAXJ);     // <r, z> in the second dots block
     } else {
       k_grestart<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
-      k_scale<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, K.r, K.V);
+      k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.r, K.V, vs, K.t);
     }
     k_gcond<<<1, 1, 0, H.stream>>>(ctl, hloop);
     FMMPC_LAUNCH_CHECK();
@@ -1347,21 +1425,32 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       FMMPC_LAUNCH_CHECK();
     });
   } else {
+    const bool fused = m <= 31;  // the fused CGS kernels hold up to 32 basis vectors in registers
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
-      k_gcopy_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, NR, K.V, vs, K.t);  // v_j into a fixed buffer
-      precond(K.t, K.zin, K.t);
+      precond(K.t, K.zin, K.t);  // K.t holds v_j (written with V_j by the previous step)
       k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, od, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
-      FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nrhs * MAXJ, H.stream));
       dim3 grid(RED_BLOCKS, nrhs);
-      for (int pass = 0; pass < 2; ++pass) {
-        k_gmdot_partial<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part);
-        k_gmdot_final<<<nrhs, 256, 0, H.stream>>>(ctl, RED_BLOCKS, K.part, K.dots, hsum);
-        k_gmupdate<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, pass ? K.part : nullptr);
+      // one block per SM: the fused kernels hold up to 32 basis values and 32 sums per thread
+      int nsm = 0;
+      FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
+      const dim3 fgrid((unsigned)std::min(std::max(nsm, 1), RED_BLOCKS), nrhs);
+      if (fused) {
+        double *d2 = K.dots + (size_t)2 * nrhs * MAXJ;
+        k_gcgs<0><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, nullptr, K.part, K.g_cnt, K.dots, hsum);
+        k_gcgs<1><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.dots, K.part, K.g_cnt, d2, hsum);
+        k_gcgs<2><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, d2, K.part, K.g_cnt, wsq, nullptr);
+      } else {
+        FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nrhs * MAXJ, H.stream));
+        for (int pass = 0; pass < 2; ++pass) {
+          k_gmdot_partial<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part);
+          k_gmdot_final<<<nrhs, 256, 0, H.stream>>>(ctl, RED_BLOCKS, K.part, K.dots, hsum);
+          k_gmupdate<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, pass ? K.part : nullptr);
+        }
+        k_mdot_final<<<dim3(nrhs, 1), 256, 0, H.stream>>>(1, RED_BLOCKS, K.part, wsq, nullptr, 0);
       }
-      k_mdot_final<<<dim3(nrhs, 1), 256, 0, H.stream>>>(1, RED_BLOCKS, K.part, wsq, nullptr, 0);
       k_gtail<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, m, hsum, wsq, K.scal, hif);
-      k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs);
+      k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs, K.t);
       FMMPC_LAUNCH_CHECK();
     });
     cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
@@ -1378,7 +1467,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       residual_c(K.b, K.x, K.r);
       gnorm2(c, K.r);
       k_grestart<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
-      k_scale<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, K.r, K.V);
+      k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.r, K.V, vs, K.t);
       FMMPC_LAUNCH_CHECK();
     });
     capture_into(H, cs, body, {n_if}, [&] {

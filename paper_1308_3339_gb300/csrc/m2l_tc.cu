@@ -23,8 +23,9 @@
 // sums of M~_0 that carry ln rho.
 // Padding targets are computed and dropped.  The low-order terms dominate the translated
 // field and meet the large log o + ln rho, so their products are split hi + lo in the
-// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded
-// input x rounded matrix, input residual x rounded matrix, rounded input x matrix residual.
+// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 64 for BF16: every M~_k up to
+// p = 11): rounded input x rounded matrix, input residual x rounded matrix, rounded input x
+// matrix residual.
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
@@ -461,9 +462,11 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   const int L = g.L, p = g.p;
   T.kind = (H.prec == FMMPC_PREC_MIXED_TF32) ? 0 : 1;
   T.width = (2 * p + 2 <= 24) ? 24 : 32;  // outputs per class
-  // hi/lo splits of the leading multipoles in the spare K columns (24 for TF32, 32 for BF16)
-  // K capacity: TF32 32 inputs (4 steps of 8, one 128-byte row); BF16 48 (3 steps of 16)
-  const int kcap = T.kind == 0 ? 32 : 48;
+  // hi/lo splits of the leading multipoles in the spare K columns of the 128-byte row: TF32
+  // holds 32 inputs (4 K steps of 8), BF16 64 (4 K steps of 16), so at p = 10 every BF16
+  // multipole is split (2p + 4p = 60 inputs) and the BF16 form rounds none of its products
+  // below about 2^-16, for the same four K steps as TF32
+  const int kcap = T.kind == 0 ? 32 : 64;
   T.nsplit = std::max(0, std::min(p, (kcap - 2 * p) / 4));
   // offset sets by class, from the lists themselves, then checked against every list
   int *dtab = tmp.get<int>(4 * 225), *derr = tmp.get<int>(1);

@@ -27,8 +27,10 @@ def dev(a):
     return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda").contiguous()
 
 
+# restart 40 takes the unfused orthogonalisation (the fused kernels hold 32 basis vectors)
 @pytest.mark.parametrize("method,prec,restart", [("fgmres", "mixed_tf32", 30), ("fgmres", "fp32", 4),
-                                                 ("gmres", "fp64", 30), ("cg", "fp32", 30)])
+                                                 ("gmres", "fp64", 30), ("cg", "fp32", 30),
+                                                 ("fgmres", "mixed_bf16", 40)])
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_graph_solve_follows_host_loop(method, prec, restart, nrhs):
     from paper_1308_3339_gb300 import FmmPreconditioner
