@@ -143,6 +143,33 @@ int fmmpc_apply_host(fmmpc_handle *h, const double *r_host, double *z_host, int3
 int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double *out_dev,
                      int32_t n_rhs);
 
+/* The boundary-integral solution of -lap u = f in the square, u = g on its boundary
+ * (Sec. 4.1): q = du/dn from Eq. e:ubound, S q = (1/2 I + K) g - (V f)|_Gamma, then
+ * Eq. e:uinter at the nodes, u = V f + int_Gamma q G - int_Gamma g dG/dn (V f by the FMM;
+ * the double-layer term -D g through the boundary tree with the element ends as point
+ * sources of weight +-i g, and closed-form element integrals next to the boundary).  This
+ * is the preconditioner's own construction with the boundary values kept: with g = 0 it is
+ * fmmpc_apply.  Constant elements make it first-order accurate in h (Sec. 6.2).
+ * f_dev, u_dev: [n_rhs][ny][nx] FP64 device (distinct); g_dev: [n_rhs][4n] FP64 device,
+ * the Dirichlet values at the 4n element midpoints (the collocation points: side length
+ * / n apart from half an element past each corner), in the order bottom (x increasing),
+ * right (y increasing), top (x decreasing), left (y decreasing).  The boundary solve is
+ * FP64 in every form.  Uses the single-layer equations whatever fmmpc_set_bem_form set.
+ * Asynchronous on the handle's stream.  Errors: _INVALID. */
+int fmmpc_apply_bc(fmmpc_handle *h, const double *f_dev, const double *g_dev, double *u_dev, int32_t n_rhs);
+
+/* Boundary correction of the preconditioner.
+ *  FMMPC_BEM_SINGLE_LAYER (default): the paper's, Eq. e:ubound with z = 0 on Gamma, a
+ *    first-kind single-layer system S q = -(V r)|_Gamma, then z = V r + int_Gamma q G.
+ *  FMMPC_BEM_DOUBLE_LAYER: a second-kind double-layer correction with the same continuum
+ *    limit, (-1/2 I + K) mu = -(V r)|_Gamma, then z = V r + int_Gamma mu dG/dn (its inverse
+ *    formed on first selection, like S's, from the side-DFT blocks).  fmmpc_apply_part
+ *    part 4 then returns mu.
+ * Captured apply and solve graphs of the other form are dropped.  Errors: _INVALID. */
+#define FMMPC_BEM_SINGLE_LAYER 0
+#define FMMPC_BEM_DOUBLE_LAYER 1
+int fmmpc_set_bem_form(fmmpc_handle *h, int32_t form);
+
 /* y = A x with zero boundary values: the operator chosen by fmmpc_set_operator (the
  * five-point stencil of Eq. e:axb by default). */
 int fmmpc_spmv(fmmpc_handle *h, const double *x_dev, double *y_dev, int32_t n_rhs);

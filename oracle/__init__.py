@@ -94,6 +94,10 @@ def _lib():
     L.orc_export.argtypes = [vp, i, vp]
     L.orc_apply.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp]
     L.orc_apply.restype = i
+    L.orc_apply_bc.argtypes = [vp, i, vp, vp, vp, vp]
+    L.orc_apply_bc.restype = i
+    L.orc_apply_dl.argtypes = [vp, i, vp, vp, vp]
+    L.orc_apply_dl.restype = i
     L.orc_solve.argtypes = [vp, i, i, i, d, i, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.orc_solve.restype = i
     _LIB = L
@@ -363,6 +367,28 @@ class Problem:
             out.update(near=near, far=far)
         return out
 
+    def apply_bc(self, f, g, mode="fmm", with_q=False):
+        """The boundary-integral solution of -lap u = f, u = g (Sec. 4.1, Eqs. e:ubound and
+        e:uinter) at the nodes; g at the 4n element midpoints, side order."""
+        N = self.n * self.n
+        f = np.ascontiguousarray(f, np.float64).reshape(-1)
+        g = np.ascontiguousarray(g, np.float64).reshape(-1)
+        assert g.size == self.NG
+        u, q = np.empty(N), np.empty(self.NG)
+        if _lib().orc_apply_bc(self._h, 0 if mode == "direct" else 1, _p(f), _p(g), _p(u), _p(q)):
+            raise RuntimeError("oracle: singular BEM matrix")
+        return (u, q) if with_q else u
+
+    def apply_dl(self, r, mode="fmm", with_mu=False):
+        """The preconditioner with the second-kind double-layer correction:
+        (-1/2 I + K) mu = -(V r)|_Gamma, z = V r + int_Gamma mu dG/dn."""
+        N = self.n * self.n
+        r = np.ascontiguousarray(r, np.float64).reshape(-1)
+        z, mu = np.empty(N), np.empty(self.NG)
+        if _lib().orc_apply_dl(self._h, 0 if mode == "direct" else 1, _p(r), _p(z), _p(mu)):
+            raise RuntimeError("oracle: singular double-layer system")
+        return (z, mu) if with_mu else z
+
     def solve(self, b, method="fgmres", restart=30, maxit=200, rtol=1e-8, prec="fmm", x0=None,
               history=False):
         """Krylov solve of A x = b (Sec. 3.1). Returns (x, iters, true relres, converged[, hist])."""
@@ -372,7 +398,7 @@ class Problem:
         it, rr = C.c_int(0), C.c_double(0.0)
         hist = np.full(maxit + 1, np.nan)
         m = {"cg": 0, "gmres": 1, "fgmres": 2}[method]
-        pr = {"none": 0, "direct": 1, "fmm": 2}[prec]
+        pr = {"none": 0, "direct": 1, "fmm": 2, "fmm_dl": 3}[prec]
         conv = _lib().orc_solve(self._h, m, restart, maxit, rtol, pr, _p(b), _p(x), C.byref(it),
                                 C.byref(rr), _p(hist))
         if conv < 0:

@@ -616,6 +616,9 @@ typedef struct {
   double *LU;
   int32_t *piv;
   int lu_ok;
+  double *LUdl;      /* LU factors of -1/2 I + K (second-kind variant), made on first use */
+  int32_t *pivdl;
+  int dl_ok;
   /* operator of the Krylov solves: 0 five-point (Eq. e:axb), 1 five-point with the
    * variable coefficient acoef (Sec. 6.4), 2 Q1 stiffness (Sec. 6.1), whose residuals
    * the preconditioner takes through the inverse Q1 mass matrix (orc_q1_mass_solve) */
@@ -781,6 +784,9 @@ orc_prob *orc_create(int n, double x0, double y0, double side, int leaf_max, int
   P->lu_ok = (orc_lu(NG, P->LU, P->piv) == 0);
   P->op = 0;
   P->acoef = NULL;
+  P->LUdl = NULL;
+  P->pivdl = NULL;
+  P->dl_ok = 0;
   return P;
 }
 
@@ -789,7 +795,7 @@ void orc_destroy(orc_prob *P) {
   free(P->keys); free(P->perm); free(P->cell_start);
   free(P->m2l.v); free(P->p2p.v); free(P->m2l_vb.v); free(P->p2p_vb.v);
   free(P->m2l_first); free(P->p2p_first); free(P->vb_first); free(P->pvb_first);
-  free(P->eax); free(P->LU); free(P->piv); free(P->acoef);
+  free(P->eax); free(P->LU); free(P->piv); free(P->acoef); free(P->LUdl); free(P->pivdl);
   free(P);
 }
 
@@ -1070,6 +1076,82 @@ int orc_apply(orc_prob *P, int mode, const double *r, double *z, double *vr, dou
 }
 
 /* ======================================================================== */
+/* 7b. The boundary-integral solution with Dirichlet data g (Sec. 4.1):      */
+/*     Eq. e:ubound  S q = (1/2 I + K) g - (V f)|_Gamma  for q = du/dn, then   */
+/*     Eq. e:uinter  u = V f + int_Gamma q G - int_Gamma g dG/dn  in Omega,    */
+/*     g and q constant on each element (values at the midpoints).  V f by    */
+/*     the FMM (mode 1) or the direct sum (mode 0); the boundary integrals in  */
+/*     closed form, summed directly.  out_q (optional) receives q.            */
+/* ======================================================================== */
+
+int orc_apply_bc(orc_prob *P, int mode, const double *f, const double *g, double *u, double *out_q) {
+  if (!P->lu_ok) return 1;
+  const int N = P->N, NG = P->NG, n = P->n;
+  double *z = malloc(sizeof(double) * N), *vr = malloc(sizeof(double) * N);
+  double *vc = malloc(sizeof(double) * NG), *q = malloc(sizeof(double) * NG);
+  double *K = malloc(sizeof(double) * (int64_t)NG * NG);
+  orc_apply(P, mode, f, z, vr, vc, NULL, NULL, NULL);
+  orc_bem_matrices(n, P->x0, P->y0, P->side, NULL, K);
+  for (int m = 0; m < NG; ++m) {
+    double kg = 0.0;
+    for (int k = 0; k < NG; ++k) kg += K[(int64_t)m * NG + k] * g[k];
+    q[m] = 0.5 * g[m] + kg - vc[m];
+  }
+  orc_lu_solve(NG, P->LU, P->piv, q);
+  if (out_q) memcpy(out_q, q, sizeof(double) * NG);
+  const double h = P->h;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < N; ++i) {
+    const double xi = P->x0 + (i % n + 1) * h, yi = P->y0 + (i / n + 1) * h;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < NG; ++k) {
+      a += q[k] * orc_seg_int_log(xi, yi, P->eax[k], P->eay[k], P->ebx[k], P->eby[k]);
+      b += g[k] * orc_seg_int_dlog(xi, yi, P->eax[k], P->eay[k], P->ebx[k], P->eby[k]);
+    }
+    u[i] = vr[i] - a / (2.0 * PI_) + b / (2.0 * PI_);
+  }
+  free(z); free(vr); free(vc); free(q); free(K);
+  return 0;
+}
+
+/* ======================================================================== */
+/* 7c. Second-kind double-layer variant of the correction (a reading of the  */
+/*     "double-layer boundary correction"): z = V r + w with w the double-     */
+/*     layer potential of a density mu on Gamma, w(x) = int_Gamma mu dG/dn_y,  */
+/*     whose limit from inside is (-1/2 I + K) mu; w = -(V r) on Gamma gives   */
+/*     (-1/2 I + K) mu = -(V r)|_Gamma (a second-kind system), then w at the   */
+/*     nodes by the closed-form element integrals.  out_mu (optional).         */
+/* ======================================================================== */
+
+int orc_apply_dl(orc_prob *P, int mode, const double *r, double *z, double *out_mu) {
+  const int N = P->N, NG = P->NG, n = P->n;
+  if (!P->LUdl) {
+    P->LUdl = malloc(sizeof(double) * (int64_t)NG * NG);
+    P->pivdl = malloc(sizeof(int32_t) * NG);
+    orc_bem_matrices(n, P->x0, P->y0, P->side, NULL, P->LUdl);
+    for (int m = 0; m < NG; ++m) P->LUdl[(int64_t)m * NG + m] -= 0.5;
+    P->dl_ok = (orc_lu(NG, P->LUdl, P->pivdl) == 0);
+  }
+  if (!P->dl_ok || !P->lu_ok) return 1;
+  double *zz = malloc(sizeof(double) * N), *vr = malloc(sizeof(double) * N);
+  double *mu = malloc(sizeof(double) * NG);
+  orc_apply(P, mode, r, zz, vr, mu, NULL, NULL, NULL); /* mu <- (V r)|_Gamma */
+  for (int m = 0; m < NG; ++m) mu[m] = -mu[m];
+  orc_lu_solve(NG, P->LUdl, P->pivdl, mu);
+  if (out_mu) memcpy(out_mu, mu, sizeof(double) * NG);
+  const double h = P->h;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < N; ++i) {
+    const double xi = P->x0 + (i % n + 1) * h, yi = P->y0 + (i / n + 1) * h;
+    double b = 0.0;
+    for (int k = 0; k < NG; ++k) b += mu[k] * orc_seg_int_dlog(xi, yi, P->eax[k], P->eay[k], P->ebx[k], P->eby[k]);
+    z[i] = vr[i] - b / (2.0 * PI_);
+  }
+  free(zz); free(vr); free(mu);
+  return 0;
+}
+
+/* ======================================================================== */
 /* 8. Krylov methods (Sec. 3.1): CG, and GMRES(m) / FGMRES(m) with right    */
 /*    preconditioning A P^{-1} y = b, x = P^{-1} y.  Zero initial iterate and  */
 /*    a relative-residual stop (Sec. 6); the returned residual is the true     */
@@ -1104,17 +1186,22 @@ static void op_apply(orc_prob *P, const double *x, double *y) {
   else orc_spmv5(P->n, P->h, x, y);
 }
 
+/* prec: 0 none, 1 direct form, 2 FMM form, 3 FMM form with the second-kind double-layer
+ * correction (orc_apply_dl) */
 static void prec_apply(orc_prob *P, int prec, const double *r, double *z) {
   if (prec == 0) {
     memcpy(z, r, sizeof(double) * P->N);
-  } else if (P->op == 2) {  /* Q1: the preconditioner acts on the function M^{-1} r */
-    double *c = malloc(sizeof(double) * P->N);
-    orc_q1_mass_solve(P->n, P->h, r, c);
-    orc_apply(P, prec == 1 ? 0 : 1, c, z, NULL, NULL, NULL, NULL, NULL);
-    free(c);
-  } else {
-    orc_apply(P, prec == 1 ? 0 : 1, r, z, NULL, NULL, NULL, NULL, NULL);
+    return;
   }
+  double *c = NULL;
+  if (P->op == 2) {  /* Q1: the preconditioner acts on the function M^{-1} r */
+    c = malloc(sizeof(double) * P->N);
+    orc_q1_mass_solve(P->n, P->h, r, c);
+    r = c;
+  }
+  if (prec == 3) orc_apply_dl(P, 1, r, z, NULL);
+  else orc_apply(P, prec == 1 ? 0 : 1, r, z, NULL, NULL, NULL, NULL, NULL);
+  free(c);
 }
 
 static double true_relres(orc_prob *P, const double *b, const double *x, double bn) {

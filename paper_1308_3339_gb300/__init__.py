@@ -94,6 +94,19 @@ class FmmPreconditioner:
         ap = C.c_void_p(0) if a is None else _ptr(a)
         check(self.lib.fmmpc_set_operator(self._h, _lib.OPERATOR[op], ap), self._h)
 
+    def set_bem_form(self, form: str = "single_layer"):
+        """Boundary correction: "single_layer" (Eq. e:ubound, the default) or "double_layer"
+        (second kind, (-1/2 I + K) mu = -(V r)|_Gamma)."""
+        check(self.lib.fmmpc_set_bem_form(self._h, {"single_layer": 0, "double_layer": 1}[form]), self._h)
+
+    def apply_bc(self, f, g, out=None):
+        """u from Eqs. e:ubound / e:uinter with Dirichlet data g at the 4n element midpoints."""
+        import torch
+        k = self._vec(f)
+        out = torch.empty_like(f) if out is None else out
+        check(self.lib.fmmpc_apply_bc(self._h, _ptr(f), _ptr(g), _ptr(out), k), self._h)
+        return out
+
     def set_graphs(self, on: bool = True):
         check(self.lib.fmmpc_set_graphs(self._h, 1 if on else 0), self._h)
 

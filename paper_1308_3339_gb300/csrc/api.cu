@@ -253,6 +253,41 @@ int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double 
   });
 }
 
+int fmmpc_apply_bc(fmmpc_handle *h, const double *f_dev, const double *g_dev, double *u_dev, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(f_dev && g_dev && u_dev && f_dev != u_dev, "apply_bc: f, g, u must be device buffers, u distinct from f");
+    check_rhs(h, n_rhs);
+    struct Restore {  // the single-layer equations of Sec. 4.1, whatever form the handle uses
+      fmmpc_handle *h;
+      int form;
+      ~Restore() {
+        h->bc_g = nullptr;
+        h->bem_form = form;
+      }
+    } restore{h, h->bem_form};
+    h->bem_form = 0;
+    h->bc_g = g_dev;
+    apply_fmm(*h, PART_BC, f_dev, u_dev, n_rhs);
+    return FMMPC_OK;
+  });
+}
+
+int fmmpc_set_bem_form(fmmpc_handle *h, int32_t form) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(form == FMMPC_BEM_SINGLE_LAYER || form == FMMPC_BEM_DOUBLE_LAYER, "set_bem_form: unknown form");
+    if (form == FMMPC_BEM_DOUBLE_LAYER) init_bem_dl(*h);
+    if (form != h->bem_form) {
+      for (auto &e : h->gcache) cudaGraphExecDestroy(e.exec);  // captured with the other form
+      h->gcache.clear();
+      clear_solve_graphs(*h);
+    }
+    h->bem_form = form;
+    return FMMPC_OK;
+  });
+}
+
 int fmmpc_spmv(fmmpc_handle *h, const double *x_dev, double *y_dev, int32_t n_rhs) {
   if (!h) return FMMPC_ERR_INVALID;
   return guarded(h, [&] {

@@ -61,6 +61,29 @@ __global__ void k_bem_S(int n, double h, double lnh, double *__restrict__ S) {
   S[t] = -(h / (2.0 * PI)) * (I + ell * lnh);
 }
 
+// First block row of -1/2 I + K, K_mk = int_k dG/dn_y(y_m, y) dGamma = (1/2pi) atan2(l d,
+// d^2 + s1 s2) with d the signed normal offset of y_m from element k's line (zero on the
+// same side): the system (-1/2 I + K) mu = -(V r)|_Gamma of the double-layer correction.
+__global__ void k_bem_Kdl(int n, double *__restrict__ A) {
+  const int NG = 4 * n;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * NG) return;
+  const int mrow = (int)(t / NG), k = (int)(t % NG);
+  const double ell = (n + 1.0) / n, np1 = n + 1.0;
+  const double x = (mrow + 0.5) * ell, y = 0.0;  // collocation point mrow of side 0
+  const int sk = k / n, kk = k % n;
+  double v = 0.0;
+  if (sk == 0) {
+    v = (k == mrow) ? -0.5 : 0.0;
+  } else {
+    double u, d;
+    side_coords_d(sk, np1, x, y, u, d);
+    const double s1 = kk * ell - u, s2 = s1 + ell;
+    v = atan2(ell * d, d * d + s1 * s2) / (2.0 * PI);
+  }
+  A[t] = v;
+}
+
 __global__ void k_gj_pivot(int N, int k, const double *__restrict__ A, int *__restrict__ piv,
                            double *__restrict__ pinv, double *__restrict__ pabs) {
   __shared__ double best[1024];
@@ -237,6 +260,45 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
     FMMPC_LAUNCH_CHECK();
   }
   FMMPC_CUDA(cudaStreamSynchronize(s));
+}
+
+// The inverse of -1/2 I + K in the side-DFT form of the single-layer inverse (the same
+// 90-degree rotation symmetry), for the double-layer correction; formed on first use.
+void init_bem_dl(fmmpc_handle &H) {
+  if (H.Kdl_inv) return;
+  const Geo &g = H.g;
+  const int n = g.n, N = g.NG;
+  cudaStream_t s = H.stream;
+  DevPool tmp;
+  try {
+    double *A = tmp.get<double>((size_t)n * N);
+    k_bem_Kdl<<<nblk((int64_t)n * N), 256, 0, s>>>(n, A);
+    FMMPC_LAUNCH_CHECK();
+    double *B0 = tmp.get<double>((size_t)n * n), *B2 = tmp.get<double>((size_t)n * n);
+    double *E = tmp.get<double>((size_t)4 * n * n);
+    k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, A, B0, B2, E);
+    FMMPC_LAUNCH_CHECK();
+    const double a0 = gj_invert(B0, n, s, tmp), a2 = gj_invert(B2, n, s, tmp), a1 = gj_invert(E, 2 * n, s, tmp);
+    if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
+      throw Error(FMMPC_ERR_INVALID, "double-layer BEM matrix is singular for this domain");
+    double *T = H.pool.get<double>((size_t)n * N);
+    k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, E, T);
+    FMMPC_LAUNCH_CHECK();
+    float *th = nullptr, *tl = nullptr;
+    if (H.prec != FMMPC_PREC_FP64) {
+      th = H.pool.get<float>((size_t)n * N);
+      tl = H.pool.get<float>((size_t)n * N);
+      k_split_f2<<<nblk((int64_t)n * N), 256, 0, s>>>((int64_t)n * N, T, th, tl);
+      FMMPC_LAUNCH_CHECK();
+    }
+    FMMPC_CUDA(cudaStreamSynchronize(s));
+    H.Kdl_inv = T;
+    H.Kdl_hi = th;
+    H.Kdl_lo = tl;
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    throw;
+  }
 }
 
 }  // namespace fmmpc

@@ -63,6 +63,7 @@ __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
 template <typename R>
 struct Mats {
   const cpx<R> *vm2m, *vl2l, *bm2m, *bp2m;
+  const cpx<R> *bdl;  // [side][element of a leaf run][P]: multipoles of a unit double layer
 };
 
 // ------------------------------------------------------------------ weights
@@ -576,9 +577,10 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
 // (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run, with
 // a barrier between levels.  The side's whole tree (2^(L+1) - 1 runs) and its M2M matrices
 // stay in shared memory; the result is written out once.
+// qm: single-layer density (NULL: none); qd: double-layer density with sign dsgn (NULL: none).
 template <typename R, int P>
 __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, Mats<R> mt,
-                                                 cpx<R> *__restrict__ Mb) {
+                                                 cpx<R> *__restrict__ Mb, const double *__restrict__ qd, R dsgn) {
   extern __shared__ __align__(16) unsigned char bnd_smem[];
   cpx<R> *T2 = reinterpret_cast<cpx<R> *>(bnd_smem);  // [2 children][P][P]
   cpx<R> *S = T2 + 2 * P * P;                          // [level l: 2^l runs][P], level 0 first
@@ -590,13 +592,24 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
   cpx<R> *SL = S + (int64_t)(nleafrun - 1) * P;
   for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
     const int k = t / P, nn = t % P;
-    const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-    const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
     cpx<R> acc = mk<R>(0, 0);
-    for (int e = 0; e < m; ++e) {
-      const R qe = (R)qr[e] * h;
-      acc.re = fma(qe, B[e * P].re, acc.re);
-      acc.im = fma(qe, B[e * P].im, acc.im);
+    if (q) {
+      const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
+      const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+      for (int e = 0; e < m; ++e) {
+        const R qe = (R)qr[e] * h;
+        acc.re = fma(qe, B[e * P].re, acc.re);
+        acc.im = fma(qe, B[e * P].im, acc.im);
+      }
+    }
+    if (qd) {
+      const double *dr = qd + (int64_t)rhs * g.NG + side * n + k * m;
+      const cpx<R> *B = mt.bdl + (int64_t)side * m * P + nn;
+      for (int e = 0; e < m; ++e) {
+        const R de = (R)dr[e] * dsgn;
+        acc.re = fma(de, B[e * P].re, acc.re);
+        acc.im = fma(de, B[e * P].im, acc.im);
+      }
     }
     SL[t] = acc;
   }
@@ -628,20 +641,31 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
 // (FP64 at the largest depths).
 template <typename R, int P>
 __global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restrict__ q, Mats<R> mt,
-                                                   cpx<R> *__restrict__ Mb) {
+                                                   cpx<R> *__restrict__ Mb, const double *__restrict__ qd, R dsgn) {
   const int side = blockIdx.x, rhs = blockIdx.y;
   const int n = g.n, m = g.m, L = g.L;
   cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
   const int nleafrun = 1 << L;
   for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
     const int k = t / P, nn = t % P;
-    const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-    const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
     cpx<R> acc = mk<R>(0, 0);
-    for (int e = 0; e < m; ++e) {
-      const R qe = (R)qr[e] * (R)g.h;
-      acc.re = fma(qe, B[e * P].re, acc.re);
-      acc.im = fma(qe, B[e * P].im, acc.im);
+    if (q) {
+      const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
+      const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+      for (int e = 0; e < m; ++e) {
+        const R qe = (R)qr[e] * (R)g.h;
+        acc.re = fma(qe, B[e * P].re, acc.re);
+        acc.im = fma(qe, B[e * P].im, acc.im);
+      }
+    }
+    if (qd) {
+      const double *dr = qd + (int64_t)rhs * g.NG + side * n + k * m;
+      const cpx<R> *B = mt.bdl + (int64_t)side * m * P + nn;
+      for (int e = 0; e < m; ++e) {
+        const R de = (R)dr[e] * dsgn;
+        acc.re = fma(de, B[e * P].re, acc.re);
+        acc.im = fma(de, B[e * P].im, acc.im);
+      }
     }
     M[(blevel_offset(L) + ((int64_t)side << L) + k) * P + nn] = acc;
   }
@@ -801,6 +825,49 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
 // P0 = C^0 v^0, P2 = C^2 v^2, R + iI = (A + iB)(a - ib), and
 //   q0 = -(P0+P2+2R)/4, q1 = -(P0-P2-2I)/4, q2 = -(P0+P2-2R)/4, q3 = -(P0-P2+2I)/4:
 // 6 n^2 FP64 multiply-adds instead of 16 n^2 (FP64 is the bound on this part).
+
+// The boundary data term of Eq. e:ubound moved to the left: vcol_m -= (1/2 g_m + (K g)_m)
+// at every collocation point, K_mk = int_k dG/dn_y(y_m, y) dGamma = (1/2pi) atan2(l d,
+// d^2 + s1 s2) (zero on the point's own side), so that the BEM solve q = S^{-1}(-vcol) gives
+// S q = (1/2 I + K) g - (V f)|_Gamma.  Block per (collocation point, rhs), FP64.
+__global__ void __launch_bounds__(256) k_dl_colloc(int n, int nrhs, const double *__restrict__ gdat,
+                                                   double *__restrict__ vcol) {
+  __shared__ double red[8];
+  const int mrow = blockIdx.x, rhs = blockIdx.y, NG = 4 * n;
+  const double ell = (n + 1.0) / n, np1 = n + 1.0;
+  const int sm = mrow / n, km = mrow % n;
+  const double tm = (km + 0.5) * ell;
+  double x, y;
+  switch (sm) {
+    case 0: x = tm; y = 0; break;
+    case 1: x = np1; y = tm; break;
+    case 2: x = np1 - tm; y = np1; break;
+    default: x = 0; y = np1 - tm; break;
+  }
+  const double *gr = gdat + (int64_t)rhs * NG;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < NG; k += blockDim.x) {
+    const int sk = k / n, kk = k % n;
+    if (sk == sm) continue;
+    double u, d;
+    switch (sk) {
+      case 0: u = x; d = -y; break;
+      case 1: u = y; d = x - np1; break;
+      case 2: u = np1 - x; d = y - np1; break;
+      default: u = np1 - y; d = -x; break;
+    }
+    const double s1 = kk * ell - u, s2 = s1 + ell;
+    acc += gr[k] * atan2(ell * d, d * d + s1 * s2);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    vcol[(int64_t)rhs * NG + mrow] -= 0.5 * gr[mrow] + t / (2.0 * PI);
+  }
+}
 
 // vt[rhs] = [v^0 | v^2 | a | b] from vcol[rhs] = [v0 | v1 | v2 | v3]
 __global__ void k_bem_vt(int n, int nrhs, const double *__restrict__ vcol, double *__restrict__ vt) {
@@ -1003,6 +1070,48 @@ __global__ void __launch_bounds__(256) k_bnd_near(Geo g, int64_t nbnear, int nrh
     R s = 0;
     for (int q2 = 0; q2 < ngrp; ++q2) s += red[q2 * mm + threadIdx.x];
     phib[((int64_t)rhs * nbnear + slot) * mm + threadIdx.x] = s;
+  }
+}
+
+// Double layer near the boundary: phib[slot][t] (+)= dsgn sum_e dens_e theta_e(x_t), theta_e =
+// int_e d/dn_y ln|x - y| ds = -atan2(l d, d^2 + s1 s2) (the signed angle element e subtends at
+// the node, outward normal; node units, so no factor h).  Same blocks and element lists as
+// k_bnd_near.  accumulate = 0 writes instead of adding (no single layer in that apply).
+template <typename R>
+__global__ void __launch_bounds__(256) k_dl_near(Geo g, int64_t nbnear, int nrhs, const int32_t *__restrict__ leaf,
+                                                 const int32_t *__restrict__ first, const int32_t *__restrict__ src,
+                                                 const double *__restrict__ dens, R dsgn, int accumulate,
+                                                 R *__restrict__ phib) {
+  __shared__ R red[256];
+  const int slot = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L, mm = m * m;
+  const int ngrp = blockDim.x / mm;
+  const int t = threadIdx.x % mm, grp = threadIdx.x / mm;
+  int a, b;
+  morton_decode((uint32_t)leaf[slot], a, b);
+  const R ell = (R)((n + 1.0) / n), invn = R(1) / (R)n;
+  const double *dr = dens + (int64_t)rhs * g.NG;
+  const int x = a * m + t % m + 1, y = b * m + t / m + 1;
+  const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
+  R acc = 0;
+  if (grp < ngrp)
+    for (int idx = grp; idx < cnt; idx += ngrp) {
+      const int bl = src[f0 + idx / m], e = idx % m;
+      const int side = bl >> L;
+      const int64_t kk = bl & ((int64_t(1) << L) - 1);
+      int u, d;
+      side_coords(side, n + 1, x, y, u, d);
+      const int64_t num = (kk * m + e) * (int64_t)(n + 1) - (int64_t)u * n;
+      const R s1 = (R)num * invn, s2 = s1 + ell, dd = (R)d;
+      acc += (R)dr[side * n + kk * m + e] * -atan2(ell * dd, dd * dd + s1 * s2);
+    }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < mm) {
+    R sacc = 0;
+    for (int q2 = 0; q2 < ngrp; ++q2) sacc += red[q2 * mm + threadIdx.x];
+    R *o = phib + ((int64_t)rhs * nbnear + slot) * mm + threadIdx.x;
+    *o = (accumulate ? *o : R(0)) + dsgn * sacc;
   }
 }
 
@@ -1461,6 +1570,7 @@ Mats<R> mats_of(fmmpc_handle &H) {
   mt.vl2l = base + 4 * P * P;
   mt.bm2m = base + 8 * P * P;
   mt.bp2m = base + 16 * P * P;
+  mt.bdl = mt.bp2m + 4 * H.g.m * P;
   return mt;
 }
 
@@ -1534,13 +1644,26 @@ template <typename R>
 int run_bnd_near(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   const Geo &g = H.g;
   const Lists &Ls = H.lists;
+  const dim3 grid((unsigned)Ls.nbnear, nrhs);
+  if (H.bem_form == 1) {  // double-layer correction: D mu only (mu in fb.q)
+    k_dl_near<R><<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first, Ls.pbv_src, H.fb.q, R(1), 0,
+                                      (R *)H.fb.phib);
+    FMMPC_LAUNCH_CHECK();
+    return 1;
+  }
   if (std::is_same<R, float>::value && H.fb.knear && g.m == 8)
-    k_bnd_near_k<<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_first, Ls.pbv_src,
-                                                                 H.fb.knear, H.fb.q, (float *)H.fb.phib);
+    k_bnd_near_k<<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_first, Ls.pbv_src, H.fb.knear, H.fb.q,
+                                      (float *)H.fb.phib);
   else
-    k_bnd_near<R><<<dim3((unsigned)Ls.nbnear, nrhs), 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first,
-                                                                 Ls.pbv_src, H.fb.q, (R *)H.fb.phib);
+    k_bnd_near<R><<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first, Ls.pbv_src, H.fb.q,
+                                       (R *)H.fb.phib);
   FMMPC_LAUNCH_CHECK();
+  if (H.bc_g) {  // boundary data: - D g of Eq. e:uinter
+    k_dl_near<R><<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first, Ls.pbv_src, H.bc_g, R(-1), 1,
+                                      (R *)H.fb.phib);
+    FMMPC_LAUNCH_CHECK();
+    return 2;
+  }
   return 1;
 }
 
@@ -1599,7 +1722,9 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     H.launches = launches;
     return;
   }
-  const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q;
+  const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q || part == PART_BC;
+  const bool dl = H.bem_form == 1;             // double-layer correction (mu from -1/2 I + K)
+  const bool bc = part == PART_BC && H.bc_g;   // boundary data g (Eqs. e:ubound / e:uinter)
   // The tensor-core near field and volume M2L do not depend on the boundary chain
   // (collocation values, BEM density, boundary tree, near-boundary correction): for the
   // full apply without stage timing they run on a second stream, forked after the weights
@@ -1624,12 +1749,19 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     mark(2);
     k_m2l_bnd<R, P><<<nblk(g.nbcell * nrhs * 32), 256, 0, s>>>(gd, g.ncell, g.nbcell, nrhs, Ls.vbb_first,
                                                               Ls.vbb_src, Mv, Lb, g.lnh);
-    const bool vt_f2 = H.Sinv_hi && H.fb.vt_hi;  // the side DFT for the two-word BEM apply, fused
+    // the side DFT for the two-word BEM apply, fused (not with boundary data, which changes
+    // vcol after this kernel)
+    const bool vt_f2 = H.Sinv_hi && H.fb.vt_hi && !bc;
     k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
                                                                H.fb.vcol, H.fb.kcol, vt_f2 ? H.fb.vt_hi : nullptr,
                                                                vt_f2 ? H.fb.vt_lo : nullptr);
     FMMPC_LAUNCH_CHECK();
     launches += 2;
+    if (bc) {  // vcol -= (1/2 I + K) g: Eq. e:ubound's data term
+      k_dl_colloc<<<dim3((unsigned)g.NG, nrhs), 256, 0, s>>>(g.n, nrhs, H.bc_g, H.fb.vcol);
+      FMMPC_LAUNCH_CHECK();
+      ++launches;
+    }
     if (part == PART_VCOL) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.vcol, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
@@ -1637,15 +1769,18 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       return;
     }
     mark(3);
-    if (H.Sinv_hi && H.fb.vt_hi) {  // vt_hi / vt_lo came with the collocation values
-      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
-      else k_bem_apply_f2<1><<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv_hi, H.Sinv_lo, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+    // q = S^{-1}(-vcol), or mu = (-1/2 I + K)^{-1}(-vcol) in the double-layer form
+    const float *Th = dl ? H.Kdl_hi : H.Sinv_hi, *Tl = dl ? H.Kdl_lo : H.Sinv_lo;
+    if (vt_f2 && Th) {  // vt_hi / vt_lo came with the collocation values
+      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, 256, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      else k_bem_apply_f2<1><<<g.n, 256, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      ++launches;
     } else {
       k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
-      k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, H.Sinv, H.fb.vt, H.fb.q);
+      k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, dl ? H.Kdl_inv : H.Sinv, H.fb.vt, H.fb.q);
+      launches += 2;
     }
     FMMPC_LAUNCH_CHECK();
-    launches += (H.Sinv_hi && H.fb.vt_hi) ? 1 : 2;
     if (part == PART_Q) {
       FMMPC_CUDA(cudaMemcpyAsync(out, H.fb.q, sizeof(double) * g.NG * nrhs, cudaMemcpyDeviceToDevice, s));
       mark_end();
@@ -1669,8 +1804,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
         FMMPC_CUDA(cudaFuncSetAttribute(k_bnd_up<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
         done = true;
       }
-      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, H.fb.q, mt, Mb);
-      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, H.fb.q, mt, Mb);
+      // single layer q (none in the double-layer form); double layer mu (+D mu) or data g (-D g)
+      const double *qm = dl ? nullptr : H.fb.q, *qd = dl ? H.fb.q : (bc ? H.bc_g : nullptr);
+      const R dsgn = dl ? R(1) : R(-1);
+      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, qm, mt, Mb, qd, dsgn);
+      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, qm, mt, Mb, qd, dsgn);
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;
@@ -1787,6 +1925,23 @@ void build_mats(fmmpc_handle &H, std::vector<cpx<R>> &out) {
       std::vector<C> el(P, C(0, 0));
       el[0] = 2.0 * a * rho;
       for (int k = 2; k < P; k += 2) el[k] = -2.0 * powc(edir[sd], k) * std::pow(a, k + 1) * rho / (k * (k + 1.0));
+      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
+      for (int nn = 0; nn < P; ++nn) {
+        C v(0, 0);
+        for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
+        all.push_back(v);
+      }
+    }
+  // The double layer of unit density on element e, int_e dG/dn_y, is -(1/2pi) times the real
+  // part of -i (log(z - b) - log(z - a)) (a, b its ends in traversal order, the outward normal
+  // the tangent turned clockwise): point weights -i at b and +i at a.  About the element
+  // midpoint at scale rho: Mt_0 = 0, Mt_k = 2 i e^k a^k / k for odd k (0 for even), a as
+  // above; shifted to the run centre like the single layer.  (No factor h: the double layer
+  // of a closed element run is scale free.)
+  for (int sd = 0; sd < 4; ++sd)
+    for (int e = 0; e < m; ++e) {
+      std::vector<C> el(P, C(0, 0));
+      for (int k = 1; k < P; k += 2) el[k] = C(0.0, 2.0) * powc(edir[sd], k) * std::pow(a, k) / (double)k;
       m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
       for (int nn = 0; nn < P; ++nn) {
         C v(0, 0);

@@ -219,3 +219,65 @@ def test_green_representation_of_a_harmonic_function():
         errs.append(np.max(np.abs(sl - dl - u(tx, ty))))
     assert errs[-1] < 2e-3
     assert errs[0] / errs[1] > 1.6 and errs[1] / errs[2] > 1.6
+
+
+# ---------------------------------------------------------------- boundary data and the
+# second-kind double-layer variant (Sec. 4.1 Eqs. e:ubound/e:uinter with g != 0)
+def _midpoint_data(n, fn, x0, y0, side):
+    _, _, _, _, cx, cy = O.elements(n, x0, y0, side)
+    return fn(cx, cy)
+
+
+def test_apply_bc_with_zero_data_is_the_preconditioner():
+    n = 16
+    r = S.random_field(n, 12)
+    R = O.Problem(n, p=10)
+    assert rel_l2(R.apply_bc(r, np.zeros(4 * n), "direct"), R.apply(r, "direct")) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["harmonic", "quadratic"])
+def test_apply_bc_reproduces_table_solutions_at_first_order(case):
+    # Table t:p2: u = 2(1+y)/((3+x)^2+(1+y)^2), f = 0; Table t:p3: u = x^2 + y^2, f = -4; on
+    # [-1,1]^2.  The boundary-integral solution with constant elements is first order in h
+    # (Sec. 6.2, Fig. f:discretization): the worst node error falls by at least about 2 per
+    # halving (midpoint collocation measures close to 4 here).
+    if case == "harmonic":
+        fn, fval = (lambda x, y: 2 * (1 + y) / ((3 + x) ** 2 + (1 + y) ** 2)), 0.0
+    else:
+        fn, fval = (lambda x, y: x * x + y * y), -4.0
+    errs = []
+    for n in (16, 32, 64):
+        X, Y, _ = S.grid_coords(n, -1.0, -1.0, 2.0)
+        R = O.Problem(n, p=10, x0=-1.0, y0=-1.0, side=2.0)
+        u = R.apply_bc(np.full(n * n, fval), _midpoint_data(n, fn, -1.0, -1.0, 2.0), "fmm")
+        errs.append(np.max(np.abs(u - fn(X, Y))))
+    print(case, "apply_bc max errors", errs)
+    assert errs[0] / errs[1] > 1.5 and errs[1] / errs[2] > 1.5
+    assert errs[2] < 0.02 * np.max(np.abs(fn(X, Y)))
+
+
+def test_double_layer_variant_converges_to_the_continuum_and_to_the_single_layer_form():
+    # (-1/2 I + K) mu = -(V f)|_Gamma, z = V f + D mu: another boundary correction with the same
+    # continuum limit, so P_dl^{-1} f -> u and P_dl^{-1} f - P^{-1} f -> 0 as h -> 0
+    e_u, e_sl = [], []
+    for n in (16, 32, 64):
+        f, u = S.manufactured_sin(n)
+        R = O.Problem(n, p=10)
+        zdl = R.apply_dl(f, "fmm")
+        e_u.append(rel_l2(zdl, u))
+        e_sl.append(rel_l2(zdl, R.apply(f, "fmm")))
+    print("double-layer variant: vs continuum", e_u, "vs single layer", e_sl)
+    assert e_u[0] / e_u[1] > 1.5 and e_u[1] / e_u[2] > 1.5 and e_u[2] < 1e-2
+    assert e_sl[0] / e_sl[1] > 1.5 and e_sl[1] / e_sl[2] > 1.5
+
+
+def test_double_layer_variant_direct_equals_fmm_and_preconditions():
+    n = 32
+    r = S.random_field(n, 5)
+    R = O.Problem(n, p=12)
+    assert rel_l2(R.apply_dl(r, "fmm"), R.apply_dl(r, "direct")) < 1e-8
+    f = S.gaussian_mixture(n, 2)
+    _, it_sl, _, c1 = R.solve(f, "fgmres", 30, 100, 1e-8, "fmm")
+    _, it_dl, _, c2 = R.solve(f, "fgmres", 30, 100, 1e-8, "fmm_dl")
+    print("fgmres iterations: single layer", it_sl, "double layer", it_dl)
+    assert c1 and c2 and abs(it_sl - it_dl) <= 3
