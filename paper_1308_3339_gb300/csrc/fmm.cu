@@ -1840,6 +1840,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
                                                              Ls.m2l_first, Ls.m2l_src, Ls.vbv_first, Ls.vbv_src,
                                                              Mv, Mb, Lv);
     ++launches;
+    mark(6);  // closes the M2L stage (its boundary sources are inside this kernel)
   }
   if (g.L < 2) {  // else the downward kernel adds the root constant
     k_root_const<R><<<1, 32, 0, s>>>(P, g.ncell, g.nbcell, nrhs, g.lnh, with_bnd ? 2 : 1, Mv, Mb, Lv, Lb);

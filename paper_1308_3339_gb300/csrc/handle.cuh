@@ -55,6 +55,7 @@ struct TcM2L {
   bool enabled = false;
   int kind = 0;  // 0 TF32, 1 BF16
   int nsplit = 0;  // leading multipoles split hi + lo
+  int sbase = 0;   // first K column of the split products
   int width = 32;  // outputs per target class (N = 4 width)
   int ntiles = 0, smem = 0, nofs_total = 0;  // nofs_total: shifts
   int nparts = 1, gpart[3] = {}, gpart_sh[3] = {};

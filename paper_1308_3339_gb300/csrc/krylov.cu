@@ -16,7 +16,7 @@ namespace fmmpc {
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 256;  // per rhs; partial sums reduced in a second kernel
+constexpr int RED_BLOCKS = 1024;  // per rhs at most; partial sums reduced in a second kernel or the last block
 constexpr int MAXJ = 64;         // largest Krylov basis handled by the fused kernels
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -894,9 +894,64 @@ __global__ void k_gspmv_store(const int *__restrict__ ctl, OpDev o, int64_t tota
   if (Zb) Zb[(int64_t)ctl[KC_J] * vs + t] = x[t];
 }
 
-// partial[rhs][i][blk] = slice sums of <V_i[rhs], w[rhs]> for i <= ctl[KC_J]
-__global__ void k_gmdot_partial(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V, int64_t vs,
-                                const double *__restrict__ w, double *__restrict__ part) {
+// x[rhs] += sum_{i < ctl[KC_JCNT]} y[rhs][i] Z_i[rhs]
+__global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ Z, int64_t vs,
+                         const double *__restrict__ y, double *__restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int rhs = (int)(t / N), nv = ctl[KC_JCNT];
+  double v = x[t];
+  for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
+  x[t] = v;
+}
+
+// V_{ctl[KC_J]}[rhs] = sc[rhs] w[rhs], and the same into t2 (the next preconditioner input)
+__global__ void k_gscale_col(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ sc,
+                             const double *__restrict__ w, double *__restrict__ V, int64_t vs, double *__restrict__ t2) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const double v = sc[t / N] * w[t];
+  V[(int64_t)ctl[KC_J] * vs + t] = v;
+  if (t2) t2[t] = v;
+}
+
+// Last block of a reduction grid to arrive: returns true in every thread of that block
+// (counter cnt reset to zero by it).  Partial sums written before the call are visible.
+__device__ __forceinline__ bool last_block(int *cnt) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(cnt, 1) == (int)(gridDim.x - 1));
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// out[rhs][i] = sum over blocks of part[rhs][i][blk], i < nout, in a fixed order (the last
+// block of the grid, warp per i); acc: 0 none, 1 hsum = out, 2 hsum += out.
+__device__ __forceinline__ void reduce_parts(const double *__restrict__ part, int rhs, int nout, double *__restrict__ out,
+                                             double *__restrict__ hsum, int acc) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < nout; i += blockDim.x >> 5) {
+    const double *pp = part + ((int64_t)rhs * MAXJ + i) * gridDim.x;
+    double sacc = 0.0;
+    for (int bb = lane; bb < (int)gridDim.x; bb += 32) sacc += __ldcg(pp + bb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+    if (lane == 0) {
+      out[rhs * MAXJ + i] = sacc;
+      if (acc == 1) hsum[rhs * MAXJ + i] = sacc;
+      else if (acc == 2) hsum[rhs * MAXJ + i] += sacc;
+    }
+  }
+}
+
+// d[rhs][i] = <V_i[rhs], w[rhs]>, i <= ctl[KC_J], with the reduction finished by the last
+// block to arrive (vectors taken 8 at a time); hacc as in reduce_parts.
+__global__ void __launch_bounds__(RED_THREADS) k_gdots(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
+                                                       int64_t vs, const double *__restrict__ w, double *__restrict__ part,
+                                                       int *__restrict__ cnt, double *__restrict__ out,
+                                                       double *__restrict__ hsum, int hacc) {
   __shared__ double red[RED_THREADS / 32][8];
   const int rhs = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -926,29 +981,18 @@ __global__ void k_gmdot_partial(const int *__restrict__ ctl, int64_t N, const do
     }
     __syncthreads();
   }
-}
-
-// out[rhs][i] = sum of the block partials for i <= ctl[KC_J]; acc[rhs][i] += the same
-__global__ void k_gmdot_final(const int *__restrict__ ctl, int nblocks, const double *__restrict__ part,
-                              double *__restrict__ out, double *__restrict__ acc) {
-  const int rhs = blockIdx.x, lane = threadIdx.x & 31;
-  const int nv = ctl[KC_J] + 1;
-  for (int i = threadIdx.x >> 5; i < nv; i += blockDim.x >> 5) {
-    const double *pp = part + ((int64_t)rhs * MAXJ + i) * nblocks;
-    double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += pp[b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      out[rhs * MAXJ + i] = s;
-      if (acc) acc[rhs * MAXJ + i] += s;
-    }
+  if (last_block(cnt + rhs)) {
+    reduce_parts(part, rhs, nv, out, hsum, hacc);
+    if (threadIdx.x == 0) cnt[rhs] = 0;
   }
 }
 
-// w[rhs] -= sum_{i <= j} c[rhs][i] V_i[rhs]; with part, also slice sums of the new |w|^2
-__global__ void k_gmupdate(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V, int64_t vs,
-                           const double *__restrict__ c, double *__restrict__ w, double *__restrict__ part) {
+// w[rhs] -= sum_{i <= j} c[rhs][i] V_i[rhs]; with wsq, also |w|^2 into wsq[rhs][0] (the
+// reduction finished by the last block).
+__global__ void __launch_bounds__(RED_THREADS) k_gupdate(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
+                                                         int64_t vs, const double *__restrict__ c, double *__restrict__ w,
+                                                         double *__restrict__ part, int *__restrict__ cnt,
+                                                         double *__restrict__ wsq) {
   __shared__ double red[RED_THREADS / 32];
   const int rhs = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -962,7 +1006,7 @@ __global__ void k_gmupdate(const int *__restrict__ ctl, int64_t N, const double 
     wr[k] = v;
     sq = fma(v, v, sq);
   }
-  if (!part) return;
+  if (!wsq) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   if (lane == 0) red[wid] = sq;
@@ -972,107 +1016,10 @@ __global__ void k_gmupdate(const int *__restrict__ ctl, int64_t N, const double 
     for (int q = 0; q < RED_THREADS / 32; ++q) t += red[q];
     part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
   }
-}
-
-// x[rhs] += sum_{i < ctl[KC_JCNT]} y[rhs][i] Z_i[rhs]
-__global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ Z, int64_t vs,
-                         const double *__restrict__ y, double *__restrict__ x) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * nrhs) return;
-  const int rhs = (int)(t / N), nv = ctl[KC_JCNT];
-  double v = x[t];
-  for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
-  x[t] = v;
-}
-
-// V_{ctl[KC_J]}[rhs] = sc[rhs] w[rhs], and the same into t2 (the next preconditioner input)
-__global__ void k_gscale_col(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ sc,
-                             const double *__restrict__ w, double *__restrict__ V, int64_t vs, double *__restrict__ t2) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * nrhs) return;
-  const double v = sc[t / N] * w[t];
-  V[(int64_t)ctl[KC_J] * vs + t] = v;
-  if (t2) t2[t] = v;
-}
-
-// One pass of classical Gram-Schmidt over the basis V_0 .. V_j (j = ctl[KC_J], at most 31)
-// fused with the reduction it needs, per right-hand side (grid y):
-//   MODE 0: d = V^T w;                      out = d, hsum = d
-//   MODE 1: w -= V c (c = the first pass);  out = V^T w (new w), hsum += out
-//   MODE 2: w -= V c (c = the second pass); out[0] = |w|^2
-// Every block writes its slice sums to part; the last block to arrive (counter cnt[rhs])
-// adds them in a fixed order, so the result does not depend on the arrival order.
-template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_gcgs(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
-                                                      int64_t vs, double *__restrict__ w, const double *__restrict__ c,
-                                                      double *__restrict__ part, int *__restrict__ cnt,
-                                                      double *__restrict__ out, double *__restrict__ hsum) {
-  constexpr int NV = 32;
-  __shared__ double red[RED_THREADS / 32][NV];
-  __shared__ double cs[NV];
-  __shared__ int last;
-  const int rhs = blockIdx.y;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nv = ctl[KC_J] + 1;
-  const int nout = MODE == 2 ? 1 : nv;
-  if (MODE != 0 && threadIdx.x < NV) cs[threadIdx.x] = threadIdx.x < nv ? c[rhs * MAXJ + threadIdx.x] : 0.0;
-  __syncthreads();
-  double acc[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  const double *Vr = V + (int64_t)rhs * N;
-  double *wr = w + (int64_t)rhs * N;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    double vv[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) vv[q] = q < nv ? Vr[(int64_t)q * vs + k] : 0.0;
-    double x = wr[k];
-    if (MODE != 0) {
-#pragma unroll
-      for (int q = 0; q < NV; ++q) x = fma(-cs[q], vv[q], x);
-      wr[k] = x;
-    }
-    if (MODE == 2) {
-      acc[0] = fma(x, x, acc[0]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q] = fma(vv[q], x, acc[q]);
-    }
+  if (last_block(cnt + rhs)) {
+    reduce_parts(part, rhs, 1, wsq, nullptr, 0);
+    if (threadIdx.x == 0) cnt[rhs] = 0;
   }
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    if (q < nout) {
-      double v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[wid][q] = v;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nout) {
-    double sum = 0.0;
-    for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
-    part[((int64_t)rhs * MAXJ + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&cnt[rhs], 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int i = wid; i < nout; i += RED_THREADS / 32) {
-    const double *pp = part + ((int64_t)rhs * MAXJ + i) * gridDim.x;
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(pp + b);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      out[rhs * MAXJ + i] = s;
-      if (MODE == 0) hsum[rhs * MAXJ + i] = s;
-      if (MODE == 1) hsum[rhs * MAXJ + i] += s;
-    }
-  }
-  if (threadIdx.x == 0) cnt[rhs] = 0;
 }
 
 // Per-right-hand-side state of the graph-resident (F)GMRES.
@@ -1425,30 +1372,20 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       FMMPC_LAUNCH_CHECK();
     });
   } else {
-    const bool fused = m <= 31;  // the fused CGS kernels hold up to 32 basis vectors in registers
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
       precond(K.t, K.zin, K.t);  // K.t holds v_j (written with V_j by the previous step)
       k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, od, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
-      dim3 grid(RED_BLOCKS, nrhs);
-      // one block per SM: the fused kernels hold up to 32 basis values and 32 sums per thread
+      // CGS2: dots, update, dots, update with |w|^2; each reduction finished in its grid's
+      // last block (a grid of a few blocks per SM keeps enough loads in flight)
       int nsm = 0;
       FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
-      const dim3 fgrid((unsigned)std::min(std::max(nsm, 1), RED_BLOCKS), nrhs);
-      if (fused) {
-        double *d2 = K.dots + (size_t)2 * nrhs * MAXJ;
-        k_gcgs<0><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, nullptr, K.part, K.g_cnt, K.dots, hsum);
-        k_gcgs<1><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.dots, K.part, K.g_cnt, d2, hsum);
-        k_gcgs<2><<<fgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, d2, K.part, K.g_cnt, wsq, nullptr);
-      } else {
-        FMMPC_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double) * nrhs * MAXJ, H.stream));
-        for (int pass = 0; pass < 2; ++pass) {
-          k_gmdot_partial<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part);
-          k_gmdot_final<<<nrhs, 256, 0, H.stream>>>(ctl, RED_BLOCKS, K.part, K.dots, hsum);
-          k_gmupdate<<<grid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, pass ? K.part : nullptr);
-        }
-        k_mdot_final<<<dim3(nrhs, 1), 256, 0, H.stream>>>(1, RED_BLOCKS, K.part, wsq, nullptr, 0);
-      }
+      const dim3 rgrid((unsigned)std::min(std::max(4 * nsm, 1), RED_BLOCKS), nrhs);
+      double *d2 = K.dots + (size_t)2 * nrhs * MAXJ;
+      k_gdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part, K.g_cnt, K.dots, hsum, 1);
+      k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, K.part, K.g_cnt, nullptr);
+      k_gdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part, K.g_cnt, d2, hsum, 2);
+      k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, d2, K.w, K.part, K.g_cnt, wsq);
       k_gtail<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, m, hsum, wsq, K.scal, hif);
       k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs, K.t);
       FMMPC_LAUNCH_CHECK();

@@ -23,9 +23,9 @@
 // sums of M~_0 that carry ln rho.
 // Padding targets are computed and dropped.  The low-order terms dominate the translated
 // field and meet the large log o + ln rho, so their products are split hi + lo in the
-// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 64 for BF16: every M~_k up to
-// p = 11): rounded input x rounded matrix, input residual x rounded matrix, rounded input x
-// matrix residual.
+// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 64 for BF16: M~_0..7, in K steps
+// of their own): rounded input x rounded matrix, input residual x rounded matrix, rounded
+// input x matrix residual.
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
@@ -84,7 +84,7 @@ struct M2lArgs {
   int64_t lev_row0[24];         // first image row of level l (parity 0)
   int lev_P[24];
   int gpart[3], gpart_sh[3];    // groups and shifts of each part
-  int p, n, nks, nsplit, nparts;
+  int p, n, nks, nsplit, nparts, sbase;
 };
 
 __device__ __forceinline__ int floor8(int x) { return x & ~7; }
@@ -100,15 +100,19 @@ __device__ __forceinline__ float m2l_round(float x) {
 }
 
 // K input v of a cell: v < 2p the rounded real parts of M~ (Re M~_0, Im M~_0, Re M~_1, ...);
-// for j < nsplit, v = 2p + 4j + {0, 1}: the rounding residual of M~_j (meets B's rounded
-// column j), v = 2p + 4j + {2, 3}: the rounded M~_j again (meets the residual of column j).
+// for j < nsplit, v = sb + 4j + {0, 1}: the rounding residual of M~_j (meets B's rounded
+// column j), v = sb + 4j + {2, 3}: the rounded M~_j again (meets the residual of column j).
+// sb (split base) is 2p for TF32; for BF16 it is 2p rounded up to a whole K step of 16, so
+// the small correction products never share an MMA's K step with the main products (the
+// tensor core adds a step's products at the scale of its largest one).
 template <int KIND>
-__device__ __forceinline__ float m2l_input(const cpx<float> *M, int v, int p, int nsplit) {
+__device__ __forceinline__ float m2l_input(const cpx<float> *M, int v, int p, int nsplit, int sb) {
   if (v < 2 * p) {
     const float x = (v & 1) ? M[v >> 1].im : M[v >> 1].re;
     return m2l_round<KIND>(x);
   }
-  const int w = v - 2 * p, j = w >> 2, e = w & 3;
+  if (v < sb) return 0.f;
+  const int w = v - sb, j = w >> 2, e = w & 3;
   if (j >= nsplit) return 0.f;
   const float x = (e & 1) ? M[j].im : M[j].re;
   const float hi = m2l_round<KIND>(x);
@@ -147,12 +151,12 @@ __global__ void k_m2l_pack(M2lArgs a, int nrhs, int64_t ncell_lo, int64_t ncell_
   uint32_t w[4];
   if (KIND == 0) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) w[e] = __float_as_uint(m2l_input<KIND>(M, 4 * chunk + e, a.p, a.nsplit));
+    for (int e = 0; e < 4; ++e) w[e] = __float_as_uint(m2l_input<KIND>(M, 4 * chunk + e, a.p, a.nsplit, a.sbase));
   } else {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const __nv_bfloat16 b0 = __float2bfloat16_rn(m2l_input<KIND>(M, 8 * chunk + 2 * e, a.p, a.nsplit));
-      const __nv_bfloat16 b1 = __float2bfloat16_rn(m2l_input<KIND>(M, 8 * chunk + 2 * e + 1, a.p, a.nsplit));
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(m2l_input<KIND>(M, 8 * chunk + 2 * e, a.p, a.nsplit, a.sbase));
+      const __nv_bfloat16 b1 = __float2bfloat16_rn(m2l_input<KIND>(M, 8 * chunk + 2 * e + 1, a.p, a.nsplit, a.sbase));
       w[e] = (uint32_t)*reinterpret_cast<const uint16_t *>(&b0) | ((uint32_t)*reinterpret_cast<const uint16_t *>(&b1) << 16);
     }
   }
@@ -463,11 +467,11 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   T.kind = (H.prec == FMMPC_PREC_MIXED_TF32) ? 0 : 1;
   T.width = (2 * p + 2 <= 24) ? 24 : 32;  // outputs per class
   // hi/lo splits of the leading multipoles in the spare K columns of the 128-byte row: TF32
-  // holds 32 inputs (4 K steps of 8), BF16 64 (4 K steps of 16), so at p = 10 every BF16
-  // multipole is split (2p + 4p = 60 inputs) and the BF16 form rounds none of its products
-  // below about 2^-16, for the same four K steps as TF32
+  // holds 32 inputs (4 K steps of 8), BF16 64 (4 K steps of 16); the BF16 corrections start
+  // at the next whole K step (at p = 10: main terms in steps 0-1, M~_0..7 split in 2-3)
   const int kcap = T.kind == 0 ? 32 : 64;
-  T.nsplit = std::max(0, std::min(p, (kcap - 2 * p) / 4));
+  T.sbase = T.kind == 0 ? 2 * p : (2 * p + 15) / 16 * 16;
+  T.nsplit = std::max(0, std::min(p, (kcap - T.sbase) / 4));
   // offset sets by class, from the lists themselves, then checked against every list
   int *dtab = tmp.get<int>(4 * 225), *derr = tmp.get<int>(1);
   FMMPC_CUDA(cudaMemsetAsync(dtab, 0, sizeof(int) * 4 * 225, H.stream));
@@ -604,8 +608,8 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
           for (int e = 0; e < 2; ++e) {
             const double full = Breal(u, 2 * j + e);
             const double hi = T.kind == 0 ? (double)tf32_round_host_m2l(full) : bf16_value(bf16_round_host(full));
-            put(u, 2 * p + 4 * j + e, full);
-            put(u, 2 * p + 4 * j + 2 + e, full - hi);
+            put(u, T.sbase + 4 * j + e, full);
+            put(u, T.sbase + 4 * j + 2 + e, full - hi);
           }
     }
   T.smem = W == 24 ? M2lShape<24>::SMEM : M2lShape<32>::SMEM;
@@ -661,7 +665,8 @@ int run_m2l_tc(fmmpc_handle &H, const void *Mv, void *Lv, int nrhs, cudaStream_t
   a.n = g.n;
   a.nsplit = T.nsplit;
   a.nparts = T.nparts;
-  a.nks = T.kind == 0 ? (2 * g.p + 4 * T.nsplit + 7) / 8 : (2 * g.p + 4 * T.nsplit + 15) / 16;
+  a.sbase = T.sbase;
+  a.nks = T.kind == 0 ? (T.sbase + 4 * T.nsplit + 7) / 8 : (T.sbase + 4 * T.nsplit + 15) / 16;
   const int64_t lo = level_offset(2), hi = level_offset(g.L + 1);
   const int64_t threads = std::max<int64_t>((int64_t)nrhs * (hi - lo) * 8, (int64_t)nrhs * lo * g.p);
   const cpx<float> *M = (const cpx<float> *)Mv;

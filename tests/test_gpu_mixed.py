@@ -3,7 +3,7 @@ FP32 accumulation) inside the FP64 Krylov solve, against the FP64 oracle.
 
 Error bars.  Rounding both operands of an M2L product to TF32 (unit roundoff 2^-11) or
 BF16 (2^-9) perturbs it by about sqrt(2) u.  The leading multipoles and their translation
-columns are split hi + lo in the spare K columns (M~_0..2 for TF32, every M~_k for BF16), so
+columns are split hi + lo in the spare K columns (M~_0..2 for TF32, M~_0..7 for BF16), so
 only the small high-order terms carry u; the far field is a fraction of z, and the error
 of z stays well below u.  The contract bars are 1e-5 (TF32, the FP32 gate) and 2e-3 (BF16
 against the direct sum); the gates below sit at about ten times the errors measured on
