@@ -158,6 +158,20 @@ int fmmpc_apply_part(fmmpc_handle *h, int32_t part, const double *r_dev, double 
  * Asynchronous on the handle's stream.  Errors: _INVALID. */
 int fmmpc_apply_bc(fmmpc_handle *h, const double *f_dev, const double *g_dev, double *u_dev, int32_t n_rhs);
 
+/* The transpose of the preconditioner, rb = P^{-T} zb: the gradient of a loss of z = P^{-1} r
+ * with respect to the source weights r, given its gradient zb with respect to z.  With
+ * P^{-1} = V - S_OG S^{-1} V_GO (Sec. 3.2, Eqs. e:ubound and e:uinter with z = 0 on Gamma):
+ * P^{-T} = V - V_GO^T S^{-T} S_OG^T, V symmetric.  The FMM-transpose pass runs the apply's
+ * volume FMM on zb, takes the element integrals of that potential over the 4n boundary
+ * elements (S_OG^T zb: the local expansions integrated in closed form, closed-form log
+ * integrals next to the boundary), applies S^{-T} (the side-DFT blocks transposed, FP64;
+ * formed on first use), and sums the resulting point sources at the collocation points
+ * back into the nodes through the boundary FMM tree (V_GO^T).  Accurate to the FMM
+ * truncation against the exact transpose.  zb_dev, rb_dev: [n_rhs][ny][nx] FP64 device,
+ * distinct.  Single-layer form only (_UNSUPPORTED after fmmpc_set_bem_form(DOUBLE_LAYER)).
+ * Errors: _INVALID, _UNSUPPORTED. */
+int fmmpc_apply_transpose(fmmpc_handle *h, const double *zb_dev, double *rb_dev, int32_t n_rhs);
+
 /* Boundary correction of the preconditioner.
  *  FMMPC_BEM_SINGLE_LAYER (default): the paper's, Eq. e:ubound with z = 0 on Gamma, a
  *    first-kind single-layer system S q = -(V r)|_Gamma, then z = V r + int_Gamma q G.

@@ -97,6 +97,9 @@ def _lib():
     L.orc_apply_bc.argtypes = [vp, i, vp, vp, vp, vp]
     L.orc_apply_bc.restype = i
     L.orc_apply_dl.argtypes = [vp, i, vp, vp, vp]
+    L.orc_apply_transpose.argtypes = [vp, i, vp, vp]
+    L.orc_apply_transpose.restype = i
+    L.orc_lu_solve_transpose.argtypes = [i, vp, vp, vp]
     L.orc_apply_dl.restype = i
     L.orc_solve.argtypes = [vp, i, i, i, d, i, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.orc_solve.restype = i
@@ -290,6 +293,23 @@ def layers_at(n, x0, y0, side, tx, ty, q=None, mu=None):
 
 
 # ---------------------------------------------------------------- tree (Sec. 5.1)
+def lu_solve_transpose(LU, piv, b):
+    """x with A^T x = b from orc_lu's factors of A."""
+    N = LU.shape[0]
+    x = np.array(b, np.float64)
+    _lib().orc_lu_solve_transpose(N, _p(np.ascontiguousarray(LU)), _p(np.ascontiguousarray(piv, np.int32)), _p(x))
+    return x
+
+
+def lu(A):
+    """orc_lu's in-place factors of A (copied) and pivots."""
+    LU = np.array(A, np.float64)
+    piv = np.empty(LU.shape[0], np.int32)
+    if _lib().orc_lu(LU.shape[0], _p(LU), _p(piv)):
+        raise RuntimeError("oracle: singular matrix")
+    return LU, piv
+
+
 def morton_keys(n):
     k = np.empty(n * n, np.uint32)
     _lib().orc_morton_keys(n, _p(k))
@@ -378,6 +398,14 @@ class Problem:
         if _lib().orc_apply_bc(self._h, 0 if mode == "direct" else 1, _p(f), _p(g), _p(u), _p(q)):
             raise RuntimeError("oracle: singular BEM matrix")
         return (u, q) if with_q else u
+
+    def apply_transpose(self, zb, mode="fmm"):
+        """rb = P^{-T} zb, the transpose of apply (gradient with respect to the source weights)."""
+        zb = np.ascontiguousarray(zb, np.float64).reshape(-1)
+        rb = np.empty_like(zb)
+        if _lib().orc_apply_transpose(self._h, 0 if mode == "direct" else 1, _p(zb), _p(rb)):
+            raise RuntimeError("oracle: singular BEM matrix")
+        return rb
 
     def apply_dl(self, r, mode="fmm", with_mu=False):
         """The preconditioner with the second-kind double-layer correction:

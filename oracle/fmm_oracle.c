@@ -517,6 +517,19 @@ void orc_lu_solve(int N, const double *LU, const int32_t *piv, double *x) {
   }
 }
 
+/* Solves A^T x = b with the factors of orc_lu (P A = L U, so A^T = U^T L^T P): U^T y = b,
+ * L^T w = y, then x = P^T w (the row swaps undone in reverse order). */
+void orc_lu_solve_transpose(int N, const double *LU, const int32_t *piv, double *x) {
+  for (int i = 0; i < N; ++i) {
+    for (int j = 0; j < i; ++j) x[i] -= LU[(int64_t)j * N + i] * x[j];
+    x[i] /= LU[(int64_t)i * N + i];
+  }
+  for (int i = N - 1; i >= 0; --i)
+    for (int j = i + 1; j < N; ++j) x[i] -= LU[(int64_t)j * N + i] * x[j];
+  for (int k = N - 1; k >= 0; --k)
+    if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+}
+
 /* ======================================================================== */
 /* 5. Tree (Sec. 5.1): split at centre lines until a cell holds at most      */
 /*    leaf_max nodes.  On an n = m 2^L grid this gives the complete quadtree. */
@@ -1111,6 +1124,47 @@ int orc_apply_bc(orc_prob *P, int mode, const double *f, const double *g, double
     u[i] = vr[i] - a / (2.0 * PI_) + b / (2.0 * PI_);
   }
   free(z); free(vr); free(vc); free(q); free(K);
+  return 0;
+}
+
+/* ======================================================================== */
+/* 7d. The transpose of the preconditioner, for gradients with respect to the */
+/*     source weights.  P^{-1} r = V r + S_OG q with S q = -V_GO r (Eqs.       */
+/*     e:ubound/e:uinter with z = 0 on Gamma), so                              */
+/*     P^{-T} zb = V zb - V_GO^T S^{-T} S_OG^T zb: V is symmetric (G_ij = G_ji, */
+/*     equal cell weights h^2); (S_OG^T zb)_k = sum_i zb_i int_k G(x_i, y);     */
+/*     (V_GO^T c)_j = h^2 sum_m c_m G(y_m, x_j).  V zb by the FMM (mode 1) or   */
+/*     the direct sum (mode 0); the boundary parts summed directly.            */
+/* ======================================================================== */
+
+int orc_apply_transpose(orc_prob *P, int mode, const double *zb, double *rb) {
+  if (!P->lu_ok) return 1;
+  const int N = P->N, NG = P->NG, n = P->n;
+  const double h = P->h;
+  double *z = malloc(sizeof(double) * N), *vr = malloc(sizeof(double) * N);
+  double *t = calloc(NG, sizeof(double));
+  orc_apply(P, mode, zb, z, vr, NULL, NULL, NULL, NULL);  /* vr = V zb */
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < NG; ++k) {
+    double a = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double xi = P->x0 + (i % n + 1) * h, yi = P->y0 + (i / n + 1) * h;
+      a += zb[i] * orc_seg_int_log(xi, yi, P->eax[k], P->eay[k], P->ebx[k], P->eby[k]);
+    }
+    t[k] = -a / (2.0 * PI_);
+  }
+  orc_lu_solve_transpose(NG, P->LU, P->piv, t);  /* t <- S^{-T} S_OG^T zb */
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < N; ++j) {
+    const double xj = P->x0 + (j % n + 1) * h, yj = P->y0 + (j / n + 1) * h;
+    double a = 0.0;
+    for (int m = 0; m < NG; ++m) {
+      const double dx = P->ecx[m] - xj, dy = P->ecy[m] - yj;
+      a += t[m] * 0.5 * log(dx * dx + dy * dy);
+    }
+    rb[j] = vr[j] + h * h * a / (2.0 * PI_);  /* - V_GO^T t, G = -(1/2pi) ln r */
+  }
+  free(z); free(vr); free(t);
   return 0;
 }
 

@@ -99,6 +99,14 @@ class FmmPreconditioner:
         (second kind, (-1/2 I + K) mu = -(V r)|_Gamma)."""
         check(self.lib.fmmpc_set_bem_form(self._h, {"single_layer": 0, "double_layer": 1}[form]), self._h)
 
+    def apply_transpose(self, zb, out=None):
+        """rb = P^{-T} zb (fmmpc_apply_transpose): the FMM-transpose pass."""
+        import torch
+        k = self._vec(zb)
+        out = torch.empty_like(zb) if out is None else out
+        check(self.lib.fmmpc_apply_transpose(self._h, _ptr(zb), _ptr(out), k), self._h)
+        return out
+
     def apply_bc(self, f, g, out=None):
         """u from Eqs. e:ubound / e:uinter with Dirichlet data g at the 4n element midpoints."""
         import torch

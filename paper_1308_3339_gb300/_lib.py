@@ -68,6 +68,7 @@ SIGNATURES = {
     "fmmpc_set_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fmmpc_apply_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "fmmpc_set_bem_form": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fmmpc_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "fmmpc_set_p2p_engine": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "fmmpc_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),

@@ -273,6 +273,24 @@ int fmmpc_apply_bc(fmmpc_handle *h, const double *f_dev, const double *g_dev, do
   });
 }
 
+int fmmpc_apply_transpose(fmmpc_handle *h, const double *zb_dev, double *rb_dev, int32_t n_rhs) {
+  if (!h) return FMMPC_ERR_INVALID;
+  return guarded(h, [&] {
+    require(zb_dev && rb_dev && zb_dev != rb_dev, "apply_transpose: zb and rb must be distinct device buffers");
+    check_rhs(h, n_rhs);
+    if (h->bem_form != FMMPC_BEM_SINGLE_LAYER)
+      throw Error(FMMPC_ERR_UNSUPPORTED, "apply_transpose: the single-layer correction only");
+    init_bem_transpose(*h);
+    struct Restore {
+      fmmpc_handle *h;
+      ~Restore() { h->trans_pass = false; }
+    } restore{h};
+    h->trans_pass = true;
+    apply_fmm(*h, PART_TRANS, zb_dev, rb_dev, n_rhs);
+    return FMMPC_OK;
+  });
+}
+
 int fmmpc_set_bem_form(fmmpc_handle *h, int32_t form) {
   if (!h) return FMMPC_ERR_INVALID;
   return guarded(h, [&] {

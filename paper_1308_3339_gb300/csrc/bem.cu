@@ -262,6 +262,29 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   FMMPC_CUDA(cudaStreamSynchronize(s));
 }
 
+// T' for S^T from T for S (first block rows in the side-DFT form [C0 | C2 | A | B]): S^T is
+// block circulant with the blocks transposed and the side index reversed, so its DFT blocks
+// are C0^T, C2^T and (A + iB)^H = A^T - i B^T: T'[m][blk n + k] = +-T[k][blk n + m].
+__global__ void k_bem_transpose(int n, const double *__restrict__ T, double *__restrict__ Tt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * 4 * n) return;
+  const int64_t mrow = t / (4 * n);
+  const int c = (int)(t % (4 * n)), blk = c / n, k = c % n;
+  const double v = T[(int64_t)k * 4 * n + blk * n + mrow];
+  Tt[t] = (blk == 3) ? -v : v;
+}
+
+// S^{-T} for the transpose pass, formed on first use.
+void init_bem_transpose(fmmpc_handle &H) {
+  if (H.SinvT) return;
+  const int n = H.g.n;
+  double *Tt = H.pool.get<double>((size_t)n * 4 * n);
+  k_bem_transpose<<<nblk((int64_t)n * 4 * n), 256, 0, H.stream>>>(n, H.Sinv, Tt);
+  FMMPC_LAUNCH_CHECK();
+  FMMPC_CUDA(cudaStreamSynchronize(H.stream));
+  H.SinvT = Tt;
+}
+
 // The inverse of -1/2 I + K in the side-DFT form of the single-layer inverse (the same
 // 90-degree rotation symmetry), for the double-layer correction; formed on first use.
 void init_bem_dl(fmmpc_handle &H) {

@@ -64,6 +64,7 @@ template <typename R>
 struct Mats {
   const cpx<R> *vm2m, *vl2l, *bm2m, *bp2m;
   const cpx<R> *bdl;  // [side][element of a leaf run][P]: multipoles of a unit double layer
+  const cpx<R> *bpt;  // [side][element][P]: multipoles of a unit point source at its midpoint
 };
 
 // ------------------------------------------------------------------ weights
@@ -577,10 +578,13 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
 // (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run, with
 // a barrier between levels.  The side's whole tree (2^(L+1) - 1 runs) and its M2M matrices
 // stay in shared memory; the result is written out once.
-// qm: single-layer density (NULL: none); qd: double-layer density with sign dsgn (NULL: none).
+// q: single-layer density with its leaf P2M matrix bq and scale qscale (bp2m and h for
+// element densities; bpt and h^2 for point sources at the midpoints, the transpose pass;
+// NULL: none); qd: double-layer density with sign dsgn (NULL: none).
 template <typename R, int P>
-__global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, Mats<R> mt,
-                                                 cpx<R> *__restrict__ Mb, const double *__restrict__ qd, R dsgn) {
+__global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, const cpx<R> *__restrict__ bq,
+                                                 R qscale, Mats<R> mt, cpx<R> *__restrict__ Mb,
+                                                 const double *__restrict__ qd, R dsgn) {
   extern __shared__ __align__(16) unsigned char bnd_smem[];
   cpx<R> *T2 = reinterpret_cast<cpx<R> *>(bnd_smem);  // [2 children][P][P]
   cpx<R> *S = T2 + 2 * P * P;                          // [level l: 2^l runs][P], level 0 first
@@ -595,9 +599,9 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
     cpx<R> acc = mk<R>(0, 0);
     if (q) {
       const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+      const cpx<R> *B = bq + (int64_t)side * m * P + nn;
       for (int e = 0; e < m; ++e) {
-        const R qe = (R)qr[e] * h;
+        const R qe = (R)qr[e] * qscale;
         acc.re = fma(qe, B[e * P].re, acc.re);
         acc.im = fma(qe, B[e * P].im, acc.im);
       }
@@ -640,8 +644,9 @@ __global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict
 // The same pass through global memory, for trees whose levels do not fit in shared memory
 // (FP64 at the largest depths).
 template <typename R, int P>
-__global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restrict__ q, Mats<R> mt,
-                                                   cpx<R> *__restrict__ Mb, const double *__restrict__ qd, R dsgn) {
+__global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restrict__ q, const cpx<R> *__restrict__ bq,
+                                                   R qscale, Mats<R> mt, cpx<R> *__restrict__ Mb,
+                                                   const double *__restrict__ qd, R dsgn) {
   const int side = blockIdx.x, rhs = blockIdx.y;
   const int n = g.n, m = g.m, L = g.L;
   cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
@@ -651,9 +656,9 @@ __global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restri
     cpx<R> acc = mk<R>(0, 0);
     if (q) {
       const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = mt.bp2m + (int64_t)side * m * P + nn;
+      const cpx<R> *B = bq + (int64_t)side * m * P + nn;
       for (int e = 0; e < m; ++e) {
-        const R qe = (R)qr[e] * (R)g.h;
+        const R qe = (R)qr[e] * qscale;
         acc.re = fma(qe, B[e * P].re, acc.re);
         acc.im = fma(qe, B[e * P].im, acc.im);
       }
@@ -1115,6 +1120,110 @@ __global__ void __launch_bounds__(256) k_dl_near(Geo g, int64_t nbnear, int nrhs
   }
 }
 
+// Point sources at the collocation points next to the boundary (the transpose pass):
+// phib[slot][t] = sum_e c_e h^2 ln|x_t - y_e| (node units) over the elements of the leaf's
+// near boundary runs; y_e the element midpoint.  Same blocks and lists as k_bnd_near.
+template <typename R>
+__global__ void __launch_bounds__(256) k_pt_near(Geo g, int64_t nbnear, int nrhs, const int32_t *__restrict__ leaf,
+                                                 const int32_t *__restrict__ first, const int32_t *__restrict__ src,
+                                                 const double *__restrict__ c, R *__restrict__ phib) {
+  __shared__ double red[256];
+  const int slot = blockIdx.x, rhs = blockIdx.y;
+  const int n = g.n, m = g.m, L = g.L, mm = m * m;
+  const int ngrp = blockDim.x / mm;
+  const int t = threadIdx.x % mm, grp = threadIdx.x / mm;
+  int a, b;
+  morton_decode((uint32_t)leaf[slot], a, b);
+  const double h2 = g.h * g.h;
+  const double *cr = c + (int64_t)rhs * g.NG;
+  const int x = a * m + t % m + 1, y = b * m + t / m + 1;
+  const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
+  double acc = 0;
+  if (grp < ngrp)
+    for (int idx = grp; idx < cnt; idx += ngrp) {
+      const int bl = src[f0 + idx / m], e = idx % m;
+      const int side = bl >> L;
+      const int64_t kk = bl & ((int64_t(1) << L) - 1);
+      int u, d;
+      side_coords(side, n + 1, x, y, u, d);
+      // midpoint minus node along the side: ((2(k m + e) + 1)(n + 1) - 2 u n) / (2n)
+      const double ds = (double)((2 * (kk * m + e) + 1) * (int64_t)(n + 1) - 2 * (int64_t)u * n) / (2.0 * n);
+      acc += cr[side * n + kk * m + e] * h2 * 0.5 * log(ds * ds + (double)d * (double)d);
+    }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < mm) {
+    double sacc = 0;
+    for (int q2 = 0; q2 < ngrp; ++q2) sacc += red[q2 * mm + threadIdx.x];
+    phib[((int64_t)rhs * nbnear + slot) * mm + threadIdx.x] = (R)sacc;
+  }
+}
+
+// The transpose pass's boundary values: t_k = int_{element k} Phi(y) dGamma_y / h^2 for the
+// volume potential Phi of the weights (h^2 zb) whose local expansions Lb and near nodes the
+// collocation pass uses, i.e. (S_OG^T zb)_k = sum_i zb_i int_k G(x_i, y) dGamma.  Far part:
+// int_e Re sum_k Lt_k z^k over the element, z the offset from each ancestor run's centre in
+// run units, in closed form; near part: the closed-form element integrals of ln|y - x_j|.
+// Block per (boundary leaf run, rhs); FP64 arithmetic.
+template <typename R>
+__global__ void __launch_bounds__(256) k_colloc_T(Geo g, int nrhs, const R *__restrict__ wpad,
+                                                  const cpx<R> *__restrict__ Lb, const int32_t *__restrict__ pfirst,
+                                                  const int32_t *__restrict__ psrc, double *__restrict__ tout) {
+  __shared__ double red[8][16];
+  const int n = g.n, m = g.m, L = g.L, p = g.p, mm = m * m;
+  const int64_t bl = blockIdx.x;
+  const int rhs = blockIdx.y;
+  const int side = (int)(bl >> L);
+  const int64_t kk = bl & ((int64_t(1) << L) - 1);
+  const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
+  const double ell = (n + 1.0) / n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int c_near = pfirst[bl + 1] - pfirst[bl];
+  for (int e = 0; e < m; ++e) {
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < c_near * mm; it += blockDim.x) {
+      const int el = it / mm, t = it % mm;
+      int a, b;
+      morton_decode((uint32_t)psrc[pfirst[bl] + el], a, b);
+      const int i = a * m + t % m, j = b * m + t / m;
+      int u, d;
+      side_coords(side, n + 1, i + 1, j + 1, u, d);
+      const int64_t num = (kk * m + e) * (int64_t)(n + 1) - (int64_t)u * n;
+      acc += (double)W[(int64_t)(j + g.pad) * g.npad + i + g.pad] * seg_log_int<double>((double)num / n, ell, (double)d);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[wid][e] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    const int e = threadIdx.x;
+    double near = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) near += red[w][e];
+    const int along = (int)(kk * m + e);  // element index along the side
+    const double ex = (side == 0) ? 1.0 : (side == 2 ? -1.0 : 0.0);
+    const double ey = (side == 1) ? 1.0 : (side == 3 ? -1.0 : 0.0);
+    double far = 0.0;
+    for (int l = 0; l <= L; ++l) {
+      const int nl = n >> l;
+      const int64_t id = ((int64_t)side << l) + along / nl;
+      const double o1 = ell * ((double)(along % nl) - 0.5 * nl) / nl, o2 = o1 + ell / nl;
+      const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
+      // sum_k Lt_k e^k nl (o2^{k+1} - o1^{k+1}) / (k + 1)
+      double pr = 1.0, pi = 0.0, p1 = o1, p2 = o2;  // e^k; o^{k+1}
+      for (int k = 0; k < p; ++k) {
+        const double w = nl * (p2 - p1) / (k + 1);
+        far += w * ((double)Lc[k].re * pr - (double)Lc[k].im * pi);
+        const double nr = pr * ex - pi * ey, ni = pr * ey + pi * ex;
+        pr = nr;
+        pi = ni;
+        p1 *= o1;
+        p2 *= o2;
+      }
+    }
+    tout[(int64_t)rhs * g.NG + side * n + along] = (near + far) * NEG_INV_2PI / (g.h * g.h) * g.h;
+  }
+}
+
 // The same integrals formed once at set-up (FP64, stored FP32) for the single-precision
 // forms: K[(first[slot] m + idx) m^2 + t] = h int_{element idx} ln|x_t - y| ds, so each apply
 // is a product with q instead of ~5e6 log/atan2 evaluations at 1024^2.
@@ -1571,6 +1680,7 @@ Mats<R> mats_of(fmmpc_handle &H) {
   mt.bm2m = base + 8 * P * P;
   mt.bp2m = base + 16 * P * P;
   mt.bdl = mt.bp2m + 4 * H.g.m * P;
+  mt.bpt = mt.bdl + 4 * H.g.m * P;
   return mt;
 }
 
@@ -1645,6 +1755,12 @@ int run_bnd_near(fmmpc_handle &H, int nrhs, cudaStream_t s) {
   const Geo &g = H.g;
   const Lists &Ls = H.lists;
   const dim3 grid((unsigned)Ls.nbnear, nrhs);
+  if (H.trans_pass) {  // point sources c' at the collocation points (transpose pass)
+    k_pt_near<R><<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first, Ls.pbv_src, H.fb.q,
+                                      (R *)H.fb.phib);
+    FMMPC_LAUNCH_CHECK();
+    return 1;
+  }
   if (H.bem_form == 1) {  // double-layer correction: D mu only (mu in fb.q)
     k_dl_near<R><<<grid, 256, 0, s>>>(g, Ls.nbnear, nrhs, Ls.pbv_leaf, Ls.pbv_first, Ls.pbv_src, H.fb.q, R(1), 0,
                                       (R *)H.fb.phib);
@@ -1722,7 +1838,9 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     H.launches = launches;
     return;
   }
-  const bool with_bnd = part == PART_FULL || part == PART_VCOL || part == PART_Q || part == PART_BC;
+  const bool with_bnd =
+      part == PART_FULL || part == PART_VCOL || part == PART_Q || part == PART_BC || part == PART_TRANS;
+  const bool trans = part == PART_TRANS;       // P^{-T}: element integrals, S^{-T}, point sources
   const bool dl = H.bem_form == 1;             // double-layer correction (mu from -1/2 I + K)
   const bool bc = part == PART_BC && H.bc_g;   // boundary data g (Eqs. e:ubound / e:uinter)
   // The tensor-core near field and volume M2L do not depend on the boundary chain
@@ -1751,10 +1869,14 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
                                                               Ls.vbb_src, Mv, Lb, g.lnh);
     // the side DFT for the two-word BEM apply, fused (not with boundary data, which changes
     // vcol after this kernel)
-    const bool vt_f2 = H.Sinv_hi && H.fb.vt_hi && !bc;
-    k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
-                                                               H.fb.vcol, H.fb.kcol, vt_f2 ? H.fb.vt_hi : nullptr,
-                                                               vt_f2 ? H.fb.vt_lo : nullptr);
+    const bool vt_f2 = H.Sinv_hi && H.fb.vt_hi && !bc && !trans;
+    if (trans)  // t = S_OG^T zb: element integrals of the volume potential, into vcol
+      k_colloc_T<R><<<dim3((unsigned)g.nbleaf, nrhs), 256, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
+                                                                   H.fb.vcol);
+    else
+      k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
+                                                                 H.fb.vcol, H.fb.kcol, vt_f2 ? H.fb.vt_hi : nullptr,
+                                                                 vt_f2 ? H.fb.vt_lo : nullptr);
     FMMPC_LAUNCH_CHECK();
     launches += 2;
     if (bc) {  // vcol -= (1/2 I + K) g: Eq. e:ubound's data term
@@ -1777,7 +1899,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       ++launches;
     } else {
       k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
-      k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, dl ? H.Kdl_inv : H.Sinv, H.fb.vt, H.fb.q);
+      k_bem_apply<<<g.n, 256, 0, s>>>(g.n, nrhs, dl ? H.Kdl_inv : (trans ? H.SinvT : H.Sinv), H.fb.vt, H.fb.q);
       launches += 2;
     }
     FMMPC_LAUNCH_CHECK();
@@ -1807,8 +1929,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       // single layer q (none in the double-layer form); double layer mu (+D mu) or data g (-D g)
       const double *qm = dl ? nullptr : H.fb.q, *qd = dl ? H.fb.q : (bc ? H.bc_g : nullptr);
       const R dsgn = dl ? R(1) : R(-1);
-      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, qm, mt, Mb, qd, dsgn);
-      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, qm, mt, Mb, qd, dsgn);
+      // the transpose pass places point sources h^2 c' at the collocation points
+      const cpx<R> *bq = trans ? mt.bpt : mt.bp2m;
+      const R qscale = trans ? (R)(g.h * g.h) : (R)g.h;
+      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, qm, bq, qscale, mt, Mb, qd, dsgn);
+      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, qm, bq, qscale, mt, Mb, qd, dsgn);
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;
@@ -1949,6 +2074,13 @@ void build_mats(fmmpc_handle &H, std::vector<cpx<R>> &out) {
         for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
         all.push_back(v);
       }
+    }
+  // a unit point source at the element midpoint (the transpose pass): Mt = (1, 0, ...) about
+  // the midpoint, shifted to the run centre
+  for (int sd = 0; sd < 4; ++sd)
+    for (int e = 0; e < m; ++e) {
+      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
+      for (int nn = 0; nn < P; ++nn) all.push_back(T[nn * P]);
     }
   out.resize(all.size());
   for (size_t i = 0; i < all.size(); ++i) out[i] = mk<R>((R)all[i].real(), (R)all[i].imag());

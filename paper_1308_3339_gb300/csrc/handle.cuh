@@ -15,6 +15,7 @@ enum ApplyPart {
   PART_VCOL = 3,   // V r at the collocation points
   PART_Q = 4,      // BEM density q (mu in the double-layer form)
   PART_BC = 5,     // the boundary-integral solution with Dirichlet data H.bc_g (fmmpc_apply_bc)
+  PART_TRANS = 6,  // the transpose P^{-T} (fmmpc_apply_transpose)
 };
 
 // FMM buffers for one arithmetic type (float or double).
@@ -119,9 +120,11 @@ struct fmmpc_handle {
   fmmpc::FmmBufs fb{};
   double *Sinv = nullptr;   // [n][4n] first block row of the FP64 inverse of the single-layer matrix
   double *Kdl_inv = nullptr;  // the same for -1/2 I + K (double-layer correction), made on first use
+  double *SinvT = nullptr;    // the same for S^T (the transpose pass), made on first use
   float *Kdl_hi = nullptr, *Kdl_lo = nullptr;  // and as two FP32 words (single-precision forms)
   int bem_form = 0;         // 0: single-layer correction (Eq. e:ubound), 1: second-kind double layer
   const double *bc_g = nullptr;  // boundary data of the running fmmpc_apply_bc call (else NULL)
+  bool trans_pass = false;       // the running apply is the transpose pass
   float *Sinv_hi = nullptr, *Sinv_lo = nullptr;  // the same as two FP32 words (single-precision forms)
   double *stage_in = nullptr, *stage_out = nullptr, *stage_g = nullptr;  // device staging for *_host calls
   fmmpc::KrylovWs kw{};
@@ -170,6 +173,7 @@ int solve_batched_graphed(std::vector<fmmpc_handle *> &hs, const double *const *
 void init_fmm(fmmpc_handle &H);
 void init_bem(fmmpc_handle &H, DevPool &tmp);
 void init_bem_dl(fmmpc_handle &H);
+void init_bem_transpose(fmmpc_handle &H);
 void spmv5(fmmpc_handle &H, const double *x, double *y, int nrhs);
 int solve(fmmpc_handle &H, const double *f, const double *g, double *u, int nrhs,
           const fmmpc_solve_opts &o, fmmpc_solve_info &info);

@@ -281,3 +281,33 @@ def test_double_layer_variant_direct_equals_fmm_and_preconditions():
     _, it_dl, _, c2 = R.solve(f, "fgmres", 30, 100, 1e-8, "fmm_dl")
     print("fgmres iterations: single layer", it_sl, "double layer", it_dl)
     assert c1 and c2 and abs(it_sl - it_dl) <= 3
+
+
+# ---------------------------------------------------------------- the transpose of P^{-1}
+def test_lu_solves_and_transpose_solves_match_numpy():
+    # pins orc_lu / orc_lu_solve_transpose directly (and so the BEM solves)
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((40, 40)) + 8 * np.eye(40)
+    b = rng.standard_normal(40)
+    LU, piv = O.lu(A)
+    assert np.max(np.abs(O.lu_solve_transpose(LU, piv, b) - np.linalg.solve(A.T, b))) < 1e-13
+    S_, _ = O.bem_matrices(8, 0.0, 0.0, 1.0)
+    LU, piv = O.lu(S_)
+    assert rel_l2(O.lu_solve_transpose(LU, piv, b[:32]), np.linalg.solve(S_.T, b[:32])) < 1e-12
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_transpose_is_the_adjoint_of_the_preconditioner(n):
+    # <P^{-1} a, b> = <a, P^{-T} b> for the direct form, to rounding; the FMM forms within
+    # the FMM truncation
+    rng = np.random.default_rng(n)
+    a, b = rng.standard_normal(n * n), rng.standard_normal(n * n)
+    R = O.Problem(n, p=12)
+    lhs = R.apply(a, "direct") @ b
+    rhs = a @ R.apply_transpose(b, "direct")
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # and the dense transpose, column by column
+    if n == 8:
+        Pm = np.stack([R.apply(e, "direct") for e in np.eye(n * n)], 1)
+        assert np.max(np.abs(R.apply_transpose(b, "direct") - Pm.T @ b)) < 1e-12 * np.max(np.abs(Pm.T @ b))
+    assert rel_l2(R.apply_transpose(b, "fmm"), R.apply_transpose(b, "direct")) < 1e-8
