@@ -35,10 +35,10 @@ struct OpDev {
 OpDev op_of(const fmmpc_handle &H) { return OpDev{H.op, H.g.n, 1.0 / (H.g.h * H.g.h), H.acoef}; }
 
 __device__ __forceinline__ double op_at(const OpDev &o, const double *__restrict__ x, int64_t t) {
-  const int n = o.n;
+  const int n = o.n, lgn = __ffs(n) - 1;  // n is a power of two: shifts, not divisions
   const int64_t N = (int64_t)n * n;
-  const int64_t k = t % N;
-  const int i = (int)(k % n), j = (int)(k / n);
+  const int64_t k = t & (N - 1);
+  const int i = (int)(k & (n - 1)), j = (int)(k >> lgn);
   if (o.op == 2) {
     double nb = 0.0;
 #pragma unroll
@@ -84,11 +84,11 @@ __global__ void k_fold_rhs(OpDev o, int64_t total, const double *__restrict__ f,
                            double *__restrict__ b) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
-  const int n = o.n;
+  const int n = o.n, lgn = __ffs(n) - 1;
   const double s = o.s;
   const int64_t N = (int64_t)n * n;
-  const int64_t rhs = t / N, k = t % N;
-  const int i = (int)(k % n), j = (int)(k / n);
+  const int64_t rhs = t >> (2 * lgn), k = t & (N - 1);
+  const int i = (int)(k & (n - 1)), j = (int)(k >> lgn);
   if (o.op == 2) {
     b[t] = f[t] / s;
     return;
@@ -122,7 +122,8 @@ __global__ void k_mass_sweep(int n, int nrhs, int cols, double scale, const doub
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nrhs * n) return;
   const int64_t N = (int64_t)n * n;
-  const int64_t rhs = t / n, line = t % n;
+  const int lgn = __ffs(n) - 1;
+  const int64_t rhs = t >> lgn, line = t & (n - 1);
   const int64_t base = rhs * N + (cols ? line : line * n), st = cols ? n : 1;
   double y = 0.0;
   for (int k = 0; k < n; ++k) {
@@ -133,6 +134,48 @@ __global__ void k_mass_sweep(int n, int nrhs, int cols, double scale, const doub
     y = dst[base + k * st] - cp[k] * y;
     dst[base + k * st] = y;
   }
+}
+
+// acc[q] += <V_{i0+q}, w> (q < 8, i0 + q < nv; with self, index nv is <w, w>) over this
+// thread's share of the N elements of one right-hand side, two elements per load (N is even
+// and every vector starts 16-byte aligned).  Vr and wr point at that right-hand side.
+__device__ __forceinline__ void mdot_chunk(int64_t N, const double *__restrict__ Vr, int64_t vs,
+                                           const double *__restrict__ wr, int i0, int nv, bool with_self,
+                                           double (&acc)[8]) {
+  const int64_t N2 = N >> 1;
+  const double2 *w2 = reinterpret_cast<const double2 *>(wr);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N2; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 wk = w2[k];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (i0 + q < nv) {
+        const double2 v = reinterpret_cast<const double2 *>(Vr + (int64_t)(i0 + q) * vs)[k];
+        acc[q] = fma(v.x, wk.x, fma(v.y, wk.y, acc[q]));
+      } else if (with_self && i0 + q == nv) {
+        acc[q] = fma(wk.x, wk.x, fma(wk.y, wk.y, acc[q]));
+      }
+    }
+  }
+}
+
+// w -= sum_{i < nv} c[i] V_i over this thread's share of one right-hand side (two elements
+// per load); returns this share of |w|^2 after the update.
+__device__ __forceinline__ double update_chunk(int64_t N, const double *__restrict__ Vr, int64_t vs,
+                                               const double *__restrict__ c, int nv, double *__restrict__ wr) {
+  const int64_t N2 = N >> 1;
+  double2 *w2 = reinterpret_cast<double2 *>(wr);
+  double sq = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N2; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = w2[k];
+    for (int i = 0; i < nv; ++i) {
+      const double2 b = reinterpret_cast<const double2 *>(Vr + (int64_t)i * vs)[k];
+      v.x = fma(-c[i], b.x, v.x);
+      v.y = fma(-c[i], b.y, v.y);
+    }
+    w2[k] = v;
+    sq = fma(v.x, v.x, fma(v.y, v.y, sq));
+  }
+  return sq;
 }
 
 // partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
@@ -148,14 +191,7 @@ __global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, 
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-      const double wk = wr[k];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (i0 + q < nv) acc[q] = fma(V[(int64_t)(i0 + q) * vs + (int64_t)rhs * N + k], wk, acc[q]);
-        else if (i0 + q == nv && with_self) acc[q] = fma(wk, wk, acc[q]);
-      }
-    }
+    mdot_chunk(N, V + (int64_t)rhs * N, vs, wr, i0, nv, with_self != 0, acc);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       double v = acc[q];
@@ -196,14 +232,7 @@ __global__ void k_mupdate_sq(int64_t N, int nv, const double *__restrict__ V, in
   __shared__ double red[RED_THREADS / 32];
   const int rhs = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double *wr = w + (int64_t)rhs * N;
-  double sq = 0.0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    double v = wr[k];
-    for (int i = 0; i < nv; ++i) v = fma(-c[rhs * MAXJ + i], V[(int64_t)i * vs + (int64_t)rhs * N + k], v);
-    wr[k] = v;
-    sq = fma(v, v, sq);
-  }
+  double sq = update_chunk(N, V + (int64_t)rhs * N, vs, c + rhs * MAXJ, nv, w + (int64_t)rhs * N);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   if (lane == 0) red[wid] = sq;
@@ -220,7 +249,7 @@ __global__ void k_mupdate(int64_t N, int nrhs, int nv, const double *__restrict_
                           const double *__restrict__ c, double *__restrict__ w) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  const int rhs = (int)(t / N);
+  const int rhs = (int)(t >> (__ffsll(N) - 1));  // N = n^2, a power of two
   double v = w[t];
   for (int i = 0; i < nv; ++i) v = fma(-c[rhs * MAXJ + i], V[i * vs + t], v);
   w[t] = v;
@@ -231,7 +260,7 @@ __global__ void k_maxpy(int64_t N, int nrhs, int nv, const double *__restrict__ 
                         const double *__restrict__ y, double *__restrict__ x) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  const int rhs = (int)(t / N);
+  const int rhs = (int)(t >> (__ffsll(N) - 1));  // N = n^2, a power of two
   double v = x[t];
   for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
   x[t] = v;
@@ -242,7 +271,7 @@ __global__ void k_scale(int64_t N, int nrhs, const double *__restrict__ a, const
                         double *__restrict__ y) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  y[t] = a[t / N] * x[t];
+  y[t] = a[t >> (__ffsll(N) - 1)] * x[t];
 }
 
 // x += y
@@ -264,7 +293,7 @@ __global__ void k_cg_xr(int64_t N, int nrhs, const double *__restrict__ a, const
                         const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  const double al = a[t / N];
+  const double al = a[t >> (__ffsll(N) - 1)];
   x[t] = fma(al, p[t], x[t]);
   r[t] = fma(-al, q[t], r[t]);
 }
@@ -274,7 +303,7 @@ __global__ void k_cg_p(int64_t N, int nrhs, const double *__restrict__ beta, con
                        double *__restrict__ p) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  p[t] = fma(beta[t / N], p[t], z[t]);
+  p[t] = fma(beta[t >> (__ffsll(N) - 1)], p[t], z[t]);
 }
 
 }  // namespace
@@ -899,7 +928,7 @@ __global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const
                          const double *__restrict__ y, double *__restrict__ x) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  const int rhs = (int)(t / N), nv = ctl[KC_JCNT];
+  const int rhs = (int)(t >> (__ffsll(N) - 1)), nv = ctl[KC_JCNT];
   double v = x[t];
   for (int i = 0; i < nv; ++i) v = fma(y[rhs * MAXJ + i], Z[i * vs + t], v);
   x[t] = v;
@@ -910,7 +939,7 @@ __global__ void k_gscale_col(const int *__restrict__ ctl, int64_t N, int nrhs, c
                              const double *__restrict__ w, double *__restrict__ V, int64_t vs, double *__restrict__ t2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * nrhs) return;
-  const double v = sc[t / N] * w[t];
+  const double v = sc[t >> (__ffsll(N) - 1)] * w[t];
   V[(int64_t)ctl[KC_J] * vs + t] = v;
   if (t2) t2[t] = v;
 }
@@ -961,12 +990,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gdots(const int *__restrict__ c
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-      const double wk = wr[k];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (i0 + q < nv) acc[q] = fma(V[(int64_t)(i0 + q) * vs + (int64_t)rhs * N + k], wk, acc[q]);
-    }
+    mdot_chunk(N, V + (int64_t)rhs * N, vs, wr, i0, nv, false, acc);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       double v = acc[q];
@@ -997,15 +1021,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gupdate(const int *__restrict__
   const int rhs = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nv = ctl[KC_J] + 1;
-  double *wr = w + (int64_t)rhs * N;
-  const double *cr = c + rhs * MAXJ;
-  double sq = 0.0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    double v = wr[k];
-    for (int i = 0; i < nv; ++i) v = fma(-cr[i], V[(int64_t)i * vs + (int64_t)rhs * N + k], v);
-    wr[k] = v;
-    sq = fma(v, v, sq);
-  }
+  double sq = update_chunk(N, V + (int64_t)rhs * N, vs, c + rhs * MAXJ, nv, w + (int64_t)rhs * N);
   if (!wsq) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);

@@ -23,9 +23,8 @@
 // sums of M~_0 that carry ln rho.
 // Padding targets are computed and dropped.  The low-order terms dominate the translated
 // field and meet the large log o + ln rho, so their products are split hi + lo in the
-// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 64 for BF16: M~_0..7, in K steps
-// of their own): rounded input x rounded matrix, input residual x rounded matrix, rounded
-// input x matrix residual.
+// spare K columns (K = 32 for TF32: M~_0..2 at p = 10; K = 48 for BF16: M~_0..6): rounded
+// input x rounded matrix, input residual x rounded matrix, rounded input x matrix residual.
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
@@ -102,9 +101,7 @@ __device__ __forceinline__ float m2l_round(float x) {
 // K input v of a cell: v < 2p the rounded real parts of M~ (Re M~_0, Im M~_0, Re M~_1, ...);
 // for j < nsplit, v = sb + 4j + {0, 1}: the rounding residual of M~_j (meets B's rounded
 // column j), v = sb + 4j + {2, 3}: the rounded M~_j again (meets the residual of column j).
-// sb (split base) is 2p for TF32; for BF16 it is 2p rounded up to a whole K step of 16, so
-// the small correction products never share an MMA's K step with the main products (the
-// tensor core adds a step's products at the scale of its largest one).
+// sb (split base) is 2p.
 template <int KIND>
 __device__ __forceinline__ float m2l_input(const cpx<float> *M, int v, int p, int nsplit, int sb) {
   if (v < 2 * p) {
@@ -466,11 +463,13 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
   const int L = g.L, p = g.p;
   T.kind = (H.prec == FMMPC_PREC_MIXED_TF32) ? 0 : 1;
   T.width = (2 * p + 2 <= 24) ? 24 : 32;  // outputs per class
-  // hi/lo splits of the leading multipoles in the spare K columns of the 128-byte row: TF32
-  // holds 32 inputs (4 K steps of 8), BF16 64 (4 K steps of 16); the BF16 corrections start
-  // at the next whole K step (at p = 10: main terms in steps 0-1, M~_0..7 split in 2-3)
-  const int kcap = T.kind == 0 ? 32 : 64;
-  T.sbase = T.kind == 0 ? 2 * p : (2 * p + 15) / 16 * 16;
+  // hi/lo splits of the leading multipoles in the spare K columns: TF32 32 inputs (4 K steps
+  // of 8, one 128-byte row), BF16 48 (3 K steps of 16).  A BF16 hi + lo pair carries about
+  // 16 bits, so the BF16 products stay near 2^-16 relative however many terms are split
+  // (splitting every term, or moving the corrections to K steps of their own, measured the
+  // same z error, 4.5e-5 at 1024^2): three K steps are the cheapest at that accuracy.
+  const int kcap = T.kind == 0 ? 32 : 48;
+  T.sbase = 2 * p;
   T.nsplit = std::max(0, std::min(p, (kcap - T.sbase) / 4));
   // offset sets by class, from the lists themselves, then checked against every list
   int *dtab = tmp.get<int>(4 * 225), *derr = tmp.get<int>(1);

