@@ -58,13 +58,15 @@ __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
 // Fixed translation matrices (complex R, row-major [n][k], P = p):
 //   vm2m[ch]    volume M2M from child ch (Morton position) to its parent
 //   vl2l[ch]    volume L2L from a parent to child ch
-//   bm2m[s][j]  boundary M2M from run child j of side s to its parent run
-//   bp2m[s][e]  row vector: multipole of element e of a leaf run of side s, unit density
+//   lvq, lvd, lvp  boundary-element multipole tables per level (described in the struct)
 template <typename R>
 struct Mats {
-  const cpx<R> *vm2m, *vl2l, *bm2m, *bp2m;
-  const cpx<R> *bdl;  // [side][element of a leaf run][P]: multipoles of a unit double layer
-  const cpx<R> *bpt;  // [side][element][P]: multipoles of a unit point source at its midpoint
+  const cpx<R> *vm2m, *vl2l;
+  // Multipoles of a boundary element about the centre of its run at every level l (scale
+  // n >> l) for a unit single layer (lvq), a unit double layer (lvd) and a unit point source
+  // at its midpoint (lvp); level-major, level l at offset 4 P (2n - 2 (n >> l)), then
+  // [side][element of the run][P]
+  const cpx<R> *lvq, *lvd, *lvp;
 };
 
 // ------------------------------------------------------------------ weights
@@ -574,126 +576,61 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
   }
 }
 
-// Boundary trees, one block per side: P2M of each leaf run from its element densities
-// (Mt_n = sum_e q_e h bp2m[s][e][n]), then the M2M levels up to the side's root run, with
-// a barrier between levels.  The side's whole tree (2^(L+1) - 1 runs) and its M2M matrices
-// stay in shared memory; the result is written out once.
-// q: single-layer density with its leaf P2M matrix bq and scale qscale (bp2m and h for
-// element densities; bpt and h^2 for point sources at the midpoints, the transpose pass;
-// NULL: none); qd: double-layer density with sign dsgn (NULL: none).
+// Multipoles of every boundary cell at every level in one launch: warp per (boundary cell,
+// rhs), lanes striding over the cell's elements, Mt_n = sum_e (q_e qscale Bq_l[e][n] +
+// qd_e dsgn Bd_l[e][n]) with the level tables of Mats (element single layer, double layer,
+// or point source at the midpoint); q or qd may be NULL.
 template <typename R, int P>
-__global__ void __launch_bounds__(1024) k_bnd_up(Geo g, const double *__restrict__ q, const cpx<R> *__restrict__ bq,
-                                                 R qscale, Mats<R> mt, cpx<R> *__restrict__ Mb,
-                                                 const double *__restrict__ qd, R dsgn) {
-  extern __shared__ __align__(16) unsigned char bnd_smem[];
-  cpx<R> *T2 = reinterpret_cast<cpx<R> *>(bnd_smem);  // [2 children][P][P]
-  cpx<R> *S = T2 + 2 * P * P;                          // [level l: 2^l runs][P], level 0 first
-  const int side = blockIdx.x, rhs = blockIdx.y;
-  const int n = g.n, m = g.m, L = g.L;
-  const R h = (R)g.h;
-  for (int t = threadIdx.x; t < 2 * P * P; t += blockDim.x) T2[t] = mt.bm2m[(int64_t)side * 2 * P * P + t];
-  const int nleafrun = 1 << L;
-  cpx<R> *SL = S + (int64_t)(nleafrun - 1) * P;
-  for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
-    const int k = t / P, nn = t % P;
-    cpx<R> acc = mk<R>(0, 0);
-    if (q) {
-      const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = bq + (int64_t)side * m * P + nn;
-      for (int e = 0; e < m; ++e) {
-        const R qe = (R)qr[e] * qscale;
-        acc.re = fma(qe, B[e * P].re, acc.re);
-        acc.im = fma(qe, B[e * P].im, acc.im);
+__global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double *__restrict__ q,
+                                                   const cpx<R> *__restrict__ Bq, R qscale,
+                                                   const double *__restrict__ qd, const cpx<R> *__restrict__ Bd,
+                                                   R dsgn, cpx<R> *__restrict__ Mb) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)nrhs * g.nbcell) return;
+  const int rhs = (int)(wid / g.nbcell);
+  const int64_t c = wid % g.nbcell;
+  int l = 0;
+  while (blevel_offset(l + 1) <= c) ++l;
+  const int64_t id = c - blevel_offset(l);
+  const int n = g.n, len = n >> l;
+  const int side = (int)(id >> l);
+  const int64_t run = id & ((int64_t(1) << l) - 1);
+  const int64_t e0 = (int64_t)side * n + run * len;  // first element of the cell
+  const int64_t toff = (int64_t)4 * P * (2 * n - 2 * len) + (int64_t)side * len * P;
+  cpx<R> acc[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) acc[k] = mk<R>(0, 0);
+  const double *qr = q ? q + (int64_t)rhs * g.NG + e0 : nullptr;
+  const double *dr = qd ? qd + (int64_t)rhs * g.NG + e0 : nullptr;
+  for (int e = lane; e < len; e += 32) {
+    if (qr) {
+      const R w = (R)qr[e] * qscale;
+      const cpx<R> *B = Bq + toff + (int64_t)e * P;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        acc[k].re = fma(w, B[k].re, acc[k].re);
+        acc[k].im = fma(w, B[k].im, acc[k].im);
       }
     }
-    if (qd) {
-      const double *dr = qd + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = mt.bdl + (int64_t)side * m * P + nn;
-      for (int e = 0; e < m; ++e) {
-        const R de = (R)dr[e] * dsgn;
-        acc.re = fma(de, B[e * P].re, acc.re);
-        acc.im = fma(de, B[e * P].im, acc.im);
+    if (dr) {
+      const R w = (R)dr[e] * dsgn;
+      const cpx<R> *B = Bd + toff + (int64_t)e * P;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        acc[k].re = fma(w, B[k].re, acc[k].re);
+        acc[k].im = fma(w, B[k].im, acc[k].im);
       }
     }
-    SL[t] = acc;
   }
-  __syncthreads();
-  for (int l = L - 1; l >= 0; --l) {
-    const cpx<R> *Sc = S + (int64_t)((1 << (l + 1)) - 1) * P;
-    cpx<R> *Sp = S + (int64_t)((1 << l) - 1) * P;
-    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) {
-      const int k = t / P, nn = t % P;
-      cpx<R> acc = mk<R>(0, 0);
-      for (int j = 0; j < 2; ++j) {
-        const cpx<R> *Mc = Sc + (2 * k + j) * P;
-        const cpx<R> *T = T2 + (j * P + nn) * P;
-        for (int kk = 0; kk <= nn; ++kk) cmac(acc, T[kk], Mc[kk]);
-      }
-      Sp[t] = acc;
-    }
-    __syncthreads();
-  }
-  cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
-  for (int l = 0; l <= L; ++l) {
-    const cpx<R> *Sl = S + (int64_t)((1 << l) - 1) * P;
-    cpx<R> *Ml = M + (blevel_offset(l) + ((int64_t)side << l)) * P;
-    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) Ml[t] = Sl[t];
+  cpx<R> *M = Mb + ((int64_t)rhs * g.nbcell + c) * P;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const R re = warp_sum(acc[k].re), im = warp_sum(acc[k].im);
+    if (lane == 0) M[k] = mk<R>(re, im);
   }
 }
 
-// The same pass through global memory, for trees whose levels do not fit in shared memory
-// (FP64 at the largest depths).
-template <typename R, int P>
-__global__ void __launch_bounds__(1024) k_bnd_up_g(Geo g, const double *__restrict__ q, const cpx<R> *__restrict__ bq,
-                                                   R qscale, Mats<R> mt, cpx<R> *__restrict__ Mb,
-                                                   const double *__restrict__ qd, R dsgn) {
-  const int side = blockIdx.x, rhs = blockIdx.y;
-  const int n = g.n, m = g.m, L = g.L;
-  cpx<R> *M = Mb + (int64_t)rhs * g.nbcell * P;
-  const int nleafrun = 1 << L;
-  for (int t = threadIdx.x; t < nleafrun * P; t += blockDim.x) {
-    const int k = t / P, nn = t % P;
-    cpx<R> acc = mk<R>(0, 0);
-    if (q) {
-      const double *qr = q + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = bq + (int64_t)side * m * P + nn;
-      for (int e = 0; e < m; ++e) {
-        const R qe = (R)qr[e] * qscale;
-        acc.re = fma(qe, B[e * P].re, acc.re);
-        acc.im = fma(qe, B[e * P].im, acc.im);
-      }
-    }
-    if (qd) {
-      const double *dr = qd + (int64_t)rhs * g.NG + side * n + k * m;
-      const cpx<R> *B = mt.bdl + (int64_t)side * m * P + nn;
-      for (int e = 0; e < m; ++e) {
-        const R de = (R)dr[e] * dsgn;
-        acc.re = fma(de, B[e * P].re, acc.re);
-        acc.im = fma(de, B[e * P].im, acc.im);
-      }
-    }
-    M[(blevel_offset(L) + ((int64_t)side << L) + k) * P + nn] = acc;
-  }
-  __syncthreads();
-  for (int l = L - 1; l >= 0; --l) {
-    for (int t = threadIdx.x; t < (P << l); t += blockDim.x) {
-      const int k = t / P, nn = t % P;
-      cpx<R> acc = mk<R>(0, 0);
-      for (int j = 0; j < 2; ++j) {
-        const cpx<R> *Mc = M + (blevel_offset(l + 1) + ((int64_t)side << (l + 1)) + 2 * k + j) * P;
-        const cpx<R> *T = mt.bm2m + ((side * 2 + j) * P + nn) * P;
-        for (int kk = 0; kk <= nn; ++kk) cmac(acc, T[kk], Mc[kk]);
-      }
-      M[(blevel_offset(l) + ((int64_t)side << l) + k) * P + nn] = acc;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename R, int P>
-size_t bnd_up_smem(int L) {
-  return sizeof(cpx<R>) * ((size_t)2 * P * P + (size_t)((1 << (L + 1)) - 1) * P);
-}
 
 // ------------------------------------------------------------------ collocation points
 // Set-up for the single-precision forms: the near-field log kernel between each collocation
@@ -1677,10 +1614,10 @@ Mats<R> mats_of(fmmpc_handle &H) {
   Mats<R> mt;
   mt.vm2m = base;
   mt.vl2l = base + 4 * P * P;
-  mt.bm2m = base + 8 * P * P;
-  mt.bp2m = base + 16 * P * P;
-  mt.bdl = mt.bp2m + 4 * H.g.m * P;
-  mt.bpt = mt.bdl + 4 * H.g.m * P;
+  const int64_t lvsize = (int64_t)4 * P * 2 * H.g.n;
+  mt.lvq = base + 8 * P * P;
+  mt.lvd = mt.lvq + lvsize;
+  mt.lvp = mt.lvd + lvsize;
   return mt;
 }
 
@@ -1917,23 +1854,14 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     }
     mark(4);
     {
-      const size_t sm = bnd_up_smem<R, P>(g.L);
-      static int maxsm = 0;
-      static bool raised[2][17] = {};
-      bool &done = raised[std::is_same<R, double>::value ? 1 : 0][P];
-      if (!done) {
-        FMMPC_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
-        FMMPC_CUDA(cudaFuncSetAttribute(k_bnd_up<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-        done = true;
-      }
-      // single layer q (none in the double-layer form); double layer mu (+D mu) or data g (-D g)
+      // single layer q (none in the double-layer form); double layer mu (+D mu) or data g
+      // (-D g); the transpose pass places point sources h^2 c' at the collocation points
       const double *qm = dl ? nullptr : H.fb.q, *qd = dl ? H.fb.q : (bc ? H.bc_g : nullptr);
       const R dsgn = dl ? R(1) : R(-1);
-      // the transpose pass places point sources h^2 c' at the collocation points
-      const cpx<R> *bq = trans ? mt.bpt : mt.bp2m;
+      const cpx<R> *bq = trans ? mt.lvp : mt.lvq;
       const R qscale = trans ? (R)(g.h * g.h) : (R)g.h;
-      if (sm <= (size_t)maxsm) k_bnd_up<R, P><<<dim3(4, nrhs), 1024, sm, s>>>(g, qm, bq, qscale, mt, Mb, qd, dsgn);
-      else k_bnd_up_g<R, P><<<dim3(4, nrhs), 1024, 0, s>>>(g, qm, bq, qscale, mt, Mb, qd, dsgn);
+      k_bnd_up_lv<R, P><<<nblk((int64_t)nrhs * g.nbcell * 32), 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn,
+                                                                          Mb);
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;
@@ -2034,53 +1962,41 @@ void build_mats(fmmpc_handle &H, std::vector<cpx<R>> &out) {
     l2l(C((ch & 1) ? 0.25 : -0.25, (ch & 2) ? 0.25 : -0.25), T);
     all.insert(all.end(), T.begin(), T.end());
   }
-  const int m = g.m, n = g.n;
+  const int n = g.n;
   const C edir[4] = {C(1, 0), C(0, 1), C(-1, 0), C(0, -1)};
-  // boundary run child j of side s sits at w = (2j - 1)(n+1)/(4n) e_s parent run-widths
-  for (int sd = 0; sd < 4; ++sd)
-    for (int j = 0; j < 2; ++j) {
-      m2m((2 * j - 1) * (n + 1.0) / (4.0 * n) * edir[sd], 2.0, T);
-      all.insert(all.end(), T.begin(), T.end());
-    }
-  // element e of a leaf run, unit density, about its midpoint at scale rho = m:
-  // Mt_0 = 2 a rho, Mt_k = -2 e^k a^{k+1} rho / (k (k+1)) for even k (0 for odd), then
-  // shifted to the run centre at equal scale (w = (y_e - c) / rho)
-  const double ell = (n + 1.0) / n, rho = m, a = ell / (2.0 * rho);
-  for (int sd = 0; sd < 4; ++sd)
-    for (int e = 0; e < m; ++e) {
-      std::vector<C> el(P, C(0, 0));
-      el[0] = 2.0 * a * rho;
-      for (int k = 2; k < P; k += 2) el[k] = -2.0 * powc(edir[sd], k) * std::pow(a, k + 1) * rho / (k * (k + 1.0));
-      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
-      for (int nn = 0; nn < P; ++nn) {
-        C v(0, 0);
-        for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
-        all.push_back(v);
-      }
-    }
-  // The double layer of unit density on element e, int_e dG/dn_y, is -(1/2pi) times the real
-  // part of -i (log(z - b) - log(z - a)) (a, b its ends in traversal order, the outward normal
-  // the tangent turned clockwise): point weights -i at b and +i at a.  About the element
-  // midpoint at scale rho: Mt_0 = 0, Mt_k = 2 i e^k a^k / k for odd k (0 for even), a as
-  // above; shifted to the run centre like the single layer.  (No factor h: the double layer
-  // of a closed element run is scale free.)
-  for (int sd = 0; sd < 4; ++sd)
-    for (int e = 0; e < m; ++e) {
-      std::vector<C> el(P, C(0, 0));
-      for (int k = 1; k < P; k += 2) el[k] = C(0.0, 2.0) * powc(edir[sd], k) * std::pow(a, k) / (double)k;
-      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
-      for (int nn = 0; nn < P; ++nn) {
-        C v(0, 0);
-        for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
-        all.push_back(v);
-      }
-    }
-  // a unit point source at the element midpoint (the transpose pass): Mt = (1, 0, ...) about
-  // the midpoint, shifted to the run centre
-  for (int sd = 0; sd < 4; ++sd)
-    for (int e = 0; e < m; ++e) {
-      m2m(((e + 0.5 - 0.5 * m) * ell / rho) * edir[sd], 1.0, T);
-      for (int nn = 0; nn < P; ++nn) all.push_back(T[nn * P]);
+  const double ell = (n + 1.0) / n;
+  // Element e of a run at scale rho about its midpoint: unit single layer Mt_0 = 2 a rho,
+  // Mt_k = -2 e^k a^{k+1} rho / (k (k+1)) for even k (0 for odd), a = ell / (2 rho); unit
+  // double layer (int_e dG/dn_y is -(1/2pi) Re of -i (log(z - b) - log(z - a)) with a, b
+  // its ends in traversal order and the outward normal the tangent turned clockwise: point
+  // weights -i at b, +i at a; no factor h, a closed element run being scale free): Mt_0 = 0,
+  // Mt_k = 2 i e^k a^k / k for odd k (0 for even); unit point source at the midpoint (the
+  // transpose pass): Mt = (1, 0, ...); each shifted to the run centre at equal scale.  The
+  // tables are formed for the run of every level l of the boundary tree, at that level's
+  // scale n >> l: since M2M is exact, each level's multipoles follow directly from the
+  // element densities, with no pass from level to level.
+  for (int kind = 0; kind < 3; ++kind)
+    for (int l = 0; l <= g.L; ++l) {
+      const int len = n >> l;
+      const double rl = len, al = ell / (2.0 * rl);
+      for (int sd = 0; sd < 4; ++sd)
+        for (int e = 0; e < len; ++e) {
+          std::vector<C> el(P, C(0, 0));
+          if (kind == 0) {
+            el[0] = 2.0 * al * rl;
+            for (int k = 2; k < P; k += 2) el[k] = -2.0 * powc(edir[sd], k) * std::pow(al, k + 1) * rl / (k * (k + 1.0));
+          } else if (kind == 1) {
+            for (int k = 1; k < P; k += 2) el[k] = C(0.0, 2.0) * powc(edir[sd], k) * std::pow(al, k) / (double)k;
+          } else {
+            el[0] = 1.0;
+          }
+          m2m(((e + 0.5 - 0.5 * len) * ell / rl) * edir[sd], 1.0, T);
+          for (int nn = 0; nn < P; ++nn) {
+            C v(0, 0);
+            for (int k = 0; k <= nn; ++k) v += T[nn * P + k] * el[k];
+            all.push_back(v);
+          }
+        }
     }
   out.resize(all.size());
   for (size_t i = 0; i < all.size(); ++i) out[i] = mk<R>((R)all[i].real(), (R)all[i].imag());

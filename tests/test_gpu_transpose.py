@@ -47,31 +47,39 @@ def test_transpose_matches_oracle(prec, n, leaf_max):
     P.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
-def test_apply_gradient_matches_finite_differences(prec):
+def test_apply_gradient_matches_finite_differences():
+    # FP64 form: the loss is quadratic in r, so the central difference is exact up to rounding;
+    # the mixed form's gradient is then compared with the FP64 form's (a central difference
+    # through an FP32 apply cannot resolve 1e-5: its rounding noise in the loss, divided by
+    # 2 delta, is of that order)
     from paper_1308_3339_gb300 import FmmPreconditioner
     from paper_1308_3339_gb300.autograd import fmm_apply
     n = 64
-    P = FmmPreconditioner(n, p=10, precision=prec)
     target = dev(S.random_field(n, 3))
-    r0 = dev(S.gaussian_mixture(n, 4)).requires_grad_(True)
+    grads = {}
+    for prec in ("fp64", "mixed_tf32"):
+        P = FmmPreconditioner(n, p=10, precision=prec)
+        r0 = dev(S.gaussian_mixture(n, 4)).requires_grad_(True)
 
-    def loss(r):
-        return ((fmm_apply(r, P) - target) ** 2).sum()
+        def loss(r):
+            return ((fmm_apply(r, P) - target) ** 2).sum()
 
-    L = loss(r0)
-    L.backward()
-    g = r0.grad.detach()
-    rng = np.random.default_rng(2)
-    for _ in range(3):
-        d = dev(rng.standard_normal(n * n))
-        d /= d.norm()
-        delta = 1e-2
-        with torch.no_grad():
-            fd = (loss(r0 + delta * d) - loss(r0 - delta * d)).item() / (2 * delta)  # exact for a quadratic
-        gd = float(g @ d)
-        print(f"APPLY-GRAD {prec}: directional {gd:.10e} central difference {fd:.10e}")
-        assert abs(fd - gd) <= GATE[prec] * 10 * max(abs(fd), 1e-30)
+        loss(r0).backward()
+        grads[prec] = r0.grad.detach().cpu().numpy()
+        if prec == "fp64":
+            g = r0.grad.detach()
+            rng = np.random.default_rng(2)
+            for _ in range(3):
+                d = dev(rng.standard_normal(n * n))
+                d /= d.norm()
+                delta = 1e-2
+                with torch.no_grad():
+                    fd = (loss(r0 + delta * d) - loss(r0 - delta * d)).item() / (2 * delta)
+                gd = float(g @ d)
+                print(f"APPLY-GRAD fp64: directional {gd:.10e} central difference {fd:.10e}")
+                assert abs(fd - gd) <= 1e-7 * max(abs(fd), 1e-30)
+        P.close()
+    check_close("apply gradient mixed_tf32 vs fp64", grads["mixed_tf32"], grads["fp64"], 3e-5, 3e-5)
 
 
 def test_transpose_rejects_double_layer_form():
