@@ -54,6 +54,13 @@ def parse():
                     help="FMM form of the headline apply (FP64 Krylov in every form)")
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--oracle-legs", action="store_true",
+                    help="also time the FP64 oracle on the 64^2, 2048^2, 4096^2 and batched workloads (minutes)")
+    ap.add_argument("--p2p", choices=["tc", "simt"], default="tc",
+                    help="near-field engine of the headline apply (tensor cores or CUDA cores)")
+    ap.add_argument("--solve-mode", choices=["graph", "host"], default="graph",
+                    help="time-to-solution solves as one CUDA graph, or driven by the host "
+                         "(kernel by kernel, as a profiler can see them)")
     ap.add_argument("--configs", default="c1,c3,c4,c5",
                     help="further workloads timed after the headline (comma list of c1,c3,c4,c5; '' for none)")
     a = ap.parse_args()
@@ -65,6 +72,7 @@ def workload(args):
     return {"workload": f"poisson-fd {args.n}x{args.n} gaussian-mixture(16) FMM-BEM precond",
             "n": args.n, "N": args.n * args.n, "p": args.p, "leaf_max": args.leaf,
             "theta": args.theta, "krylov": "FGMRES(30) FP64", "fmm": FORMS[args.precision],
+            "p2p_engine": "tensor cores" if args.p2p == "tc" else "CUDA cores",
             "l2": "flushed: 256 MB write between timed applies"}
 
 
@@ -173,6 +181,43 @@ def cpu_baseline(args, repeats=1):
             "seconds_per_apply": t}
 
 
+def oracle_legs(args):
+    """The FP64 oracle on the host cores for the other workloads, one right-hand side each,
+    not extrapolated: c1 a full GMRES(30) solve at 64^2; c3 one apply at 4096^2; c5 one
+    apply and one FGMRES(30) solve at 2048^2; c4 one apply and one solve of a stated subset
+    of the 64 problems (one of each side 128 .. 1024).  Set-up (tree, lists, the dense
+    BEM LU) is reported apart.  Opt-in (--oracle-legs): the 4096^2 LU alone takes minutes."""
+    import oracle as O
+    import synth_inputs as S
+    out = {"cores": O.threads()}
+
+    def leg(n, f, solve, method="fgmres"):
+        t0 = time.perf_counter()
+        R = O.Problem(n, p=10)
+        rec = {"n": n, "setup_s": time.perf_counter() - t0}
+        t0 = time.perf_counter()
+        R.apply(f, "fmm")
+        rec["apply_s"] = time.perf_counter() - t0
+        rec["apply_points_per_s"] = n * n / rec["apply_s"]
+        if solve:
+            t0 = time.perf_counter()
+            _, it, rr, conv = R.solve(f, method, 30, 200, 1e-8, "fmm")
+            rec.update(solve_s=time.perf_counter() - t0, iters=it, rel_res=rr, converged=bool(conv))
+        return rec
+
+    f1, _ = S.manufactured_sin(64)
+    t0 = time.perf_counter()
+    R = O.Problem(64, p=8)
+    _, it, rr, _ = R.solve(f1, "gmres", 30, 200, 1e-8, "fmm")
+    out["c1"] = {"n": 64, "solve_s": time.perf_counter() - t0, "iters": it, "rel_res": rr, "note": "set-up included"}
+    sides = [int(v) for v in S.batched_sides(0, 64)]
+    subset = [sides.index(n) for n in (128, 256, 512, 1024) if n in sides]
+    out["c4_subset"] = [dict(problem=k, **leg(sides[k], S.gaussian_mixture(sides[k], 1000 + k), True)) for k in subset]
+    out["c5"] = leg(2048, S.gaussian_mixture(2048, 3), True)
+    out["c3"] = leg(4096, S.gaussian_mixture(4096, 0), False)
+    return out
+
+
 def run_reference(args):
     world, rank, local, pg = dist_setup()
     if rank != 0:
@@ -243,7 +288,7 @@ def rooflines(P, stage_ms, nrhs=1):
                       "work": f"{pairs:.4e} pairs/launch x 2 flop", "launch_ms": t}
     else:
         peak = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        out["p2p"] = {"bound": "alu", "kernel": "k_p2p_final (lattice P2P + L2P, CUDA cores)",
+        out["p2p"] = {"bound": "alu", "kernel": "k_p2p (lattice P2P, CUDA cores)",
                       "achieved": 2.0 * pairs / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                       "peak_source": f"FP32 FMA lanes {SMS}x{LANES} x 2 flop x {SM_MAX_MHZ:.0f} MHz max SM clock",
                       "work": f"{pairs:.4e} pairs/launch x 2 flop", "launch_ms": t}
@@ -472,6 +517,7 @@ def run_ours(args):
     N = n * n
     f = S.gaussian_mixture(n, rank)
     P = FmmPreconditioner(n, p=args.p, leaf_max=args.leaf, theta=args.theta, precision=args.precision)
+    P.set_p2p_engine(args.p2p)
     r = torch.tensor(f, dtype=torch.float64, device=dev)
     z = torch.empty_like(r)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -554,7 +600,12 @@ def run_ours(args):
             torch.cuda.synchronize()
             setup_ms = (time.perf_counter() - t0) * 1e3 if Pf is not P else None
             Pf.set_graphs(True)
-            tts[form] = {"apply_ms": time_apply(Pf, r, z, flush), **time_solves(Pf, r, 3 if form != "fp64" else 2)}
+            mode = 2 if args.solve_mode == "graph" else 0
+            tts[form] = {"apply_ms": time_apply(Pf, r, z, flush),
+                         **time_solves(Pf, r, 3 if form != "fp64" else 2, graphs=mode)}
+            # preconditioned CG, the paper's own Krylov method (Sec. 6): a short recurrence,
+            # so far fewer FP64 vector operations per iteration than FGMRES's CGS2
+            tts[form]["pcg"] = time_solves(Pf, r, 3 if form != "fp64" else 2, graphs=mode, method="cg")
             _, inf = Pf.solve(r, rtol=1e-8)
             tts[form]["t_setup_ms"] = inf["t_setup_ms"]
             if form == args.precision:
@@ -579,6 +630,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
+        if args.oracle_legs:
+            cpu["other_workloads"] = oracle_legs(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -576,20 +576,22 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
   }
 }
 
-// Multipoles of every boundary cell at every level in one launch: warp per (boundary cell,
-// rhs), lanes striding over the cell's elements, Mt_n = sum_e (q_e qscale Bq_l[e][n] +
-// qd_e dsgn Bd_l[e][n]) with the level tables of Mats (element single layer, double layer,
-// or point source at the midpoint); q or qd may be NULL.
+// Multipoles of every boundary cell at every level in one launch: block per (boundary cell,
+// rhs); thread (k, el) of the 16 x 16 block accumulates coefficient k over the elements
+// el, el + 16, ... of the cell, Mt_k = sum_e (q_e qscale Bq_l[e][k] + qd_e dsgn Bd_l[e][k])
+// with the level tables of Mats (element single layer, double layer, or point source at
+// the midpoint); q or qd may be NULL.  The 16 partial sums of a coefficient meet in shared
+// memory in a fixed order.
 template <typename R, int P>
 __global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double *__restrict__ q,
                                                    const cpx<R> *__restrict__ Bq, R qscale,
                                                    const double *__restrict__ qd, const cpx<R> *__restrict__ Bd,
                                                    R dsgn, cpx<R> *__restrict__ Mb) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= (int64_t)nrhs * g.nbcell) return;
-  const int rhs = (int)(wid / g.nbcell);
-  const int64_t c = wid % g.nbcell;
+  static_assert(P <= 16, "one coefficient slot per thread row");
+  __shared__ R sre[16][17], sim[16][17];
+  const int64_t c = blockIdx.x;
+  const int rhs = blockIdx.y;
+  const int k = threadIdx.x & 15, el = threadIdx.x >> 4;
   int l = 0;
   while (blevel_offset(l + 1) <= c) ++l;
   const int64_t id = c - blevel_offset(l);
@@ -598,36 +600,35 @@ __global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double
   const int64_t run = id & ((int64_t(1) << l) - 1);
   const int64_t e0 = (int64_t)side * n + run * len;  // first element of the cell
   const int64_t toff = (int64_t)4 * P * (2 * n - 2 * len) + (int64_t)side * len * P;
-  cpx<R> acc[P];
-#pragma unroll
-  for (int k = 0; k < P; ++k) acc[k] = mk<R>(0, 0);
-  const double *qr = q ? q + (int64_t)rhs * g.NG + e0 : nullptr;
-  const double *dr = qd ? qd + (int64_t)rhs * g.NG + e0 : nullptr;
-  for (int e = lane; e < len; e += 32) {
-    if (qr) {
-      const R w = (R)qr[e] * qscale;
-      const cpx<R> *B = Bq + toff + (int64_t)e * P;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        acc[k].re = fma(w, B[k].re, acc[k].re);
-        acc[k].im = fma(w, B[k].im, acc[k].im);
+  R are = 0, aim = 0;
+  if (k < P) {
+    const double *qr = q ? q + (int64_t)rhs * g.NG + e0 : nullptr;
+    const double *dr = qd ? qd + (int64_t)rhs * g.NG + e0 : nullptr;
+    for (int e = el; e < len; e += 16) {
+      if (qr) {
+        const R w = (R)qr[e] * qscale;
+        const cpx<R> b = Bq[toff + (int64_t)e * P + k];
+        are = fma(w, b.re, are);
+        aim = fma(w, b.im, aim);
       }
-    }
-    if (dr) {
-      const R w = (R)dr[e] * dsgn;
-      const cpx<R> *B = Bd + toff + (int64_t)e * P;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        acc[k].re = fma(w, B[k].re, acc[k].re);
-        acc[k].im = fma(w, B[k].im, acc[k].im);
+      if (dr) {
+        const R w = (R)dr[e] * dsgn;
+        const cpx<R> b = Bd[toff + (int64_t)e * P + k];
+        are = fma(w, b.re, are);
+        aim = fma(w, b.im, aim);
       }
     }
   }
-  cpx<R> *M = Mb + ((int64_t)rhs * g.nbcell + c) * P;
-#pragma unroll
-  for (int k = 0; k < P; ++k) {
-    const R re = warp_sum(acc[k].re), im = warp_sum(acc[k].im);
-    if (lane == 0) M[k] = mk<R>(re, im);
+  sre[el][k] = are;
+  sim[el][k] = aim;
+  __syncthreads();
+  if (threadIdx.x < P) {
+    R re = 0, im = 0;
+    for (int j = 0; j < 16; ++j) {
+      re += sre[j][threadIdx.x];
+      im += sim[j][threadIdx.x];
+    }
+    Mb[((int64_t)rhs * g.nbcell + c) * P + threadIdx.x] = mk<R>(re, im);
   }
 }
 
@@ -1614,7 +1615,8 @@ Mats<R> mats_of(fmmpc_handle &H) {
   Mats<R> mt;
   mt.vm2m = base;
   mt.vl2l = base + 4 * P * P;
-  const int64_t lvsize = (int64_t)4 * P * 2 * H.g.n;
+  // each kind holds sum over l = 0..L of 4 (n >> l) P entries = 4 P (2n - m)
+  const int64_t lvsize = (int64_t)4 * P * (2 * H.g.n - H.g.m);
   mt.lvq = base + 8 * P * P;
   mt.lvd = mt.lvq + lvsize;
   mt.lvp = mt.lvd + lvsize;
@@ -1860,8 +1862,7 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       const R dsgn = dl ? R(1) : R(-1);
       const cpx<R> *bq = trans ? mt.lvp : mt.lvq;
       const R qscale = trans ? (R)(g.h * g.h) : (R)g.h;
-      k_bnd_up_lv<R, P><<<nblk((int64_t)nrhs * g.nbcell * 32), 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn,
-                                                                          Mb);
+      k_bnd_up_lv<R, P><<<dim3((unsigned)g.nbcell, nrhs), 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;
