@@ -220,8 +220,9 @@ int fmmpc_query(const fmmpc_handle *h, int32_t what, int64_t *value);
 int fmmpc_export(fmmpc_handle *h, int32_t what, void *dst, int64_t bytes);
 
 /* Near-field engine: 0 (the default) the tensor-core lattice P2P where the grid allows it
- * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision; three TF32 products
- * per pair, FP32-accurate in every single-precision form), 1 the CUDA-core kernel. */
+ * (8x8 leaves, at least 128 leaves per row, FP32 or mixed precision; three FP16 products
+ * per pair with each source leaf's weights scaled by a power of two, FP32-accurate in every
+ * single-precision form), 1 the CUDA-core kernel. */
 int fmmpc_set_p2p_engine(fmmpc_handle *h, int32_t engine);
 
 /* Operator of the Krylov solves, fmmpc_spmv and the right-hand side folding (the

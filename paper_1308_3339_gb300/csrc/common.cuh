@@ -111,6 +111,71 @@ __host__ __device__ __forceinline__ cpx<R> cinv(cpx<R> a) {
   return cpx<R>{a.re * d, -a.im * d};
 }
 
+// ------------------------------------------------------------------ FP64 <-> FP32
+// Conversions by the IEEE-754 field layouts on the integer units.  The hardware conversion
+// instructions run on the FP64 pipe, which is narrow on this GPU (2 lanes per clock per SM),
+// so a kernel that converts once per loaded value can be bound by them.  Values outside the
+// range the field arithmetic handles take an out-of-line call to the hardware conversion:
+// a real branch, so its FP64 instructions issue only when such a value occurs.
+#ifdef __CUDACC__
+static __device__ __noinline__ float2 cvt_f64_f32x2_hw(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+static __device__ __noinline__ double cvt_f32_f64_hw(float f) { return (double)f; }
+
+// x = hi + lo with hi = fl32(x) (round to nearest even) and lo = fl32(x - hi).
+__device__ __forceinline__ float2 f64_to_f32x2(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7ffu;
+  const uint64_t m = u & 0xfffffffffffffull;
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  if (e >= 923u && e <= 1123u) {  // |x| in [2^-100, 2^101): hi and lo are normal FP32 numbers
+    uint32_t f = sign | ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint32_t rest = (uint32_t)(m & 0x1fffffffu);  // the 29 bits below FP32 precision
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (f & 1u));
+    f += up ? 1u : 0u;  // a carry out of the mantissa moves into the exponent, as it should
+    const int32_t rr = (int32_t)rest - (up ? 0x20000000 : 0);  // x - hi in units of 2^(e - 1075)
+    const float mag = __int2float_rn(rr) * 0x1p-29f * __uint_as_float((e - 1046u + 127u) << 23);
+    return make_float2(__uint_as_float(f), sign ? -mag : mag);
+  }
+  if (e == 0 && m == 0) return make_float2(__uint_as_float(sign), __uint_as_float(sign));
+  return cvt_f64_f32x2_hw(x);
+}
+
+// fl32(x), round to nearest even, as (float)x.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7ffu;
+  const uint64_t m = u & 0xfffffffffffffull;
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  if (e >= 897u && e <= 1150u) {  // normal FP32 range; rounding past the largest gives inf
+    uint32_t f = sign | ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint32_t rest = (uint32_t)(m & 0x1fffffffu);
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if (e == 0 && m == 0) return __uint_as_float(sign);
+  return f64_to_f32x2(x).x;
+}
+
+// (double)f, exact.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)((uint64_t)u << 32));
+  if (e == 0 || e == 0xffu) return cvt_f32_f64_hw(f);
+  return __longlong_as_double((long long)(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                                          ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
+// R(x) for a value loaded as FP64: the field conversion for FP32, the value itself for FP64
+template <typename R>
+__device__ __forceinline__ R from_f64(double x) {
+  if constexpr (sizeof(R) == 4) return f64_to_f32(x);
+  else return x;
+}
+#endif
+
 // ------------------------------------------------------------------ Morton helpers
 __host__ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
   x &= 0xffffu;

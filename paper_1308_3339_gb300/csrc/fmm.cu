@@ -580,9 +580,11 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
 // rhs); thread (k, el) of the 16 x 16 block accumulates coefficient k over the elements
 // el, el + 16, ... of the cell, Mt_k = sum_e (q_e qscale Bq_l[e][k] + qd_e dsgn Bd_l[e][k])
 // with the level tables of Mats (element single layer, double layer, or point source at
-// the midpoint); q or qd may be NULL.  The 16 partial sums of a coefficient meet in shared
+// the midpoint); HQ, HD say whether q and qd are given.  The coarse cells hold up to n
+// elements, so a thread issues the loads of eight elements before it adds them (latency,
+// not bandwidth, bounds this pass).  The 16 partial sums of a coefficient meet in shared
 // memory in a fixed order.
-template <typename R, int P>
+template <typename R, int P, bool HQ, bool HD>
 __global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double *__restrict__ q,
                                                    const cpx<R> *__restrict__ Bq, R qscale,
                                                    const double *__restrict__ qd, const cpx<R> *__restrict__ Bd,
@@ -602,20 +604,37 @@ __global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double
   const int64_t toff = (int64_t)4 * P * (2 * n - 2 * len) + (int64_t)side * len * P;
   R are = 0, aim = 0;
   if (k < P) {
-    const double *qr = q ? q + (int64_t)rhs * g.NG + e0 : nullptr;
-    const double *dr = qd ? qd + (int64_t)rhs * g.NG + e0 : nullptr;
-    for (int e = el; e < len; e += 16) {
-      if (qr) {
-        const R w = (R)qr[e] * qscale;
-        const cpx<R> b = Bq[toff + (int64_t)e * P + k];
-        are = fma(w, b.re, are);
-        aim = fma(w, b.im, aim);
+    constexpr int U = 8;
+    const int64_t rbase = (int64_t)rhs * g.NG + e0;
+    const cpx<R> *bq = Bq + toff + k, *bd = Bd + toff + k;
+    for (int e = el; e < len; e += 16 * U) {
+      double wq[U], wd[U];
+      cpx<R> b1[U], b2[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ee = e + 16 * u;
+        const bool in = ee < len;
+        if (HQ) {
+          wq[u] = in ? q[rbase + ee] : 0.0;
+          b1[u] = in ? bq[(int64_t)ee * P] : mk<R>(0, 0);
+        }
+        if (HD) {
+          wd[u] = in ? qd[rbase + ee] : 0.0;
+          b2[u] = in ? bd[(int64_t)ee * P] : mk<R>(0, 0);
+        }
       }
-      if (dr) {
-        const R w = (R)dr[e] * dsgn;
-        const cpx<R> b = Bd[toff + (int64_t)e * P + k];
-        are = fma(w, b.re, are);
-        aim = fma(w, b.im, aim);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (HQ) {
+          const R w1 = from_f64<R>(wq[u]) * qscale;
+          are = fma(w1, b1[u].re, are);
+          aim = fma(w1, b1[u].im, aim);
+        }
+        if (HD) {
+          const R w2 = from_f64<R>(wd[u]) * dsgn;
+          are = fma(w2, b2[u].re, are);
+          aim = fma(w2, b2[u].im, aim);
+        }
       }
     }
   }
@@ -680,6 +699,28 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
   const R inv2n = R(1) / (R)(2 * n);
   const int64_t numc = (2 * (int64_t)along + 1) * (n + 1);
+  // far field (first, so that its loads overlap the near sum): the local expansion of
+  // every ancestor run evaluated at y (L2L re-centring is exact, so this equals pushing the
+  // locals down to the leaf run and evaluating there)
+  R far = 0;
+  if (lane <= L) {
+    const int l = lane, nl = n >> l;
+    const int64_t id = ((int64_t)side << l) + along / nl;
+    // offset of the point from the run centre, in run units: (n+1)/n (j + 1/2 - nl/2) / nl
+    const R off = (R)(n + 1) * ((R)(along % nl) + R(0.5) - R(0.5) * (R)nl) / ((R)n * (R)nl);
+    const R ex = (side == 0) ? R(1) : (side == 2 ? R(-1) : R(0));
+    const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
+    const cpx<R> z = mk<R>(off * ex, off * ey);
+    const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
+    cpx<R> lc[16];  // all p <= 16 coefficients loaded before the Horner chain uses them
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) lc[kk] = kk < p ? Lc[kk] : mk<R>(0, 0);
+    cpx<R> v = mk<R>(0, 0);
+#pragma unroll
+    for (int kk = 15; kk >= 0; --kk)
+      if (kk < p) v = v * z + lc[kk];
+    far = v.re;
+  }
   R acc = 0;
   // precomputed (single-precision forms): Kc[(pfirst m + ip c) m^2 + el m^2 + t] = ln|y - x_t|
   const int c_near = pfirst[bl + 1] - pfirst[bl];
@@ -721,22 +762,6 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
     }
   }
   acc = warp_sum(acc);
-  // far field: the local expansion of every ancestor run evaluated at y (L2L re-centring
-  // is exact, so this equals pushing the locals down to the leaf run and evaluating there)
-  R far = 0;
-  if (lane <= L) {
-    const int l = lane, nl = n >> l;
-    const int64_t id = ((int64_t)side << l) + along / nl;
-    // offset of the point from the run centre, in run units: (n+1)/n (j + 1/2 - nl/2) / nl
-    const R off = (R)(n + 1) * ((R)(along % nl) + R(0.5) - R(0.5) * (R)nl) / ((R)n * (R)nl);
-    const R ex = (side == 0) ? R(1) : (side == 2 ? R(-1) : R(0));
-    const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
-    const cpx<R> z = mk<R>(off * ex, off * ey);
-    const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
-    cpx<R> v = mk<R>(0, 0);
-    for (int kk = p - 1; kk >= 0; --kk) v = v * z + Lc[kk];
-    far = v.re;
-  }
   far = warp_sum(far);
   const double v = ((double)acc + (double)far) * NEG_INV_2PI;
   if (lane == 0) {
@@ -888,14 +913,19 @@ __device__ __forceinline__ void dot2_mac(float &s, float &c, float ah, float al,
 }
 
 // The BEM apply of k_bem_apply in two-word FP32 arithmetic: block per row m of
-// T = [C^0 | C^2 | A | B], each thread a strided share of the row, RB right-hand sides per
-// pass over it; the partial two-word sums are combined with TwoSum (warp shuffles, then
-// across the 8 warps) and converted to FP64 once per row and right-hand side.
+// T = [C^0 | C^2 | A | B], each of its BEM_T threads a strided share of the row, RB
+// right-hand sides per pass over it; the partial two-word sums are combined with TwoSum
+// (warp shuffles, then across the warps) and converted to FP64 once per row and right-hand
+// side.  Two warps per row keep every row of a 1024-side grid resident at once, each thread
+// with many row loads in flight: the pass is one sweep over T at memory speed, not waves of
+// blocks each waiting on its loads.
+constexpr int BEM_T = 64;
 template <int RB>
-__global__ void __launch_bounds__(256, RB == 1 ? 3 : 2) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
+__global__ void __launch_bounds__(BEM_T) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
                                                       const float *__restrict__ Tl, const float *__restrict__ vh,
                                                       const float *__restrict__ vl, double *__restrict__ q) {
-  __shared__ float rs[8][RB][4], rc[8][RB][4];
+  constexpr int NW = BEM_T / 32;
+  __shared__ float rs[NW][RB][4], rc[NW][RB][4];
   __shared__ double tot[RB][4];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int mrow = blockIdx.x;
@@ -908,7 +938,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 2) k_bem_apply_f2(int n, in
 #pragma unroll
       for (int g = 0; g < 4; ++g) sa[j][g] = ca[j][g] = 0.f;
 #pragma unroll 4
-    for (int k = tid; k < n; k += 256) {
+    for (int k = tid; k < n; k += BEM_T) {
       const float c0h = th[k], c2h = th[n + k], cah = th[2 * n + k], cbh = th[3 * n + k];
       const float c0l = tl[k], c2l = tl[n + k], cal = tl[2 * n + k], cbl = tl[3 * n + k];
 #pragma unroll
@@ -945,7 +975,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 2) k_bem_apply_f2(int n, in
     if (tid < RB * 4) {
       const int j = tid >> 2, g = tid & 3;
       float s0 = rs[0][j][g], c0 = rc[0][j][g];
-      for (int ww = 1; ww < 8; ++ww) {
+      for (int ww = 1; ww < NW; ++ww) {
         two_sum_acc(s0, c0, rs[ww][j][g]);
         c0 += rc[ww][j][g];
       }
@@ -1206,7 +1236,7 @@ __global__ void __launch_bounds__(256) k_bnd_near_k(Geo g, int64_t nbnear, int n
   for (int idx = grp; idx < cnt; idx += 16) {
     const int bl = src[f0 + idx / m], e = idx % m;
     const int64_t kk = bl & ((int64_t(1) << L) - 1);
-    const float qe = (float)qr[(bl >> L) * n + kk * m + e];
+    const float qe = f64_to_f32(qr[(bl >> L) * n + kk * m + e]);
     const float4 kv = K4[(int64_t)idx * 16 + t4];
     acc.x = fmaf(kv.x, qe, acc.x);
     acc.y = fmaf(kv.y, qe, acc.y);
@@ -1329,16 +1359,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_p2p(P2PArgs<R> 
   for (int t = 0; t < M; ++t) o[t] = ((double)sum[t] - (double)comp[t]) * NEG_INV_2PI;
 }
 
-// FP32 -> FP64 by the IEEE-754 field layout (exponent bias 127 -> 1023) on the integer
-// units; zeros included, the subnormal / infinite / NaN cases through the conversion unit.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)((uint64_t)u << 32));
-  if (e == 0 || e == 0xffu) return (double)f;
-  return __longlong_as_double((long long)(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
-                                          ((uint64_t)(u & 0x7fffffu) << 29)));
-}
-
 // -(1/2pi) (a + b) + u, u = v (float)(-1/2pi): a + b exactly as a two-word sum (Knuth's
 // TwoSum), times -1/(2pi) held as two floats (the product's error word from an FMA, as in
 // Dekker's product), u added with TwoSum, and the two words converted to FP64 and added.
@@ -1374,6 +1394,28 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   const uint32_t blk = blockIdx.x;
   const int L = g.L;
   const cpx<R> *Lr = Lv + (int64_t)rhs * g.ncell * P;
+  // this thread's NPT consecutive nodes of one row; their near-field and near-boundary
+  // values are loaded first, so those loads overlap the expansion work below
+  constexpr int NPT = M * M / 16;  // nodes per thread: (4M)^2 nodes over 256 threads
+  const int e0 = tid * NPT, y = e0 / (4 * M), x0 = e0 % (4 * M);
+  const int lf = (int)morton_encode((uint32_t)(x0 / M), (uint32_t)(y / M));
+  const int tx0 = x0 % M, ty = y % M;
+  int bx, by;
+  morton_decode(blk, bx, by);
+  const int64_t off = (int64_t)rhs * g.n * g.n + (int64_t)(by * 4 * M + y) * g.n + bx * 4 * M + x0;
+  const R *pb = nullptr;
+  if (do_bnd) {
+    const int slot = bslot[16 * (int64_t)blk + lf];
+    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M + tx0;
+  }
+  float nr1[NPT], nr2[NPT];
+  R pbv[NPT];
+#pragma unroll
+  for (int e = 0; e < NPT; ++e) {
+    nr1[e] = near1 ? near1[off + e] : 0.0f;
+    nr2[e] = near1 ? near2[off + e] : 0.0f;
+    pbv[e] = pb ? pb[e] : R(0);
+  }
   // every value the block needs, loaded at once: the translation matrices, the M2L parts of
   // the ancestors (levels 0 .. L - 2), of the 4 children and of the 16 leaves
   for (int i = tid; i < 4 * P * P; i += nthr) sS[i] = vl2l[i];
@@ -1430,18 +1472,6 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   __syncthreads();
   if (tid < 16 * P) s2[tid / P][tid % P] = v2;
   __syncthreads();
-  constexpr int NPT = M * M / 16;  // nodes per thread: (4M)^2 nodes over 256 threads
-  const int e0 = tid * NPT, y = e0 / (4 * M), x0 = e0 % (4 * M);
-  const int lf = (int)morton_encode((uint32_t)(x0 / M), (uint32_t)(y / M));
-  const int tx0 = x0 % M, ty = y % M;
-  int bx, by;
-  morton_decode(blk, bx, by);
-  const int64_t off = (int64_t)rhs * g.n * g.n + (int64_t)(by * 4 * M + y) * g.n + bx * 4 * M + x0;
-  const R *pb = nullptr;
-  if (do_bnd) {
-    const int slot = bslot[16 * (int64_t)blk + lf];
-    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M + tx0;
-  }
   const R zy = (ty - R(0.5) * (M - 1)) / M;
   cpx<R> acc[NPT];
 #pragma unroll
@@ -1459,14 +1489,14 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
 #pragma unroll
     for (int e = 0; e < NPT; ++e) {
       float v = (float)acc[e].re;
-      if (pb) v += (float)pb[e];
-      o[e] = near_far_sum(near1[off + e], near2[off + e], v);
+      if (pb) v += (float)pbv[e];
+      o[e] = near_far_sum(nr1[e], nr2[e], v);
     }
   } else {
 #pragma unroll
     for (int e = 0; e < NPT; ++e) {
       double v = (double)acc[e].re;
-      if (pb) v += (double)pb[e];
+      if (pb) v += (double)pbv[e];
       o[e] += v * NEG_INV_2PI;
     }
   }
@@ -1833,8 +1863,8 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     // q = S^{-1}(-vcol), or mu = (-1/2 I + K)^{-1}(-vcol) in the double-layer form
     const float *Th = dl ? H.Kdl_hi : H.Sinv_hi, *Tl = dl ? H.Kdl_lo : H.Sinv_lo;
     if (vt_f2 && Th) {  // vt_hi / vt_lo came with the collocation values
-      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, 256, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
-      else k_bem_apply_f2<1><<<g.n, 256, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, BEM_T, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      else k_bem_apply_f2<1><<<g.n, BEM_T, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
       ++launches;
     } else {
       k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
@@ -1862,7 +1892,11 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       const R dsgn = dl ? R(1) : R(-1);
       const cpx<R> *bq = trans ? mt.lvp : mt.lvq;
       const R qscale = trans ? (R)(g.h * g.h) : (R)g.h;
-      k_bnd_up_lv<R, P><<<dim3((unsigned)g.nbcell, nrhs), 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
+      const dim3 grid((unsigned)g.nbcell, nrhs);
+      if (qm && qd) k_bnd_up_lv<R, P, true, true><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
+      else if (qm) k_bnd_up_lv<R, P, true, false><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
+      else if (qd) k_bnd_up_lv<R, P, false, true><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
+      else FMMPC_CUDA(cudaMemsetAsync(Mb, 0, sizeof(cpx<R>) * P * g.nbcell * nrhs, s));
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;

@@ -46,8 +46,10 @@ struct TcP2P {
   bool enabled = false;
   int NLX = 0, NLY = 0, NS = 0, npass = 3, nrows = 0, nofs = 0, smem = 0, usplit = 0;
   int row_oy[33] = {}, row_q0[33] = {}, row_q1[33] = {}, row_ox0[33] = {};
-  float *ahi = nullptr, *alo = nullptr, *bmat = nullptr, *bmat_lnh = nullptr;
+  uint16_t *ahi = nullptr, *alo = nullptr;        // FP16 weight strips (scaled), hi and lo words
+  uint16_t *bmat = nullptr, *bmat_lnh = nullptr;  // FP16 kernel tables, hi and lo words
   float *near1 = nullptr, *near2 = nullptr;  // the two halves of the near-field sum, FP32 images
+  float *lsc = nullptr;                      // [nrhs][NLY][NLX] 2^-e of each leaf's FP16 weights
   int *err = nullptr;
 };
 

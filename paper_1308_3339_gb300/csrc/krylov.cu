@@ -3,8 +3,9 @@
 // initial iterate by default and a relative-residual stop (Sec. 6).  Several right-hand
 // sides run side by side, each with its own Krylov space; vectors are [nrhs][N] FP64.
 // Arnoldi uses classical Gram-Schmidt applied twice (CGS2), so each orthogonalisation is
-// a fused multi-dot and a fused update; the small Hessenberg least-squares problem
-// (Givens rotations) stays on the host.
+// a fused multi-dot and a fused update.  The small Hessenberg least-squares problem (Givens
+// rotations) and the convergence test run on the host in the host-driven loop, and on the
+// device in the graph-resident solver (one CUDA graph with a device-side loop condition).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,6 +21,16 @@ constexpr int RED_BLOCKS = 1024;  // per rhs at most; partial sums reduced in a 
 constexpr int MAXJ = 64;         // largest Krylov basis handled by the fused kernels
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Blocks of a reduction grid: four per SM (enough loads in flight for the vector sweeps;
+// every further warp adds its own FP64 cross-lane sums, and FP64 issue is the scarce
+// resource of these kernels on this GPU).
+int red_blocks() {
+  int dev = 0, nsm = 0;
+  FMMPC_CUDA(cudaGetDevice(&dev));
+  FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  return std::min(std::max(4 * nsm, 1), RED_BLOCKS);
+}
 
 // The operator A of the solves (fmmpc_set_operator), zero Dirichlet values outside the
 // n x n block: 0 the five-point stencil (1/h^2)(4 u - neighbours) of Eq. e:axb; 1 the
@@ -64,12 +75,11 @@ __device__ __forceinline__ double op_at(const OpDev &o, const double *__restrict
     if (j < n - 1) v -= aN * x[t + n];
     return o.s * v;
   }
-  double v = 4.0 * x[t];
-  if (i > 0) v -= x[t - 1];
-  if (i < n - 1) v -= x[t + 1];
-  if (j > 0) v -= x[t - n];
-  if (j < n - 1) v -= x[t + n];
-  return o.s * v;
+  // five FP64 operations per node (three adds, one FMA, one product): the FP64 pipe, not
+  // memory, bounds this stencil on this GPU
+  const double xw = i > 0 ? x[t - 1] : 0.0, xe = i < n - 1 ? x[t + 1] : 0.0;
+  const double xs = j > 0 ? x[t - n] : 0.0, xn = j < n - 1 ? x[t + n] : 0.0;
+  return o.s * fma(4.0, x[t], -((xw + xe) + (xs + xn)));
 }
 
 __global__ void k_spmv5(OpDev o, int64_t total, const double *__restrict__ x, double *__restrict__ y) {
@@ -178,13 +188,55 @@ __device__ __forceinline__ double update_chunk(int64_t N, const double *__restri
   return sq;
 }
 
+// Sums a[q], q < 8, over the warp; lane 4q ends with the total of a[q].  A transposing
+// butterfly: in each of the first three steps a lane keeps half of its values and adds the
+// partner's copy of that half (4 + 2 + 1 adds), then two plain steps sum over the four lanes
+// that hold the same value -- 9 FP64 adds where eight separate trees take 40.
+__device__ __forceinline__ double warp_sum8(const double (&a)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool u4 = (lane & 16) != 0, u3 = (lane & 8) != 0, u2 = (lane & 4) != 0;
+  double b[4], c[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    b[i] = (u4 ? a[4 + i] : a[i]) + __shfl_xor_sync(0xffffffffu, u4 ? a[i] : a[4 + i], 16);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    c[i] = (u3 ? b[2 + i] : b[i]) + __shfl_xor_sync(0xffffffffu, u3 ? b[i] : b[2 + i], 8);
+  double d = (u2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, u2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+// The block's sums of acc[q], q < nq (nq <= 8, block-uniform), into red[q] (a fixed order:
+// lanes by the butterfly, then warps in turn).  red must hold 8 x (warps + 1) doubles.
+__device__ __forceinline__ void block_sum8(const double (&acc)[8], int nq, double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (nq == 1) {
+    double v = acc[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[8 + wid * 8] = v;
+  } else {
+    const double v = warp_sum8(acc);
+    if ((lane & 3) == 0 && (lane >> 2) < nq) red[8 + wid * 8 + (lane >> 2)] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double sum = 0.0;
+    for (int q = 0; q < nw; ++q) sum += red[8 + q * 8 + threadIdx.x];
+    red[threadIdx.x] = sum;
+  }
+  __syncthreads();
+}
+
 // partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
 // Vectors are taken in register groups of 8.
-__global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, int64_t vs,
-                               const double *__restrict__ w, double *__restrict__ part, int with_self) {
-  __shared__ double red[RED_THREADS / 32][8];
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(int64_t N, int nv, const double *__restrict__ V,
+                                                              int64_t vs, const double *__restrict__ w,
+                                                              double *__restrict__ part, int with_self) {
+  __shared__ double red[8 * (RED_THREADS / 32 + 1)];
   const int rhs = blockIdx.y;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double *wr = w + (int64_t)rhs * N;
   const int nt = nv + (with_self ? 1 : 0);  // index nv: <w, w>
   for (int i0 = 0; i0 < nt; i0 += 8) {
@@ -192,18 +244,9 @@ __global__ void k_mdot_partial(int64_t N, int nv, const double *__restrict__ V, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
     mdot_chunk(N, V + (int64_t)rhs * N, vs, wr, i0, nv, with_self != 0, acc);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[wid][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nt) {
-      double sum = 0.0;
-      for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
-      part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
-    }
+    const int nq = min(8, nt - i0);
+    block_sum8(acc, nq, red);
+    if (threadIdx.x < nq) part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
     __syncthreads();
   }
 }
@@ -386,18 +429,18 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
 // with_self: out[rhs][nv] = <w, w> as well (not accumulated into acc)
 void mdot(Ctx &c, int nv, const double *V, int64_t vs, const double *w, double *out, double *acc,
           bool with_self = false) {
-  dim3 grid(RED_BLOCKS, c.nrhs);
-  k_mdot_partial<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, w, c.H.kw.part, with_self ? 1 : 0);
+  const int nb = red_blocks();
+  k_mdot_partial<<<dim3(nb, c.nrhs), RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, w, c.H.kw.part, with_self ? 1 : 0);
   const int nt = nv + (with_self ? 1 : 0);
-  k_mdot_final<<<dim3(c.nrhs, (nt + 7) / 8), 256, 0, c.s>>>(nt, RED_BLOCKS, c.H.kw.part, out, acc, nv);
+  k_mdot_final<<<dim3(c.nrhs, (nt + 7) / 8), 256, 0, c.s>>>(nt, nb, c.H.kw.part, out, acc, nv);
   FMMPC_LAUNCH_CHECK();
 }
 
 // w -= V coef (nv vectors), then out[rhs][0] = ||w||^2
 void update_sq(Ctx &c, int nv, const double *V, int64_t vs, const double *coef, double *w, double *out) {
-  dim3 grid(RED_BLOCKS, c.nrhs);
-  k_mupdate_sq<<<grid, RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, coef, w, c.H.kw.part);
-  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.s>>>(1, RED_BLOCKS, c.H.kw.part, out, nullptr, 0);
+  const int nb = red_blocks();
+  k_mupdate_sq<<<dim3(nb, c.nrhs), RED_THREADS, 0, c.s>>>(c.N, nv, V, vs, coef, w, c.H.kw.part);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.s>>>(1, nb, c.H.kw.part, out, nullptr, 0);
   FMMPC_LAUNCH_CHECK();
 }
 
@@ -981,9 +1024,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_gdots(const int *__restrict__ c
                                                        int64_t vs, const double *__restrict__ w, double *__restrict__ part,
                                                        int *__restrict__ cnt, double *__restrict__ out,
                                                        double *__restrict__ hsum, int hacc) {
-  __shared__ double red[RED_THREADS / 32][8];
+  __shared__ double red[8 * (RED_THREADS / 32 + 1)];
   const int rhs = blockIdx.y;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double *wr = w + (int64_t)rhs * N;
   const int nv = ctl[KC_J] + 1;
   for (int i0 = 0; i0 < nv; i0 += 8) {
@@ -991,18 +1033,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gdots(const int *__restrict__ c
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
     mdot_chunk(N, V + (int64_t)rhs * N, vs, wr, i0, nv, false, acc);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[wid][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8 && i0 + (int)threadIdx.x < nv) {
-      double sum = 0.0;
-      for (int q = 0; q < RED_THREADS / 32; ++q) sum += red[q][threadIdx.x];
-      part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
-    }
+    const int nq = min(8, nv - i0);
+    block_sum8(acc, nq, red);
+    if (threadIdx.x < nq) part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
     __syncthreads();
   }
   if (last_block(cnt + rhs)) {
@@ -1294,17 +1327,17 @@ GmState gm_state(KrylovWs &K) {
 
 // norms |v[rhs]|^2 into dots[rhs][0] (captured)
 void gnorm2(Ctx &c, const double *v) {
-  dim3 grid(RED_BLOCKS, c.nrhs);
-  k_mdot_partial<<<grid, RED_THREADS, 0, c.H.stream>>>(c.N, 1, v, 0, v, c.H.kw.part, 0);
-  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, RED_BLOCKS, c.H.kw.part, c.H.kw.dots, nullptr, 0);
+  const int nb = red_blocks();
+  k_mdot_partial<<<dim3(nb, c.nrhs), RED_THREADS, 0, c.H.stream>>>(c.N, 1, v, 0, v, c.H.kw.part, 0);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, nb, c.H.kw.part, c.H.kw.dots, nullptr, 0);
   FMMPC_LAUNCH_CHECK();
 }
 
 // <a, b> into out[rhs][0] (captured)
 void gdot(Ctx &c, const double *a, const double *b, double *out) {
-  dim3 grid(RED_BLOCKS, c.nrhs);
-  k_mdot_partial<<<grid, RED_THREADS, 0, c.H.stream>>>(c.N, 1, a, 0, b, c.H.kw.part, 0);
-  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, RED_BLOCKS, c.H.kw.part, out, nullptr, 0);
+  const int nb = red_blocks();
+  k_mdot_partial<<<dim3(nb, c.nrhs), RED_THREADS, 0, c.H.stream>>>(c.N, 1, a, 0, b, c.H.kw.part, 0);
+  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, nb, c.H.kw.part, out, nullptr, 0);
   FMMPC_LAUNCH_CHECK();
 }
 
@@ -1394,9 +1427,7 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, od, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
       // CGS2: dots, update, dots, update with |w|^2; each reduction finished in its grid's
       // last block (a grid of a few blocks per SM keeps enough loads in flight)
-      int nsm = 0;
-      FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
-      const dim3 rgrid((unsigned)std::min(std::max(4 * nsm, 1), RED_BLOCKS), nrhs);
+      const dim3 rgrid((unsigned)red_blocks(), nrhs);
       double *d2 = K.dots + (size_t)2 * nrhs * MAXJ;
       k_gdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part, K.g_cnt, K.dots, hsum, 1);
       k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, K.part, K.g_cnt, nullptr);

@@ -303,10 +303,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
             if (KIND == 0) {
               tc::mma_tf32(d, ad, bd, idesc, acc);
             } else {
-              asm volatile(
-                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              tc::mma_f16(d, ad, bd, idesc, acc);
             }
             acc = 1;
           }

@@ -6,29 +6,35 @@
 // a matrix product: D[leaf][t] += sum_k W[leaf + o][k] * B_o[t][k], B_o[t][k] = ln|d(t, k, o)|
 // (node units, cell-mean value at d = 0), t, k the 64 nodes of an 8x8 leaf.  One CTA takes
 // 128 consecutive target leaves of one leaf row (M = 128, N = 64) and sweeps the 37 stencil
-// offsets in two halves of K = 32.  FP32 accuracy from TF32 inputs: each operand is split
-// hi + lo (both TF32 numbers, rounded to nearest) and the product is taken as
-// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
+// offsets, K = the 64 source nodes of a leaf.
+//
+// FP32 accuracy from FP16 operands: each operand is split hi + lo (both FP16, rounded to
+// nearest; an FP16 word has the 11-bit significand of a TF32 word, so hi + lo carries 22
+// bits) and the product is taken as hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
+// rounding).  FP16's narrow exponent range is met by scaling each source leaf's 64 weights
+// by a power of two 2^e chosen from the leaf's largest |h^2 r|, so that it lies in
+// [2^13, 2^14); the epilogue scales each offset's sums back by the source leaf's 2^-e
+// (exact) as it adds them up.  Against TF32 operands the same three products move half the
+// bytes and run at twice the rate, and a leaf's 64 source nodes fill one 128-byte row.
 //
 // The tensor core truncates when it adds into its FP32 accumulator, so a long chain of
-// MMAs into one accumulator drifts (~2^-24 of the partial sum per MMA).  Each (offset,
-// K half) group therefore starts a fresh accumulator -- the two small correction products
-// first, the hi*hi products last -- and four epilogue warps drain it into per-thread FP32
-// sums while the next groups run in the other TMEM buffers (four in flight: the
-// commit-to-barrier round trip is longer than two groups of MMAs).  Each tile's 74 groups
-// are split between two CTAs (37 each; the second writes a scratch image that the L2P pass
-// adds), and two CTAs share an SM, so one's copies and barrier round trips overlap the
-// other's MMAs.  Both halves are written as FP32 images of the raw sums.
+// MMAs into one accumulator drifts (~2^-24 of the partial sum per MMA).  Each offset's group
+// therefore starts a fresh accumulator -- the two small correction products first, the
+// hi*hi products last -- and four epilogue warps drain it into per-thread FP32 sums while
+// the next groups run in the other TMEM buffers (four in flight).  The stencil rows are
+// split between two CTAs (the second writes a scratch image that the L2P pass adds), and
+// two CTAs share an SM, so one's copies and barrier round trips overlap the other's MMAs.
 //
-// Data: per padded leaf row and K half, each leaf's 32 weights are one 128-byte row in the
-// 128-byte swizzle (chunk c of leaf X at position c ^ (X % 8)), leaves contiguous, so the
-// 134 leaves a tile needs are one 1-D bulk copy straight into the MMA operand layout, and
-// a shift by ox leaves is a 128-byte shift of the descriptor start whose eight-row reads
-// stay free of bank conflicts.  The B_o pairs (hi, lo) are precomputed per K half in the
-// same layout (16 KB per group).  Warp 0 streams strips
-// (two slots) and B groups (eight slots); warp 1 issues the MMAs; warps 2-5 drain TMEM.
+// Data: per padded leaf row, each leaf's 64 scaled weights are one 128-byte row in the
+// 128-byte swizzle (16-byte chunk c of leaf X at position c ^ (X % 8)), leaves contiguous,
+// so the 134 leaves a tile needs are one 1-D bulk copy straight into the MMA operand layout,
+// and a shift by ox leaves is a 128-byte shift of the descriptor start.  The B_o pairs
+// (hi, lo) are precomputed in the same layout (16 KB per offset).  Warp 0 streams strips
+// (two slots) and B groups (two slots); warp 1 issues the MMAs; warps 2-5 drain TMEM.
 #include <cmath>
 #include <cstring>
+
+#include <cuda_fp16.h>
 
 #include "handle.cuh"
 #include "tc.cuh"
@@ -40,102 +46,92 @@ namespace {
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 constexpr int TC_TILE = 128;       // target leaves per CTA
-constexpr int TC_BGRP = 16384;     // one (offset, K half) group of B: hi + lo, 64 x 32 FP32 each
+constexpr int TC_BGRP = 16384;     // one offset's B: hi + lo, 64 x 64 FP16 each
 constexpr int TC_NB = 2;           // B stages per CTA (two CTAs per SM)
 constexpr int TC_NACC = 4;         // TMEM accumulators (64 columns each) in flight
 constexpr int TC_THREADS = 192;    // producer, MMA issuer, four epilogue warps
 constexpr int TC_MAXROWS = 33;
+constexpr int TC_TOP = 13;         // the largest scaled weight lies in [2^TC_TOP, 2^(TC_TOP+1))
+
+// instruction descriptor of tcgen05.mma kind::f16 with FP16 A and B, FP32 accumulation,
+// K-major operands: bits 4-5 D format (1 = F32), 7-9 / 10-12 A / B format (0 = F16),
+// 17-22 N >> 3, 24-28 M >> 4
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t M, uint32_t N) { return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24); }
 
 struct TcArgs {
-  const float *ahi, *alo;  // [nrhs][NLY][K half][NLX][32], swizzled per leaf
-  const float *bmat;       // [nofs][K half][hi, lo][64][32], swizzled per row t
-  float *out1, *out2;  // near-field sums (unscaled), first and second half of the stencil (z = 2 rhs + half)
+  const uint16_t *ahi, *alo;  // [nrhs][NLY][NLX][64] FP16, swizzled per leaf
+  const uint16_t *bmat;       // [nofs][hi, lo][64][64] FP16, swizzled per row t
+  const float *lsc;           // [nrhs][NLY][NLX] 2^-e of each (padded) source leaf
+  float *out1, *out2;  // near-field sums (unscaled), first and second part of the stencil rows
   int *err;
   int n, R, NLX, NLY, NS, nrows, nofs, npass, usplit;
   int row_oy[TC_MAXROWS], row_q0[TC_MAXROWS], row_q1[TC_MAXROWS], row_ox0[TC_MAXROWS];
 };
 
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.  Thread
-// per (rhs, leaf, node row of the leaf): it reads the row's 8 weights, writes their two
-// 32-byte pieces of the leaf's swizzled 128-byte rows (hi, lo) and the same 8 weights of the
-// FP32 zero-padded weight image the other stages read (w, npad, pad).  Leaves are the
-// fastest index, so reads and writes of neighbouring threads are contiguous.
 // h^2 as two FP32 words for the weight product
 inline float h2_hi(double h) { return (float)(h * h); }
 inline float h2_lo(double h) { return (float)(h * h - (double)(float)(h * h)); }
 
-// x = hi + lo, hi = fl32(x) rounded to nearest even and lo = fl32(x - hi), from the IEEE-754
-// fields on the integer units (FP64 arithmetic is scarce on this GPU); |x| outside
-// [2^-100, 2^101) goes through the conversion unit.  (Below about 2^-100 the error words of
-// the product below lose bits as FP32 subnormals; the weights are far above that.)
-__device__ __forceinline__ void f64_to_f32x2(double x, float &hi, float &lo) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const uint32_t e = (uint32_t)(u >> 52) & 0x7ffu;
-  const uint64_t m = u & 0xfffffffffffffull;
-  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
-  if (e >= 923u && e <= 1123u) {
-    uint32_t f = sign | ((e - 896u) << 23) | (uint32_t)(m >> 29);
-    const uint32_t rest = (uint32_t)(m & 0x1fffffffu);  // the 29 bits below FP32 precision
-    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (f & 1u));
-    f += up ? 1u : 0u;  // a carry out of the mantissa moves into the exponent, as it should
-    hi = __uint_as_float(f);
-    const int32_t rr = (int32_t)rest - (up ? 0x20000000 : 0);  // x - hi in units of 2^(e - 1075)
-    const float mag = __int2float_rn(rr) * 0x1p-29f * __uint_as_float((e - 1046u + 127u) << 23);
-    lo = sign ? -mag : mag;
-  } else if (e == 0 && m == 0) {
-    hi = lo = __uint_as_float(sign);
-  } else {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
-  }
+// w = fl32(h^2 r) from a two-word FP32 product (h^2 and r each as hi + lo, the product of
+// the high words split exactly by an FMA): the FP32 weight of the CUDA-core engine's image
+__device__ __forceinline__ float weight_of(double r, float h2h, float h2l) {
+  const float2 x2 = f64_to_f32x2(r);
+  const float xh = x2.x, xl = x2.y;
+  const float p = __fmul_rn(xh, h2h);
+  const float t = fmaf(xh, h2l, fmaf(xl, h2h, fmaf(xh, h2h, -p)));
+  return p + t;
 }
 
-__global__ void k_tc_strips(int n, int R, int NLX, int NLY, float h2_hi, float h2_lo, int nrhs,
-                            const double *__restrict__ r,
-                            float *__restrict__ ahi, float *__restrict__ alo, float *__restrict__ wimg, int npad,
-                            int pad) {
-  const int NL = n / 8;
+// Weight strips: node (i, j) -> leaf (X, Y) = (i/8 + R, j/8 + R), k = (j%8) 8 + i%8.  Thread
+// per (rhs, leaf, node row jr = j%8 of the leaf), jr fastest, so the eight lanes of a leaf
+// find its largest |w| by three shuffles.  Each writes its row's FP16 hi and lo words (the
+// weights times the leaf's 2^e) as 16-byte chunk jr of the leaf's swizzled 128-byte rows,
+// so a leaf's eight lanes write whole rows, and the same 8 weights unscaled into the FP32
+// zero-padded weight image the other stages read (w, npad, pad).  lsc gets the leaf's 2^-e.
+// 2^e puts the leaf's largest weight in [2^TC_TOP, 2^(TC_TOP+1)); e is capped at 126 so that
+// 2^e and 2^-e stay FP32 numbers (a leaf whose largest weight is below 2^-113 keeps fewer
+// than 22 bits in the split; its near field is within a few FP32 ulps of underflow anyway).
+__global__ void k_tc_strips(int n, int lgNL, int R, int NLX, int NLY, float h2h, float h2l, int nrhs,
+                            const double *__restrict__ r, uint16_t *__restrict__ ahi, uint16_t *__restrict__ alo,
+                            float *__restrict__ lsc, float *__restrict__ wimg, int npad, int pad) {
+  const int NL = 1 << lgNL;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nrhs * NL * NL * 8) return;
-  const int Xl = (int)(t % NL);
-  const int64_t rest = t / NL;
-  const int jr = (int)(rest % 8);  // node row of the leaf: K half jr / 4, row jj = jr % 4 in it
-  const int64_t rest2 = rest / 8;
-  const int Yl = (int)(rest2 % NL);
-  const int64_t rhs = rest2 / NL;
-  const int kh = jr >> 2, jj = jr & 3;
+  const bool in = t < ((int64_t)nrhs << (2 * lgNL + 3));  // every lane takes part in the shuffles
+  const int jr = (int)(t & 7);
+  const int Xl = (int)((t >> 3) & (NL - 1));
+  const int Yl = (int)((t >> (3 + lgNL)) & (NL - 1));
+  const int64_t rhs = t >> (3 + 2 * lgNL);
   const int X = Xl + R, Y = Yl + R;
-  const int64_t rowoff = (((rhs * NLY + Y) * 2 + kh) * NLX + X) * 32;
-  float4 *hrow = reinterpret_cast<float4 *>(ahi + rowoff), *lrow = reinterpret_cast<float4 *>(alo + rowoff);
+  const int64_t leaf = (rhs * NLY + Y) * NLX + X, rowoff = leaf * 64;
   const int j = 8 * Yl + jr, i0 = 8 * Xl;
   const double *src = r + rhs * (int64_t)n * n + (int64_t)j * n + i0;
-  float w[8], hi[8], lo[8];
+  float w[8];
+  float m = 0.0f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    // w = fl32(h^2 r) rounded once from a two-word FP32 product (h^2 and r each as hi + lo,
-    // the product of the high words split exactly by an FMA): the FP32 value the other
-    // engine's weight image holds, but for exact near-ties; then hi + lo TF32 words of w
-    float xh, xl;
-    f64_to_f32x2(src[q], xh, xl);
-    const float p = __fmul_rn(xh, h2_hi);
-    const float t = fmaf(xh, h2_lo, fmaf(xl, h2_hi, fmaf(xh, h2_hi, -p)));
-    w[q] = p + t;
-    hi[q] = tf32_round(w[q]);
-    lo[q] = tf32_round(w[q] - hi[q]);
+    w[q] = in ? weight_of(src[q], h2h, h2l) : 0.0f;
+    m = fmaxf(m, fabsf(w[q]));
   }
-  // k = 32 kh + 8 jj + q: chunk c = 2 jj + q / 4 of the K half, stored at c ^ (X & 7)
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  // floor(log2 m) from the FP32 fields (a subnormal m counts as 2^-127: e is capped anyway)
+  const int e = m > 0.0f ? min(TC_TOP - ((int)((__float_as_uint(m) >> 23) & 0xffu) - 127), 126) : 0;
+  const float sc = ldexpf(1.0f, e);
+  if (!in) return;
+  if (jr == 0) lsc[leaf] = ldexpf(1.0f, -e);
+  uint32_t hw[4], lw[4];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int c = 2 * jj + h;
-    hrow[c ^ (X & 7)] = make_float4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
-    lrow[c ^ (X & 7)] = make_float4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+  for (int q = 0; q < 8; q += 2) {
+    const float a = w[q] * sc, b = w[q + 1] * sc;  // exact: scaling by a power of two
+    const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
+    const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
+    hw[q / 2] = (uint32_t)__half_as_ushort(ah) | ((uint32_t)__half_as_ushort(bh) << 16);
+    lw[q / 2] = (uint32_t)__half_as_ushort(al) | ((uint32_t)__half_as_ushort(bl) << 16);
   }
+  const int pos = jr ^ (X & 7);
+  reinterpret_cast<uint4 *>(ahi + rowoff)[pos] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  reinterpret_cast<uint4 *>(alo + rowoff)[pos] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   float *wr = wimg + rhs * (int64_t)npad * npad + (int64_t)(j + pad) * npad + i0 + pad;
   reinterpret_cast<float4 *>(wr)[0] = make_float4(w[0], w[1], w[2], w[3]);
   reinterpret_cast<float4 *>(wr)[1] = make_float4(w[4], w[5], w[6], w[7]);
@@ -147,15 +143,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, used_s, used_b;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int SH = (a.NS * 128 + 1023) & ~1023;  // bytes of one K half of a strip (hi or lo)
+  const int SH = (a.NS * 128 + 1023) & ~1023;  // bytes of one strip (hi or lo)
   // the swizzle is taken from absolute address bits: operands start on 1024-byte boundaries
   unsigned char *strips = smem + ((1024u - (tc::smem_addr(smem) & 1023u)) & 1023u);  // [2][hi, lo][SH]
   unsigned char *bm = strips + 4 * SH;                                                 // [TC_NB][TC_BGRP]
   const int lx0 = blockIdx.x * TC_TILE, ly = blockIdx.y, rhs = blockIdx.z >> 1, half = blockIdx.z & 1;
-  // this CTA's strip units (stencil row, K half): [u0, u1); the other half goes to a.out2
-  const int u0 = half ? a.usplit : 0, u1 = half ? 2 * a.nrows : a.usplit;
+  // this CTA's stencil rows [u0, u1); the other part goes to a.out2
+  const int u0 = half ? a.usplit : 0, u1 = half ? a.nrows : a.usplit;
   int ngroups = 0;
-  for (int u = u0; u < u1; ++u) ngroups += a.row_q1[u >> 1] - a.row_q0[u >> 1];
+  for (int u = u0; u < u1; ++u) ngroups += a.row_q1[u] - a.row_q0[u];
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&full_s[b], 1);
@@ -180,27 +176,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  const int64_t rhs_off = (int64_t)rhs * a.NLY * 2 * a.NLX * 32;
+  const int64_t rhs_off = (int64_t)rhs * a.NLY * a.NLX * 64;
   int issued_s = 0, issued_b = 0;
   if (warp == 0) {
     if (lane == 0) {
-      // producer: per (stencil row, K half) the weight strip, then that row's B groups
+      // producer: per stencil row the weight strip, then that row's B groups
       int g = 0;
       bool ok = true;
       for (int u = u0; u < u1 && ok && !abort_flag; ++u) {
-        const int lu = u - u0, r = u >> 1, kh = u & 1, slot = lu & 1;
+        const int lu = u - u0, slot = lu & 1;
         if (lu >= 2 && !tc::mbar_wait(&empty_s[slot], ((lu >> 1) - 1) & 1, &abort_flag)) { ok = false; break; }
         tc::mbar_expect_tx(&full_s[slot], 2 * a.NS * 128);
-        const int64_t Y = ly + a.R + a.row_oy[r];
-        const int64_t off = rhs_off + ((Y * 2 + kh) * a.NLX + lx0) * 32;
+        const int64_t Y = ly + a.R + a.row_oy[u];
+        const int64_t off = rhs_off + (Y * a.NLX + lx0) * 64;
         tc::bulk_g2s(strips + (slot * 2) * SH, a.ahi + off, a.NS * 128, &full_s[slot]);
         tc::bulk_g2s(strips + (slot * 2 + 1) * SH, a.alo + off, a.NS * 128, &full_s[slot]);
         issued_s = lu + 1;
-        for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
+        for (int q = a.row_q0[u]; q < a.row_q1[u]; ++q) {
           const int bi = g % TC_NB;
           if (g >= TC_NB && !tc::mbar_wait(&empty_b[bi], ((g / TC_NB) - 1) & 1, &abort_flag)) { ok = false; break; }
           tc::mbar_expect_tx(&full_b[bi], TC_BGRP);
-          tc::bulk_g2s(bm + bi * TC_BGRP, a.bmat + ((int64_t)q * 2 + kh) * (TC_BGRP / 4), TC_BGRP, &full_b[bi]);
+          tc::bulk_g2s(bm + bi * TC_BGRP, a.bmat + (int64_t)q * (TC_BGRP / 2), TC_BGRP, &full_b[bi]);
           issued_b = ++g;
         }
       }
@@ -211,17 +207,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: one fresh accumulator per (offset, K half) group, alternating buffers
-      const uint32_t idesc = tc::idesc_tf32(128, 64);
+      // MMA issuer: one fresh accumulator per offset group, four buffers in turn
+      const uint32_t idesc = idesc_f16(128, 64);
       int g = 0;
       bool ok = true;
       for (int u = u0; u < u1 && ok; ++u) {
-        const int lu = u - u0, r = u >> 1, slot = lu & 1;
+        const int lu = u - u0, slot = lu & 1;
         if (!tc::mbar_wait(&full_s[slot], (lu >> 1) & 1, &abort_flag)) { ok = false; break; }
         used_s = lu + 1;
         tc::fence_after();
         const uint32_t sh = tc::smem_addr(strips + (slot * 2) * SH), sl = tc::smem_addr(strips + (slot * 2 + 1) * SH);
-        for (int q = a.row_q0[r]; q < a.row_q1[r]; ++q) {
+        for (int q = a.row_q0[u]; q < a.row_q1[u]; ++q) {
           const int bi = g % TC_NB, ab = g % TC_NACC;
           if (!tc::mbar_wait(&full_b[bi], (g / TC_NB) & 1, &abort_flag)) { ok = false; break; }
           used_b = g + 1;
@@ -230,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
             break;
           }
           tc::fence_after();
-          const int ox = a.row_ox0[r] + (q - a.row_q0[r]);
+          const int ox = a.row_ox0[u] + (q - a.row_q0[u]);
           const uint32_t bh = tc::smem_addr(bm + bi * TC_BGRP), bl = bh + TC_BGRP / 2;
           const uint32_t d = tmem + 64 * ab;
           uint32_t acc = 0;
@@ -238,14 +234,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
           if (a.npass == 3) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-              tc::mma_tf32(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bl + 32 * s), idesc, acc);
+              tc::mma_f16(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bl + 32 * s), idesc, acc);
               acc = 1;
-              tc::mma_tf32(d, tc::desc_sw128(lrow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, 1u);
+              tc::mma_f16(d, tc::desc_sw128(lrow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, 1u);
             }
           }
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
-            tc::mma_tf32(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, acc);
+            tc::mma_f16(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, acc);
             acc = 1;
           }
           tc::commit(&acc_full[ab]);  // the epilogue also releases the B and strip slots
@@ -265,7 +261,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) sum[i] = 0.0f;
     bool ok = true;
-    int u = u0, uend = a.row_q1[u0 >> 1] - a.row_q0[u0 >> 1];  // groups of the current unit end at uend
+    int u = u0, uend = a.row_q1[u0] - a.row_q0[u0];  // groups of the current row end at uend
+    // 2^-e of this thread's source leaf for offset (ox, oy): row of the padded leaf grid
+    const int Xp = lx0 + 32 * qd + lane + a.R;
+    const float *lrow = a.lsc + ((int64_t)rhs * a.NLY + ly + a.R) * a.NLX + Xp;
     for (int g = 0; g < ngroups; ++g) {
       const int ab = g % TC_NACC;
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[ab], (g / TC_NACC) & 1, &abort_flag))) {
@@ -273,18 +272,21 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
         break;
       }
       if (warp == 2 && lane == 0) {
-        // the group's MMAs have completed: its B slot, and at a unit's end the strip slot, are free
+        // the group's MMAs have completed: its B slot, and at a row's end the strip slot, are free
         tc::mbar_arrive(&empty_b[g % TC_NB]);
         if (g + 1 == uend) tc::mbar_arrive(&empty_s[(u - u0) & 1]);
       }
-      if (g + 1 == uend && ++u < u1) uend += a.row_q1[u >> 1] - a.row_q0[u >> 1];
+      const int nu = a.row_q1[u] - a.row_q0[u];
+      const int ox = a.row_ox0[u] + (g - (uend - nu)), oy = a.row_oy[u];
+      const float us = __ldg(lrow + (int64_t)oy * a.NLX + ox);
+      if (g + 1 == uend && ++u < u1) uend += a.row_q1[u] - a.row_q0[u];
       tc::fence_after();
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * ab + 32 * hf, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sum[32 * hf + i] += v[i];
+        for (int i = 0; i < 32; ++i) sum[32 * hf + i] = fmaf(v[i], us, sum[32 * hf + i]);  // v 2^-e exact
       }
       tc::fence_before();
       __syncwarp();
@@ -296,8 +298,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
     }
     if (ok && !abort_flag) {
       const int X = lx0 + 32 * qd + lane;
-      // the half's sum as accumulated (FP32, unscaled): the -1/(2 pi) and the sum of the two
-      // halves are applied once, in FP64, where the near field meets the far field
+      // the part's sum as accumulated: the -1/(2 pi) and the sum of the two parts are applied
+      // once, in FP64, where the near field meets the far field
       float *o = (half ? a.out2 : a.out1) + (int64_t)rhs * a.n * a.n + (int64_t)(ly * 8) * a.n + X * 8;
 #pragma unroll
       for (int tr = 0; tr < 8; ++tr) {
@@ -330,18 +332,13 @@ __global__ void k_near_combine(int64_t total, const float *__restrict__ a, const
   if (t < total) out[t] = ((double)a[t] + (double)b[t]) * NEG_INV_2PI;
 }
 
-float tf32_round_host(double v) {
-  float f = (float)v;
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  if ((u & 0x7f800000u) != 0x7f800000u) {
-    u += 0x1000u;  // half of the lowest kept mantissa bit: round to nearest
-    u &= 0xffffe000u;
-  }
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
+// FP16 word of v, rounded to nearest even (host; v within FP16's normal range)
+uint16_t f16_round_host(double v) {
+  const __half h = __float2half_rn((float)v);
+  return __half_as_ushort(h);
 }
+
+double f16_value_host(uint16_t b) { return (double)__half2float(__ushort_as_half(b)); }
 
 }  // namespace
 
@@ -360,11 +357,11 @@ void init_tc_p2p(fmmpc_handle &H) {
   H.tcp.NLY = NL;
   H.tcp.NS = TC_TILE + 2 * g.R;
   H.tcp.npass = 3;  // the near field stays FP32-accurate in every single-precision form
-  const size_t strip_floats = (size_t)H.nrhs_max * NL * 2 * NL * 32;
-  H.tcp.ahi = H.pool.get<float>(strip_floats);
-  H.tcp.alo = H.pool.get<float>(strip_floats);
-  FMMPC_CUDA(cudaMemsetAsync(H.tcp.ahi, 0, sizeof(float) * strip_floats, H.stream));
-  FMMPC_CUDA(cudaMemsetAsync(H.tcp.alo, 0, sizeof(float) * strip_floats, H.stream));
+  const size_t strip_words = (size_t)H.nrhs_max * NL * NL * 64;
+  H.tcp.ahi = H.pool.get<uint16_t>(strip_words);
+  H.tcp.alo = H.pool.get<uint16_t>(strip_words);
+  FMMPC_CUDA(cudaMemsetAsync(H.tcp.ahi, 0, sizeof(uint16_t) * strip_words, H.stream));
+  FMMPC_CUDA(cudaMemsetAsync(H.tcp.alo, 0, sizeof(uint16_t) * strip_words, H.stream));
   // B pairs for every stencil offset, rows in the order (oy, ox); without and with ln h
   std::vector<int> oys, q0s, q1s, ox0s;
   int nofs = 0;
@@ -386,41 +383,42 @@ void init_tc_p2p(fmmpc_handle &H) {
   }
   const double cself = -0.5 * std::log(2.0) - 1.5 + 0.25 * PI;
   for (int variant = 0; variant < 2; ++variant) {
-    // group (q, K half): [hi: 64 rows t][32 k] swizzled, then [lo: same]
-    std::vector<float> B((size_t)nofs * 2 * (TC_BGRP / 4), 0.0f);
+    // offset q: [hi: 64 rows t][64 k] swizzled, then [lo: same]
+    std::vector<uint16_t> B((size_t)nofs * (TC_BGRP / 2), 0);
     for (int r = 0; r < H.tcp.nrows; ++r)
       for (int q = q0s[r]; q < q1s[r]; ++q) {
         const int ox = ox0s[r] + (q - q0s[r]), oy = oys[r];
+        uint16_t *Bg = B.data() + (size_t)q * (TC_BGRP / 2);
         for (int t = 0; t < 64; ++t)
           for (int k = 0; k < 64; ++k) {
             const int dx = (t % 8) - (k % 8) - 8 * ox, dy = (t / 8) - (k / 8) - 8 * oy;
             double v = (dx == 0 && dy == 0) ? cself : 0.5 * std::log((double)dx * dx + (double)dy * dy);
             if (variant) v += g.lnh;
-            const float hi = tf32_round_host(v);
-            const int kh = k / 32, kk = k % 32;
-            float *Bg = B.data() + ((size_t)q * 2 + kh) * (TC_BGRP / 4);
-            const size_t e = (size_t)t * 32 + (((kk / 4) ^ (t & 7)) * 4) + (kk % 4);
+            const uint16_t hi = f16_round_host(v);
+            const size_t e = (size_t)t * 64 + (((k / 8) ^ (t & 7)) * 8) + (k % 8);
             Bg[e] = hi;
-            Bg[TC_BGRP / 8 + e] = tf32_round_host(v - (double)hi);
+            Bg[TC_BGRP / 4 + e] = f16_round_host(v - f16_value_host(hi));
           }
       }
-    float *dB = H.pool.get<float>(B.size());
-    FMMPC_CUDA(cudaMemcpyAsync(dB, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice, H.stream));
+    uint16_t *dB = H.pool.get<uint16_t>(B.size());
+    FMMPC_CUDA(cudaMemcpyAsync(dB, B.data(), sizeof(uint16_t) * B.size(), cudaMemcpyHostToDevice, H.stream));
     FMMPC_CUDA(cudaStreamSynchronize(H.stream));
     (variant ? H.tcp.bmat_lnh : H.tcp.bmat) = dB;
   }
   H.tcp.nofs = nofs;
-  {  // split the strip units (row, K half) into two halves of about equal group counts
+  {  // split the stencil rows into two parts of about equal offset counts
     int acc = 0, best = 1, bestd = 1 << 30;
-    for (int u = 0; u < 2 * H.tcp.nrows; ++u) {
-      acc += q1s[u >> 1] - q0s[u >> 1];
-      const int d = std::abs(2 * acc - 2 * nofs);
-      if (u + 1 < 2 * H.tcp.nrows && d < bestd) { bestd = d; best = u + 1; }
+    for (int u = 0; u < H.tcp.nrows; ++u) {
+      acc += q1s[u] - q0s[u];
+      const int d = std::abs(2 * acc - nofs);
+      if (u + 1 < H.tcp.nrows && d < bestd) { bestd = d; best = u + 1; }
     }
     H.tcp.usplit = best;
   }
   H.tcp.near1 = H.pool.get<float>((size_t)H.nrhs_max * g.n * g.n);
   H.tcp.near2 = H.pool.get<float>((size_t)H.nrhs_max * g.n * g.n);
+  H.tcp.lsc = H.pool.get<float>((size_t)H.nrhs_max * NL * NL);
+  FMMPC_CUDA(cudaMemsetAsync(H.tcp.lsc, 0, sizeof(float) * H.nrhs_max * NL * NL, H.stream));  // padding leaves
   H.tcp.err = H.pool.get<int>(1);
   FMMPC_CUDA(cudaMemsetAsync(H.tcp.err, 0, sizeof(int), H.stream));
   const int smem = 4 * ((H.tcp.NS * 128 + 1023) & ~1023) + TC_NB * TC_BGRP + 1024;  // + alignment slack
@@ -428,12 +426,14 @@ void init_tc_p2p(fmmpc_handle &H) {
   H.tcp.smem = smem;
 }
 
-// TF32 hi/lo weight strips of the right-hand side r (FP64), for run_p2p_tc, and the FP32 weight image.
+// FP16 hi/lo weight strips of the right-hand side r (FP64) with their per-leaf scales, for
+// run_p2p_tc, and the FP32 weight image, in one pass.
 int prep_p2p_tc(fmmpc_handle &H, const double *r, int nrhs, cudaStream_t s, float *wimg) {
   const Geo &g = H.g;
-  const int64_t threads = (int64_t)nrhs * (g.n / 8) * (g.n / 8) * 8;
-  k_tc_strips<<<nblk(threads), 256, 0, s>>>(g.n, g.R, H.tcp.NLX, H.tcp.NLY, h2_hi(g.h), h2_lo(g.h), nrhs, r, H.tcp.ahi, H.tcp.alo,
-                                            wimg, g.npad, g.pad);
+  const int lgNL = g.L;  // n / 8 = 2^L leaves per side (8 x 8 leaves)
+  const int64_t threads = ((int64_t)nrhs << (2 * lgNL)) * 8;
+  k_tc_strips<<<nblk(threads), 256, 0, s>>>(g.n, lgNL, g.R, H.tcp.NLX, H.tcp.NLY, h2_hi(g.h), h2_lo(g.h), nrhs, r,
+                                            H.tcp.ahi, H.tcp.alo, H.tcp.lsc, wimg, g.npad, g.pad);
   FMMPC_LAUNCH_CHECK();
   return 1;
 }
@@ -445,6 +445,7 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
   a.ahi = H.tcp.ahi;
   a.alo = H.tcp.alo;
   a.bmat = with_lnh ? H.tcp.bmat_lnh : H.tcp.bmat;
+  a.lsc = H.tcp.lsc;
   a.out1 = H.tcp.near1;
   (void)out;
   a.err = H.tcp.err;
@@ -470,7 +471,7 @@ int run_p2p_tc(fmmpc_handle &H, bool with_lnh, double *out, int nrhs, cudaStream
   return 1;
 }
 
-// out = the two halves of the near field (PART_NEAR, where no L2P pass follows).
+// out = the two parts of the near field (PART_NEAR, where no L2P pass follows).
 int add_near2(fmmpc_handle &H, double *out, int nrhs, cudaStream_t s) {
   const int64_t total = (int64_t)H.g.n * H.g.n * nrhs;
   k_near_combine<<<nblk(total), 256, 0, s>>>(total, H.tcp.near1, H.tcp.near2, out);

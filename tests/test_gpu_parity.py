@@ -92,6 +92,25 @@ def test_multi_rhs_equals_single_rhs():
         check_close(f"multi-rhs z[{i}] vs single", zb[i], zi, 1e-6, 1e-6)
 
 
+def test_tensor_core_near_field_per_leaf_scale():
+    # FP16 spans 2^-24 .. 2^16, so each source leaf's weights get their own power-of-two
+    # scale.  Here the left half of the grid is 1e14 times larger than the right half (more
+    # than FP16's whole range): the right half's near field, away from the stencil reach of
+    # the large leaves, must still match the oracle at the FP32 bar, element by element.
+    n = 1024
+    r = S.random_field(n, 31).reshape(n, n)  # [row j][column i]
+    r[:, : n // 2] *= 1e4
+    r[:, n // 2:] *= 1e-10
+    P = gpu(n, p=10)
+    assert P.query("tc_p2p") == 1
+    near = host(P.apply_part("near", dev(r.ravel()))).reshape(n, n)
+    assert P.query("device_errors") == 0
+    ref = O.Problem(n, p=10).apply(r, "fmm", stages=True)["near"].reshape(n, n)
+    far = n // 2 + 64  # the stencil reaches (R + 1) 8 = 32 nodes at most
+    check_close("tc near, small half", near[:, far:], ref[:, far:], 1e-6, 1e-6)
+    check_close("tc near, whole grid", near, ref, 1e-6, 1e-6)
+
+
 def test_tensor_core_near_field_multi_rhs_matches_single_rhs():
     # each right-hand side is its own grid z slice of the tensor-core launch
     n, k = 1024, 3
@@ -202,7 +221,7 @@ def test_graph_replay_matches_direct_launches():
 
 @pytest.mark.parametrize("seed,kind", [(21, "random"), (0, "mixture")])
 def test_tensor_core_near_field_matches_oracle(seed, kind):
-    # 1024^2 with 8x8 leaves: 128 leaves per row, the tensor-core P2P runs (3 TF32 products)
+    # 1024^2 with 8x8 leaves: 128 leaves per row, the tensor-core P2P runs (3 FP16 products)
     n = 1024
     r = S.random_field(n, seed) if kind == "random" else S.gaussian_mixture(n, seed)
     P = gpu(n, p=10)
@@ -215,10 +234,10 @@ def test_tensor_core_near_field_matches_oracle(seed, kind):
     assert P.query("tc_p2p") == 0
     z_simt = host(P.apply(rd))
     ref = O.Problem(n, p=10).apply(r, "fmm", stages=True)
-    # Each (offset, K half) group starts a fresh TMEM accumulator and ends with its four
-    # hi*hi MMAs, so the tensor core's truncating adds cost ~4 * 2^-24 of a group's partial;
-    # the 74 partials per tile are summed in FP32 with Kahan compensation, and the TF32
-    # splits leave ~2^-22 per product: ~1e-7 in all, bounded here by 1e-6.
+    # Each offset's group starts a fresh TMEM accumulator and ends with its four hi*hi
+    # MMAs, so the tensor core's truncating adds cost ~4 * 2^-24 of a group's partial; the
+    # 37 partials per target are summed in FP32, and the FP16 hi + lo splits leave ~2^-22
+    # per product: ~1e-7 in all, bounded here by 1e-6.
     check_close(f"tc near n=1024 {kind}", near_tc, ref["near"], 1e-6, 1e-6)
     check_close(f"tc z n=1024 {kind}", z_tc, ref["z"], FP32_TOL, FP32_TOL)
     check_close(f"tc z vs simt z n=1024 {kind}", z_tc, z_simt, 1e-6, 1e-6)
