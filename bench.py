@@ -61,10 +61,13 @@ def parse():
     ap.add_argument("--solve-mode", choices=["graph", "host"], default="graph",
                     help="time-to-solution solves as one CUDA graph, or driven by the host "
                          "(kernel by kernel, as a profiler can see them)")
+    ap.add_argument("--tts-forms", default="mixed_tf32,mixed_bf16,fp32,fp64",
+                    help="precision forms whose time to solution is measured (comma list)")
     ap.add_argument("--configs", default="c1,c3,c4,c5",
                     help="further workloads timed after the headline (comma list of c1,c3,c4,c5; '' for none)")
     a = ap.parse_args()
     a.configs = [c for c in a.configs.split(",") if c]
+    a.tts_forms = [f for f in a.tts_forms.split(",") if f]
     return a
 
 
@@ -597,6 +600,8 @@ def run_ours(args):
         P.set_timing(False)
         tts = {}
         for form in ("mixed_tf32", "mixed_bf16", "fp32", "fp64"):
+            if form not in args.tts_forms:
+                continue
             t0 = time.perf_counter()
             Pf = P if form == args.precision else FmmPreconditioner(n, p=args.p, leaf_max=args.leaf,
                                                                      theta=args.theta, precision=form)

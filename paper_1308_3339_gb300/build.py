@@ -66,7 +66,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     out = lib_path()
     if todo or not os.path.exists(out):
         tmp = out + f".tmp{os.getpid()}"
-        cmd = [nvcc(), "-shared", "-gencode", ARCH, "-o", tmp, *objs]
+        # cuSOLVER factorises the BEM blocks at set-up; the run path finds it next to nvcc
+        libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        cmd = [nvcc(), "-shared", "-gencode", ARCH, "-o", tmp, *objs, "-lcusolver",
+               "-Xlinker", f"-rpath={libdir}"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

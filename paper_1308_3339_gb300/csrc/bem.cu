@@ -3,8 +3,11 @@
 // matrix S_mk = int_{Gamma_k} G(y_m, y) dGamma (left side of Eq. e:ubound) is assembled in
 // FP64 from the closed-form element integral (Sec. 4.2).  The square's 90-degree rotation
 // symmetry makes S block circulant over the four sides, so a 4-point DFT over the side
-// index splits it into three n x n blocks (one complex); each is inverted once by
-// Gauss-Jordan elimination with partial pivoting, and the apply works in that basis.
+// index splits it into three n x n blocks (one complex); each is inverted once (LU with
+// partial pivoting by cuSOLVER, then the triangular solves against the identity), and the
+// apply works in that basis.  The inversion is set-up, not the apply's path.
+#include <cusolverDn.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -84,78 +87,6 @@ __global__ void k_bem_Kdl(int n, double *__restrict__ A) {
   A[t] = v;
 }
 
-__global__ void k_gj_pivot(int N, int k, const double *__restrict__ A, int *__restrict__ piv,
-                           double *__restrict__ pinv, double *__restrict__ pabs) {
-  __shared__ double best[1024];
-  __shared__ int bi[1024];
-  double b = -1.0;
-  int ib = k;
-  for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
-    double v = fabs(A[(int64_t)i * N + k]);
-    if (v > b) { b = v; ib = i; }
-  }
-  best[threadIdx.x] = b;
-  bi[threadIdx.x] = ib;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      double o = best[threadIdx.x + s];
-      int oi = bi[threadIdx.x + s];
-      if (o > best[threadIdx.x] || (o == best[threadIdx.x] && oi < bi[threadIdx.x])) {
-        best[threadIdx.x] = o;
-        bi[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    piv[k] = bi[0];
-    const double pv = A[(int64_t)bi[0] * N + k];
-    pabs[k] = fabs(pv);
-    *pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
-  }
-}
-
-// swap rows k and piv[k]; row k <- row k / pivot with A[k][k] replaced by 1 first
-__global__ void k_gj_swap_scale(int N, int k, double *__restrict__ A, const int *__restrict__ piv,
-                                const double *__restrict__ pinv, double *__restrict__ col) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  const int p = piv[k];
-  double a = A[(int64_t)k * N + j], b = A[(int64_t)p * N + j];
-  if (p != k) A[(int64_t)p * N + j] = a;
-  const double v = (j == k) ? 1.0 : b;
-  A[(int64_t)k * N + j] = v * (*pinv);
-  (void)col;
-}
-
-__global__ void k_gj_colsave(int N, int k, const double *__restrict__ A, double *__restrict__ col) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  col[i] = (i == k) ? 0.0 : A[(int64_t)i * N + k];
-}
-
-// rows i != k: A[i][j] = (j == k ? 0 : A[i][j]) - col[i] A[k][j]
-__global__ void k_gj_elim(int N, int k, double *__restrict__ A, const double *__restrict__ col) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= N || i == k) return;
-  const double f = col[i];
-  if (f == 0.0 && j != k) return;
-  double *row = A + (int64_t)i * N;
-  const double base = (j == k) ? 0.0 : row[j];
-  row[j] = base - f * A[(int64_t)k * N + j];
-}
-
-__global__ void k_swap_cols(int N, double *__restrict__ A, int c1, int c2) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double *row = A + (int64_t)i * N;
-  double t = row[c1];
-  row[c1] = row[c2];
-  row[c2] = t;
-}
-
 // From the first block row of S (n x 4n): S^0 and S^2 (n x n) and the real form of S^1,
 // E = [[S0 - S2, -(S1 - S3)], [S1 - S3, S0 - S2]] (2n x 2n).
 __global__ void k_bem_blocks(int n, const double *__restrict__ S, double *__restrict__ B0, double *__restrict__ B2,
@@ -190,28 +121,56 @@ __global__ void k_bem_pack(int n, const double *__restrict__ B0, const double *_
   o[3 * n + k] = E[(m + n) * 2 * n + k];
 }
 
-// In-place Gauss-Jordan inverse of the N x N matrix A (row-major, device) with partial
-// pivoting; returns the smallest pivot magnitude (0 for a singular matrix).
-double gj_invert(double *A, int N, cudaStream_t s, DevPool &tmp) {
-  int *piv = tmp.get<int>(N);
-  double *pinv = tmp.get<double>(1), *pabs = tmp.get<double>(N), *col = tmp.get<double>(N);
-  for (int k = 0; k < N; ++k) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(N, k, A, piv, pinv, pabs);
-    k_gj_swap_scale<<<nblk(N), 256, 0, s>>>(N, k, A, piv, pinv, col);
-    k_gj_colsave<<<nblk(N), 256, 0, s>>>(N, k, A, col);
-    k_gj_elim<<<dim3(nblk(N), N), 256, 0, s>>>(N, k, A, col);
-  }
+__global__ void k_identity(int N, double *__restrict__ B) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)N * N) B[t] = (t / N == t % N) ? 1.0 : 0.0;
+}
+
+__global__ void k_diag_abs(int N, const double *__restrict__ A, double *__restrict__ d) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) d[k] = fabs(A[(int64_t)k * N + k]);
+}
+
+#define FMMPC_CUSOLVER(call)                                                                   \
+  do {                                                                                          \
+    const cusolverStatus_t st_ = (call);                                                        \
+    if (st_ != CUSOLVER_STATUS_SUCCESS)                                                         \
+      throw ::fmmpc::Error(FMMPC_ERR_CUDA, std::string(#call) + ": cuSOLVER status " + std::to_string((int)st_)); \
+  } while (0)
+
+// In-place inverse of the N x N matrix A (row-major, device), by LU with partial pivoting
+// and the two triangular solves against the identity.  Row-major A is the column-major
+// A^T, and inv(A^T) read row-major is inv(A), so the factorisation runs on the buffer as
+// it is.  Returns the smallest |U_kk| (0 for a singular matrix).
+double lu_invert(double *A, int N, cudaStream_t s, DevPool &tmp) {
+  cusolverDnHandle_t h = nullptr;
+  FMMPC_CUSOLVER(cusolverDnCreate(&h));
+  struct Guard {
+    cusolverDnHandle_t h;
+    ~Guard() { cusolverDnDestroy(h); }
+  } guard{h};
+  FMMPC_CUSOLVER(cusolverDnSetStream(h, s));
+  int lwork = 0;
+  FMMPC_CUSOLVER(cusolverDnDgetrf_bufferSize(h, N, N, A, N, &lwork));
+  double *work = tmp.get<double>((size_t)std::max(lwork, 1));
+  int *ipiv = tmp.get<int>(N), *info = tmp.get<int>(2);
+  double *dabs = tmp.get<double>(N), *B = tmp.get<double>((size_t)N * N);
+  FMMPC_CUSOLVER(cusolverDnDgetrf(h, N, N, A, N, work, ipiv, info));
+  k_diag_abs<<<nblk(N), 256, 0, s>>>(N, A, dabs);
+  k_identity<<<nblk((int64_t)N * N), 256, 0, s>>>(N, B);
   FMMPC_LAUNCH_CHECK();
-  std::vector<int> hp(N);
+  FMMPC_CUSOLVER(cusolverDnDgetrs(h, CUBLAS_OP_N, N, N, A, N, ipiv, B, N, info + 1));
+  FMMPC_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
   std::vector<double> ha(N);
-  FMMPC_CUDA(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  FMMPC_CUDA(cudaMemcpyAsync(ha.data(), pabs, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  int hinfo[2] = {0, 0};
+  FMMPC_CUDA(cudaMemcpyAsync(ha.data(), dabs, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  FMMPC_CUDA(cudaMemcpyAsync(hinfo, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
   FMMPC_CUDA(cudaStreamSynchronize(s));
+  if (hinfo[0] > 0) return 0.0;  // U_kk == 0 at k = info - 1
+  if (hinfo[0] < 0 || hinfo[1] != 0)
+    throw Error(FMMPC_ERR_CUDA, "cuSOLVER getrf/getrs: invalid argument " + std::to_string(hinfo[0] ? hinfo[0] : hinfo[1]));
   double amin = ha[0];
   for (int k = 0; k < N; ++k) amin = std::min(amin, ha[k]);
-  for (int k = N - 1; k >= 0; --k)
-    if (hp[k] != k) k_swap_cols<<<nblk(N), 256, 0, s>>>(N, A, k, hp[k]);
-  FMMPC_LAUNCH_CHECK();
   return amin;
 }
 
@@ -247,7 +206,7 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   double *E = tmp.get<double>((size_t)4 * n * n);
   k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, S, B0, B2, E);
   FMMPC_LAUNCH_CHECK();
-  const double a0 = gj_invert(B0, n, s, tmp), a2 = gj_invert(B2, n, s, tmp), a1 = gj_invert(E, 2 * n, s, tmp);
+  const double a0 = lu_invert(B0, n, s, tmp), a2 = lu_invert(B2, n, s, tmp), a1 = lu_invert(E, 2 * n, s, tmp);
   if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
     throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
   H.Sinv = H.pool.get<double>((size_t)n * N);
@@ -301,7 +260,7 @@ void init_bem_dl(fmmpc_handle &H) {
     double *E = tmp.get<double>((size_t)4 * n * n);
     k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, A, B0, B2, E);
     FMMPC_LAUNCH_CHECK();
-    const double a0 = gj_invert(B0, n, s, tmp), a2 = gj_invert(B2, n, s, tmp), a1 = gj_invert(E, 2 * n, s, tmp);
+    const double a0 = lu_invert(B0, n, s, tmp), a2 = lu_invert(B2, n, s, tmp), a1 = lu_invert(E, 2 * n, s, tmp);
     if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
       throw Error(FMMPC_ERR_INVALID, "double-layer BEM matrix is singular for this domain");
     double *T = H.pool.get<double>((size_t)n * N);

@@ -124,6 +124,29 @@ __device__ __forceinline__ cpx<R> m2m_row(const cpx<R> *__restrict__ T, const cp
   return acc;
 }
 
+// Sums acc[k] (P <= 16 complex values) over the 16 lanes of a half-warp, transposed: lane c
+// of the half ends with the total of acc[c].  The 2P real values, padded to 32, go through a
+// butterfly in which each lane keeps half of its values at each of the four steps and adds
+// the partner's copy of that half: 30 shuffles where separate trees take 8P.
+template <typename R, int P>
+__device__ __forceinline__ cpx<R> seg16_sum_coeffs(const cpx<R> (&acc)[P], int c) {
+  static_assert(P <= 16, "two values per lane after the butterfly");
+  R v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = i < 2 * P ? ((i & 1) ? acc[i >> 1].im : acc[i >> 1].re) : R(0);
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int o = 8 >> st, h = 16 >> st;
+    const bool up = (c & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const R keep = up ? v[h + i] : v[i], give = up ? v[i] : v[h + i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  return mk<R>(v[0], v[1]);
+}
+
 // k M2M levels (item 2) over the 4^k consecutive (Morton) cells of level l held in
 // buf[0 .. 4^k), the first of them cell c0: each level's parents overwrite buf[0 ..) and
 // are written to M.  Per output the sum over the four children is split into per-child
@@ -159,7 +182,7 @@ __device__ __forceinline__ void m2m_levels_smem(const cpx<R> *sT, cpx<R> (*buf)[
 // reset by that block) computes the k levels above it.  Any block that does a step
 // computes the same sums, so the result does not depend on which block it is.
 template <typename R, int P, int MS>
-__global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict__ wpad, const cpx<R> *__restrict__ vm2m,
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && P <= 10 && MS <= 8) ? 6 : 1) k_upward_tree(Geo g, const R *__restrict__ wpad, const cpx<R> *__restrict__ vm2m,
                                                      cpx<R> *__restrict__ Mv, int *__restrict__ counter, int64_t ncount) {
   // three-level steps need 64 cells in shared memory; two-level steps where that would not fit
   constexpr int NBUF = sizeof(cpx<R>) * P * (4 * P + 128) <= 45000 ? 64 : 16, MAXSTEP = NBUF == 64 ? 3 : 2;
@@ -224,21 +247,13 @@ __global__ void __launch_bounds__(256) k_upward_tree(Geo g, const R *__restrict_
         }
       }
     }
-#pragma unroll
-    for (int k = 0; k < P; ++k)
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
-        acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
-        acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
-      }
-#pragma unroll
-    for (int k = 0; k < P; ++k)
-      if ((k & 15) == c) {
-        const R sk = k == 0 ? R(1) : R(-1) / R(k);
-        const cpx<R> v = mk<R>(sk * acc[k].re, sk * acc[k].im);
-        buf[leaf][k] = v;
-        M[(level_offset(g.L) + lc) * P + k] = v;
-      }
+    const cpx<R> tot = seg16_sum_coeffs<R, P>(acc, c);  // lane c: coefficient c
+    if (c < P) {
+      const R sk = c == 0 ? R(1) : R(-1) / R(c);
+      const cpx<R> v = mk<R>(sk * tot.re, sk * tot.im);
+      buf[leaf][c] = v;
+      M[(level_offset(g.L) + lc) * P + c] = v;
+    }
   }
   __syncthreads();
   m2m_levels_smem<R, P>(sT, buf, part, M, g.L, 16 * blk, 2, tid, nthr);
@@ -576,79 +591,143 @@ __device__ __forceinline__ void side_coords(int side, int np1, int x, int y, int
   }
 }
 
-// Multipoles of every boundary cell at every level in one launch: block per (boundary cell,
-// rhs); thread (k, el) of the 16 x 16 block accumulates coefficient k over the elements
-// el, el + 16, ... of the cell, Mt_k = sum_e (q_e qscale Bq_l[e][k] + qd_e dsgn Bd_l[e][k])
+// Multipoles of every boundary cell at every level in one launch,
+// Mt_k = sum_e (q_e qscale Bq_l[e][k] + qd_e dsgn Bd_l[e][k]) over the elements e of the cell,
 // with the level tables of Mats (element single layer, double layer, or point source at
-// the midpoint); HQ, HD say whether q and qd are given.  The coarse cells hold up to n
-// elements, so a thread issues the loads of eight elements before it adds them (latency,
-// not bandwidth, bounds this pass).  The 16 partial sums of a coefficient meet in shared
-// memory in a fixed order.
+// the midpoint; [side][element of the cell][p] per level); HQ, HD say whether q and qd are
+// given.  Work units are runs of at most 16 consecutive elements of one cell (a level's
+// units are consecutive in element order); a block of 16 x 16 threads takes 16 units of
+// one level, converts their element weights once each into shared memory, and thread
+// (unit, k) accumulates coefficient k over its unit's elements, the table loads of a batch
+// of eight issued before they are added.  The units of a cell then meet in shared memory in
+// a fixed order.  Cells of more than 256 elements (the Lc coarse levels) span several
+// blocks: each block writes its partial to part, and the last block of the cell to arrive
+// (an atomic count per cell, reset by that block) adds the partials in order.  So fine cells
+// share blocks, and no thread waits on more than 16 elements' loads at any level.
+constexpr int BUP_CHUNK = 256;  // elements per block at most (16 units of 16)
 template <typename R, int P, bool HQ, bool HD>
-__global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, const double *__restrict__ q,
+__global__ void __launch_bounds__(256) k_bnd_up_lv(Geo g, int nrhs, int Lc, const double *__restrict__ q,
                                                    const cpx<R> *__restrict__ Bq, R qscale,
                                                    const double *__restrict__ qd, const cpx<R> *__restrict__ Bd,
-                                                   R dsgn, cpx<R> *__restrict__ Mb) {
-  static_assert(P <= 16, "one coefficient slot per thread row");
+                                                   R dsgn, cpx<R> *__restrict__ Mb, cpx<R> *__restrict__ part,
+                                                   int *__restrict__ cnt) {
+  static_assert(P <= 16, "one coefficient slot per thread");
   __shared__ R sre[16][17], sim[16][17];
-  const int64_t c = blockIdx.x;
+  __shared__ R swq[BUP_CHUNK], swd[BUP_CHUNK];  // the block's element weights, converted once
+  __shared__ int s_last;
   const int rhs = blockIdx.y;
-  const int k = threadIdx.x & 15, el = threadIdx.x >> 4;
-  int l = 0;
-  while (blevel_offset(l + 1) <= c) ++l;
-  const int64_t id = c - blevel_offset(l);
-  const int n = g.n, len = n >> l;
-  const int side = (int)(id >> l);
-  const int64_t run = id & ((int64_t(1) << l) - 1);
-  const int64_t e0 = (int64_t)side * n + run * len;  // first element of the cell
-  const int64_t toff = (int64_t)4 * P * (2 * n - 2 * len) + (int64_t)side * len * P;
+  const int ul = threadIdx.x >> 4, k = threadIdx.x & 15;
+  const int n = g.n;
+  // level of this block, and its first unit in the level
+  int l = 0, bi = (int)blockIdx.x;
+  for (;;) {
+    const int len = n >> l, upc = len > 16 ? len / 16 : 1;
+    const int nb = (((4 << l) * upc) + 15) / 16;
+    if (bi < nb || l == g.L) break;
+    bi -= nb;
+    ++l;
+  }
+  const int len = n >> l, upc = len > 16 ? len / 16 : 1, ue = len < 16 ? len : 16;
+  const int units = (4 << l) * upc, u0 = bi * 16;
+  const int64_t E0 = (int64_t)u0 * ue;  // first element of the block (level element order)
+  const int nel = min(16, units - u0) * ue;
+  const int64_t rbase = (int64_t)rhs * g.NG;
+  if ((int)threadIdx.x < nel) {
+    if (HQ) swq[threadIdx.x] = from_f64<R>(q[rbase + E0 + threadIdx.x]) * qscale;
+    if (HD) swd[threadIdx.x] = from_f64<R>(qd[rbase + E0 + threadIdx.x]) * dsgn;
+  }
+  __syncthreads();
+  const int u = u0 + ul;
   R are = 0, aim = 0;
-  if (k < P) {
+  if (k < P && u < units) {
+    const int64_t cellid = u / upc;            // id = side 2^l + run
+    const int side = (int)(cellid >> l);
+    const int e1 = (u % upc) * ue;             // first element of the unit within its cell
+    const int64_t toff = (int64_t)4 * P * (2 * n - 2 * len) + ((int64_t)side * len + e1) * P + k;
+    const int s0 = ul * ue;                     // the unit's weights in shared memory
     constexpr int U = 8;
-    const int64_t rbase = (int64_t)rhs * g.NG + e0;
-    const cpx<R> *bq = Bq + toff + k, *bd = Bd + toff + k;
-    for (int e = el; e < len; e += 16 * U) {
-      double wq[U], wd[U];
+#pragma unroll
+    for (int b0 = 0; b0 < 16; b0 += U) {
+      if (b0 >= ue) break;
       cpx<R> b1[U], b2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int ee = e + 16 * u;
-        const bool in = ee < len;
-        if (HQ) {
-          wq[u] = in ? q[rbase + ee] : 0.0;
-          b1[u] = in ? bq[(int64_t)ee * P] : mk<R>(0, 0);
-        }
-        if (HD) {
-          wd[u] = in ? qd[rbase + ee] : 0.0;
-          b2[u] = in ? bd[(int64_t)ee * P] : mk<R>(0, 0);
-        }
+      for (int i = 0; i < U; ++i) {
+        if (HQ) b1[i] = b0 + i < ue ? Bq[toff + (int64_t)(b0 + i) * P] : mk<R>(0, 0);
+        if (HD) b2[i] = b0 + i < ue ? Bd[toff + (int64_t)(b0 + i) * P] : mk<R>(0, 0);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (HQ) {
-          const R w1 = from_f64<R>(wq[u]) * qscale;
-          are = fma(w1, b1[u].re, are);
-          aim = fma(w1, b1[u].im, aim);
-        }
-        if (HD) {
-          const R w2 = from_f64<R>(wd[u]) * dsgn;
-          are = fma(w2, b2[u].re, are);
-          aim = fma(w2, b2[u].im, aim);
+      for (int i = 0; i < U; ++i) {
+        if (b0 + i < ue) {
+          if (HQ) {
+            const R w1 = swq[s0 + b0 + i];
+            are = fma(w1, b1[i].re, are);
+            aim = fma(w1, b1[i].im, aim);
+          }
+          if (HD) {
+            const R w2 = swd[s0 + b0 + i];
+            are = fma(w2, b2[i].re, are);
+            aim = fma(w2, b2[i].im, aim);
+          }
         }
       }
     }
   }
-  sre[el][k] = are;
-  sim[el][k] = aim;
+  sre[ul][k] = are;
+  sim[ul][k] = aim;
   __syncthreads();
+  if (upc <= 16) {  // whole cells in this block: 16 / upc of them
+    const int cb = threadIdx.x >> 4, ncb = 16 / upc;
+    const int64_t cellid = (int64_t)u0 / upc + cb;
+    if (cb < ncb && k < P && cellid < (4 << l)) {
+      R re = 0, im = 0;
+      for (int j = 0; j < upc; ++j) {
+        re += sre[cb * upc + j][k];
+        im += sim[cb * upc + j][k];
+      }
+      Mb[((int64_t)rhs * g.nbcell + blevel_offset(l) + cellid) * P + k] = mk<R>(re, im);
+    }
+    return;  // block-uniform
+  }
+  // a coarse cell: this block's partial, then the cell's last block adds them in order
+  const int nch = upc / 16, chunk = (u0 % upc) / 16;
+  const int64_t cell = blevel_offset(l) + u0 / upc;
   if (threadIdx.x < P) {
     R re = 0, im = 0;
     for (int j = 0; j < 16; ++j) {
       re += sre[j][threadIdx.x];
       im += sim[j][threadIdx.x];
     }
-    Mb[((int64_t)rhs * g.nbcell + c) * P + threadIdx.x] = mk<R>(re, im);
+    part[((int64_t)rhs * gridDim.x + blockIdx.x) * P + threadIdx.x] = mk<R>(re, im);
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int *ct = cnt + (int64_t)rhs * blevel_offset(Lc) + cell;
+    s_last = atomicAdd(ct, 1) == nch - 1;
+    if (s_last) *ct = 0;  // ready for the next launch
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < P) {
+    const cpx<R> *pp = part + ((int64_t)rhs * gridDim.x + blockIdx.x - chunk) * P + threadIdx.x;
+    R sr = 0, si = 0;
+    for (int c = 0; c < nch; ++c) {
+      sr += __ldcg(&pp[(int64_t)c * P].re);
+      si += __ldcg(&pp[(int64_t)c * P].im);
+    }
+    Mb[((int64_t)rhs * g.nbcell + cell) * P + threadIdx.x] = mk<R>(sr, si);
+  }
+}
+
+// Blocks of k_bnd_up_lv for an n-side grid with L + 1 boundary levels.
+inline int64_t bup_blocks(int n, int L) {
+  int64_t nb = 0;
+  for (int l = 0; l <= L; ++l) {
+    const int len = n >> l, upc = len > 16 ? len / 16 : 1;
+    nb += (((int64_t)(4 << l) * upc) + 15) / 16;
+  }
+  return nb;
 }
 
 
@@ -699,28 +778,6 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   const R *W = wpad + (int64_t)rhs * g.npad * g.npad;
   const R inv2n = R(1) / (R)(2 * n);
   const int64_t numc = (2 * (int64_t)along + 1) * (n + 1);
-  // far field (first, so that its loads overlap the near sum): the local expansion of
-  // every ancestor run evaluated at y (L2L re-centring is exact, so this equals pushing the
-  // locals down to the leaf run and evaluating there)
-  R far = 0;
-  if (lane <= L) {
-    const int l = lane, nl = n >> l;
-    const int64_t id = ((int64_t)side << l) + along / nl;
-    // offset of the point from the run centre, in run units: (n+1)/n (j + 1/2 - nl/2) / nl
-    const R off = (R)(n + 1) * ((R)(along % nl) + R(0.5) - R(0.5) * (R)nl) / ((R)n * (R)nl);
-    const R ex = (side == 0) ? R(1) : (side == 2 ? R(-1) : R(0));
-    const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
-    const cpx<R> z = mk<R>(off * ex, off * ey);
-    const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
-    cpx<R> lc[16];  // all p <= 16 coefficients loaded before the Horner chain uses them
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) lc[kk] = kk < p ? Lc[kk] : mk<R>(0, 0);
-    cpx<R> v = mk<R>(0, 0);
-#pragma unroll
-    for (int kk = 15; kk >= 0; --kk)
-      if (kk < p) v = v * z + lc[kk];
-    far = v.re;
-  }
   R acc = 0;
   // precomputed (single-precision forms): Kc[(pfirst m + ip c) m^2 + el m^2 + t] = ln|y - x_t|
   const int c_near = pfirst[bl + 1] - pfirst[bl];
@@ -729,15 +786,23 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   if constexpr (std::is_same<R, float>::value) {
     if (Kc && m == 8 && (g.pad & 3) == 0 && (g.npad & 3) == 0) {
       // 16 lanes per near leaf, 4 consecutive nodes of a leaf row per lane (float4)
+      // the near leaves' Morton codes are read once, lane i holding leaf i, and passed round
+      // by shuffles, so that the loop's weight and kernel loads depend on nothing else
       const float4 *k4 = reinterpret_cast<const float4 *>(Kc + kbase);
-      for (int it = lane; it < c_near * 16; it += 32) {
-        const int el = it >> 4, t4 = it & 15;
-        int a, b;
-        morton_decode((uint32_t)psrc[pfirst[bl] + el], a, b);
-        const int row = b * 8 + (t4 >> 1), col = a * 8 + (t4 & 1) * 4;
-        const float4 wv = *reinterpret_cast<const float4 *>(W + (int64_t)(row + g.pad) * g.npad + col + g.pad);
-        const float4 kv = k4[it];
-        acc += wv.x * kv.x + wv.y * kv.y + wv.z * kv.z + wv.w * kv.w;
+      const int pf = pfirst[bl], nit = (c_near * 16 + 31) >> 5;
+      const uint32_t mycode = lane < c_near ? (uint32_t)psrc[pf + lane] : 0u;
+#pragma unroll 4
+      for (int t = 0; t < nit; ++t) {  // every lane runs every step: the shuffle is warp-wide
+        const int it = lane + 32 * t, el = it >> 4, t4 = it & 15;
+        const uint32_t code = __shfl_sync(0xffffffffu, mycode, el & 31);
+        if (it < c_near * 16) {
+          int a, b;
+          morton_decode(c_near <= 32 ? code : (uint32_t)psrc[pf + el], a, b);
+          const int row = b * 8 + (t4 >> 1), col = a * 8 + (t4 & 1) * 4;
+          const float4 wv = *reinterpret_cast<const float4 *>(W + (int64_t)(row + g.pad) * g.npad + col + g.pad);
+          const float4 kv = k4[it];
+          acc += wv.x * kv.x + wv.y * kv.y + wv.z * kv.z + wv.w * kv.w;
+        }
       }
       done_near = true;
     }
@@ -762,6 +827,27 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
     }
   }
   acc = warp_sum(acc);
+  // far field: the local expansion of every ancestor run evaluated at y (L2L re-centring
+  // is exact, so this equals pushing the locals down to the leaf run and evaluating there)
+  R far = 0;
+  if (lane <= L) {
+    const int l = lane, nl = n >> l;
+    const int64_t id = ((int64_t)side << l) + along / nl;
+    // offset of the point from the run centre, in run units: (n+1)/n (j + 1/2 - nl/2) / nl
+    const R off = (R)(n + 1) * ((R)(along % nl) + R(0.5) - R(0.5) * (R)nl) / ((R)n * (R)nl);
+    const R ex = (side == 0) ? R(1) : (side == 2 ? R(-1) : R(0));
+    const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
+    const cpx<R> z = mk<R>(off * ex, off * ey);
+    const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
+    cpx<R> lc[16];  // the p <= 16 coefficients, all loads issued before the Horner chain
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) lc[kk] = kk < p ? Lc[kk] : mk<R>(0, 0);
+    cpx<R> v = mk<R>(0, 0);
+#pragma unroll
+    for (int kk = 15; kk >= 0; --kk)
+      if (kk < p) v = v * z + lc[kk];
+    far = v.re;
+  }
   far = warp_sum(far);
   const double v = ((double)acc + (double)far) * NEG_INV_2PI;
   if (lane == 0) {
@@ -912,47 +998,60 @@ __device__ __forceinline__ void dot2_mac(float &s, float &c, float ah, float al,
   c = fmaf(al, bh, fmaf(ah, bl, c + e));
 }
 
-// The BEM apply of k_bem_apply in two-word FP32 arithmetic: block per row m of
-// T = [C^0 | C^2 | A | B], each of its BEM_T threads a strided share of the row, RB
-// right-hand sides per pass over it; the partial two-word sums are combined with TwoSum
-// (warp shuffles, then across the warps) and converted to FP64 once per row and right-hand
-// side.  Two warps per row keep every row of a 1024-side grid resident at once, each thread
-// with many row loads in flight: the pass is one sweep over T at memory speed, not waves of
-// blocks each waiting on its loads.
-constexpr int BEM_T = 64;
+// The BEM apply of k_bem_apply in two-word FP32 arithmetic: two warps per row m of
+// T = [C^0 | C^2 | A | B], each half of its columns (two rows per block), RB right-hand sides
+// per pass over it.  A lane takes four consecutive columns at a time (16-byte loads of the
+// four blocks, hi and lo) and two such steps at once, so that a row's loads are in flight
+// together and the pass is a sweep over T at memory speed rather than a chain of load round
+// trips.  The partial two-word sums are combined with TwoSum over the warp's lanes, then
+// over the row's two warps, and converted to FP64 once per row and right-hand side.  n is a
+// multiple of 8 and the rows start 16-byte aligned.
+constexpr int BEM_ROWS = 2;  // rows per block, two warps each
 template <int RB>
-__global__ void __launch_bounds__(BEM_T) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
-                                                      const float *__restrict__ Tl, const float *__restrict__ vh,
-                                                      const float *__restrict__ vl, double *__restrict__ q) {
-  constexpr int NW = BEM_T / 32;
-  __shared__ float rs[NW][RB][4], rc[NW][RB][4];
-  __shared__ double tot[RB][4];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int mrow = blockIdx.x;
-  const int NG = 4 * n;
-  const float *th = Th + (int64_t)mrow * NG, *tl = Tl + (int64_t)mrow * NG;
+__global__ void __launch_bounds__(64 * BEM_ROWS) k_bem_apply_f2(int n, int nrhs, const float *__restrict__ Th,
+                                                              const float *__restrict__ Tl, const float *__restrict__ vh,
+                                                              const float *__restrict__ vl, double *__restrict__ q) {
+  __shared__ float xs[BEM_ROWS][RB][4], xc[BEM_ROWS][RB][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, rb = w >> 1, hw = w & 1;
+  const int mrow = blockIdx.x * BEM_ROWS + rb;
+  const bool live = mrow < n;  // block-uniform for the barrier below: n is a multiple of BEM_ROWS
+  const int NG = 4 * n, n4 = n >> 2, kbeg = hw * (n4 >> 1), kend = kbeg + (n4 >> 1);
+  const float4 *th = reinterpret_cast<const float4 *>(Th + (int64_t)mrow * NG);
+  const float4 *tl = reinterpret_cast<const float4 *>(Tl + (int64_t)mrow * NG);
   for (int r0 = 0; r0 < nrhs; r0 += RB) {
     float sa[RB][4], ca[RB][4];
 #pragma unroll
     for (int j = 0; j < RB; ++j)
 #pragma unroll
       for (int g = 0; g < 4; ++g) sa[j][g] = ca[j][g] = 0.f;
-#pragma unroll 4
-    for (int k = tid; k < n; k += BEM_T) {
-      const float c0h = th[k], c2h = th[n + k], cah = th[2 * n + k], cbh = th[3 * n + k];
-      const float c0l = tl[k], c2l = tl[n + k], cal = tl[2 * n + k], cbl = tl[3 * n + k];
+#pragma unroll 2
+    for (int k4 = kbeg + lane; live && k4 < kend; k4 += 32) {
+      const float4 c0h = th[k4], c2h = th[n4 + k4], cah = th[2 * n4 + k4], cbh = th[3 * n4 + k4];
+      const float4 c0l = tl[k4], c2l = tl[n4 + k4], cal = tl[2 * n4 + k4], cbl = tl[3 * n4 + k4];
 #pragma unroll
       for (int j = 0; j < RB; ++j) {
         if (r0 + j < nrhs) {
-          const float *xh = vh + (int64_t)(r0 + j) * NG, *xl = vl + (int64_t)(r0 + j) * NG;
-          const float v0h = xh[k], v2h = xh[n + k], ah = xh[2 * n + k], bh = xh[3 * n + k];
-          const float v0l = xl[k], v2l = xl[n + k], al = xl[2 * n + k], bl = xl[3 * n + k];
-          dot2_mac(sa[j][0], ca[j][0], c0h, c0l, v0h, v0l);
-          dot2_mac(sa[j][1], ca[j][1], c2h, c2l, v2h, v2l);
-          dot2_mac(sa[j][2], ca[j][2], cah, cal, ah, al);  // re = A a + B b
-          dot2_mac(sa[j][2], ca[j][2], cbh, cbl, bh, bl);
-          dot2_mac(sa[j][3], ca[j][3], cbh, cbl, ah, al);  // im = B a - A b
-          dot2_mac(sa[j][3], ca[j][3], -cah, -cal, bh, bl);
+          const float4 *xh = reinterpret_cast<const float4 *>(vh + (int64_t)(r0 + j) * NG);
+          const float4 *xl = reinterpret_cast<const float4 *>(vl + (int64_t)(r0 + j) * NG);
+          const float4 v0h = xh[k4], v2h = xh[n4 + k4], ah = xh[2 * n4 + k4], bh = xh[3 * n4 + k4];
+          const float4 v0l = xl[k4], v2l = xl[n4 + k4], al = xl[2 * n4 + k4], bl = xl[3 * n4 + k4];
+          const float c0h_[4] = {c0h.x, c0h.y, c0h.z, c0h.w}, c0l_[4] = {c0l.x, c0l.y, c0l.z, c0l.w};
+          const float c2h_[4] = {c2h.x, c2h.y, c2h.z, c2h.w}, c2l_[4] = {c2l.x, c2l.y, c2l.z, c2l.w};
+          const float cah_[4] = {cah.x, cah.y, cah.z, cah.w}, cal_[4] = {cal.x, cal.y, cal.z, cal.w};
+          const float cbh_[4] = {cbh.x, cbh.y, cbh.z, cbh.w}, cbl_[4] = {cbl.x, cbl.y, cbl.z, cbl.w};
+          const float v0h_[4] = {v0h.x, v0h.y, v0h.z, v0h.w}, v0l_[4] = {v0l.x, v0l.y, v0l.z, v0l.w};
+          const float v2h_[4] = {v2h.x, v2h.y, v2h.z, v2h.w}, v2l_[4] = {v2l.x, v2l.y, v2l.z, v2l.w};
+          const float ah_[4] = {ah.x, ah.y, ah.z, ah.w}, al_[4] = {al.x, al.y, al.z, al.w};
+          const float bh_[4] = {bh.x, bh.y, bh.z, bh.w}, bl_[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            dot2_mac(sa[j][0], ca[j][0], c0h_[c], c0l_[c], v0h_[c], v0l_[c]);
+            dot2_mac(sa[j][1], ca[j][1], c2h_[c], c2l_[c], v2h_[c], v2l_[c]);
+            dot2_mac(sa[j][2], ca[j][2], cah_[c], cal_[c], ah_[c], al_[c]);  // re = A a + B b
+            dot2_mac(sa[j][2], ca[j][2], cbh_[c], cbl_[c], bh_[c], bl_[c]);
+            dot2_mac(sa[j][3], ca[j][3], cbh_[c], cbl_[c], ah_[c], al_[c]);  // im = B a - A b
+            dot2_mac(sa[j][3], ca[j][3], -cah_[c], -cal_[c], bh_[c], bl_[c]);
+          }
         }
       }
     }
@@ -966,32 +1065,32 @@ __global__ void __launch_bounds__(BEM_T) k_bem_apply_f2(int n, int nrhs, const f
           two_sum_acc(sa[j][g], ca[j][g], s2);
           ca[j][g] += c2;
         }
-        if (lane == 0) {
-          rs[w][j][g] = sa[j][g];
-          rc[w][j][g] = ca[j][g];
+        if (hw == 1 && lane == 0) {
+          xs[rb][j][g] = sa[j][g];
+          xc[rb][j][g] = ca[j][g];
         }
       }
     __syncthreads();
-    if (tid < RB * 4) {
-      const int j = tid >> 2, g = tid & 3;
-      float s0 = rs[0][j][g], c0 = rc[0][j][g];
-      for (int ww = 1; ww < NW; ++ww) {
-        two_sum_acc(s0, c0, rs[ww][j][g]);
-        c0 += rc[ww][j][g];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      double tot[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float s0 = sa[j][g], c0 = ca[j][g];  // the first half's sums (lane 0 of warp hw = 0)
+        two_sum_acc(s0, c0, xs[rb][j][g]);
+        c0 += xc[rb][j][g];
+        tot[g] = (double)s0 + (double)c0;
       }
-      tot[j][g] = (double)s0 + (double)c0;
+      if (hw == 0 && lane == 0 && live && r0 + j < nrhs) {
+        const double P0 = tot[0], P2 = tot[1], R = tot[2], I = tot[3];
+        double *qr = q + (int64_t)(r0 + j) * NG;
+        qr[mrow] = -0.25 * (P0 + P2 + 2.0 * R);
+        qr[n + mrow] = -0.25 * (P0 - P2 - 2.0 * I);
+        qr[2 * n + mrow] = -0.25 * (P0 + P2 - 2.0 * R);
+        qr[3 * n + mrow] = -0.25 * (P0 - P2 + 2.0 * I);
+      }
     }
-    __syncthreads();
-    if (tid < RB && r0 + tid < nrhs) {
-      const int j = tid;
-      const double P0 = tot[j][0], P2 = tot[j][1], R = tot[j][2], I = tot[j][3];
-      double *qr = q + (int64_t)(r0 + j) * NG;
-      qr[mrow] = -0.25 * (P0 + P2 + 2.0 * R);
-      qr[n + mrow] = -0.25 * (P0 - P2 - 2.0 * I);
-      qr[2 * n + mrow] = -0.25 * (P0 + P2 - 2.0 * R);
-      qr[3 * n + mrow] = -0.25 * (P0 - P2 + 2.0 * I);
-    }
-    __syncthreads();
+    __syncthreads();  // xs, xc are rewritten by the next pass
   }
 }
 
@@ -1233,10 +1332,11 @@ __global__ void __launch_bounds__(256) k_bnd_near_k(Geo g, int64_t nbnear, int n
   const int f0 = first[slot], cnt = (first[slot + 1] - f0) * m;
   const float4 *K4 = reinterpret_cast<const float4 *>(K) + (int64_t)f0 * m * 16;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
   for (int idx = grp; idx < cnt; idx += 16) {
     const int bl = src[f0 + idx / m], e = idx % m;
     const int64_t kk = bl & ((int64_t(1) << L) - 1);
-    const float qe = f64_to_f32(qr[(bl >> L) * n + kk * m + e]);
+    const float qe = (float)qr[(bl >> L) * n + kk * m + e];
     const float4 kv = K4[(int64_t)idx * 16 + t4];
     acc.x = fmaf(kv.x, qe, acc.x);
     acc.y = fmaf(kv.y, qe, acc.y);
@@ -1394,28 +1494,7 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   const uint32_t blk = blockIdx.x;
   const int L = g.L;
   const cpx<R> *Lr = Lv + (int64_t)rhs * g.ncell * P;
-  // this thread's NPT consecutive nodes of one row; their near-field and near-boundary
-  // values are loaded first, so those loads overlap the expansion work below
-  constexpr int NPT = M * M / 16;  // nodes per thread: (4M)^2 nodes over 256 threads
-  const int e0 = tid * NPT, y = e0 / (4 * M), x0 = e0 % (4 * M);
-  const int lf = (int)morton_encode((uint32_t)(x0 / M), (uint32_t)(y / M));
-  const int tx0 = x0 % M, ty = y % M;
-  int bx, by;
-  morton_decode(blk, bx, by);
-  const int64_t off = (int64_t)rhs * g.n * g.n + (int64_t)(by * 4 * M + y) * g.n + bx * 4 * M + x0;
-  const R *pb = nullptr;
-  if (do_bnd) {
-    const int slot = bslot[16 * (int64_t)blk + lf];
-    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M + tx0;
-  }
-  float nr1[NPT], nr2[NPT];
-  R pbv[NPT];
-#pragma unroll
-  for (int e = 0; e < NPT; ++e) {
-    nr1[e] = near1 ? near1[off + e] : 0.0f;
-    nr2[e] = near1 ? near2[off + e] : 0.0f;
-    pbv[e] = pb ? pb[e] : R(0);
-  }
+
   // every value the block needs, loaded at once: the translation matrices, the M2L parts of
   // the ancestors (levels 0 .. L - 2), of the 4 children and of the 16 leaves
   for (int i = tid; i < 4 * P * P; i += nthr) sS[i] = vl2l[i];
@@ -1441,19 +1520,24 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
     sanc[0][0].re = sanc[0][0].re + (R)(g.lnh * W);
   }
   __syncthreads();
-  // complete local expansions down the ancestor chain, in place: sanc[l] += L2L(sanc[l - 1])
-  for (int l = 1; l <= L - 2; ++l) {
-    const int q = (blk >> (2 * (L - 2 - l))) & 3;
-    cpx<R> acc = mk<R>(0, 0);
-    if (tid < P) {
-      const int n = tid;
-      acc = sanc[l][n];
-      for (int k = n; k < P; ++k) cmac(acc, sS[(q * P + n) * P + k], sanc[l - 1][k]);
+  // complete local expansions down the ancestor chain, in place: sanc[l] += L2L(sanc[l - 1]),
+  // by the first warp alone (P <= 32 outputs per step), so the steps meet at warp barriers
+  // and the other warps wait at a single block barrier
+  if (tid < 32) {
+    for (int l = 1; l <= L - 2; ++l) {
+      const int q = (blk >> (2 * (L - 2 - l))) & 3;
+      cpx<R> acc = mk<R>(0, 0);
+      if (tid < P) {
+        const int n = tid;
+        acc = sanc[l][n];
+        for (int k = n; k < P; ++k) cmac(acc, sS[(q * P + n) * P + k], sanc[l - 1][k]);
+      }
+      __syncwarp();
+      if (tid < P) sanc[l][tid] = acc;
+      __syncwarp();
     }
-    __syncthreads();
-    if (tid < P) sanc[l][tid] = acc;
-    __syncthreads();
   }
+  __syncthreads();
   const cpx<R> *cur = sanc[L - 2];
   cpx<R> v1 = mk<R>(0, 0), v2 = mk<R>(0, 0);
   if (tid < 4 * P) {
@@ -1472,6 +1556,18 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   __syncthreads();
   if (tid < 16 * P) s2[tid / P][tid % P] = v2;
   __syncthreads();
+  constexpr int NPT = M * M / 16;  // nodes per thread: (4M)^2 nodes over 256 threads
+  const int e0 = tid * NPT, y = e0 / (4 * M), x0 = e0 % (4 * M);
+  const int lf = (int)morton_encode((uint32_t)(x0 / M), (uint32_t)(y / M));
+  const int tx0 = x0 % M, ty = y % M;
+  int bx, by;
+  morton_decode(blk, bx, by);
+  const int64_t off = (int64_t)rhs * g.n * g.n + (int64_t)(by * 4 * M + y) * g.n + bx * 4 * M + x0;
+  const R *pb = nullptr;
+  if (do_bnd) {
+    const int slot = bslot[16 * (int64_t)blk + lf];
+    if (slot >= 0) pb = phib + ((int64_t)rhs * nbnear + slot) * M * M + ty * M + tx0;
+  }
   const R zy = (ty - R(0.5) * (M - 1)) / M;
   cpx<R> acc[NPT];
 #pragma unroll
@@ -1489,14 +1585,14 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
 #pragma unroll
     for (int e = 0; e < NPT; ++e) {
       float v = (float)acc[e].re;
-      if (pb) v += (float)pbv[e];
-      o[e] = near_far_sum(nr1[e], nr2[e], v);
+      if (pb) v += (float)pb[e];
+      o[e] = near_far_sum(near1[off + e], near2[off + e], v);
     }
   } else {
 #pragma unroll
     for (int e = 0; e < NPT; ++e) {
       double v = (double)acc[e].re;
-      if (pb) v += (double)pbv[e];
+      if (pb) v += (double)pb[e];
       o[e] += v * NEG_INV_2PI;
     }
   }
@@ -1863,8 +1959,9 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     // q = S^{-1}(-vcol), or mu = (-1/2 I + K)^{-1}(-vcol) in the double-layer form
     const float *Th = dl ? H.Kdl_hi : H.Sinv_hi, *Tl = dl ? H.Kdl_lo : H.Sinv_lo;
     if (vt_f2 && Th) {  // vt_hi / vt_lo came with the collocation values
-      if (nrhs >= 4) k_bem_apply_f2<4><<<g.n, BEM_T, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
-      else k_bem_apply_f2<1><<<g.n, BEM_T, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      const unsigned nb = (unsigned)((g.n + BEM_ROWS - 1) / BEM_ROWS);
+      if (nrhs >= 4) k_bem_apply_f2<4><<<nb, 64 * BEM_ROWS, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
+      else k_bem_apply_f2<1><<<nb, 64 * BEM_ROWS, 0, s>>>(g.n, nrhs, Th, Tl, H.fb.vt_hi, H.fb.vt_lo, H.fb.q);
       ++launches;
     } else {
       k_bem_vt<<<nblk((int64_t)nrhs * g.n), 256, 0, s>>>(g.n, nrhs, H.fb.vcol, H.fb.vt);
@@ -1892,11 +1989,18 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
       const R dsgn = dl ? R(1) : R(-1);
       const cpx<R> *bq = trans ? mt.lvp : mt.lvq;
       const R qscale = trans ? (R)(g.h * g.h) : (R)g.h;
-      const dim3 grid((unsigned)g.nbcell, nrhs);
-      if (qm && qd) k_bnd_up_lv<R, P, true, true><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
-      else if (qm) k_bnd_up_lv<R, P, true, false><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
-      else if (qd) k_bnd_up_lv<R, P, false, true><<<grid, 256, 0, s>>>(g, nrhs, qm, bq, qscale, qd, mt.lvd, dsgn, Mb);
-      else FMMPC_CUDA(cudaMemsetAsync(Mb, 0, sizeof(cpx<R>) * P * g.nbcell * nrhs, s));
+      const int Lc = H.fb.bup_lc;
+      const dim3 grid((unsigned)bup_blocks(g.n, g.L), nrhs);
+      cpx<R> *bpart = (cpx<R> *)H.fb.bup_part;
+      int *bcnt = H.fb.bup_cnt;
+      if (qm && qd)
+        k_bnd_up_lv<R, P, true, true><<<grid, 256, 0, s>>>(g, nrhs, Lc, qm, bq, qscale, qd, mt.lvd, dsgn, Mb, bpart, bcnt);
+      else if (qm)
+        k_bnd_up_lv<R, P, true, false><<<grid, 256, 0, s>>>(g, nrhs, Lc, qm, bq, qscale, qd, mt.lvd, dsgn, Mb, bpart, bcnt);
+      else if (qd)
+        k_bnd_up_lv<R, P, false, true><<<grid, 256, 0, s>>>(g, nrhs, Lc, qm, bq, qscale, qd, mt.lvd, dsgn, Mb, bpart, bcnt);
+      else
+        FMMPC_CUDA(cudaMemsetAsync(Mb, 0, sizeof(cpx<R>) * P * g.nbcell * nrhs, s));
     }
     FMMPC_LAUNCH_CHECK();
     ++launches;
@@ -2055,6 +2159,14 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.vt = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.Lvb = H.pool.get<cpx<R>>((size_t)nr * std::max<int64_t>(1, H.lists.n_vbv_cells) * g.p);
+  // boundary upward pass: chunk partials and arrival counts of the coarse levels (cells of
+  // more than BUP_CHUNK elements)
+  H.fb.bup_lc = 0;
+  while ((g.n >> H.fb.bup_lc) > BUP_CHUNK && H.fb.bup_lc < g.L) ++H.fb.bup_lc;
+  const int64_t ncc = std::max<int64_t>(1, blevel_offset(H.fb.bup_lc));
+  H.fb.bup_part = H.pool.get<cpx<R>>((size_t)nr * bup_blocks(g.n, g.L) * g.p);
+  H.fb.bup_cnt = H.pool.get<int>((size_t)nr * ncc);
+  FMMPC_CUDA(cudaMemsetAsync(H.fb.bup_cnt, 0, sizeof(int) * (size_t)nr * ncc, H.stream));
   if (std::is_same<R, float>::value) {  // two-word FP32 BEM apply
     H.fb.vt_hi = H.pool.get<float>((size_t)nr * g.NG);
     H.fb.vt_lo = H.pool.get<float>((size_t)nr * g.NG);

@@ -39,6 +39,9 @@ struct FmmBufs {
   void *Lvb = nullptr;       // [nrhs][n_vbv_cells][p] boundary-source part of L of those cells
   int *up_count = nullptr;   // [nrhs][up_ncount] upward-pass arrival counts (zero between launches)
   int64_t up_ncount = 0;
+  int bup_lc = 0;            // boundary upward pass: levels whose cells are split into chunks
+  void *bup_part = nullptr;  // [nrhs][bup_lc n/64][p] chunk partial multipoles
+  int *bup_cnt = nullptr;    // [nrhs][coarse boundary cells] arrival counts (zero between launches)
 };
 
 // tensor-core lattice P2P (p2p_tc.cu)

@@ -230,6 +230,27 @@ __device__ __forceinline__ void block_sum8(const double (&acc)[8], int nq, doubl
   __syncthreads();
 }
 
+// Sum of the np block partials pp[0 .. np) by one warp, lane l taking l, l + 32, ...: the
+// loads go out eight at a time (an unrolled, predicated batch) rather than one round trip
+// per step, then a shuffle tree.  The order of the additions is fixed.
+__device__ __forceinline__ double warp_sum_parts(const double *__restrict__ pp, int np) {
+  const int lane = threadIdx.x & 31;
+  double sacc = 0.0;
+  for (int b0 = 0; b0 < np; b0 += 256) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int bb = b0 + lane + 32 * u;
+      v[u] = bb < np ? __ldcg(pp + bb) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sacc += v[u];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+  return sacc;
+}
+
 // partial[rhs][i][blk] = sum over a slice of <V_i[rhs], w[rhs]>, i in [0, nv); V_i at V + i*vs.
 // Vectors are taken in register groups of 8.
 __global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(int64_t N, int nv, const double *__restrict__ V,
@@ -258,11 +279,7 @@ __global__ void k_mdot_final(int nv, int nblocks, const double *__restrict__ par
   const int rhs = blockIdx.x, lane = threadIdx.x & 31;
   const int i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= nv) return;
-  const double *pp = part + ((int64_t)rhs * MAXJ + i) * nblocks;
-  double sacc = 0.0;
-  for (int b = lane; b < nblocks; b += 32) sacc += pp[b];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+  const double sacc = warp_sum_parts(part + ((int64_t)rhs * MAXJ + i) * nblocks, nblocks);
   if (lane == 0) {
     out[rhs * MAXJ + i] = sacc;
     if (acc && i < nacc) acc[rhs * MAXJ + i] += sacc;
@@ -415,9 +432,9 @@ void ensure_ws(fmmpc_handle &H, int64_t nvec, bool flexible) {
   k.g_rel = H.kpool.get<double>(nr);
   k.g_sc = H.kpool.get<double>(nr);
   k.g_rtol = H.kpool.get<double>(1);
-  k.g_cnt = H.kpool.get<int>(nr);
+  k.g_cnt = H.kpool.get<int>(nr + 1);  // per right-hand side, then one over all of them
   FMMPC_CUDA(cudaMemsetAsync(k.g_ctl, 0, sizeof(int) * 16, H.stream));
-  FMMPC_CUDA(cudaMemsetAsync(k.g_cnt, 0, sizeof(int) * nr, H.stream));
+  FMMPC_CUDA(cudaMemsetAsync(k.g_cnt, 0, sizeof(int) * (nr + 1), H.stream));
   k.dots = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 4);
   k.part = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * RED_BLOCKS);
   k.scal = H.kpool.get<double>((size_t)H.nrhs_max * MAXJ * 2);
@@ -957,15 +974,6 @@ enum {
   KC_COUNT = 8
 };
 
-// y = A x and, if Zb, Z_j = x
-__global__ void k_gspmv_store(const int *__restrict__ ctl, OpDev o, int64_t total, const double *__restrict__ x,
-                              double *__restrict__ y, double *__restrict__ Zb, int64_t vs) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  y[t] = op_at(o, x, t);
-  if (Zb) Zb[(int64_t)ctl[KC_J] * vs + t] = x[t];
-}
-
 // x[rhs] += sum_{i < ctl[KC_JCNT]} y[rhs][i] Z_i[rhs]
 __global__ void k_gmaxpy(const int *__restrict__ ctl, int64_t N, int nrhs, const double *__restrict__ Z, int64_t vs,
                          const double *__restrict__ y, double *__restrict__ x) {
@@ -1005,11 +1013,7 @@ __device__ __forceinline__ void reduce_parts(const double *__restrict__ part, in
                                              double *__restrict__ hsum, int acc) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < nout; i += blockDim.x >> 5) {
-    const double *pp = part + ((int64_t)rhs * MAXJ + i) * gridDim.x;
-    double sacc = 0.0;
-    for (int bb = lane; bb < (int)gridDim.x; bb += 32) sacc += __ldcg(pp + bb);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+    const double sacc = warp_sum_parts(part + ((int64_t)rhs * MAXJ + i) * gridDim.x, (int)gridDim.x);
     if (lane == 0) {
       out[rhs * MAXJ + i] = sacc;
       if (acc == 1) hsum[rhs * MAXJ + i] = sacc;
@@ -1018,28 +1022,94 @@ __device__ __forceinline__ void reduce_parts(const double *__restrict__ part, in
   }
 }
 
-// d[rhs][i] = <V_i[rhs], w[rhs]>, i <= ctl[KC_J], with the reduction finished by the last
-// block to arrive (vectors taken 8 at a time); hacc as in reduce_parts.
-__global__ void __launch_bounds__(RED_THREADS) k_gdots(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
-                                                       int64_t vs, const double *__restrict__ w, double *__restrict__ part,
-                                                       int *__restrict__ cnt, double *__restrict__ out,
-                                                       double *__restrict__ hsum, int hacc) {
+// The first CGS pass fused with the operator: w = A x (and Z_j = x for FGMRES), then
+// d[rhs][i] = <V_i[rhs], w[rhs]>, i <= ctl[KC_J], reduced by the last block (hsum = d).  The
+// first group of eight vectors takes w as it is formed; later groups reread it (each thread
+// its own elements).
+__global__ void __launch_bounds__(RED_THREADS) k_gapdots(const int *__restrict__ ctl, OpDev o, int64_t N,
+                                                         const double *__restrict__ x, double *__restrict__ w,
+                                                         double *__restrict__ Zb, const double *__restrict__ V,
+                                                         int64_t vs, double *__restrict__ part, int *__restrict__ cnt,
+                                                         double *__restrict__ out, double *__restrict__ hsum) {
   __shared__ double red[8 * (RED_THREADS / 32 + 1)];
-  const int rhs = blockIdx.y;
-  const double *wr = w + (int64_t)rhs * N;
-  const int nv = ctl[KC_J] + 1;
+  const int rhs = blockIdx.y, j = ctl[KC_J], nv = j + 1;
+  const int64_t N2 = N >> 1, base = (int64_t)rhs * N;
+  double2 *w2 = reinterpret_cast<double2 *>(w + base);
+  const double2 *x2 = reinterpret_cast<const double2 *>(x + base);
+  double2 *z2 = Zb ? reinterpret_cast<double2 *>(Zb + (int64_t)j * vs + base) : nullptr;
   for (int i0 = 0; i0 < nv; i0 += 8) {
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    mdot_chunk(N, V + (int64_t)rhs * N, vs, wr, i0, nv, false, acc);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N2; k += (int64_t)gridDim.x * blockDim.x) {
+      double2 wk;
+      if (i0 == 0) {
+        wk.x = op_at(o, x, base + 2 * k);
+        wk.y = op_at(o, x, base + 2 * k + 1);
+        w2[k] = wk;
+        if (z2) z2[k] = x2[k];
+      } else {
+        wk = w2[k];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q < nv) {
+          const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)(i0 + q) * vs + base)[k];
+          acc[q] = fma(v.x, wk.x, fma(v.y, wk.y, acc[q]));
+        }
+    }
     const int nq = min(8, nv - i0);
     block_sum8(acc, nq, red);
     if (threadIdx.x < nq) part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
     __syncthreads();
   }
   if (last_block(cnt + rhs)) {
-    reduce_parts(part, rhs, nv, out, hsum, hacc);
+    reduce_parts(part, rhs, nv, out, hsum, 1);
+    if (threadIdx.x == 0) cnt[rhs] = 0;
+  }
+}
+
+// The middle of CGS2 in one pass: w -= sum_{i <= j} c[rhs][i] V_i (c the first pass's
+// coefficients, in the order of update_chunk), then d[rhs][i] = <V_i, w> (hsum += d): one
+// sweep over the basis from memory, the second pass's reads served by L1 and L2.
+__global__ void __launch_bounds__(RED_THREADS) k_gupdots(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
+                                                         int64_t vs, const double *__restrict__ c, double *__restrict__ w,
+                                                         double *__restrict__ part, int *__restrict__ cnt,
+                                                         double *__restrict__ out, double *__restrict__ hsum) {
+  __shared__ double red[8 * (RED_THREADS / 32 + 1)];
+  const int rhs = blockIdx.y, nv = ctl[KC_J] + 1;
+  const int64_t N2 = N >> 1, base = (int64_t)rhs * N;
+  double2 *w2 = reinterpret_cast<double2 *>(w + base);
+  const double *cr = c + rhs * MAXJ;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N2; k += (int64_t)gridDim.x * blockDim.x) {
+      double2 wk = w2[k];
+      if (i0 == 0) {
+        for (int i = 0; i < nv; ++i) {
+          const double2 b = reinterpret_cast<const double2 *>(V + (int64_t)i * vs + base)[k];
+          wk.x = fma(-cr[i], b.x, wk.x);
+          wk.y = fma(-cr[i], b.y, wk.y);
+        }
+        w2[k] = wk;
+      }
+      // the second pass rereads V_i, which the update just brought into L1
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q < nv) {
+          const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)(i0 + q) * vs + base)[k];
+          acc[q] = fma(v.x, wk.x, fma(v.y, wk.y, acc[q]));
+        }
+    }
+    const int nq = min(8, nv - i0);
+    block_sum8(acc, nq, red);
+    if (threadIdx.x < nq) part[((int64_t)rhs * MAXJ + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
+    __syncthreads();
+  }
+  if (last_block(cnt + rhs)) {
+    reduce_parts(part, rhs, nv, out, hsum, 2);
     if (threadIdx.x == 0) cnt[rhs] = 0;
   }
 }
@@ -1207,53 +1277,8 @@ __global__ void k_gfinal(GmState st, int nrhs, const double *__restrict__ dots) 
   if (r < nrhs) st.rel[r] = sqrt(fmax(0.0, dots[r * MAXJ])) / st.bn[r];
 }
 
-// ---- CG (Sec. 3.1) with per-right-hand-side masks
-// alpha = <r, z> / <p, A p> (0 when done or p A p = 0)
-__global__ void k_cg_alpha(GmState st, int nrhs, const double *__restrict__ rz, const double *__restrict__ pq) {
-  const int r = threadIdx.x;
-  if (r < nrhs) {
-    const double d = pq[r * MAXJ];
-    st.sc[r] = (st.done[r] || d == 0.0) ? 0.0 : rz[r * MAXJ] / d;
-  }
-}
-
-// after x += alpha p, r -= alpha q: |r|^2 in dots; done; iterations; the IF condition of
-// the second half of the iteration (preconditioner, beta, p) is "some right-hand side runs"
-__global__ void k_cg_check(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots,
-                           cudaGraphConditionalHandle if_more) {
-  __shared__ int s_all, s_nan;
-  const int r = threadIdx.x;
-  const int it = ctl[KC_IT] + 1;
-  if (r == 0) { s_all = 1; s_nan = 0; }
-  __syncthreads();
-  if (r < nrhs) {
-    const double rn = sqrt(fmax(0.0, dots[r * MAXJ]));
-    if (!isfinite(rn)) atomicOr(&s_nan, 1);
-    if (!st.done[r]) st.iters[r] = it;
-    const int d = st.done[r] || rn / st.bn[r] <= st.rtol[0];
-    st.done[r] = d;
-    if (!d) atomicAnd(&s_all, 0);
-  }
-  __syncthreads();
-  if (r == 0) {
-    ctl[KC_IT] = it;
-    ctl[KC_DONE] = s_all;
-    ctl[KC_NAN] |= s_nan;
-    const int more = (!s_all && !s_nan && it < ctl[KC_MAXIT]) ? 1 : 0;
-    cudaGraphSetConditional(if_more, (unsigned)more);
-  }
-}
-
-// beta = <r, z>_new / <r, z>_old (0 when done); rz_old = rz_new
-__global__ void k_cg_beta(GmState st, int nrhs, const double *__restrict__ rz_new, double *__restrict__ rz_old) {
-  const int r = threadIdx.x;
-  if (r < nrhs) {
-    const double o = rz_old[r * MAXJ], nw = rz_new[r * MAXJ];
-    st.sc[r] = (st.done[r] || o == 0.0) ? 0.0 : nw / o;
-    rz_old[r * MAXJ] = nw;
-  }
-}
-
+// ---- CG (Sec. 3.1) with per-right-hand-side masks: the iteration's kernels are the fused
+// k_cgf_* below
 __global__ void k_cg_init(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots) {
   const int r = threadIdx.x;
   __shared__ int s_all;
@@ -1267,6 +1292,121 @@ __global__ void k_cg_init(int *__restrict__ ctl, GmState st, int nrhs, const dou
   }
   __syncthreads();
   if (r == 0) ctl[KC_DONE] = s_all;
+}
+
+// ---- fused CG steps: each vector pass carries its inner product, finished in the grid's last
+// block per right-hand side (a fixed order of block partials), which also takes the scalar
+// step that follows, so one CG iteration is four vector kernels and the preconditioner.
+
+// The block's sum of v into part[rhs][0][blockIdx.x]; true in every thread of the grid's last
+// block to arrive for this right-hand side, whose warp 0 then holds the total in `tot`.
+__device__ __forceinline__ bool block_partial_last(double v, double *__restrict__ part, int rhs, int *cnt,
+                                                   double &tot) {
+  __shared__ double red[RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
+  }
+  if (!last_block(cnt + rhs)) return false;
+  if (threadIdx.x == 0) cnt[rhs] = 0;
+  tot = 0.0;
+  if (wid == 0) tot = warp_sum_parts(part + (int64_t)rhs * MAXJ * gridDim.x, (int)gridDim.x);
+  return true;
+}
+
+// q = A p and <p, q>; then alpha = <r, z> / <p, q> (0 for a finished right-hand side)
+__global__ void __launch_bounds__(RED_THREADS) k_cgf_apdot(OpDev o, int64_t N, GmState st, const double *__restrict__ p,
+                                                         double *__restrict__ q, double *__restrict__ part, int *cnt,
+                                                         double *__restrict__ pq, const double *__restrict__ rz_old) {
+  const int rhs = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)rhs * N + k;
+    const double v = op_at(o, p, t);
+    q[t] = v;
+    acc = fma(p[t], v, acc);
+  }
+  double tot;
+  if (block_partial_last(acc, part, rhs, cnt, tot) && threadIdx.x == 0) {
+    pq[rhs * MAXJ] = tot;
+    st.sc[rhs] = (st.done[rhs] || tot == 0.0) ? 0.0 : rz_old[rhs * MAXJ] / tot;
+  }
+}
+
+// x += alpha p, r -= alpha q and |r|^2; the last right-hand side to finish then does the
+// convergence test of every right-hand side (iteration counts, done flags, NaN) and sets
+// the IF condition of the iteration's second half (preconditioner, beta, p): some
+// right-hand side still runs
+__global__ void __launch_bounds__(RED_THREADS) k_cgf_xr(int *__restrict__ ctl, int64_t N, int nrhs, GmState st,
+                                                      const double *__restrict__ p, const double *__restrict__ q,
+                                                      double *__restrict__ x, double *__restrict__ r,
+                                                      double *__restrict__ part, int *cnt, double *__restrict__ dots,
+                                                      cudaGraphConditionalHandle if_more) {
+  __shared__ int s_fin, s_all, s_nan;
+  const int rhs = blockIdx.y;
+  const double al = st.sc[rhs];
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)rhs * N + k;
+    x[t] = fma(al, p[t], x[t]);
+    const double rv = fma(-al, q[t], r[t]);
+    r[t] = rv;
+    acc = fma(rv, rv, acc);
+  }
+  double tot;
+  if (!block_partial_last(acc, part, rhs, cnt, tot)) return;
+  if (threadIdx.x == 0) {
+    dots[rhs * MAXJ] = tot;
+    __threadfence();
+    s_fin = atomicAdd(cnt + nrhs, 1) == nrhs - 1;
+    if (s_fin) cnt[nrhs] = 0;
+    s_all = 1;
+    s_nan = 0;
+  }
+  __syncthreads();
+  if (!s_fin) return;
+  __threadfence();
+  const int it = ctl[KC_IT] + 1;
+  for (int rr = threadIdx.x; rr < nrhs; rr += blockDim.x) {
+    const double rn = sqrt(fmax(0.0, __ldcg(dots + rr * MAXJ)));
+    if (!isfinite(rn)) atomicOr(&s_nan, 1);
+    if (!st.done[rr]) st.iters[rr] = it;
+    const int d = st.done[rr] || rn / st.bn[rr] <= st.rtol[0];
+    st.done[rr] = d;
+    if (!d) atomicAnd(&s_all, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[KC_IT] = it;
+    ctl[KC_DONE] = s_all;
+    ctl[KC_NAN] |= s_nan;
+    const int more = (!s_all && !s_nan && it < ctl[KC_MAXIT]) ? 1 : 0;
+    cudaGraphSetConditional(if_more, (unsigned)more);
+  }
+}
+
+// <r, z>; then beta = <r, z> / <r, z>_old (0 for a finished right-hand side), rz_old = <r, z>
+__global__ void __launch_bounds__(RED_THREADS) k_cgf_rz(int64_t N, GmState st, const double *__restrict__ r,
+                                                      const double *__restrict__ z, double *__restrict__ part, int *cnt,
+                                                      double *__restrict__ rz_old) {
+  const int rhs = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)rhs * N + k;
+    acc = fma(r[t], z[t], acc);
+  }
+  double tot;
+  if (block_partial_last(acc, part, rhs, cnt, tot) && threadIdx.x == 0) {
+    const double o = rz_old[rhs * MAXJ];
+    st.sc[rhs] = (st.done[rhs] || o == 0.0) ? 0.0 : tot / o;
+    rz_old[rhs * MAXJ] = tot;
+  }
 }
 
 __global__ void k_copy(int64_t total, const double *__restrict__ a, double *__restrict__ b) {
@@ -1397,22 +1537,18 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     // p in V_0, q in t, z in w; <r, z> of the last iteration in the second dots block
     double *p = K.V, *q = K.t, *z = K.w, *rz_old = K.dots + (size_t)nrhs * MAXJ;
     double *pq = K.dots + (size_t)2 * nrhs * MAXJ;
+    const dim3 rgrid((unsigned)red_blocks(), nrhs);
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
-      k_spmv5<<<nblk(NR), 256, 0, H.stream>>>(od, NR, p, q);
-      gdot(c, p, q, pq);
-      k_cg_alpha<<<1, 64, 0, H.stream>>>(st, nrhs, rz_old, pq);
-      k_cg_xr<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, p, q, K.x, K.r);
-      gnorm2(c, K.r);
-      k_cg_check<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots, hif);
+      k_cgf_apdot<<<rgrid, RED_THREADS, 0, H.stream>>>(od, N, st, p, q, K.part, K.g_cnt, pq, rz_old);
+      k_cgf_xr<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, nrhs, st, p, q, K.x, K.r, K.part, K.g_cnt, K.dots, hif);
       FMMPC_LAUNCH_CHECK();
     });
     cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
     capture_into(H, cs, ifb, none, [&] {
       c.s = H.stream;
       precond(K.r, z, K.zin);
-      gdot(c, K.r, z, K.dots);
-      k_cg_beta<<<1, 64, 0, H.stream>>>(st, nrhs, K.dots, rz_old);
+      k_cgf_rz<<<rgrid, RED_THREADS, 0, H.stream>>>(N, st, K.r, z, K.part, K.g_cnt, rz_old);
       k_cg_p<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, z, p);
       FMMPC_LAUNCH_CHECK();
     });
@@ -1424,14 +1560,14 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     f_step = capture_into(H, cs, body, none, [&] {
       c.s = H.stream;
       precond(K.t, K.zin, K.t);  // K.t holds v_j (written with V_j by the previous step)
-      k_gspmv_store<<<nblk(NR), 256, 0, H.stream>>>(ctl, od, NR, K.zin, K.w, flexible ? K.Z : nullptr, vs);
-      // CGS2: dots, update, dots, update with |w|^2; each reduction finished in its grid's
+      // w = A z_j with the first CGS pass, the first update with the second pass, the second
+      // update with |w|^2: three sweeps over the basis, each reduction finished in its grid's
       // last block (a grid of a few blocks per SM keeps enough loads in flight)
       const dim3 rgrid((unsigned)red_blocks(), nrhs);
       double *d2 = K.dots + (size_t)2 * nrhs * MAXJ;
-      k_gdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part, K.g_cnt, K.dots, hsum, 1);
-      k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, K.part, K.g_cnt, nullptr);
-      k_gdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.w, K.part, K.g_cnt, d2, hsum, 2);
+      k_gapdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, od, N, K.zin, K.w, flexible ? K.Z : nullptr, K.V, vs,
+                                                     K.part, K.g_cnt, K.dots, hsum);
+      k_gupdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, K.part, K.g_cnt, d2, hsum);
       k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, d2, K.w, K.part, K.g_cnt, wsq);
       k_gtail<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, m, hsum, wsq, K.scal, hif);
       k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs, K.t);
