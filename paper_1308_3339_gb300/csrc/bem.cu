@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "handle.cuh"
@@ -87,10 +89,10 @@ __global__ void k_bem_Kdl(int n, double *__restrict__ A) {
   A[t] = v;
 }
 
-// From the first block row of S (n x 4n): S^0 and S^2 (n x n) and the real form of S^1,
-// E = [[S0 - S2, -(S1 - S3)], [S1 - S3, S0 - S2]] (2n x 2n).
+// From the first block row of S (n x 4n): S^0 and S^2 (n x n, real) and
+// S^1 = (S0 - S2) + i (S1 - S3) (n x n, complex, interleaved re / im).
 __global__ void k_bem_blocks(int n, const double *__restrict__ S, double *__restrict__ B0, double *__restrict__ B2,
-                             double *__restrict__ E) {
+                             double *__restrict__ C1) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
   const int64_t m = t / n;
@@ -99,17 +101,13 @@ __global__ void k_bem_blocks(int n, const double *__restrict__ S, double *__rest
   const double s0 = row[k], s1 = row[n + k], s2 = row[2 * n + k], s3 = row[3 * n + k];
   B0[m * n + k] = (s0 + s2) + (s1 + s3);
   B2[m * n + k] = (s0 + s2) - (s1 + s3);
-  const double re = s0 - s2, im = s1 - s3;
-  E[m * 2 * n + k] = re;
-  E[m * 2 * n + n + k] = -im;
-  E[(m + n) * 2 * n + k] = im;
-  E[(m + n) * 2 * n + n + k] = re;
+  C1[2 * (m * n + k)] = s0 - s2;
+  C1[2 * (m * n + k) + 1] = s1 - s3;
 }
 
-// T[m] = [inv(S^0) | inv(S^2) | A | B][m] with A + i B = inv(S^1): A, B from the left
-// column blocks of inv(E).
+// T[m] = [inv(S^0) | inv(S^2) | A | B][m] with A + i B = inv(S^1).
 __global__ void k_bem_pack(int n, const double *__restrict__ B0, const double *__restrict__ B2,
-                           const double *__restrict__ E, double *__restrict__ T) {
+                           const double *__restrict__ C1, double *__restrict__ T) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
   const int64_t m = t / n;
@@ -117,18 +115,28 @@ __global__ void k_bem_pack(int n, const double *__restrict__ B0, const double *_
   double *o = T + m * 4 * n;
   o[k] = B0[m * n + k];
   o[n + k] = B2[m * n + k];
-  o[2 * n + k] = E[m * 2 * n + k];
-  o[3 * n + k] = E[(m + n) * 2 * n + k];
+  o[2 * n + k] = C1[2 * (m * n + k)];
+  o[3 * n + k] = C1[2 * (m * n + k) + 1];
 }
 
-__global__ void k_identity(int N, double *__restrict__ B) {
+__global__ void k_identity(int N, double *__restrict__ B, int cplx) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (int64_t)N * N) B[t] = (t / N == t % N) ? 1.0 : 0.0;
+  if (t >= (int64_t)N * N) return;
+  const double v = (t / N == t % N) ? 1.0 : 0.0;
+  if (cplx) {
+    B[2 * t] = v;
+    B[2 * t + 1] = 0.0;
+  } else {
+    B[t] = v;
+  }
 }
 
-__global__ void k_diag_abs(int N, const double *__restrict__ A, double *__restrict__ d) {
+// |A_kk| of the N x N (real or interleaved complex) matrix A
+__global__ void k_diag_abs(int N, const double *__restrict__ A, double *__restrict__ d, int cplx) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) d[k] = fabs(A[(int64_t)k * N + k]);
+  if (k >= N) return;
+  const int64_t i = (int64_t)k * N + k;
+  d[k] = cplx ? hypot(A[2 * i], A[2 * i + 1]) : fabs(A[i]);
 }
 
 #define FMMPC_CUSOLVER(call)                                                                   \
@@ -138,29 +146,50 @@ __global__ void k_diag_abs(int N, const double *__restrict__ A, double *__restri
       throw ::fmmpc::Error(FMMPC_ERR_CUDA, std::string(#call) + ": cuSOLVER status " + std::to_string((int)st_)); \
   } while (0)
 
-// In-place inverse of the N x N matrix A (row-major, device), by LU with partial pivoting
-// and the two triangular solves against the identity.  Row-major A is the column-major
-// A^T, and inv(A^T) read row-major is inv(A), so the factorisation runs on the buffer as
-// it is.  Returns the smallest |U_kk| (0 for a singular matrix).
-double lu_invert(double *A, int N, cudaStream_t s, DevPool &tmp) {
+// One cuSOLVER handle per device for the process (creating one costs milliseconds).
+cusolverDnHandle_t solver_handle() {
+  static std::mutex mu;
+  static std::map<int, cusolverDnHandle_t> handles;
+  int dev = 0;
+  FMMPC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = handles.find(dev);
+  if (it != handles.end()) return it->second;
   cusolverDnHandle_t h = nullptr;
   FMMPC_CUSOLVER(cusolverDnCreate(&h));
-  struct Guard {
-    cusolverDnHandle_t h;
-    ~Guard() { cusolverDnDestroy(h); }
-  } guard{h};
+  handles[dev] = h;
+  return h;
+}
+
+// In-place inverse of the N x N matrix A (row-major, device; real, or complex with re / im
+// interleaved), by LU with partial pivoting and the two triangular solves against the
+// identity.  Row-major A is the column-major A^T, and inv(A^T) read row-major is inv(A), so
+// the factorisation runs on the buffer as it is.  Returns the smallest |U_kk| (0 for a
+// singular matrix).  Calls are serialised on the handle's stream.
+double lu_invert(double *A, int N, bool cplx, cudaStream_t s, DevPool &tmp) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);  // the per-device solver handle is shared
+  cusolverDnHandle_t h = solver_handle();
   FMMPC_CUSOLVER(cusolverDnSetStream(h, s));
+  const size_t w = cplx ? 2 : 1;
   int lwork = 0;
-  FMMPC_CUSOLVER(cusolverDnDgetrf_bufferSize(h, N, N, A, N, &lwork));
-  double *work = tmp.get<double>((size_t)std::max(lwork, 1));
+  cuDoubleComplex *Az = reinterpret_cast<cuDoubleComplex *>(A);
+  if (cplx) FMMPC_CUSOLVER(cusolverDnZgetrf_bufferSize(h, N, N, Az, N, &lwork));
+  else FMMPC_CUSOLVER(cusolverDnDgetrf_bufferSize(h, N, N, A, N, &lwork));
+  double *work = tmp.get<double>(w * (size_t)std::max(lwork, 1));
   int *ipiv = tmp.get<int>(N), *info = tmp.get<int>(2);
-  double *dabs = tmp.get<double>(N), *B = tmp.get<double>((size_t)N * N);
-  FMMPC_CUSOLVER(cusolverDnDgetrf(h, N, N, A, N, work, ipiv, info));
-  k_diag_abs<<<nblk(N), 256, 0, s>>>(N, A, dabs);
-  k_identity<<<nblk((int64_t)N * N), 256, 0, s>>>(N, B);
+  double *dabs = tmp.get<double>(N), *B = tmp.get<double>(w * (size_t)N * N);
+  if (cplx) FMMPC_CUSOLVER(cusolverDnZgetrf(h, N, N, Az, N, reinterpret_cast<cuDoubleComplex *>(work), ipiv, info));
+  else FMMPC_CUSOLVER(cusolverDnDgetrf(h, N, N, A, N, work, ipiv, info));
+  k_diag_abs<<<nblk(N), 256, 0, s>>>(N, A, dabs, cplx ? 1 : 0);
+  k_identity<<<nblk((int64_t)N * N), 256, 0, s>>>(N, B, cplx ? 1 : 0);
   FMMPC_LAUNCH_CHECK();
-  FMMPC_CUSOLVER(cusolverDnDgetrs(h, CUBLAS_OP_N, N, N, A, N, ipiv, B, N, info + 1));
-  FMMPC_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
+  if (cplx)
+    FMMPC_CUSOLVER(cusolverDnZgetrs(h, CUBLAS_OP_N, N, N, Az, N, ipiv, reinterpret_cast<cuDoubleComplex *>(B), N,
+                                    info + 1));
+  else
+    FMMPC_CUSOLVER(cusolverDnDgetrs(h, CUBLAS_OP_N, N, N, A, N, ipiv, B, N, info + 1));
+  FMMPC_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * w * N * N, cudaMemcpyDeviceToDevice, s));
   std::vector<double> ha(N);
   int hinfo[2] = {0, 0};
   FMMPC_CUDA(cudaMemcpyAsync(ha.data(), dabs, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -194,8 +223,7 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   // it: with S_d = S[(0, .), (d, .)], S^0 = S0+S1+S2+S3, S^2 = S0-S1+S2-S3 (real) and
   // S^1 = (S0 - S2) + i (S1 - S3).  The apply needs exactly the inverses of these blocks,
   // [inv(S^0) | inv(S^2) | Re inv(S^1) | Im inv(S^1)] per row, so only the first block row
-  // of S is assembled and three n x n systems are inverted (the complex one through its
-  // 2n x 2n real form [[Re, -Im], [Im, Re]], whose inverse is [[A, -B], [B, A]]).
+  // of S is assembled and three n x n systems are inverted (two real, one complex).
   const Geo &g = H.g;
   const int n = g.n, N = g.NG;
   cudaStream_t s = H.stream;
@@ -203,14 +231,14 @@ void init_bem(fmmpc_handle &H, DevPool &tmp) {
   k_bem_S<<<nblk((int64_t)n * N), 256, 0, s>>>(n, g.h, g.lnh, S);
   FMMPC_LAUNCH_CHECK();
   double *B0 = tmp.get<double>((size_t)n * n), *B2 = tmp.get<double>((size_t)n * n);
-  double *E = tmp.get<double>((size_t)4 * n * n);
-  k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, S, B0, B2, E);
+  double *C1 = tmp.get<double>((size_t)2 * n * n);
+  k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, S, B0, B2, C1);
   FMMPC_LAUNCH_CHECK();
-  const double a0 = lu_invert(B0, n, s, tmp), a2 = lu_invert(B2, n, s, tmp), a1 = lu_invert(E, 2 * n, s, tmp);
+  const double a0 = lu_invert(B0, n, false, s, tmp), a2 = lu_invert(B2, n, false, s, tmp), a1 = lu_invert(C1, n, true, s, tmp);
   if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
     throw Error(FMMPC_ERR_INVALID, "single-layer BEM matrix is singular for this domain");
   H.Sinv = H.pool.get<double>((size_t)n * N);
-  k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, E, H.Sinv);
+  k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, C1, H.Sinv);
   FMMPC_LAUNCH_CHECK();
   if (H.prec != FMMPC_PREC_FP64) {  // the single-precision forms apply it in two-word FP32
     H.Sinv_hi = H.pool.get<float>((size_t)n * N);
@@ -257,14 +285,14 @@ void init_bem_dl(fmmpc_handle &H) {
     k_bem_Kdl<<<nblk((int64_t)n * N), 256, 0, s>>>(n, A);
     FMMPC_LAUNCH_CHECK();
     double *B0 = tmp.get<double>((size_t)n * n), *B2 = tmp.get<double>((size_t)n * n);
-    double *E = tmp.get<double>((size_t)4 * n * n);
-    k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, A, B0, B2, E);
+    double *C1 = tmp.get<double>((size_t)2 * n * n);
+    k_bem_blocks<<<nblk((int64_t)n * n), 256, 0, s>>>(n, A, B0, B2, C1);
     FMMPC_LAUNCH_CHECK();
-    const double a0 = lu_invert(B0, n, s, tmp), a2 = lu_invert(B2, n, s, tmp), a1 = lu_invert(E, 2 * n, s, tmp);
+    const double a0 = lu_invert(B0, n, false, s, tmp), a2 = lu_invert(B2, n, false, s, tmp), a1 = lu_invert(C1, n, true, s, tmp);
     if (!(a0 > 0.0) || !(a2 > 0.0) || !(a1 > 0.0))
       throw Error(FMMPC_ERR_INVALID, "double-layer BEM matrix is singular for this domain");
     double *T = H.pool.get<double>((size_t)n * N);
-    k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, E, T);
+    k_bem_pack<<<nblk((int64_t)n * n), 256, 0, s>>>(n, B0, B2, C1, T);
     FMMPC_LAUNCH_CHECK();
     float *th = nullptr, *tl = nullptr;
     if (H.prec != FMMPC_PREC_FP64) {

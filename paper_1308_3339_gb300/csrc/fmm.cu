@@ -124,6 +124,27 @@ __device__ __forceinline__ cpx<R> m2m_row(const cpx<R> *__restrict__ T, const cp
   return acc;
 }
 
+// Sums v[i] (NV values, NV a multiple of W) over the W lanes of an aligned segment of the
+// warp (W a power of two), transposed: lane l of the segment ends with the totals of values
+// C l .. C l + C - 1 in v[0 .. C), C = NV / W.  At each step a lane keeps half of its values
+// and adds the partner's copy of that half: NV - C shuffles in all, where a tree per value
+// takes NV log2(W).
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+template <typename R, int W, int NV>
+__device__ __forceinline__ void seg_sum_t(R (&v)[NV], int l) {
+  static_assert(NV % W == 0 && (W & (W - 1)) == 0 && W <= 32, "segment layout");
+#pragma unroll
+  for (int st = 0; st < ilog2(W); ++st) {
+    const int o = (W / 2) >> st, h = (NV / 2) >> st;
+    const bool up = (l & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const R keep = up ? v[h + i] : v[i], give = up ? v[i] : v[h + i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+}
+
 // Sums acc[k] (P <= 16 complex values) over the 16 lanes of a half-warp, transposed: lane c
 // of the half ends with the total of acc[c].  The 2P real values, padded to 32, go through a
 // butterfly in which each lane keeps half of its values at each of the four steps and adds
@@ -159,7 +180,9 @@ __device__ __forceinline__ void m2m_levels_smem(const cpx<R> *sT, cpx<R> (*buf)[
     for (int t = tid; t < 4 * npar * P; t += nthr) {  // (parent, child q, output n)
       const int ch = t / P, q = ch & 3, n = t % P;
       cpx<R> acc = mk<R>(0, 0);
-      for (int kk = 0; kk <= n; ++kk) cmac(acc, sT[(q * P + n) * P + kk], buf[ch][kk]);
+#pragma unroll
+      for (int kk = 0; kk < P; ++kk)  // fixed trip count: the shared-memory loads go out together
+        if (kk <= n) cmac(acc, sT[(q * P + n) * P + kk], buf[ch][kk]);
       part[ch][n] = acc;
     }
     __syncthreads();
@@ -404,15 +427,19 @@ __device__ __forceinline__ R scaled_offset(int64_t d, const OffsetScale &o) {
 
 template <typename R, int P>
 __device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__restrict__ out, int add) {
-  R f = 1;
+  static_assert(P <= 16, "one value per lane");
+  // the 2P real parts (re, im interleaved), padded to 32, summed transposed: lane i ends
+  // with value i
+  R v[32];
 #pragma unroll
-  for (int n = 0; n < P; ++n) {
-    if (n > 0) f = -f / R(n);
-    R re = warp_sum(H[n].re), im = warp_sum(H[n].im);
-    if (lane == 0) {
-      cpx<R> v = mk(f * re, f * im);
-      out[n] = add ? out[n] + v : v;
-    }
+  for (int i = 0; i < 32; ++i) v[i] = i < 2 * P ? ((i & 1) ? H[i >> 1].im : H[i >> 1].re) : R(0);
+  seg_sum_t<R, 32, 32>(v, lane);
+  if (lane < 2 * P) {
+    const int n = lane >> 1;
+    R f = 1;  // (-1)^n / n!
+    for (int k = 1; k <= n; ++k) f = -f / R(k);
+    R *o = reinterpret_cast<R *>(out + n) + (lane & 1);
+    *o = add ? *o + f * v[0] : f * v[0];
   }
 }
 
@@ -507,18 +534,25 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
                       mk<R>(scaled_offset<R>(X - BX, scale), scaled_offset<R>(Y - BY, scale)), lnrho);
     }
   }
-  R f = 1;
   cpx<R> *out = Lsep ? Lsep + ((int64_t)rhs * ntgt + gg % ntgt) * P : Lv + (int64_t)rhs * ncell * P + gidx * P;
+  // the 2P real parts (re, im interleaved), padded to a multiple of 8, summed over the
+  // eight lanes transposed: lane sub ends with values C sub .. C sub + C - 1
+  constexpr int NV = (2 * P + 7) / 8 * 8, C = NV / 8;
+  R v[NV];
 #pragma unroll
-  for (int n = 0; n < P; ++n) {
-    if (n > 0) f = -f / R(n);
-    R re = H[n].re, im = H[n].im;
+  for (int i = 0; i < NV; ++i) v[i] = i < 2 * P ? ((i & 1) ? H[i >> 1].im : H[i >> 1].re) : R(0);
+  seg_sum_t<R, 8, NV>(v, sub);
+  if (active) {
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
+    for (int c = 0; c < C; ++c) {
+      const int i = C * sub + c, n = i >> 1;
+      if (i < 2 * P) {
+        R f = 1;  // (-1)^n / n!
+        for (int k = 1; k <= n; ++k) f = -f / R(k);
+        R *o = reinterpret_cast<R *>(out + n) + (i & 1);
+        *o = Lsep ? f * v[c] : *o + f * v[c];
+      }
     }
-    if (active && sub == 0) out[n] = Lsep ? mk(f * re, f * im) : out[n] + mk(f * re, f * im);
   }
 }
 
@@ -1530,7 +1564,9 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
       if (tid < P) {
         const int n = tid;
         acc = sanc[l][n];
-        for (int k = n; k < P; ++k) cmac(acc, sS[(q * P + n) * P + k], sanc[l - 1][k]);
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+          if (k >= n) cmac(acc, sS[(q * P + n) * P + k], sanc[l - 1][k]);
       }
       __syncwarp();
       if (tid < P) sanc[l][tid] = acc;
@@ -1543,7 +1579,9 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   if (tid < 4 * P) {
     const int q = tid / P, n = tid % P;
     v1 = s1[q][n];
-    for (int k = n; k < P; ++k) cmac(v1, sS[(q * P + n) * P + k], cur[k]);
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if (k >= n) cmac(v1, sS[(q * P + n) * P + k], cur[k]);
   }
   __syncthreads();
   if (tid < 4 * P) s1[tid / P][tid % P] = v1;
@@ -1551,7 +1589,9 @@ __global__ void __launch_bounds__(256) k_downward_tree(Geo g, int nrhs, int do_b
   if (tid < 16 * P) {
     const int lf = tid / P, n = tid % P, q = lf & 3;
     v2 = s2[lf][n];
-    for (int k = n; k < P; ++k) cmac(v2, sS[(q * P + n) * P + k], s1[lf >> 2][k]);
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if (k >= n) cmac(v2, sS[(q * P + n) * P + k], s1[lf >> 2][k]);
   }
   __syncthreads();
   if (tid < 16 * P) s2[tid / P][tid % P] = v2;
@@ -2242,12 +2282,20 @@ void init_fmm(fmmpc_handle &H) {
       FMMPC_CUDA(cudaStreamSynchronize(H.stream));
     }
   }
-  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
+  // Stream priorities (copied into the kernel nodes of captured graphs, which are
+  // instantiated to use them): the apply's critical chain (weights, upward pass, boundary
+  // chain, downward pass) runs on the graph stream at the highest priority; the near-
+  // boundary correction, which joins later, in between; the near field and the volume M2L,
+  // which have slack, at the lowest, so that their many CTAs do not hold back the chain's
+  // latency-bound kernels.
+  int prio_low = 0, prio_high = 0;
+  FMMPC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  FMMPC_CUDA(cudaStreamCreateWithPriority(&H.gstream, cudaStreamNonBlocking, prio_high));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_in, cudaEventDisableTiming));
   FMMPC_CUDA(cudaEventCreateWithFlags(&H.gev_out, cudaEventDisableTiming));
-  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream, cudaStreamNonBlocking));
-  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream2, cudaStreamNonBlocking));
-  FMMPC_CUDA(cudaStreamCreateWithFlags(&H.sstream3, cudaStreamNonBlocking));
+  FMMPC_CUDA(cudaStreamCreateWithPriority(&H.sstream, cudaStreamNonBlocking, prio_low));
+  FMMPC_CUDA(cudaStreamCreateWithPriority(&H.sstream2, cudaStreamNonBlocking, (prio_low + prio_high) / 2));
+  FMMPC_CUDA(cudaStreamCreateWithPriority(&H.sstream3, cudaStreamNonBlocking, prio_low));
   for (auto &e : H.sev) FMMPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
@@ -2287,7 +2335,7 @@ void apply_graph(fmmpc_handle &H, const double *r, double *out, int nrhs) {
     H.stream = user;
     FMMPC_CUDA(cudaStreamEndCapture(H.gstream, &graph));
     GraphEntry e{r, out, nrhs, H.timing, nullptr, 0};
-    cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     FMMPC_CUDA(ie);
     H.gcache.push_back(e);

@@ -1486,7 +1486,11 @@ void gdot(Ctx &c, const double *a, const double *b, double *out) {
 // (and K.gin), the iterate is K.x.
 void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bool has_g) {
   KrylovWs &K = H.kw;
-  if (!H.cstream) FMMPC_CUDA(cudaStreamCreateWithFlags(&H.cstream, cudaStreamNonBlocking));
+  if (!H.cstream) {  // the capture stream of solve graphs, at the highest priority (see the apply's streams)
+    int prio_low = 0, prio_high = 0;
+    FMMPC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    FMMPC_CUDA(cudaStreamCreateWithPriority(&H.cstream, cudaStreamNonBlocking, prio_high));
+  }
   cudaStream_t cs = H.cstream;
   const int64_t N = (int64_t)H.g.n * H.g.n, NR = N * nrhs, vs = N * H.nrhs_max;
   const double s = 1.0 / (H.g.h * H.g.h);
@@ -1636,7 +1640,7 @@ cudaGraphExec_t solve_graph(std::vector<fmmpc_handle *> &hs, int method, int m, 
     throw;
   }
   SolveGraph e{method, m, nrhs, (int)has_g, (int)hs.size(), nullptr, gens};
-  const cudaError_t ie = cudaGraphInstantiate(&e.exec, G, 0);
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, G, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(G);
   FMMPC_CUDA(ie);
   H0.sgraphs.push_back(e);
