@@ -124,27 +124,6 @@ __device__ __forceinline__ cpx<R> m2m_row(const cpx<R> *__restrict__ T, const cp
   return acc;
 }
 
-// Sums v[i] (NV values, NV a multiple of W) over the W lanes of an aligned segment of the
-// warp (W a power of two), transposed: lane l of the segment ends with the totals of values
-// C l .. C l + C - 1 in v[0 .. C), C = NV / W.  At each step a lane keeps half of its values
-// and adds the partner's copy of that half: NV - C shuffles in all, where a tree per value
-// takes NV log2(W).
-constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
-template <typename R, int W, int NV>
-__device__ __forceinline__ void seg_sum_t(R (&v)[NV], int l) {
-  static_assert(NV % W == 0 && (W & (W - 1)) == 0 && W <= 32, "segment layout");
-#pragma unroll
-  for (int st = 0; st < ilog2(W); ++st) {
-    const int o = (W / 2) >> st, h = (NV / 2) >> st;
-    const bool up = (l & o) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const R keep = up ? v[h + i] : v[i], give = up ? v[i] : v[h + i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
-    }
-  }
-}
-
 // Sums acc[k] (P <= 16 complex values) over the 16 lanes of a half-warp, transposed: lane c
 // of the half ends with the total of acc[c].  The 2P real values, padded to 32, go through a
 // butterfly in which each lane keeps half of its values at each of the four steps and adds
@@ -427,19 +406,15 @@ __device__ __forceinline__ R scaled_offset(int64_t d, const OffsetScale &o) {
 
 template <typename R, int P>
 __device__ __forceinline__ void m2l_finish(cpx<R> (&H)[P], int lane, cpx<R> *__restrict__ out, int add) {
-  static_assert(P <= 16, "one value per lane");
-  // the 2P real parts (re, im interleaved), padded to 32, summed transposed: lane i ends
-  // with value i
-  R v[32];
+  R f = 1;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = i < 2 * P ? ((i & 1) ? H[i >> 1].im : H[i >> 1].re) : R(0);
-  seg_sum_t<R, 32, 32>(v, lane);
-  if (lane < 2 * P) {
-    const int n = lane >> 1;
-    R f = 1;  // (-1)^n / n!
-    for (int k = 1; k <= n; ++k) f = -f / R(k);
-    R *o = reinterpret_cast<R *>(out + n) + (lane & 1);
-    *o = add ? *o + f * v[0] : f * v[0];
+  for (int n = 0; n < P; ++n) {
+    if (n > 0) f = -f / R(n);
+    R re = warp_sum(H[n].re), im = warp_sum(H[n].im);
+    if (lane == 0) {
+      cpx<R> v = mk(f * re, f * im);
+      out[n] = add ? out[n] + v : v;
+    }
   }
 }
 
@@ -534,25 +509,18 @@ __global__ void k_m2l_vbv(GeoDev gd, int64_t ncell, int64_t nbcell, int nrhs, co
                       mk<R>(scaled_offset<R>(X - BX, scale), scaled_offset<R>(Y - BY, scale)), lnrho);
     }
   }
+  R f = 1;
   cpx<R> *out = Lsep ? Lsep + ((int64_t)rhs * ntgt + gg % ntgt) * P : Lv + (int64_t)rhs * ncell * P + gidx * P;
-  // the 2P real parts (re, im interleaved), padded to a multiple of 8, summed over the
-  // eight lanes transposed: lane sub ends with values C sub .. C sub + C - 1
-  constexpr int NV = (2 * P + 7) / 8 * 8, C = NV / 8;
-  R v[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = i < 2 * P ? ((i & 1) ? H[i >> 1].im : H[i >> 1].re) : R(0);
-  seg_sum_t<R, 8, NV>(v, sub);
-  if (active) {
+  for (int n = 0; n < P; ++n) {
+    if (n > 0) f = -f / R(n);
+    R re = H[n].re, im = H[n].im;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int i = C * sub + c, n = i >> 1;
-      if (i < 2 * P) {
-        R f = 1;  // (-1)^n / n!
-        for (int k = 1; k <= n; ++k) f = -f / R(k);
-        R *o = reinterpret_cast<R *>(out + n) + (i & 1);
-        *o = Lsep ? f * v[c] : *o + f * v[c];
-      }
+    for (int o = 4; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
     }
+    if (active && sub == 0) out[n] = Lsep ? mk(f * re, f * im) : out[n] + mk(f * re, f * im);
   }
 }
 
@@ -796,12 +764,14 @@ __global__ void k_colloc_mat(Geo g, const int32_t *__restrict__ pfirst, const in
 
 
 // (V r)(y_m) = -(1/2pi)[ Re sum_n Lt_n zt^n  +  sum_{near nodes} w_j ln|y_m - x_j| ].
-// Warp per (collocation point, rhs); requires L < 32.
+// Warp per (collocation point, rhs); requires L < 32.  mode 0: both sums; mode 1: the near
+// sum alone, into vnear (it needs only the weights, so it can run beside the volume
+// upward pass); mode 2: the far sum, added to the near sum read from vnear.
 template <typename R>
 __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<R> *__restrict__ Lb,
                          const int32_t *__restrict__ pfirst, const int32_t *__restrict__ psrc,
                          double *__restrict__ vcol, const float *__restrict__ Kc, float *__restrict__ vt_hi,
-                         float *__restrict__ vt_lo) {
+                         float *__restrict__ vt_lo, int mode, R *__restrict__ vnear) {
   // block (rhs, along): warp w takes the collocation point `along` of side w
   __shared__ double sv[4];
   const int lane = threadIdx.x & 31;
@@ -816,27 +786,21 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
   // precomputed (single-precision forms): Kc[(pfirst m + ip c) m^2 + el m^2 + t] = ln|y - x_t|
   const int c_near = pfirst[bl + 1] - pfirst[bl];
   const int64_t kbase = ((int64_t)pfirst[bl] * m + (int64_t)(along % m) * c_near) * (m * m);
-  bool done_near = false;
+  bool done_near = mode == 2;
+  if (mode == 2) acc = vnear[(int64_t)rhs * g.NG + ge];
   if constexpr (std::is_same<R, float>::value) {
-    if (Kc && m == 8 && (g.pad & 3) == 0 && (g.npad & 3) == 0) {
+    if (!done_near && Kc && m == 8 && (g.pad & 3) == 0 && (g.npad & 3) == 0) {
       // 16 lanes per near leaf, 4 consecutive nodes of a leaf row per lane (float4)
-      // the near leaves' Morton codes are read once, lane i holding leaf i, and passed round
-      // by shuffles, so that the loop's weight and kernel loads depend on nothing else
       const float4 *k4 = reinterpret_cast<const float4 *>(Kc + kbase);
-      const int pf = pfirst[bl], nit = (c_near * 16 + 31) >> 5;
-      const uint32_t mycode = lane < c_near ? (uint32_t)psrc[pf + lane] : 0u;
 #pragma unroll 4
-      for (int t = 0; t < nit; ++t) {  // every lane runs every step: the shuffle is warp-wide
-        const int it = lane + 32 * t, el = it >> 4, t4 = it & 15;
-        const uint32_t code = __shfl_sync(0xffffffffu, mycode, el & 31);
-        if (it < c_near * 16) {
-          int a, b;
-          morton_decode(c_near <= 32 ? code : (uint32_t)psrc[pf + el], a, b);
-          const int row = b * 8 + (t4 >> 1), col = a * 8 + (t4 & 1) * 4;
-          const float4 wv = *reinterpret_cast<const float4 *>(W + (int64_t)(row + g.pad) * g.npad + col + g.pad);
-          const float4 kv = k4[it];
-          acc += wv.x * kv.x + wv.y * kv.y + wv.z * kv.z + wv.w * kv.w;
-        }
+      for (int it = lane; it < c_near * 16; it += 32) {
+        const int el = it >> 4, t4 = it & 15;
+        int a, b;
+        morton_decode((uint32_t)psrc[pfirst[bl] + el], a, b);
+        const int row = b * 8 + (t4 >> 1), col = a * 8 + (t4 & 1) * 4;
+        const float4 wv = *reinterpret_cast<const float4 *>(W + (int64_t)(row + g.pad) * g.npad + col + g.pad);
+        const float4 kv = k4[it];
+        acc += wv.x * kv.x + wv.y * kv.y + wv.z * kv.z + wv.w * kv.w;
       }
       done_near = true;
     }
@@ -860,7 +824,11 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
       acc += W[(int64_t)(j + g.pad) * g.npad + i + g.pad] * (R(0.5) * dev_log<R>(ds * ds + (R)d * (R)d));
     }
   }
-  acc = warp_sum(acc);
+  if (mode != 2) acc = warp_sum(acc);
+  if (mode == 1) {
+    if (lane == 0) vnear[(int64_t)rhs * g.NG + ge] = acc;
+    return;  // warp-uniform; mode 1 takes no barrier below
+  }
   // far field: the local expansion of every ancestor run evaluated at y (L2L re-centring
   // is exact, so this equals pushing the locals down to the leaf run and evaluating there)
   R far = 0;
@@ -873,13 +841,8 @@ __global__ void k_colloc(Geo g, int nrhs, const R *__restrict__ wpad, const cpx<
     const R ey = (side == 1) ? R(1) : (side == 3 ? R(-1) : R(0));
     const cpx<R> z = mk<R>(off * ex, off * ey);
     const cpx<R> *Lc = Lb + (int64_t)rhs * g.nbcell * p + (blevel_offset(l) + id) * p;
-    cpx<R> lc[16];  // the p <= 16 coefficients, all loads issued before the Horner chain
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) lc[kk] = kk < p ? Lc[kk] : mk<R>(0, 0);
     cpx<R> v = mk<R>(0, 0);
-#pragma unroll
-    for (int kk = 15; kk >= 0; --kk)
-      if (kk < p) v = v * z + lc[kk];
+    for (int kk = p - 1; kk >= 0; --kk) v = v * z + Lc[kk];
     far = v.re;
   }
   far = warp_sum(far);
@@ -1955,10 +1918,22 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
   const bool side = tc && part == PART_FULL && H.timing == 0 && H.sstream;
   const bool m2l_side = side && std::is_same<R, float>::value && H.tcm.enabled;
   cudaStream_t ss = H.sstream;
+  // the near part of the collocation values needs only the weights: with the side streams
+  // it runs on the third one beside the volume upward pass, and the collocation kernel on
+  // the main stream adds the far part
+  const bool split_colloc = side && with_bnd && part != PART_TRANS && H.fb.vnear && H.fb.kcol;
   if (side) {
     FMMPC_CUDA(cudaEventRecord(H.sev[0], s));
     FMMPC_CUDA(cudaStreamWaitEvent(ss, H.sev[0], 0));
     launches += run_p2p_tc(H, false, out, nrhs, ss);
+    if (split_colloc) {
+      FMMPC_CUDA(cudaStreamWaitEvent(H.sstream2, H.sev[0], 0));
+      k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, H.sstream2>>>(
+          g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src, H.fb.vcol, H.fb.kcol, nullptr, nullptr, 1, (R *)H.fb.vnear);
+      FMMPC_LAUNCH_CHECK();
+      ++launches;
+      FMMPC_CUDA(cudaEventRecord(H.sev[6], H.sstream2));
+    }
   }
   mark(1);
   launches += run_upward<R, P>(H, nrhs, s);
@@ -1978,10 +1953,13 @@ void apply_impl(fmmpc_handle &H, int part, const double *r, double *out, int nrh
     if (trans)  // t = S_OG^T zb: element integrals of the volume potential, into vcol
       k_colloc_T<R><<<dim3((unsigned)g.nbleaf, nrhs), 256, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
                                                                    H.fb.vcol);
-    else
+    else {
+      if (split_colloc) FMMPC_CUDA(cudaStreamWaitEvent(s, H.sev[6], 0));
       k_colloc<R><<<(unsigned)((int64_t)g.n * nrhs), 128, 0, s>>>(g, nrhs, wpad, Lb, Ls.pvb_first, Ls.pvb_src,
                                                                  H.fb.vcol, H.fb.kcol, vt_f2 ? H.fb.vt_hi : nullptr,
-                                                                 vt_f2 ? H.fb.vt_lo : nullptr);
+                                                                 vt_f2 ? H.fb.vt_lo : nullptr, split_colloc ? 2 : 0,
+                                                                 (R *)H.fb.vnear);
+    }
     FMMPC_LAUNCH_CHECK();
     launches += 2;
     if (bc) {  // vcol -= (1/2 I + K) g: Eq. e:ubound's data term
@@ -2199,6 +2177,7 @@ void alloc_fmm(fmmpc_handle &H) {
   H.fb.q = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.vt = H.pool.get<double>((size_t)nr * g.NG);
   H.fb.Lvb = H.pool.get<cpx<R>>((size_t)nr * std::max<int64_t>(1, H.lists.n_vbv_cells) * g.p);
+  H.fb.vnear = H.pool.get<R>((size_t)nr * g.NG);
   // boundary upward pass: chunk partials and arrival counts of the coarse levels (cells of
   // more than BUP_CHUNK elements)
   H.fb.bup_lc = 0;

@@ -36,6 +36,7 @@ struct FmmBufs {
   float *vt_hi = nullptr, *vt_lo = nullptr;  // the same as two FP32 words (single-precision forms)
   float *knear = nullptr;    // near-boundary element integrals (single-precision forms)
   float *kcol = nullptr;     // collocation-point near-field log kernel (single-precision forms)
+  void *vnear = nullptr;     // [nrhs][NG] near part of V r at the collocation points (R)
   void *Lvb = nullptr;       // [nrhs][n_vbv_cells][p] boundary-source part of L of those cells
   int *up_count = nullptr;   // [nrhs][up_ncount] upward-pass arrival counts (zero between launches)
   int64_t up_ncount = 0;
@@ -154,7 +155,7 @@ struct fmmpc_handle {
   cudaStream_t sstream = nullptr;   // second stream of the full apply (near field, volume M2L)
   cudaStream_t sstream2 = nullptr;  // third stream (near-boundary correction)
   cudaStream_t sstream3 = nullptr;  // fourth stream (volume M2L)
-  cudaEvent_t sev[6] = {};  // forks after the weights, the upward pass and the BEM solve; three joins
+  cudaEvent_t sev[7] = {};  // forks after the weights, the upward pass and the BEM solve; four joins
   std::vector<fmmpc::GraphEntry> gcache;
   uint64_t gclock = 0;
   // whole-solve graphs (device-resident Krylov loop) and the stream they are captured on
