@@ -383,8 +383,8 @@ def bench_c1(args, flush):
 
 
 def bench_c3(args, flush):
-    """4096 x 4096 x 32 right-hand sides, p = 10: apply points/s (N R / t) and FGMRES(15)
-    time to 1e-8 in the mixed TF32 and plain FP32 forms; M2L roofline of the 32-RHS apply."""
+    """4096 x 4096 x 32 right-hand sides, p = 10: apply points/s (N R / t), FGMRES(15) and
+    PCG time to 1e-8 in the mixed TF32 and plain FP32 forms; M2L roofline of the 32-RHS apply."""
     import torch
     import synth_inputs as S
     from paper_1308_3339_gb300 import FmmPreconditioner
@@ -408,6 +408,9 @@ def bench_c3(args, flush):
             rec[f"{k}_roofline"] = {q: allr[k][q] for q in ("kernel", "achieved", "peak", "unit", "frac", "launch_ms",
                                                             "work")}
         rec.update(time_solves(P, rs, 1, restart=15))
+        # preconditioned CG on the same 32 right-hand sides: the short recurrence keeps the
+        # FP64 vector work per iteration (the FP64 pipe's share of the step) small
+        rec["pcg"] = time_solves(P, rs, 1, method="cg")
         out[form] = rec
         P.close()
         torch.cuda.empty_cache()

@@ -1114,33 +1114,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_gupdots(const int *__restrict__
   }
 }
 
-// w[rhs] -= sum_{i <= j} c[rhs][i] V_i[rhs]; with wsq, also |w|^2 into wsq[rhs][0] (the
-// reduction finished by the last block).
-__global__ void __launch_bounds__(RED_THREADS) k_gupdate(const int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
-                                                         int64_t vs, const double *__restrict__ c, double *__restrict__ w,
-                                                         double *__restrict__ part, int *__restrict__ cnt,
-                                                         double *__restrict__ wsq) {
-  __shared__ double red[RED_THREADS / 32];
-  const int rhs = blockIdx.y;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nv = ctl[KC_J] + 1;
-  double sq = update_chunk(N, V + (int64_t)rhs * N, vs, c + rhs * MAXJ, nv, w + (int64_t)rhs * N);
-  if (!wsq) return;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if (lane == 0) red[wid] = sq;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < RED_THREADS / 32; ++q) t += red[q];
-    part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
-  }
-  if (last_block(cnt + rhs)) {
-    reduce_parts(part, rhs, 1, wsq, nullptr, 0);
-    if (threadIdx.x == 0) cnt[rhs] = 0;
-  }
-}
-
 // Per-right-hand-side state of the graph-resident (F)GMRES.
 struct GmState {
   double *Hm;    // [nrhs][(MAXJ + 1) MAXJ], entry (i, j) at i MAXJ + j (rotated)
@@ -1202,9 +1175,11 @@ __global__ void k_grestart(int *__restrict__ ctl, GmState st, int nrhs, const do
 // |w| (wsq), the previous rotations, a new rotation, the residual estimate |g_{j+1}| / |b|,
 // the scale of V_{j+1}; the cycle ends when every right-hand side is within rtol (or has
 // a zero |w|), at j + 1 = m, at maxit, or on a NaN; then y from the triangular system.
-// Sets the condition of the end-of-cycle IF node.
-__global__ void k_gtail(int *__restrict__ ctl, GmState st, int nrhs, int m, const double *__restrict__ hsum,
-                        const double *__restrict__ wsq, double *__restrict__ y, cudaGraphConditionalHandle if_end) {
+// Sets the condition of the end-of-cycle IF node.  Run by all threads of one block (one
+// thread per right-hand side, nrhs <= blockDim.x).
+__device__ __forceinline__ void gtail_run(int *__restrict__ ctl, GmState st, int nrhs, int m,
+                                          const double *__restrict__ hsum, const double *__restrict__ wsq,
+                                          double *__restrict__ y, cudaGraphConditionalHandle if_end) {
   __shared__ int s_ok, s_nan, s_cyc;
   const int r = threadIdx.x;
   const int j = ctl[KC_J], it = ctl[KC_IT] + 1;
@@ -1261,6 +1236,45 @@ __global__ void k_gtail(int *__restrict__ ctl, GmState st, int nrhs, int m, cons
         yr[i] = (Hr[i * MAXJ + i] != 0.0) ? acc / Hr[i * MAXJ + i] : 0.0;
       }
   }
+}
+
+// The second CGS update, w -= V c, with |w|^2 reduced by each right-hand side's last block;
+// the last right-hand side to finish then runs the step's tail (gtail_run) in the same
+// launch: one kernel boundary fewer per Arnoldi step.
+__global__ void __launch_bounds__(RED_THREADS) k_gupdate_tail(int *__restrict__ ctl, int64_t N, const double *__restrict__ V,
+                                                              int64_t vs, const double *__restrict__ c,
+                                                              double *__restrict__ w, double *__restrict__ part,
+                                                              int *__restrict__ cnt, double *__restrict__ wsq, GmState st,
+                                                              int nrhs, int m, const double *__restrict__ hsum,
+                                                              double *__restrict__ y, cudaGraphConditionalHandle if_end) {
+  __shared__ double red[RED_THREADS / 32];
+  __shared__ int s_fin;
+  const int rhs = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nv = ctl[KC_J] + 1;
+  double sq = update_chunk(N, V + (int64_t)rhs * N, vs, c + rhs * MAXJ, nv, w + (int64_t)rhs * N);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) red[wid] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) t += red[q];
+    part[(int64_t)rhs * MAXJ * gridDim.x + blockIdx.x] = t;
+  }
+  if (!last_block(cnt + rhs)) return;
+  reduce_parts(part, rhs, 1, wsq, nullptr, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cnt[rhs] = 0;
+    __threadfence();
+    s_fin = atomicAdd(cnt + nrhs, 1) == nrhs - 1;
+    if (s_fin) cnt[nrhs] = 0;
+  }
+  __syncthreads();
+  if (!s_fin) return;
+  __threadfence();
+  gtail_run(ctl, st, nrhs, m, hsum, wsq, y, if_end);
 }
 
 // Condition of the loop: continue while some right-hand side is above rtol, no NaN was met
@@ -1572,8 +1586,8 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
       k_gapdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, od, N, K.zin, K.w, flexible ? K.Z : nullptr, K.V, vs,
                                                      K.part, K.g_cnt, K.dots, hsum);
       k_gupdots<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, K.dots, K.w, K.part, K.g_cnt, d2, hsum);
-      k_gupdate<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, d2, K.w, K.part, K.g_cnt, wsq);
-      k_gtail<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, m, hsum, wsq, K.scal, hif);
+      k_gupdate_tail<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, K.V, vs, d2, K.w, K.part, K.g_cnt, wsq, st, nrhs, m,
+                                                            hsum, K.scal, hif);
       k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.w, K.V, vs, K.t);
       FMMPC_LAUNCH_CHECK();
     });
