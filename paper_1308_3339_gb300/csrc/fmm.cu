@@ -2238,8 +2238,19 @@ void init_fmm(fmmpc_handle &H) {
   const int side = 1 << H.g.L;
   const int m = H.g.m;
   int tx = (m == 16) ? 4 : 8, ty = (m == 4) ? 8 : 4;
-  H.tile_x = std::min(tx, side);
-  H.tile_y = std::min(ty, side);
+  tx = std::min(tx, side);
+  ty = std::min(ty, side);
+  // the CUDA-core near field: on small grids, smaller tiles until there are two CTAs per SM
+  // (down to 2 x 2 leaves), so that a 512^2 or 256^2 grid does not leave SMs idle
+  int dev = 0, nsm = 0;
+  FMMPC_CUDA(cudaGetDevice(&dev));
+  FMMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  while ((int64_t)(side / tx) * (side / ty) < 2 * (int64_t)nsm && (tx > 2 || ty > 2)) {
+    if (tx >= ty) tx /= 2;
+    else ty /= 2;
+  }
+  H.tile_x = tx;
+  H.tile_y = ty;
   if (H.prec == FMMPC_PREC_FP64) {
     if (m == 16) throw Error(FMMPC_ERR_UNSUPPORTED, "FP64 mode supports leaf side 4 or 8");
     set_p2p_smem_limit<double>();
