@@ -1355,13 +1355,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgf_apdot(OpDev o, int64_t N, G
 
 // x += alpha p, r -= alpha q and |r|^2; the last right-hand side to finish then does the
 // convergence test of every right-hand side (iteration counts, done flags, NaN) and sets
-// the IF condition of the iteration's second half (preconditioner, beta, p): some
-// right-hand side still runs
+// the condition of the solve's WHILE loop: some right-hand side still runs, below maxit
 __global__ void __launch_bounds__(RED_THREADS) k_cgf_xr(int *__restrict__ ctl, int64_t N, int nrhs, GmState st,
                                                       const double *__restrict__ p, const double *__restrict__ q,
                                                       double *__restrict__ x, double *__restrict__ r,
                                                       double *__restrict__ part, int *cnt, double *__restrict__ dots,
-                                                      cudaGraphConditionalHandle if_more) {
+                                                      cudaGraphConditionalHandle loop) {
   __shared__ int s_fin, s_all, s_nan;
   const int rhs = blockIdx.y;
   const double al = st.sc[rhs];
@@ -1401,7 +1400,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgf_xr(int *__restrict__ ctl, i
     ctl[KC_DONE] = s_all;
     ctl[KC_NAN] |= s_nan;
     const int more = (!s_all && !s_nan && it < ctl[KC_MAXIT]) ? 1 : 0;
-    cudaGraphSetConditional(if_more, (unsigned)more);
+    ctl[KC_CONT] = more;
+    cudaGraphSetConditional(loop, (unsigned)more);
   }
 }
 
@@ -1421,11 +1421,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgf_rz(int64_t N, GmState st, c
     st.sc[rhs] = (st.done[rhs] || o == 0.0) ? 0.0 : tot / o;
     rz_old[rhs * MAXJ] = tot;
   }
-}
-
-__global__ void k_copy(int64_t total, const double *__restrict__ a, double *__restrict__ b) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < total) b[t] = a[t];
 }
 
 // Captures the work fn() issues on H.stream into `graph` after the nodes deps (H.stream is
@@ -1533,10 +1528,11 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     residual_c(K.b, K.x, K.r);
     gnorm2(c, K.r);
     if (method == FMMPC_CG) {
+      // the loop body starts with z = P^{-1} r; p = 0 and <r, z>_old = 0 make its first
+      // beta 0, so that p = z
       k_cg_init<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
-      precond(K.r, K.w, K.zin);
-      k_copy<<<nblk(NR), 256, 0, H.stream>>>(NR, K.w, K.V);  // p = z
-      gdot(c, K.r, K.w, K.dots + (size_t)nrhs * MAXJ);     // <r, z> in the second dots block
+      FMMPC_CUDA(cudaMemsetAsync(K.V, 0, sizeof(double) * NR, H.stream));
+      FMMPC_CUDA(cudaMemsetAsync(K.dots + (size_t)nrhs * MAXJ, 0, sizeof(double) * nrhs * MAXJ, H.stream));
     } else {
       k_grestart<<<1, 64, 0, H.stream>>>(ctl, st, nrhs, K.dots);
       k_gscale_col<<<nblk(NR), 256, 0, H.stream>>>(ctl, N, nrhs, K.g_sc, K.r, K.V, vs, K.t);
@@ -1546,8 +1542,8 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
   });
   cudaGraph_t body = nullptr;
   cudaGraphNode_t n_loop = add_conditional(G, f_init, hloop, cudaGraphCondTypeWhile, &body);
-  cudaGraphConditionalHandle hif;
-  FMMPC_CUDA(cudaGraphConditionalHandleCreate(&hif, body, 0, 0));
+  cudaGraphConditionalHandle hif{};
+  if (method != FMMPC_CG) FMMPC_CUDA(cudaGraphConditionalHandleCreate(&hif, body, 0, 0));
   double *hsum = K.dots + (size_t)nrhs * MAXJ, *wsq = K.scal + (size_t)nrhs * MAXJ;
   std::vector<cudaGraphNode_t> f_step;
   cudaGraph_t ifb = nullptr;
@@ -1555,23 +1551,18 @@ void build_chain(fmmpc_handle &H, cudaGraph_t G, int method, int m, int nrhs, bo
     // p in V_0, q in t, z in w; <r, z> of the last iteration in the second dots block
     double *p = K.V, *q = K.t, *z = K.w, *rz_old = K.dots + (size_t)nrhs * MAXJ;
     double *pq = K.dots + (size_t)2 * nrhs * MAXJ;
+    // one iteration, rotated so that the convergence test ends it and sets the loop's own
+    // condition (no IF node): z = P^{-1} r, beta, p = z + beta p, q = A p with alpha, then
+    // x, r and the test
     const dim3 rgrid((unsigned)red_blocks(), nrhs);
     f_step = capture_into(H, cs, body, none, [&] {
-      c.s = H.stream;
-      k_cgf_apdot<<<rgrid, RED_THREADS, 0, H.stream>>>(od, N, st, p, q, K.part, K.g_cnt, pq, rz_old);
-      k_cgf_xr<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, nrhs, st, p, q, K.x, K.r, K.part, K.g_cnt, K.dots, hif);
-      FMMPC_LAUNCH_CHECK();
-    });
-    cudaGraphNode_t n_if = add_conditional(body, f_step, hif, cudaGraphCondTypeIf, &ifb);
-    capture_into(H, cs, ifb, none, [&] {
       c.s = H.stream;
       precond(K.r, z, K.zin);
       k_cgf_rz<<<rgrid, RED_THREADS, 0, H.stream>>>(N, st, K.r, z, K.part, K.g_cnt, rz_old);
       k_cg_p<<<nblk(NR), 256, 0, H.stream>>>(N, nrhs, K.g_sc, z, p);
-      FMMPC_LAUNCH_CHECK();
-    });
-    capture_into(H, cs, body, {n_if}, [&] {
-      k_gcond<<<1, 1, 0, H.stream>>>(ctl, hloop);
+      k_cgf_apdot<<<rgrid, RED_THREADS, 0, H.stream>>>(od, N, st, p, q, K.part, K.g_cnt, pq, rz_old);
+      k_cgf_xr<<<rgrid, RED_THREADS, 0, H.stream>>>(ctl, N, nrhs, st, p, q, K.x, K.r, K.part, K.g_cnt, K.dots,
+                                                     hloop);
       FMMPC_LAUNCH_CHECK();
     });
   } else {

@@ -71,17 +71,38 @@ def test_graph_solve_stops_at_maxit_and_on_nan():
     for method in ("fgmres", "cg"):
         _, info = P.solve(f, method=method, maxit=2, rtol=1e-14, use_graphs=2, raise_on_fail=False)
         assert info["status"] == -4 and info["iters"] == 2
-    # an exact initial iterate needs no iteration
-    u, info = P.solve(f, rtol=1e-8, use_graphs=2)
-    _, info2 = P.solve(f, u0=u, rtol=1e-6, use_graphs=2)
-    assert info2["status"] == 0 and info2["iters"] == 0
-    bad = S.gaussian_mixture(n, 1)
-    bad[100] = np.nan
     from paper_1308_3339_gb300 import FmmpcError
-    with pytest.raises(FmmpcError):
-        P.solve(dev(bad), rtol=1e-8, use_graphs=2)
-    _, info3 = P.solve(f, rtol=1e-8, use_graphs=2)  # the handle still works afterwards
-    assert info3["status"] == 0
+    for method in ("fgmres", "cg"):
+        # an exact initial iterate needs no iteration
+        u, info = P.solve(f, method=method, rtol=1e-8, use_graphs=2)
+        _, info2 = P.solve(f, method=method, u0=u, rtol=1e-6, use_graphs=2)
+        assert info2["status"] == 0 and info2["iters"] == 0
+        bad = S.gaussian_mixture(n, 1)
+        bad[100] = np.nan
+        with pytest.raises(FmmpcError):
+            P.solve(dev(bad), method=method, rtol=1e-8, use_graphs=2)
+        _, info3 = P.solve(f, method=method, rtol=1e-8, use_graphs=2)  # the handle still works afterwards
+        assert info3["status"] == 0
+
+
+@pytest.mark.parametrize("method", ["fgmres", "cg"])
+def test_graph_solve_right_hand_side_done_at_set_up(method):
+    # a zero right-hand side is done before the first iteration; its neighbours in the
+    # batch must still converge, to the same solutions as when solved alone
+    from paper_1308_3339_gb300 import FmmPreconditioner
+    n = 64
+    fs = np.stack([S.gaussian_mixture(n, 7), np.zeros(n * n), S.gaussian_mixture(n, 8)])
+    P = FmmPreconditioner(n, p=8, precision="fp32", n_rhs=3)
+    u, info = P.solve(dev(fs), method=method, rtol=1e-9, use_graphs=2)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-9
+    un = u.cpu().numpy().reshape(3, -1)
+    assert np.all(un[1] == 0.0)
+    for k in (0, 2):
+        P1 = FmmPreconditioner(n, p=8, precision="fp32")
+        u1, i1 = P1.solve(dev(fs[k]), method=method, rtol=1e-9, use_graphs=2)
+        check_close(f"graph {method} rhs {k} in a batch with a zero rhs", un[k], u1.cpu().numpy(), 1e-7, 1e-7)
+        P1.close()
+    P.close()
 
 
 def test_graph_solve_with_boundary_data():
