@@ -1295,17 +1295,21 @@ __global__ void k_gfinal(GmState st, int nrhs, const double *__restrict__ dots) 
 // k_cgf_* below
 __global__ void k_cg_init(int *__restrict__ ctl, GmState st, int nrhs, const double *__restrict__ dots) {
   const int r = threadIdx.x;
-  __shared__ int s_all;
-  if (r == 0) s_all = 1;
+  __shared__ int s_all, s_nan;
+  if (r == 0) { s_all = 1; s_nan = 0; }
   __syncthreads();
   if (r < nrhs) {
     const double rn = sqrt(fmax(0.0, dots[r * MAXJ]));
+    if (!isfinite(dots[r * MAXJ])) atomicOr(&s_nan, 1);  // fmax(0, NaN) would hide it
     const int d = rn / st.bn[r] <= st.rtol[0];
     st.done[r] = d;
     if (!d) atomicAnd(&s_all, 0);
   }
   __syncthreads();
-  if (r == 0) ctl[KC_DONE] = s_all;
+  if (r == 0) {
+    ctl[KC_DONE] = s_all;
+    ctl[KC_NAN] |= s_nan;
+  }
 }
 
 // ---- fused CG steps: each vector pass carries its inner product, finished in the grid's last

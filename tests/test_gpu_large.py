@@ -72,7 +72,8 @@ def test_4096_with_32_right_hand_sides():
 
 def test_64_uneven_problems_batched():
     # 64 grids with sides drawn from {128, 256, 512, 1024, 2048} (seed 0), each with its own
-    # Gaussian mixture (seed 1000 + k), solved together by lockstep FGMRES(30), mixed TF32
+    # Gaussian mixture (seed 1000 + k), solved together by FGMRES(30) in one CUDA graph
+    # (one chain per problem, each stopping at its own convergence), mixed TF32
     from paper_1308_3339_gb300 import FmmBatch, FmmPreconditioner
     sides = [int(v) for v in S.batched_sides(0, 64)]
     assert sum(n * n for n in sides) > 5e7
