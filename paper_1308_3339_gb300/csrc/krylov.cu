@@ -1486,14 +1486,6 @@ void gnorm2(Ctx &c, const double *v) {
   FMMPC_LAUNCH_CHECK();
 }
 
-// <a, b> into out[rhs][0] (captured)
-void gdot(Ctx &c, const double *a, const double *b, double *out) {
-  const int nb = red_blocks();
-  k_mdot_partial<<<dim3(nb, c.nrhs), RED_THREADS, 0, c.H.stream>>>(c.N, 1, a, 0, b, c.H.kw.part, 0);
-  k_mdot_final<<<dim3(c.nrhs, 1), 256, 0, c.H.stream>>>(1, nb, c.H.kw.part, out, nullptr, 0);
-  FMMPC_LAUNCH_CHECK();
-}
-
 // Builds one problem's chain [set-up] -> WHILE [step (-> IF cycle end)] -> [final] into
 // graph G.  Solves A u = b for the handle's internal vectors: b is folded from K.fin
 // (and K.gin), the iterate is K.x.

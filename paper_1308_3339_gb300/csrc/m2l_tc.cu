@@ -28,9 +28,10 @@
 //
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
-// source sub-image serves every dx of a group.  Warp 0 streams windows and per-shift B
-// blocks through separate rings, warp 1 issues the MMAs, one fresh 128-column TMEM
-// accumulator per group (four in flight), and warps 2-9 add each into FP32 sums: one long
+// source sub-image serves every dx of a group.  Warp 0 streams the windows and warp 10 the
+// per-shift B blocks, each through its own ring, so the B blocks run several groups ahead
+// of the MMAs while a window waits for its slot; warp 1 issues the MMAs, one fresh
+// 128-column TMEM accumulator per group (four in flight), and warps 2-9 add each into FP32 sums: one long
 // chain of MMAs would drift with the tensor core's truncating adds (~2^-24 of the partial
 // per MMA).  When a level has too few tiles to fill the GPU, each tile's groups are split
 // into two parts run by two CTAs, which add into zeroed L~.
@@ -54,11 +55,11 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 constexpr int M2L_WROWS = 144;                  // window rows (128 targets + 2 x 4 shift + alignment)
 constexpr int M2L_WBYTES = M2L_WROWS * 128;     // 18 KB
-constexpr int M2L_NWIN = 2;                     // window slots
+constexpr int M2L_NWIN = 3;                     // window slots
 constexpr int M2L_NACC = 4;                     // TMEM accumulators in flight (128-column stride)
 constexpr int M2L_NGR = 16;                     // group barriers (> B slots, > M2L_NACC)
 constexpr int M2L_EPI_WARPS = 8;
-constexpr int M2L_THREADS = 64 + 32 * M2L_EPI_WARPS;
+constexpr int M2L_THREADS = 96 + 32 * M2L_EPI_WARPS;  // window producer, MMA, epilogue, B producer
 constexpr int M2L_TAIL = 256;                   // zero rows after each sub-image (window overrun)
 constexpr int M2L_MAXGRP = 64, M2L_MAXSH = 255;  // per part: (source parity, dy) groups, shifts
 // W outputs per class (2p real parts of L~, the two M~_0 sums in the last two): N = 4 W;
@@ -67,7 +68,7 @@ template <int W>
 struct M2lShape {
   static constexpr int N = 4 * W;
   static constexpr int BBYTES = N * 128;
-  static constexpr int NB = W == 24 ? 14 : 11;
+  static constexpr int NB = W == 24 ? 13 : 10;
   static constexpr int SMEM = M2L_NWIN * M2L_WBYTES + NB * BBYTES + 1024;
 };
 
@@ -197,9 +198,11 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   __shared__ uint64_t wfull[M2L_NWIN], bfull[NB], gdone[M2L_NGR], acc_empty[M2L_NACC], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, w_used, b_used;
-  __shared__ int4 sgrp[M2L_MAXGRP];  // this part's groups and shifts, off the issue path
-  __shared__ int sdx[M2L_MAXSH];
-  __shared__ unsigned char sgof[M2L_MAXSH];  // group of each shift of the part
+  // this part's groups and shifts in this CTA's order, off the issue path
+  __shared__ int4 sgrp[M2L_MAXGRP];           // (source parity, dy, first local shift, count)
+  __shared__ unsigned char sdx_b[M2L_MAXSH];  // dx + 4 of each local shift (0 .. 8)
+  __shared__ unsigned char sgof[M2L_MAXSH];   // local group of each local shift
+  __shared__ short sbi[M2L_MAXSH];            // B block (shift index) of each local shift
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
   unsigned char *wbuf = smem, *bbuf = smem + M2L_NWIN * M2L_WBYTES;
@@ -208,12 +211,23 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   const int P = a.lev_P[l];
   const int g0 = a.gpart[part], ng = a.gpart[part + 1] - g0;
   const int sh0 = a.gpart_sh[part], nsh = a.gpart_sh[part + 1] - sh0;
-  for (int i = tid; i < ng; i += blockDim.x) {
-    const int4 g = a.groups[g0 + i];
-    sgrp[i] = g;
-    for (int k = 0; k < g.w; ++k) sgof[g.z - sh0 + k] = (unsigned char)i;
+  // Every CTA sweeps the same shifts; started in step they would all read the same B block
+  // from the same few L2 slices at the same time.  Each tile therefore starts its sweep at
+  // group (tile mod ng) and wraps around.  The order of the sums is then fixed per tile and
+  // the same for every right-hand side.
+  const int rot = (int)(blockIdx.x % (unsigned)max(ng, 1));
+  const int shr = ng > 0 ? a.groups[g0 + rot].z : sh0;  // first shift of the sweep
+  for (int j = tid; j < ng; j += blockDim.x) {
+    const int o = j + rot < ng ? j + rot : j + rot - ng;
+    const int4 g = a.groups[g0 + o];
+    const int st = g.z >= shr ? g.z - shr : g.z - sh0 + (sh0 + nsh - shr);  // first local shift
+    sgrp[j] = make_int4(g.x, g.y, st, g.w);
+    for (int k = 0; k < g.w; ++k) {
+      sgof[st + k] = (unsigned char)j;
+      sdx_b[st + k] = (unsigned char)(a.dxs[g.z + k] + 4);
+      sbi[st + k] = (short)(g.z + k);
+    }
   }
-  for (int i = tid; i < nsh; i += blockDim.x) sdx[i] = a.dxs[sh0 + i];
   if (tid == 0) {
     for (int s = 0; s < M2L_NWIN; ++s) tc::mbar_init(&wfull[s], 1);
     for (int s = 0; s < NB; ++s) tc::mbar_init(&bfull[s], 1);
@@ -230,22 +244,22 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   tc::fence_after();
   const uint32_t tmem = tmem_base;
   int w_issued = 0, b_issued = 0;
+  // window slot gi % M2L_NWIN is free once group gi - M2L_NWIN is done, B slot b % NB once
+  // the group holding shift b - NB is done; groups complete in order.  Each producer keeps
+  // the highest group it has seen done.
+  int known = -1;
+  auto wait_done = [&](int gq) -> bool {
+    if (gq <= known) return true;
+    if (!tc::mbar_wait(&gdone[gq % M2L_NGR], (gq / M2L_NGR) & 1, &abort_flag)) return false;
+    known = gq;
+    return true;
+  };
   if (warp == 0) {
     if (lane == 0) {
-      // producer: per group its source window into window slot gi % M2L_NWIN (free once
-      // group gi - M2L_NWIN is done), then per shift its B block (the four classes'
-      // translation matrices stacked along N) into B slot b % NB (free once the group
-      // holding shift b - NB is done); groups complete in order
+      // window producer: per group its 144-row source window
       bool ok = true;
-      int known = -1;  // groups known to be done: 0 .. known
-      auto wait_done = [&](int gq) -> bool {
-        if (gq <= known) return true;
-        if (!tc::mbar_wait(&gdone[gq % M2L_NGR], (gq / M2L_NGR) & 1, &abort_flag)) return false;
-        known = gq;
-        return true;
-      };
-      for (int gi = 0; gi < ng && ok && !abort_flag; ++gi) {
-        const int4 g = sgrp[gi];  // (source parity, dy, first shift, count)
+      for (int gi = 0; gi < ng && !abort_flag; ++gi) {
+        const int4 g = sgrp[gi];  // (source parity, dy, first local shift, count)
         if (!wait_done(gi - M2L_NWIN)) { ok = false; break; }
         const int w0 = floor8(f0 + g.y * P - 4);
         const unsigned char *src = a.img + ((int64_t)rhs * a.rows_per_rhs + a.lev_row0[l] +
@@ -254,13 +268,23 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
         tc::mbar_expect_tx(&wfull[ws], M2L_WBYTES);
         tc::bulk_g2s(wbuf + ws * M2L_WBYTES, src, M2L_WBYTES, &wfull[ws]);
         w_issued = gi + 1;
-        for (int k = 0; k < g.w; ++k) {
-          const int b = b_issued, bs = b % NB;
-          if (b >= NB && !wait_done(sgof[b - NB])) { ok = false; break; }
-          tc::mbar_expect_tx(&bfull[bs], BBYTES);
-          tc::bulk_g2s(bbuf + bs * BBYTES, a.bmat + (int64_t)(g.z + k) * BBYTES, BBYTES, &bfull[bs]);
-          b_issued = b + 1;
-        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(a.err, 1);
+      }
+    }
+  } else if (warp == 1 + M2L_EPI_WARPS + 1) {
+    if (lane == 0) {
+      // B producer: per shift its B block (the four classes' translation matrices stacked
+      // along N), up to NB shifts ahead of the MMAs
+      bool ok = true;
+      for (int b = 0; b < nsh && !abort_flag; ++b) {
+        if (b >= NB && !wait_done(sgof[b - NB])) { ok = false; break; }
+        const int bs = b % NB;
+        tc::mbar_expect_tx(&bfull[bs], BBYTES);
+        tc::bulk_g2s(bbuf + bs * BBYTES, a.bmat + (int64_t)sbi[b] * BBYTES, BBYTES, &bfull[bs]);
+        b_issued = b + 1;
       }
       if (!ok) {
         abort_flag = 1;
@@ -274,9 +298,12 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
       const uint32_t idesc = KIND == 0 ? tc::idesc_tf32(128, N)
                                        : ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                           ((128u >> 4) << 24));
-      const int nks = a.nks;  // K steps of 32 bytes (8 TF32 or 16 BF16 inputs each)
+      const int nks = a.nks;  // 1-4 K steps of 32 bytes (8 TF32 or 16 BF16 inputs each)
+      // descriptor low words of window slot 0 and B slot 0 (+8 per 128-byte row, +2 per K step)
+      const uint32_t wlo0 = tc::desc_lo(tc::smem_addr(wbuf)), blo0 = tc::desc_lo(tc::smem_addr(bbuf));
       bool ok = true;
-      int b = 0;
+      int b = 0, bs = 0;
+      uint32_t bph = 0;  // B slot of shift b and the parity of its fill
       for (int gi = 0; gi < ng && ok; ++gi) {
         const int ab = gi % M2L_NACC, ws = gi % M2L_NWIN;
         if (!tc::mbar_wait(&wfull[ws], (gi / M2L_NWIN) & 1, &abort_flag)) { ok = false; break; }
@@ -287,25 +314,30 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
         }
         const int4 g = sgrp[gi];
         const int w0 = floor8(f0 + g.y * P - 4);
-        const uint32_t wst = tc::smem_addr(wbuf + ws * M2L_WBYTES);
+        // first row of shift dx in the window: (f0 + dy P - w0 - 4) + (dx + 4), both terms >= 0
+        const uint32_t alo_g = wlo0 + (uint32_t)(ws * (M2L_WBYTES >> 4) + (f0 + g.y * P - w0 - 4) * 8);
+        const unsigned char *gdx = sdx_b + g.z;
         const uint32_t d = tmem + 128 * ab;
-        uint32_t acc = 0;
         for (int k = 0; k < g.w; ++k, ++b) {
-          const int bs = b % NB;
-          if (!tc::mbar_wait(&bfull[bs], (b / NB) & 1, &abort_flag)) { ok = false; break; }
+          if (!tc::mbar_wait(&bfull[bs], bph, &abort_flag)) { ok = false; break; }
           b_used = b + 1;
           tc::fence_after();
-          const int dx = sdx[g.z - sh0 + k];
-          const uint32_t arow = wst + (uint32_t)((f0 + g.y * P + dx - w0) * 128);
-          const uint32_t brow = tc::smem_addr(bbuf + bs * BBYTES);
-          for (int ks = 0; ks < nks; ++ks) {
-            const uint64_t ad = tc::desc_sw128(arow + 32 * ks), bd = tc::desc_sw128(brow + 32 * ks);
-            if (KIND == 0) {
-              tc::mma_tf32(d, ad, bd, idesc, acc);
-            } else {
-              tc::mma_f16(d, ad, bd, idesc, acc);
+          const uint32_t alo = alo_g + 8u * gdx[k], blo = blo0 + (uint32_t)bs * (BBYTES >> 4);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            if (ks < nks) {
+              const uint64_t ad = tc::desc_of(alo + 2 * ks), bd = tc::desc_of(blo + 2 * ks);
+              const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+              if (KIND == 0) {
+                tc::mma_tf32(d, ad, bd, idesc, acc);
+              } else {
+                tc::mma_f16(d, ad, bd, idesc, acc);
+              }
             }
-            acc = 1;
+          }
+          if (++bs == NB) {
+            bs = 0;
+            bph ^= 1u;
           }
         }
         if (!ok) break;
@@ -317,7 +349,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
       }
       tc::commit(&done);
     }
-  } else {
+  } else if (warp <= 1 + M2L_EPI_WARPS) {
     // epilogue: warps 2-9; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one target each) and
     // the 2W columns of classes 2h, 2h + 1, h = (w - 2) / 4, in loads of 16 columns; each
     // group's accumulator is added into plain FP32 sums (a group is at most a few dozen
@@ -364,9 +396,11 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   if (!finished && lane == 0) atomicOr(a.err, 4);
   tc::fence_before();
   __syncthreads();
-  if (abort_flag && warp == 0 && lane == 0) {  // copies still in flight land before the block exits
-    for (int u = w_used; u < w_issued; ++u) tc::mbar_wait(&wfull[u % M2L_NWIN], (u / M2L_NWIN) & 1, nullptr);
-    for (int u = b_used; u < b_issued; ++u) tc::mbar_wait(&bfull[u % NB], (u / NB) & 1, nullptr);
+  if (abort_flag && lane == 0) {  // copies still in flight land before the block exits
+    if (warp == 0)
+      for (int u = w_used; u < w_issued; ++u) tc::mbar_wait(&wfull[u % M2L_NWIN], (u / M2L_NWIN) & 1, nullptr);
+    if (warp == 1 + M2L_EPI_WARPS + 1)
+      for (int u = b_used; u < b_issued; ++u) tc::mbar_wait(&bfull[u % NB], (u / NB) & 1, nullptr);
   }
   __syncthreads();
   if (warp == 0) {
@@ -510,6 +544,9 @@ void init_tc_m2l(fmmpc_handle &H, DevPool &tmp) {
     }
   }
   const int nshift = (int)dxs.size(), ngrp = (int)groups.size();
+  // the 144-row window holds the 128 targets shifted by dx in [-4, 4]
+  for (int dx : dxs)
+    if (dx < -4 || dx > 4) throw Error(FMMPC_ERR_UNSUPPORTED, "tensor-core M2L: shift outside the source window");
   // images and tiles (128 consecutive flattened targets of one level, all four classes)
   int64_t rows = 0;
   std::vector<int2> tiles;

@@ -152,6 +152,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
   const int u0 = half ? a.usplit : 0, u1 = half ? a.nrows : a.usplit;
   int ngroups = 0;
   for (int u = u0; u < u1; ++u) ngroups += a.row_q1[u] - a.row_q0[u];
+  // Every CTA sweeps the same stencil rows; started in step they would all read the same B
+  // group from the same few L2 slices at the same time.  The CTAs of leaf row ly therefore
+  // take their rows from row (ly mod nr) on, wrapping around: the lu-th row of the sweep is
+  // urow(lu).  The order of the sums is fixed per leaf row and the same for every
+  // right-hand side.
+  const int nr = u1 - u0, rot = nr > 0 ? ly % nr : 0;
+  auto urow = [&](int lu) { return u0 + (lu + rot < nr ? lu + rot : lu + rot - nr); };
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&full_s[b], 1);
@@ -183,8 +190,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
       // producer: per stencil row the weight strip, then that row's B groups
       int g = 0;
       bool ok = true;
-      for (int u = u0; u < u1 && ok && !abort_flag; ++u) {
-        const int lu = u - u0, slot = lu & 1;
+      for (int lu = 0; lu < nr && ok && !abort_flag; ++lu) {
+        const int u = urow(lu), slot = lu & 1;
         if (lu >= 2 && !tc::mbar_wait(&empty_s[slot], ((lu >> 1) - 1) & 1, &abort_flag)) { ok = false; break; }
         tc::mbar_expect_tx(&full_s[slot], 2 * a.NS * 128);
         const int64_t Y = ly + a.R + a.row_oy[u];
@@ -209,15 +216,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
     if (lane == 0) {
       // MMA issuer: one fresh accumulator per offset group, four buffers in turn
       const uint32_t idesc = idesc_f16(128, 64);
+      // descriptor low words (+8 per 128-byte row, +2 per K step of 16 FP16 values)
+      const uint32_t slo0 = tc::desc_lo(tc::smem_addr(strips)), blo0 = tc::desc_lo(tc::smem_addr(bm));
       int g = 0;
       bool ok = true;
-      for (int u = u0; u < u1 && ok; ++u) {
-        const int lu = u - u0, slot = lu & 1;
+      for (int lu = 0; lu < nr && ok; ++lu) {
+        const int u = urow(lu), slot = lu & 1;
         if (!tc::mbar_wait(&full_s[slot], (lu >> 1) & 1, &abort_flag)) { ok = false; break; }
         used_s = lu + 1;
         tc::fence_after();
-        const uint32_t sh = tc::smem_addr(strips + (slot * 2) * SH), sl = tc::smem_addr(strips + (slot * 2 + 1) * SH);
-        for (int q = a.row_q0[u]; q < a.row_q1[u]; ++q) {
+        // strips (hi, lo) of this slot, shifted to the row's first offset
+        const uint32_t shlo = slo0 + (uint32_t)((slot * 2) * (SH >> 4) + (a.R + a.row_ox0[u]) * 8);
+        const uint32_t sllo = shlo + (uint32_t)(SH >> 4);
+        const int q0 = a.row_q0[u], q1 = a.row_q1[u];
+        for (int q = q0; q < q1; ++q) {
           const int bi = g % TC_NB, ab = g % TC_NACC;
           if (!tc::mbar_wait(&full_b[bi], (g / TC_NB) & 1, &abort_flag)) { ok = false; break; }
           used_b = g + 1;
@@ -226,24 +238,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
             break;
           }
           tc::fence_after();
-          const int ox = a.row_ox0[u] + (q - a.row_q0[u]);
-          const uint32_t bh = tc::smem_addr(bm + bi * TC_BGRP), bl = bh + TC_BGRP / 2;
+          const uint32_t bhl = blo0 + (uint32_t)(bi * (TC_BGRP >> 4)), bll = bhl + (uint32_t)(TC_BGRP / 2 >> 4);
           const uint32_t d = tmem + 64 * ab;
-          uint32_t acc = 0;
-          const uint32_t arow = sh + (uint32_t)((a.R + ox) * 128), lrow = sl + (uint32_t)((a.R + ox) * 128);
+          const uint32_t ahl = shlo + 8u * (uint32_t)(q - q0), all = sllo + 8u * (uint32_t)(q - q0);
           if (a.npass == 3) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-              tc::mma_f16(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bl + 32 * s), idesc, acc);
-              acc = 1;
-              tc::mma_f16(d, tc::desc_sw128(lrow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, 1u);
+              tc::mma_f16(d, tc::desc_of(ahl + 2 * s), tc::desc_of(bll + 2 * s), idesc, s > 0 ? 1u : 0u);
+              tc::mma_f16(d, tc::desc_of(all + 2 * s), tc::desc_of(bhl + 2 * s), idesc, 1u);
             }
           }
+          const uint32_t acc0 = a.npass == 3 ? 1u : 0u;
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            tc::mma_f16(d, tc::desc_sw128(arow + 32 * s), tc::desc_sw128(bh + 32 * s), idesc, acc);
-            acc = 1;
-          }
+          for (int s = 0; s < 4; ++s)
+            tc::mma_f16(d, tc::desc_of(ahl + 2 * s), tc::desc_of(bhl + 2 * s), idesc, s > 0 ? 1u : acc0);
           tc::commit(&acc_full[ab]);  // the epilogue also releases the B and strip slots
           ++g;
         }
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) sum[i] = 0.0f;
     bool ok = true;
-    int u = u0, uend = a.row_q1[u0] - a.row_q0[u0];  // groups of the current row end at uend
+    int lu = 0, u = urow(0), uend = a.row_q1[u] - a.row_q0[u];  // groups of the current row end at uend
     // 2^-e of this thread's source leaf for offset (ox, oy): row of the padded leaf grid
     const int Xp = lx0 + 32 * qd + lane + a.R;
     const float *lrow = a.lsc + ((int64_t)rhs * a.NLY + ly + a.R) * a.NLX + Xp;
@@ -274,12 +282,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_p2p_tc(TcArgs a) {
       if (warp == 2 && lane == 0) {
         // the group's MMAs have completed: its B slot, and at a row's end the strip slot, are free
         tc::mbar_arrive(&empty_b[g % TC_NB]);
-        if (g + 1 == uend) tc::mbar_arrive(&empty_s[(u - u0) & 1]);
+        if (g + 1 == uend) tc::mbar_arrive(&empty_s[lu & 1]);
       }
       const int nu = a.row_q1[u] - a.row_q0[u];
       const int ox = a.row_ox0[u] + (g - (uend - nu)), oy = a.row_oy[u];
       const float us = __ldg(lrow + (int64_t)oy * a.NLX + ox);
-      if (g + 1 == uend && ++u < u1) uend += a.row_q1[u] - a.row_q0[u];
+      if (g + 1 == uend && ++lu < nr) {
+        u = urow(lu);
+        uend += a.row_q1[u] - a.row_q0[u];
+      }
       tc::fence_after();
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {

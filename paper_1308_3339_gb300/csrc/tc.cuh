@@ -41,6 +41,17 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same descriptor as two 32-bit words: the high word is the same for every operand of
+// this layout, and the low word of an operand starting at saddr is its 16-byte address plus
+// the leading-byte-offset field.  The address field cannot carry into bit 14 (shared memory
+// is below 256 KB), so stepping a descriptor along K or along rows is an add to the low word:
+// +2 per 32 bytes of K, +8 per 128-byte row.  Issue loops build descriptors this way because
+// the MMA issuer is a single thread, and a few dependent 64-bit operations per MMA cost about
+// as much as the MMA itself.
+constexpr uint32_t SW128_HI = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return ((saddr >> 4) & 0x3FFFu) | (1u << 16); }
+__device__ __forceinline__ uint64_t desc_of(uint32_t lo) { return ((uint64_t)SW128_HI << 32) | lo; }
+
 __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }

@@ -66,6 +66,21 @@ def test_mixed_apply_matches_fp64_fmm(prec, n):
 
 
 @pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_mixed_apply_p12_matches_fp64_fmm(prec):
+    # p = 12 needs 2p + 2 = 26 outputs per class: the 32-wide class blocks (N = 128) and
+    # fewer B slots; fewer multipoles fit the spare K columns (M~_0..1 for TF32, M~_0..5 for
+    # BF16), so the same gates hold with less margin
+    n = 256
+    r = S.gaussian_mixture(n, 5)
+    P = gpu(n, p=12, precision=prec)
+    assert P.query("tc_m2l") == KIND[prec]
+    z = host(P.apply(dev(r)))
+    assert P.query("device_errors") == 0
+    ref = O.Problem(n, p=12).apply(r, "fmm", stages=True)["z"]
+    check_close(f"{prec} z n={n} p=12 vs oracle fmm", z, ref, *TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
 def test_mixed_apply_matches_direct_sum(prec):
     n = 128
     r = S.random_field(n, 4)
