@@ -29,11 +29,10 @@
 // Operands use the 128-byte swizzle (one 128-byte row per cell), so a shifted window is a
 // descriptor offset.  Shifts are grouped by (source parity, dy); one 144-row window of the
 // source sub-image serves every dx of a group.  Warp 0 streams the windows and warp 10 the
-// per-shift B blocks, each through its own ring, so the B blocks run several groups ahead
-// of the MMAs while a window waits for its slot; warp 1 issues the MMAs, one fresh
-// 128-column TMEM accumulator per group (four in flight), and warps 2-9 add each into FP32 sums: one long
-// chain of MMAs would drift with the tensor core's truncating adds (~2^-24 of the partial
-// per MMA).  When a level has too few tiles to fill the GPU, each tile's groups are split
+// B blocks of each group (one bulk copy per group), each through its own ring; warp 1
+// issues the MMAs, one fresh 128-column TMEM accumulator per group (four in flight), and
+// warps 2-9 add each into FP32 sums: one long chain of MMAs would drift with the tensor
+// core's truncating adds (~2^-24 of the partial per MMA).  When a level has too few tiles to fill the GPU, each tile's groups are split
 // into two parts run by two CTAs, which add into zeroed L~.
 #include <algorithm>
 #include <array>
@@ -192,10 +191,10 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   using SH = M2lShape<W>;
   constexpr int N = SH::N, NB = SH::NB, BBYTES = SH::BBYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // wfull / bfull: a window / one shift's B block landed; gdone (ring of M2L_NGR groups):
-  // the group's MMAs completed (one commit), which frees its window slot, its B slots and
-  // its accumulator
-  __shared__ uint64_t wfull[M2L_NWIN], bfull[NB], gdone[M2L_NGR], acc_empty[M2L_NACC], done;
+  // wfull: a window landed; bfull (ring of M2L_NGR groups): a group's B blocks landed;
+  // gdone (same ring): the group's MMAs completed (one commit), which frees its window slot,
+  // its B slots and its accumulator
+  __shared__ uint64_t wfull[M2L_NWIN], bfull[M2L_NGR], gdone[M2L_NGR], acc_empty[M2L_NACC], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, w_used, b_used;
   // this part's groups and shifts in this CTA's order, off the issue path
@@ -230,7 +229,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
   }
   if (tid == 0) {
     for (int s = 0; s < M2L_NWIN; ++s) tc::mbar_init(&wfull[s], 1);
-    for (int s = 0; s < NB; ++s) tc::mbar_init(&bfull[s], 1);
+    for (int s = 0; s < M2L_NGR; ++s) tc::mbar_init(&bfull[s], 1);
     for (int s = 0; s < M2L_NGR; ++s) tc::mbar_init(&gdone[s], 1);
     for (int b = 0; b < M2L_NACC; ++b) tc::mbar_init(&acc_empty[b], M2L_EPI_WARPS);
     tc::mbar_init(&done, 1);
@@ -276,15 +275,26 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
     }
   } else if (warp == 1 + M2L_EPI_WARPS + 1) {
     if (lane == 0) {
-      // B producer: per shift its B block (the four classes' translation matrices stacked
-      // along N), up to NB shifts ahead of the MMAs
+      // B producer: per group the B blocks of its shifts (each the four classes' translation
+      // matrices stacked along N) in one bulk copy, two where the ring of NB shift slots
+      // wraps.  A bulk copy costs about the same time whatever its size up to ~50 KB and an
+      // SM runs them one after another, so one copy per group instead of one per shift.
+      // The group's shifts are consecutive B blocks and consecutive local shifts, and slot
+      // b % NB was last used by shift b - NB: the group of the group's last shift minus NB
+      // must be done.  That group is at most NB groups back, so the previous phase of this
+      // group's barrier (M2L_NGR > NB groups back) has completed.
       bool ok = true;
-      for (int b = 0; b < nsh && !abort_flag; ++b) {
-        if (b >= NB && !wait_done(sgof[b - NB])) { ok = false; break; }
-        const int bs = b % NB;
-        tc::mbar_expect_tx(&bfull[bs], BBYTES);
-        tc::bulk_g2s(bbuf + bs * BBYTES, a.bmat + (int64_t)sbi[b] * BBYTES, BBYTES, &bfull[bs]);
-        b_issued = b + 1;
+      for (int gi = 0; gi < ng && !abort_flag; ++gi) {
+        const int4 g = sgrp[gi];
+        const int blast = g.z + g.w - 1;
+        if (blast >= NB && !wait_done(sgof[blast - NB])) { ok = false; break; }
+        const int s0 = g.z % NB, n1 = min(g.w, NB - s0);
+        uint64_t *bar = &bfull[gi % M2L_NGR];
+        const unsigned char *src = a.bmat + (int64_t)sbi[g.z] * BBYTES;
+        tc::mbar_expect_tx(bar, (uint32_t)(g.w * BBYTES));
+        tc::bulk_g2s(bbuf + s0 * BBYTES, src, (uint32_t)(n1 * BBYTES), bar);
+        if (n1 < g.w) tc::bulk_g2s(bbuf, src + (int64_t)n1 * BBYTES, (uint32_t)((g.w - n1) * BBYTES), bar);
+        b_issued = gi + 1;
       }
       if (!ok) {
         abort_flag = 1;
@@ -302,8 +312,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
       // descriptor low words of window slot 0 and B slot 0 (+8 per 128-byte row, +2 per K step)
       const uint32_t wlo0 = tc::desc_lo(tc::smem_addr(wbuf)), blo0 = tc::desc_lo(tc::smem_addr(bbuf));
       bool ok = true;
-      int b = 0, bs = 0;
-      uint32_t bph = 0;  // B slot of shift b and the parity of its fill
+      int bs = 0;  // B slot of the current shift (local shifts run 0, 1, ... across the groups)
       for (int gi = 0; gi < ng && ok; ++gi) {
         const int ab = gi % M2L_NACC, ws = gi % M2L_NWIN;
         if (!tc::mbar_wait(&wfull[ws], (gi / M2L_NWIN) & 1, &abort_flag)) { ok = false; break; }
@@ -312,16 +321,16 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
           ok = false;
           break;
         }
+        if (!tc::mbar_wait(&bfull[gi % M2L_NGR], (gi / M2L_NGR) & 1, &abort_flag)) { ok = false; break; }
+        b_used = gi + 1;
+        tc::fence_after();
         const int4 g = sgrp[gi];
         const int w0 = floor8(f0 + g.y * P - 4);
         // first row of shift dx in the window: (f0 + dy P - w0 - 4) + (dx + 4), both terms >= 0
         const uint32_t alo_g = wlo0 + (uint32_t)(ws * (M2L_WBYTES >> 4) + (f0 + g.y * P - w0 - 4) * 8);
         const unsigned char *gdx = sdx_b + g.z;
         const uint32_t d = tmem + 128 * ab;
-        for (int k = 0; k < g.w; ++k, ++b) {
-          if (!tc::mbar_wait(&bfull[bs], bph, &abort_flag)) { ok = false; break; }
-          b_used = b + 1;
-          tc::fence_after();
+        for (int k = 0; k < g.w; ++k) {
           const uint32_t alo = alo_g + 8u * gdx[k], blo = blo0 + (uint32_t)bs * (BBYTES >> 4);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
@@ -335,12 +344,8 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
               }
             }
           }
-          if (++bs == NB) {
-            bs = 0;
-            bph ^= 1u;
-          }
+          if (++bs == NB) bs = 0;
         }
-        if (!ok) break;
         tc::commit(&gdone[gi % M2L_NGR]);
       }
       if (!ok) {
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) k_m2l_tc(M2lArgs a) {
     if (warp == 0)
       for (int u = w_used; u < w_issued; ++u) tc::mbar_wait(&wfull[u % M2L_NWIN], (u / M2L_NWIN) & 1, nullptr);
     if (warp == 1 + M2L_EPI_WARPS + 1)
-      for (int u = b_used; u < b_issued; ++u) tc::mbar_wait(&bfull[u % NB], (u / NB) & 1, nullptr);
+      for (int u = b_used; u < b_issued; ++u) tc::mbar_wait(&bfull[u % M2L_NGR], (u / M2L_NGR) & 1, nullptr);
   }
   __syncthreads();
   if (warp == 0) {
